@@ -1,0 +1,415 @@
+"""Benchmark: one simulation step of a partitioned LIF network on GB300.
+
+A "step" is one pass of the whole hot path: ring intake + Poisson drive, LIF
+update and threshold, spike compaction, level-1 bucketing by destination
+virtual node, level-2 relay expansion, CSR fan-out delivery.  The workload is
+the 1,048,576-neuron network (64 partitions over 16 virtual nodes of 4,
+1,000 synapses per neuron, 70/20/10 locality, delays 1-8 steps, Poisson
+drive), synthetic and seeded.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line on rank 0.  Multi-GPU runs (torchrun) are independent
+replicas of the same network with different drive seeds (weak scaling, no
+collective on the data path).  `--impl reference` times the CPU oracle, the
+plain sequential simulator used by the tests, on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "synaptic events/s & sim steps/s vs HBM roofline; batched/adjoint vs plain"
+UNIT = "synaptic events/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ multi-rank
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return None, 0, 1
+    import torch.distributed as dist
+    backend = os.environ.get("SNN_BENCH_BACKEND") or ("nccl" if _cuda_ok() else "gloo")
+    dist.init_process_group(backend=backend)
+    return dist, dist.get_rank(), dist.get_world_size()
+
+
+def _cuda_ok():
+    import torch
+    return torch.cuda.is_available()
+
+
+def barrier(dist):
+    if dist is not None:
+        if dist.get_backend() == "nccl":
+            import torch
+            dist.barrier(device_ids=[torch.cuda.current_device()])
+        else:
+            dist.barrier()
+
+
+def reduce_over_ranks(dist, events: float, ms: float, extra: float = 0.0):
+    """Whole-job aggregate: summed work, maximum time over ranks."""
+    if dist is None:
+        return events, ms, extra
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    a = torch.tensor([events, extra], dtype=torch.float64, device=dev)
+    b = torch.tensor([ms], dtype=torch.float64, device=dev)
+    dist.all_reduce(a, op=dist.ReduceOp.SUM)
+    dist.all_reduce(b, op=dist.ReduceOp.MAX)
+    return float(a[0]), float(b[0]), float(a[1])
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled in the background."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.p = None
+        self.t = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.p.stdout:
+            self.rows.append((time.time(), [x.strip() for x in line.split(",")]))
+
+    def stop(self):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+        if self.t is not None:
+            self.t.join(timeout=5)
+
+    def summary(self, t0: float, t1: float):
+        rows = [r for ts, r in self.rows if t0 - 0.06 <= ts <= t1 + 0.06] or [r for _, r in self.rows]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ workload
+def workload(seed_offset: int = 0):
+    import synth
+    cfg = synth.SCALE
+    dyn = cfg.dyn
+    if seed_offset:
+        import dataclasses
+        dyn = dataclasses.replace(dyn, drive_seed=dyn.drive_seed + seed_offset)
+        cfg = cfg.scaled(dyn=dyn)
+    return cfg
+
+
+# per-unit algorithmic bytes of each phase (see the design notes)
+def phase_bytes(M: int, d_steps: int, d: dict, gid: bool) -> list:
+    upd = (18 + (4 if gid else 0)) * M * d_steps + 4 * d["spikes"]
+    l1 = 12 * d["spikes"] + 6 * (d["l1_local"] + d["l1_xvn"])
+    l1_entries = d["l1_local"] + d["l1_xvn"]
+    l2_entries = d["l2_local"] + d["l2_peer"] + d["l2_relay_local"] + d["l2_relay_remote"]
+    l2 = 12 * l1_entries + 24 * l2_entries
+    dl = 8 * l2_entries + 6 * d["events"]
+    return [upd, l1, l2, dl]
+
+
+def run_ours(args):
+    import torch
+    import synth
+    import paper_2205_07125_gb300 as snn
+
+    dist, rank, world = dist_init()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cfg = workload(rank)
+    K, W = args.steps, args.warmup
+
+    t_setup = time.time()
+    g = synth.make_network(cfg)
+    net = snn.Network.from_synth(g)
+    part, _ = snn.snn_partition(net, cfg.P, "planted")
+    rt = snn.Routing(net, part, cfg.P, cfg.n_vn, "contiguous")
+    info = rt.info()
+    raster_cap = int(cfg.M * (K + W) * 0.002) + 100000
+    prm = snn.sim_params(cfg.dyn, raster_cap=raster_cap, raster_steps=K + W, steps_per_graph=32,
+                         pin_host_tables=1)
+    sim = snn.Sim(net, rt, prm, device=dev)
+    setup_s = time.time() - t_setup
+    stream = sim.stream
+
+    # warm-up, then EXACTLY K timed steps from graph replays
+    sim.step(W)
+    if sim.sync_status() != 0:
+        raise RuntimeError("device status after warm-up: %d" % sim.sync_status())
+    c0 = sim.read_counts()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier(dist)
+    torch.cuda.synchronize()
+    wall0 = time.time()
+    e0.record(stream)
+    sim.step(K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    wall1 = time.time()
+    barrier(dist)
+    time.sleep(0.1)
+    clocks.stop()
+    ms = e0.elapsed_time(e1)
+    st = sim.sync_status()
+    if st != 0:
+        raise RuntimeError("device status after the timed steps: %d" % st)
+    c1 = sim.read_counts()
+    dc = {k: c1[k] - c0[k] for k in c1}
+    assert dc["steps"] == K
+    events_all, ms_max, spikes_all = reduce_over_ranks(dist, float(dc["events"]), ms, float(dc["spikes"]))
+
+    # per-phase CUDA-event times from an instrumented graph over more steps
+    NP = min(K, 2048)
+    ca = sim.read_counts()
+    phase_ms = sim.profile_phases(NP)
+    cb = sim.read_counts()
+    dp = {k: cb[k] - ca[k] for k in cb}
+    pbytes = phase_bytes(cfg.M, dp["steps"], dp, not info["identity_order"])
+    names = ["update", "level1", "level2", "deliver"]
+    kernel_names = ["k_update", "k_level1", "k_level2", "k_deliver"]
+    phases = {}
+    for n, kn, t_ms, b in zip(names, kernel_names, phase_ms, pbytes):
+        phases[n] = {"kernel": kn, "ms_per_step": t_ms / NP, "bytes_per_step": b / NP,
+                     "gbs": (b / (t_ms * 1e-3) / 1e9) if t_ms > 0 else None,
+                     "share": t_ms / max(1e-12, sum(phase_ms))}
+    dom = max(phases, key=lambda n: phases[n]["ms_per_step"])
+    peak, peak_kind = _peaks()
+    traffic = load_traffic(phases[dom]["kernel"])
+    roof = {"bound": "hbm", "kernel": phases[dom]["kernel"], "achieved": phases[dom]["gbs"],
+            "peak": peak, "unit": "GB/s", "frac": phases[dom]["gbs"] / peak,
+            "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured"
+            else "fallback 6.8 TB/s", "traffic": traffic}
+    step_bytes = sum(pbytes) / NP
+    delivery = phases["deliver"]
+
+    # end to end through the C ABI: upload of every table from pinned host
+    # memory, K steps, read-back of the raster and the counters
+    t_e2e0 = time.time()
+    torch.cuda.synchronize()
+    e2 = torch.cuda.Event(enable_timing=True)
+    e3 = torch.cuda.Event(enable_timing=True)
+    barrier(dist)
+    h0 = time.perf_counter()
+    sim.reset(reupload=True)
+    sim.step(K)
+    ids, off = sim.read_raster(0, K)
+    ce = sim.read_counts()
+    h1 = time.perf_counter()
+    e2e_ms = (h1 - h0) * 1e3
+    e2e_events, e2e_ms_max, _ = reduce_over_ranks(dist, float(ce["events"]), e2e_ms)
+    h2d = (info["n_synapses"] * 6 + info["n_l2"] * 16 + info["n_l1"] * 6 + (cfg.M + 1) * 4
+           + cfg.M * 6)
+    d2h = ids.nbytes + off.nbytes + 88
+    del e2, e3, t_e2e0
+
+    result = {
+        "metric": METRIC, "value": events_all / (ms_max * 1e-3), "unit": UNIT, "n_gpus": world,
+        "steps": K, "warmup": W, "ms_per_step": ms_max / K, "steps_per_s": K / (ms_max * 1e-3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+i32",
+        "data": "synthetic (seeded generator; stands in for the paper's scanned brain model)",
+        "config": {"workload": cfg.name, "neurons": cfg.M, "partitions": cfg.P,
+                   "virtual_nodes": cfg.n_vn, "synapses": info["n_synapses"],
+                   "synapses_per_neuron": cfg.K, "locality": "700/200/100", "delays": "1-%d" % cfg.dmax,
+                   "drive_lambda_per_step": cfg.dyn.drive_lambda, "w_ext": cfg.dyn.w_ext,
+                   "parallelism": "replicas x%d" % world,
+                   "l2": "inputs larger than L2: 6.3 GB synapse CSR streamed per step; neuron state "
+                         "(V, ref, delay ring ~42 MB) stays L2-resident across steps",
+                   "steps_per_graph": 32},
+        "spikes_per_step": spikes_all / world / K,
+        "events_per_step": events_all / world / K,
+        "rate_hz": spikes_all / world / K / cfg.M / (cfg.dyn.dt_ms * 1e-3),
+        "roofline": roof,
+        "step_roofline": {"bytes_per_step": step_bytes,
+                          "achieved_gbs": step_bytes / (ms_max / K * 1e-3) / 1e9,
+                          "frac": step_bytes / (ms_max / K * 1e-3) / 1e9 / peak},
+        "delivery_roofline": {"kernel": "k_deliver", "achieved": delivery["gbs"], "peak": peak,
+                              "frac": (delivery["gbs"] or 0) / peak},
+        "phases": phases,
+        "gpu_launches": int(sim.launches_per_step * K),
+        "clocks": clocks.summary(wall0, wall1),
+        "e2e": {"value": e2e_events / (e2e_ms_max * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K,
+                "what": "snn_sim_reset(reupload) from pinned host tables + snn_step(K) + "
+                        "snn_read_raster + snn_read_counts, host wall clock"},
+        "routing": routing_report(dc, info, rt),
+        "setup_s": setup_s,
+    }
+    sim.close()
+    del sim
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(cfg, g, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def routing_report(dc, info, rt):
+    S = max(1, dc["spikes"])
+    two = dc["l1_xvn"] + dc["l2_peer"] + dc["l2_relay_remote"]
+    cd, ct = rt.connections()
+    return {
+        "messages_per_spike": {"direct": dc["direct"] / S, "direct_cross_vn": dc["direct_xvn"] / S,
+                               "two_level": two / S, "two_level_l1_cross_vn": dc["l1_xvn"] / S,
+                               "two_level_l2_relay_forward": dc["l2_relay_remote"] / S},
+        "bytes_per_step": {"direct": 4 * dc["direct"] / dc["steps"],
+                           "two_level": 4 * two / dc["steps"]},
+        "connections_per_partition": {"direct_mean": float(cd.mean()), "direct_max": int(cd.max()),
+                                      "two_level_mean": float(ct.mean()),
+                                      "two_level_max": int(ct.max())},
+    }
+
+
+def load_traffic(kernel: str):
+    """dram bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel source (else null)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+    except (OSError, ValueError):
+        return None
+    ent = t.get(kernel)
+    if not ent:
+        return None
+    import hashlib
+    src = os.path.join(ROOT, "paper_2205_07125_gb300", "csrc", "snn_sim.cu")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if ent.get("source_sha") != h:
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+# ------------------------------------------------------------------ CPU oracle
+def cpu_baseline(cfg, g, seconds: float):
+    """The CPU oracle, as it stands, on the host cores: a bounded sample of
+    consecutive steps of the same network, from rest."""
+    import oracle
+    P = cfg.P
+    t0 = time.time()
+    o = oracle.Oracle(g, P, oracle.partition_planted(g.M, P), cfg.n_vn,
+                      oracle.group_contiguous(P, cfg.n_vn), cfg.dyn)
+    setup = time.time() - t0
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        o.run(10, raster=False, hashes=False)
+        steps += 10
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    ev = o.count_dict()["events"]
+    return {"value": ev / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "steps_per_s": steps / el,
+            "sample": "first %d steps from rest of the same %d-neuron network, sequential C oracle "
+                      "(%.1f s timed, %.1f s setup untimed)" % (steps, g.M, el, setup)}
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle timed on the host, rank 0 only."""
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return
+    import synth
+    import oracle
+    cfg = workload(0)
+    g = synth.make_network(cfg)
+    P = cfg.P
+    o = oracle.Oracle(g, P, oracle.partition_planted(g.M, P), cfg.n_vn,
+                      oracle.group_contiguous(P, cfg.n_vn), cfg.dyn)
+    # each "step" of this arm is one simulation step; the counts are bounded
+    # so that the whole run ends within a few minutes
+    W = min(args.warmup, 20)
+    K = min(args.steps, args.ref_steps)
+    o.run(W, raster=False, hashes=False)
+    c0 = o.count_dict()
+    t0 = time.perf_counter()
+    o.run(K, raster=False, hashes=False)
+    el = time.perf_counter() - t0
+    c1 = o.count_dict()
+    ev = c1["events"] - c0["events"]
+    v = ev / el
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+           "steps": K, "warmup": W, "ms_per_step": el * 1e3 / K, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32+i32", "data": "synthetic",
+           "config": {"workload": cfg.name, "neurons": cfg.M, "partitions": cfg.P,
+                      "virtual_nodes": cfg.n_vn, "synapses": g.E},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": "steps %d..%d of the %d-neuron network, sequential C oracle"
+                                      % (W, W + K, g.M)},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=100)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-steps", type=int, default=400)
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

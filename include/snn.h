@@ -1,0 +1,293 @@
+/*
+ * snn.h — C ABI of the GB300 partitioned spiking-network step library
+ * (libsnn.so).
+ *
+ * The calls follow the paper's statement of the problem (arXiv 2205.07125,
+ * Sec. I and Sec. IV): a network is generated, its neurons are mapped to
+ * partitions (Algorithm 1, Sec. IV.A), the partitions are grouped and a
+ * two-level routing table is built (Algorithm 2, Sec. IV.B), and the
+ * simulation then alternates computation with spike exchange.  Here all
+ * partitions ("GPUs" in the paper) live on one GPU: the spike exchange of
+ * the two-level route becomes level-1 buckets per destination group
+ * ("virtual node", VN) and level-2 relay expansion into per-partition
+ * inboxes, all in device memory.
+ *
+ * Conventions
+ *   - Every call returns int: SNN_OK (0) or a negative SNN_E_* code;
+ *     snn_strerror() names it.  No call aborts the process.
+ *   - Host arrays passed in are borrowed for the duration of the call
+ *     unless a call says otherwise; output arrays are caller-owned with an
+ *     explicit capacity.
+ *   - Opaque handles are owned by the library and freed by the matching
+ *     *_destroy call (which accepts NULL).
+ *   - Device memory comes only from the caller: snn_sim_create carves a
+ *     caller-allocated device workspace; the library never calls
+ *     cudaMalloc for simulation state.  Work is issued asynchronously on the
+ *     caller's CUDA stream.
+ *   - Neuron ids are the caller's global ids 0..M-1 in every input and
+ *     output; the internal partition-major order is never exposed.
+ */
+#ifndef SNN_H
+#define SNN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- errors */
+#define SNN_OK          0
+#define SNN_E_ARG      -1   /* invalid argument or inconsistent sizes */
+#define SNN_E_NOMEM    -2   /* host allocation failed / workspace too small */
+#define SNN_E_CAPACITY -3   /* a device bucket, inbox or record buffer overflowed */
+#define SNN_E_CUDA     -4   /* a CUDA runtime call failed */
+#define SNN_E_RANGE    -5   /* network exceeds a layout limit (ids, delays, lengths) */
+#define SNN_E_STATE    -6   /* call not valid in the object's current state */
+#define SNN_E_NODEV    -7   /* no usable CUDA device */
+
+const char *snn_strerror(int code);
+
+/* ---------------------------------------------------------------- network */
+/*
+ * A network as a source-major synapse list (host memory, borrowed):
+ * neuron i owns synapses syn_ptr[i] .. syn_ptr[i+1]-1, each with a global
+ * target id, an int16 fixed-point weight (units of 2^-10 mV) and a delay in
+ * steps (1..16).  v0 holds the initial membrane potentials (mV).
+ * Limits: M < 2^28 neurons, out-degree < 2^24 per neuron.
+ */
+typedef struct {
+    int64_t n_neurons;
+    const int64_t *syn_ptr;   /* [M+1], syn_ptr[0] == 0, nondecreasing */
+    const uint32_t *syn_tgt;  /* [E] */
+    const int16_t *syn_w;     /* [E] */
+    const uint8_t *syn_d;     /* [E] */
+    const float *v0;          /* [M] */
+} snn_network;
+
+/* -------------------------------------------------------------- partition */
+#define SNN_PART_PLANTED 0   /* contiguous id ranges: part(i) = p, floor(pM/P) <= i < floor((p+1)M/P) */
+#define SNN_PART_GREEDY  1   /* Algorithm 1 (greedy growth, best of `iters`) */
+#define SNN_PART_RANDOM  2   /* balanced random mapping (the paper's baseline) */
+
+typedef struct {
+    int32_t mode;      /* SNN_PART_* */
+    int32_t iters;     /* Algorithm 1 iterations T (>= 1) */
+    uint64_t seed;     /* seed of the random choices */
+} snn_partition_params;
+
+typedef struct {
+    int64_t objective;    /* sum over cut synapses i->j of W_i*W_j, W = out-degree */
+    int64_t min_weight;   /* smallest / largest per-part sum of W */
+    int64_t max_weight;
+} snn_partition_stats;
+
+/*
+ * Map neurons to n_parts partitions (Algorithm 1, Sec. IV.A).  Greedy
+ * reading: for t = 1..iters, parts 0..P-2 are grown one at a time from a
+ * seed (t = 1: lowest unassigned id; t > 1: a Philox4x32-10-chosen
+ * unassigned neuron, counter (t, k, 0xA1, 0), key = seed), adding the
+ * unassigned neuron with the largest sum_{i in part} (c_ij + c_ji) W_i W_j
+ * (ties: lowest id) while the part's weight is below sum(W)/P; the last part
+ * takes the rest; the mapping with the smallest objective is kept.
+ * part_of: caller-owned [M], receives partition labels.  stats may be NULL.
+ * Errors: SNN_E_ARG (bad sizes), SNN_E_NOMEM.
+ */
+int snn_partition(const snn_network *net, int32_t n_parts, const snn_partition_params *params,
+                  int32_t *part_of, snn_partition_stats *stats);
+
+/* ---------------------------------------------------------------- routing */
+#define SNN_GROUP_CONTIGUOUS 0  /* VN g = partitions g*s .. g*s+s-1, s = P/n_vn */
+#define SNN_GROUP_GREEDY     1  /* Algorithm 2 grouping (best of `iters`) */
+
+typedef struct {
+    int32_t grouping;   /* SNN_GROUP_* */
+    int32_t iters;      /* Algorithm 2 iterations T (>= 1) */
+    uint64_t seed;      /* seed of the random choices */
+    int32_t n_threads;  /* host threads for the build (0 = all) */
+    int32_t reserved;
+} snn_routing_params;
+
+typedef struct {
+    int64_t n_neurons, n_synapses;
+    int32_t n_parts, n_vn, vn_size, max_delay;
+    int64_t n_l1;              /* (neuron, destination VN) entries */
+    int64_t n_l2;              /* (neuron, destination partition) entries */
+    uint64_t group_cost_lo;    /* Algorithm 2 objective: sum over inter-group */
+    uint64_t group_cost_hi;    /*   partition pairs of PG[p][q]*WG[p]*WG[q] (128 bit) */
+    int64_t conn_direct_sum;   /* static outgoing connections summed over partitions: */
+    int64_t conn_two_level_sum;/*   direct route vs two-level route (Sec. V, Fig. 4) */
+    int32_t conn_direct_max;
+    int32_t conn_two_level_max;
+    int32_t identity_order;    /* 1 if the internal neuron order equals the global order */
+    int32_t reserved;
+} snn_routing_info;
+
+typedef struct snn_routing snn_routing;
+
+/*
+ * Group partitions into n_vn virtual nodes of equal size (Algorithm 2,
+ * Sec. IV.B) and build the two-level routing table and the device layout:
+ *   - level 1: per source neuron, the destination VNs holding its targets
+ *     (one message per VN, deduplicated);
+ *   - level 2: per (neuron, VN), the destination partitions of that VN
+ *     with the neuron's synapse segment for each;
+ *   - relay ("bridge") of destination VN g for source VN h: the
+ *     (h mod s)-th partition of g in ascending partition label; inside the
+ *     own VN the source partition sends directly.
+ * Greedy grouping reading: for t = 1..iters, groups 0..n_vn-2 are grown
+ * from a seed (t = 1: heaviest ungrouped partition by WG, ties lowest label;
+ * t > 1: Philox-chosen, counter (t, g, 0xA2, 0)) by adding the ungrouped q
+ * with the largest sum_{m in g} (PG[m][q] + PG[q][m]) WG[m] WG[q] (ties:
+ * lowest q), PG = inter-partition synapse counts, WG = summed out-degree.
+ * part_of: [M] labels 0..n_parts-1 (each partition non-empty);
+ * n_parts % n_vn == 0.  The network arrays are read during the call only.
+ * Errors: SNN_E_ARG, SNN_E_RANGE (delay outside 1..16, M >= 2^28,
+ * out-degree >= 2^24), SNN_E_NOMEM.
+ */
+int snn_routing_build(const snn_network *net, const int32_t *part_of, int32_t n_parts,
+                      int32_t n_vn, const snn_routing_params *params, snn_routing **out);
+int snn_routing_info_get(const snn_routing *rt, snn_routing_info *out);
+/* vn_of_part: caller-owned [n_parts]; relay: caller-owned [n_vn*n_vn],
+ * relay[g*n_vn + h] = partition label relaying VN h's traffic inside VN g. */
+int snn_routing_groups(const snn_routing *rt, int32_t *vn_of_part, int32_t *relay);
+/* Per-partition static connection counts (caller-owned [n_parts] each). */
+int snn_routing_connections(const snn_routing *rt, int32_t *direct, int32_t *two_level);
+void snn_routing_destroy(snn_routing *rt);
+
+/* ------------------------------------------------------------- simulation */
+typedef struct {
+    /* LIF dynamics.  Update of a non-refractory neuron (FP32, no fused
+     * multiply-add, this order): u = V - e_l; V = e_l + alpha*u;
+     * V = V + float(I) * 2^-10, alpha = fl32(exp(-dt_ms/tau_ms)); spike if
+     * V >= v_th, then V = v_reset and ref = t_ref.  A refractory neuron
+     * (ref > 0) is held at v_reset and ref decreases by one. */
+    double dt_ms, tau_ms;
+    float e_l, v_th, v_reset;
+    int32_t t_ref;               /* 0..255 */
+    /* input I = recurrent int32 input + k*w_ext + i_bias, k ~ Poisson(lambda)
+     * drawn by inverse CDF from Philox4x32-10 word 0 with key = drive_seed,
+     * counter = (global neuron id, step, 0, 0) */
+    double drive_lambda;         /* 0..16 */
+    int32_t w_ext, i_bias;
+    uint64_t drive_seed;
+    /* records */
+    int64_t raster_cap;          /* spike ids kept for snn_read_raster */
+    int64_t raster_steps;        /* steps whose raster offsets are kept */
+    int64_t hash_steps;          /* steps whose state hashes are kept */
+    int32_t cur_every;           /* snapshot consumed input every k-th step (0 = off) */
+    int32_t cur_slots;           /* number of snapshots kept */
+    /* capacities of level-1 buckets / level-2 inboxes as a fraction of
+     * their exact worst case (every neuron spiking); 1.0 never overflows */
+    float bucket_frac, inbox_frac;
+    int32_t steps_per_graph;     /* steps unrolled per CUDA graph (1..256) */
+    int32_t pin_host_tables;     /* page-lock the routing tables for uploads */
+} snn_sim_params;
+
+/* Fill p with the defaults (no records, exact capacities, 32 steps/graph). */
+void snn_sim_params_default(snn_sim_params *p);
+
+typedef struct {
+    uint64_t steps;             /* steps simulated */
+    uint64_t spikes;            /* spikes emitted */
+    uint64_t events;            /* synaptic events delivered */
+    uint64_t direct;            /* direct route: (spike, partition q != own) messages */
+    uint64_t direct_xvn;        /*   of which cross a VN boundary */
+    uint64_t l1_local;          /* level 1: own-VN bucket entries (no message) */
+    uint64_t l1_xvn;            /* level 1: cross-VN messages (one per spike and VN) */
+    uint64_t l2_local;          /* level 2: own partition (no message) */
+    uint64_t l2_peer;           /* level 2: direct messages to own-VN peers */
+    uint64_t l2_relay_local;    /* level 2: relay is itself a destination (no message) */
+    uint64_t l2_relay_remote;   /* level 2: relay forwards to another partition */
+} snn_counts;
+
+typedef struct snn_sim snn_sim;
+
+/* Device workspace size for a routing and parameters.  Errors: SNN_E_ARG. */
+int snn_sim_workspace_bytes(const snn_routing *rt, const snn_sim_params *p, size_t *bytes);
+
+/*
+ * Create a simulation: carve `workspace` (device memory of at least
+ * snn_sim_workspace_bytes, 256-byte aligned, caller-owned, must outlive the
+ * sim), upload the routing tables and the initial state (V = v0, ref = 0,
+ * empty delay ring, t = 0) on `stream` (a cudaStream_t, NULL = legacy
+ * default stream).  `rt` must outlive the sim.  Uses the current device.
+ * Errors: SNN_E_ARG, SNN_E_NOMEM (workspace too small), SNN_E_CUDA, SNN_E_NODEV.
+ */
+int snn_sim_create(const snn_network *net, const snn_routing *rt, const snn_sim_params *p,
+                   void *workspace, size_t workspace_bytes, void *stream, snn_sim **out);
+
+/*
+ * Advance T steps.  Each step: (a1) consume the delay-ring slot, add the
+ * Poisson drive; (a2) LIF update and threshold; (a3) warp-ballot/prefix-sum
+ * spike compaction; (a4) level-1 bucketing by destination VN; (a5) level-2
+ * relay expansion into per-partition inboxes; (a6) CSR fan-out of int16
+ * weights into int32 ring accumulators.  Asynchronous on the sim's stream
+ * (replays of captured CUDA graphs); errors raised on the device are
+ * reported by snn_sync_status.  Errors: SNN_E_ARG, SNN_E_CUDA.
+ */
+int snn_step(snn_sim *sim, int32_t T);
+
+/* Wait for the sim's stream and return the device status:
+ * SNN_OK, SNN_E_CAPACITY (bucket/inbox overflow; the affected steps are
+ * wrong, the raster overflow alone is reported by snn_read_raster), or
+ * SNN_E_CUDA. */
+int snn_sync_status(snn_sim *sim);
+
+/*
+ * Spikes of steps t0 .. t1-1 (global ids, ascending within a step):
+ * ids[step_off[k] .. step_off[k+1]) for step t0+k; step_off has t1-t0+1
+ * entries; *n receives the total.  Synchronises the stream.
+ * Errors: SNN_E_ARG; SNN_E_CAPACITY with *n = -1 when a step was not
+ * recorded, with *n = the total when it exceeds cap (ids may be NULL then).
+ */
+int snn_read_raster(snn_sim *sim, int64_t t0, int64_t t1, uint32_t *ids, int64_t cap,
+                    int64_t *step_off, int64_t *n);
+/* Recurrent int32 input consumed at step t (global order, [M]); t must be a
+ * snapshot step (t % cur_every == 0, t / cur_every < cur_slots). */
+int snn_read_currents(snn_sim *sim, int64_t t, int32_t *out);
+/* Order-free hashes of steps t0..t1-1: cur = sum_j mix(j<<32 | I_rec_j),
+ * v = sum_j mix(j<<32 | bits(V_j)) mod 2^64 over global ids j, mix the
+ * splitmix64 finaliser. */
+int snn_read_hashes(snn_sim *sim, int64_t t0, int64_t t1, uint64_t *cur, uint64_t *v);
+int snn_read_counts(snn_sim *sim, snn_counts *out);
+/* Current state in global order: V [M], ref [M]; *t = next step index. */
+int snn_read_state(snn_sim *sim, float *V, uint8_t *ref, int64_t *t);
+/* (spike id << 32 | destination partition label) pairs held in the
+ * level-2 inboxes after the last step, unsorted; *n = total (may exceed cap). */
+int snn_read_inbox_pairs(snn_sim *sim, uint64_t *pairs, int64_t cap, int64_t *n);
+
+/* Checkpoint: V, ref, delay ring, step index, counters (bytes from
+ * snn_state_bytes).  Restoring continues bit-exactly (the drive is
+ * counter-based).  Records are not part of the checkpoint: after a restore
+ * the raster stays off and the hash slots from the restored step on are
+ * cleared. */
+int snn_state_bytes(snn_sim *sim, size_t *bytes);
+int snn_save_state(snn_sim *sim, void *host_buf, size_t cap);
+int snn_load_state(snn_sim *sim, const void *host_buf, size_t bytes);
+
+/* Return to the initial state and clear counters and records; with
+ * reupload != 0 the routing tables are copied to the device again. */
+int snn_sim_reset(snn_sim *sim, int32_t reupload);
+
+/* Number of kernel launches one snn_step(sim, T) issues. */
+int64_t snn_launches_per_step(const snn_sim *sim);
+
+/*
+ * Advance T steps like snn_step, but from a CUDA graph that records a CUDA
+ * event before and after every kernel, and return the summed event time of
+ * each step phase in phase_ms[0..3] (update+compaction, level-1 bucketing,
+ * level-2 relay expansion, delivery), milliseconds.  For measurement; the
+ * event nodes add a little time to each step.  Synchronises the stream.
+ * Errors: SNN_E_ARG, SNN_E_CUDA.
+ */
+int snn_profile_phases(snn_sim *sim, int32_t T, double *phase_ms);
+
+void snn_sim_destroy(snn_sim *sim);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SNN_H */

@@ -1,0 +1,358 @@
+"""Python binding of libsnn.so, the GB300 partitioned spiking-network step.
+
+Argument marshalling only: every step of the simulation runs in the CUDA
+kernels of the library (csrc/snn_sim.cu); the host code of the library
+(csrc/snn_host.cpp) builds the partition and the two-level routing tables.
+PyTorch is used for device memory (the caller-owned workspace) and streams.
+
+The names follow the C ABI in include/snn.h:
+    snn_partition(net, P, mode)              -> part_of        (Algorithm 1)
+    Routing(net, part_of, P, n_vn, grouping)                   (Algorithm 2 + tables)
+    Sim(net, routing, params).step(T)                          (the hot path)
+    Sim.read_raster / read_currents / read_counts / read_hashes / read_state
+This module raises ImportError when libsnn.so has not been built; there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "libsnn.so")
+
+if not os.path.exists(_SO):
+    raise ImportError("libsnn.so is not built: run `python -c 'import __graft_entry__ as g; g.build()'`")
+
+_lib = ctypes.CDLL(_SO)
+
+SNN_PART_PLANTED, SNN_PART_GREEDY, SNN_PART_RANDOM = 0, 1, 2
+SNN_GROUP_CONTIGUOUS, SNN_GROUP_GREEDY = 0, 1
+SNN_E_CAPACITY = -3
+
+_i32, _i64, _u64, _u32, _f32, _f64, _vp = (ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64,
+                                           ctypes.c_uint32, ctypes.c_float, ctypes.c_double,
+                                           ctypes.c_void_p)
+
+
+class snn_network(ctypes.Structure):
+    _fields_ = [("n_neurons", _i64), ("syn_ptr", _vp), ("syn_tgt", _vp), ("syn_w", _vp),
+                ("syn_d", _vp), ("v0", _vp)]
+
+
+class snn_partition_params(ctypes.Structure):
+    _fields_ = [("mode", _i32), ("iters", _i32), ("seed", _u64)]
+
+
+class snn_partition_stats(ctypes.Structure):
+    _fields_ = [("objective", _i64), ("min_weight", _i64), ("max_weight", _i64)]
+
+
+class snn_routing_params(ctypes.Structure):
+    _fields_ = [("grouping", _i32), ("iters", _i32), ("seed", _u64), ("n_threads", _i32),
+                ("reserved", _i32)]
+
+
+class snn_routing_info(ctypes.Structure):
+    _fields_ = [("n_neurons", _i64), ("n_synapses", _i64), ("n_parts", _i32), ("n_vn", _i32),
+                ("vn_size", _i32), ("max_delay", _i32), ("n_l1", _i64), ("n_l2", _i64),
+                ("group_cost_lo", _u64), ("group_cost_hi", _u64), ("conn_direct_sum", _i64),
+                ("conn_two_level_sum", _i64), ("conn_direct_max", _i32),
+                ("conn_two_level_max", _i32), ("identity_order", _i32), ("reserved", _i32)]
+
+
+class snn_sim_params(ctypes.Structure):
+    _fields_ = [("dt_ms", _f64), ("tau_ms", _f64), ("e_l", _f32), ("v_th", _f32), ("v_reset", _f32),
+                ("t_ref", _i32), ("drive_lambda", _f64), ("w_ext", _i32), ("i_bias", _i32),
+                ("drive_seed", _u64), ("raster_cap", _i64), ("raster_steps", _i64),
+                ("hash_steps", _i64), ("cur_every", _i32), ("cur_slots", _i32),
+                ("bucket_frac", _f32), ("inbox_frac", _f32), ("steps_per_graph", _i32),
+                ("pin_host_tables", _i32)]
+
+
+COUNT_FIELDS = ("steps", "spikes", "events", "direct", "direct_xvn", "l1_local", "l1_xvn",
+                "l2_local", "l2_peer", "l2_relay_local", "l2_relay_remote")
+
+
+class snn_counts(ctypes.Structure):
+    _fields_ = [(n, _u64) for n in COUNT_FIELDS]
+
+
+def _sig(name, res, args):
+    f = getattr(_lib, name)
+    f.restype = res
+    f.argtypes = args
+    return f
+
+
+_P = ctypes.POINTER
+_lib_strerror = _sig("snn_strerror", ctypes.c_char_p, [ctypes.c_int])
+_sig("snn_partition", ctypes.c_int, [_P(snn_network), _i32, _P(snn_partition_params), _vp,
+                                     _P(snn_partition_stats)])
+_sig("snn_routing_build", ctypes.c_int, [_P(snn_network), _vp, _i32, _i32, _P(snn_routing_params),
+                                         _P(_vp)])
+_sig("snn_routing_info_get", ctypes.c_int, [_vp, _P(snn_routing_info)])
+_sig("snn_routing_groups", ctypes.c_int, [_vp, _vp, _vp])
+_sig("snn_routing_connections", ctypes.c_int, [_vp, _vp, _vp])
+_sig("snn_routing_destroy", None, [_vp])
+_sig("snn_sim_params_default", None, [_P(snn_sim_params)])
+_sig("snn_sim_workspace_bytes", ctypes.c_int, [_vp, _P(snn_sim_params), _P(ctypes.c_size_t)])
+_sig("snn_sim_create", ctypes.c_int, [_P(snn_network), _vp, _P(snn_sim_params), _vp, ctypes.c_size_t,
+                                      _vp, _P(_vp)])
+_sig("snn_step", ctypes.c_int, [_vp, _i32])
+_sig("snn_sync_status", ctypes.c_int, [_vp])
+_sig("snn_read_raster", ctypes.c_int, [_vp, _i64, _i64, _vp, _i64, _vp, _P(_i64)])
+_sig("snn_read_currents", ctypes.c_int, [_vp, _i64, _vp])
+_sig("snn_read_hashes", ctypes.c_int, [_vp, _i64, _i64, _vp, _vp])
+_sig("snn_read_counts", ctypes.c_int, [_vp, _P(snn_counts)])
+_sig("snn_read_state", ctypes.c_int, [_vp, _vp, _vp, _P(_i64)])
+_sig("snn_read_inbox_pairs", ctypes.c_int, [_vp, _vp, _i64, _P(_i64)])
+_sig("snn_state_bytes", ctypes.c_int, [_vp, _P(ctypes.c_size_t)])
+_sig("snn_save_state", ctypes.c_int, [_vp, _vp, ctypes.c_size_t])
+_sig("snn_load_state", ctypes.c_int, [_vp, _vp, ctypes.c_size_t])
+_sig("snn_sim_reset", ctypes.c_int, [_vp, _i32])
+_sig("snn_launches_per_step", _i64, [_vp])
+_sig("snn_profile_phases", ctypes.c_int, [_vp, _i32, _vp])
+_sig("snn_sim_destroy", None, [_vp])
+
+EXPORTS = ("snn_strerror", "snn_partition", "snn_routing_build", "snn_routing_info_get",
+           "snn_routing_groups", "snn_routing_connections", "snn_routing_destroy",
+           "snn_sim_params_default", "snn_sim_workspace_bytes", "snn_sim_create", "snn_step",
+           "snn_sync_status", "snn_read_raster", "snn_read_currents", "snn_read_hashes",
+           "snn_read_counts", "snn_read_state", "snn_read_inbox_pairs", "snn_state_bytes",
+           "snn_save_state", "snn_load_state", "snn_sim_reset", "snn_launches_per_step",
+           "snn_profile_phases", "snn_sim_destroy")
+
+
+class SnnError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__("%s: %s (%d)" % (what, _lib_strerror(code).decode(), code))
+
+
+def _ck(rc: int, what: str):
+    if rc != 0:
+        raise SnnError(rc, what)
+
+
+def library_path() -> str:
+    return _SO
+
+
+class Network:
+    """Borrowed view of a source-major synapse list (numpy arrays kept alive here)."""
+
+    def __init__(self, syn_ptr, tgt, w, d, v0):
+        self.syn_ptr = np.ascontiguousarray(syn_ptr, np.int64)
+        self.tgt = np.ascontiguousarray(tgt, np.uint32)
+        self.w = np.ascontiguousarray(w, np.int16)
+        self.d = np.ascontiguousarray(d, np.uint8)
+        self.v0 = np.ascontiguousarray(v0, np.float32)
+        self.M = int(self.v0.shape[0])
+        if self.syn_ptr.shape[0] != self.M + 1:
+            raise ValueError("syn_ptr must have M+1 entries")
+        self.s = snn_network(self.M, self.syn_ptr.ctypes.data, self.tgt.ctypes.data,
+                             self.w.ctypes.data, self.d.ctypes.data, self.v0.ctypes.data)
+
+    @classmethod
+    def from_synth(cls, net):
+        return cls(net.syn_ptr, net.tgt, net.w, net.d, net.v0)
+
+
+_PART_MODES = {"planted": SNN_PART_PLANTED, "greedy": SNN_PART_GREEDY, "random": SNN_PART_RANDOM}
+
+
+def snn_partition(net: Network, n_parts: int, mode: str = "planted", iters: int = 4, seed: int = 7):
+    """Algorithm 1 (or a baseline mapping).  Returns (part_of int32[M], stats dict)."""
+    out = np.empty(net.M, np.int32)
+    prm = snn_partition_params(_PART_MODES[mode], iters, seed)
+    st = snn_partition_stats()
+    _ck(_lib.snn_partition(ctypes.byref(net.s), n_parts, ctypes.byref(prm), out.ctypes.data,
+                           ctypes.byref(st)), "snn_partition")
+    return out, {"objective": st.objective, "min_weight": st.min_weight,
+                 "max_weight": st.max_weight}
+
+
+class Routing:
+    """Algorithm 2 grouping and the two-level routing tables (host memory)."""
+
+    def __init__(self, net: Network, part_of, n_parts: int, n_vn: int, grouping: str = "contiguous",
+                 iters: int = 4, seed: int = 7, n_threads: int = 0):
+        self.net = net
+        self.part_of = np.ascontiguousarray(part_of, np.int32)
+        g = {"contiguous": SNN_GROUP_CONTIGUOUS, "greedy": SNN_GROUP_GREEDY}[grouping]
+        prm = snn_routing_params(g, iters, seed, n_threads, 0)
+        h = _vp()
+        _ck(_lib.snn_routing_build(ctypes.byref(net.s), self.part_of.ctypes.data, n_parts, n_vn,
+                                   ctypes.byref(prm), ctypes.byref(h)), "snn_routing_build")
+        self.h = h.value
+        self.P, self.n_vn = n_parts, n_vn
+
+    def info(self) -> dict:
+        i = snn_routing_info()
+        _ck(_lib.snn_routing_info_get(self.h, ctypes.byref(i)), "snn_routing_info_get")
+        d = {f: getattr(i, f) for f, _ in snn_routing_info._fields_ if f != "reserved"}
+        d["group_cost"] = d.pop("group_cost_lo") + (d.pop("group_cost_hi") << 64)
+        return d
+
+    def groups(self):
+        vn = np.empty(self.P, np.int32)
+        relay = np.empty(self.n_vn * self.n_vn, np.int32)
+        _ck(_lib.snn_routing_groups(self.h, vn.ctypes.data, relay.ctypes.data), "snn_routing_groups")
+        return vn, relay.reshape(self.n_vn, self.n_vn)
+
+    def connections(self):
+        a = np.empty(self.P, np.int32)
+        b = np.empty(self.P, np.int32)
+        _ck(_lib.snn_routing_connections(self.h, a.ctypes.data, b.ctypes.data),
+            "snn_routing_connections")
+        return a, b
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.snn_routing_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+
+def sim_params(dyn=None, **kw) -> snn_sim_params:
+    """snn_sim_params from library defaults, a dynamics record (dt_ms, tau_ms,
+    e_l, v_th, v_reset, t_ref, drive_lambda, w_ext, i_bias, drive_seed) and
+    keyword overrides."""
+    p = snn_sim_params()
+    _lib.snn_sim_params_default(ctypes.byref(p))
+    if dyn is not None:
+        for f in ("dt_ms", "tau_ms", "e_l", "v_th", "v_reset", "t_ref", "drive_lambda", "w_ext",
+                  "i_bias", "drive_seed"):
+            setattr(p, f, getattr(dyn, f))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+class Sim:
+    """A simulation on one GPU; the workspace is a torch uint8 tensor."""
+
+    def __init__(self, net: Network, routing: Routing, params: snn_sim_params, device=None,
+                 stream=None):
+        import torch
+        self.net, self.routing, self.params = net, routing, params
+        self.M = net.M
+        dev = torch.device(device if device is not None else "cuda")
+        self.device = dev
+        nb = ctypes.c_size_t(0)
+        _ck(_lib.snn_sim_workspace_bytes(routing.h, ctypes.byref(params), ctypes.byref(nb)),
+            "snn_sim_workspace_bytes")
+        self.workspace_bytes = nb.value
+        with torch.cuda.device(dev):
+            self.workspace = torch.empty(max(256, nb.value), dtype=torch.uint8, device=dev)
+            self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+            h = _vp()
+            _ck(_lib.snn_sim_create(ctypes.byref(net.s), routing.h, ctypes.byref(params),
+                                    self.workspace.data_ptr(), nb.value, self.stream.cuda_stream,
+                                    ctypes.byref(h)), "snn_sim_create")
+        self.h = h.value
+
+    def _dev(self):
+        import torch
+        return torch.cuda.device(self.device)
+
+    def step(self, T: int):
+        with self._dev():
+            _ck(_lib.snn_step(self.h, int(T)), "snn_step")
+
+    def sync_status(self) -> int:
+        with self._dev():
+            return int(_lib.snn_sync_status(self.h))
+
+    def read_raster(self, t0: int, t1: int):
+        n = ctypes.c_int64(-1)
+        off = np.zeros(t1 - t0 + 1, np.int64)
+        with self._dev():
+            rc = _lib.snn_read_raster(self.h, t0, t1, None, 0, off.ctypes.data, ctypes.byref(n))
+            if rc != 0 and not (rc == SNN_E_CAPACITY and n.value >= 0):
+                _ck(rc, "snn_read_raster")
+            ids = np.zeros(max(1, n.value), np.uint32)
+            _ck(_lib.snn_read_raster(self.h, t0, t1, ids.ctypes.data, len(ids), off.ctypes.data,
+                                     ctypes.byref(n)), "snn_read_raster")
+        return ids[: n.value], off
+
+    def read_currents(self, t: int) -> np.ndarray:
+        out = np.empty(self.M, np.int32)
+        with self._dev():
+            _ck(_lib.snn_read_currents(self.h, t, out.ctypes.data), "snn_read_currents")
+        return out
+
+    def read_hashes(self, t0: int, t1: int):
+        a = np.zeros(t1 - t0, np.uint64)
+        b = np.zeros(t1 - t0, np.uint64)
+        with self._dev():
+            _ck(_lib.snn_read_hashes(self.h, t0, t1, a.ctypes.data, b.ctypes.data), "snn_read_hashes")
+        return a, b
+
+    def read_counts(self) -> dict:
+        c = snn_counts()
+        with self._dev():
+            _ck(_lib.snn_read_counts(self.h, ctypes.byref(c)), "snn_read_counts")
+        return {f: int(getattr(c, f)) for f in COUNT_FIELDS}
+
+    def read_state(self):
+        V = np.empty(self.M, np.float32)
+        ref = np.empty(self.M, np.uint8)
+        t = ctypes.c_int64(0)
+        with self._dev():
+            _ck(_lib.snn_read_state(self.h, V.ctypes.data, ref.ctypes.data, ctypes.byref(t)),
+                "snn_read_state")
+        return V, ref, int(t.value)
+
+    def read_inbox_pairs(self) -> np.ndarray:
+        n = ctypes.c_int64(0)
+        with self._dev():
+            _ck(_lib.snn_read_inbox_pairs(self.h, None, 0, ctypes.byref(n)), "snn_read_inbox_pairs")
+            out = np.zeros(max(1, n.value), np.uint64)
+            _ck(_lib.snn_read_inbox_pairs(self.h, out.ctypes.data, len(out), ctypes.byref(n)),
+                "snn_read_inbox_pairs")
+        return out[: n.value]
+
+    def save_state(self) -> bytes:
+        nb = ctypes.c_size_t(0)
+        _ck(_lib.snn_state_bytes(self.h, ctypes.byref(nb)), "snn_state_bytes")
+        buf = ctypes.create_string_buffer(nb.value)
+        with self._dev():
+            _ck(_lib.snn_save_state(self.h, buf, nb.value), "snn_save_state")
+        return buf.raw
+
+    def load_state(self, blob: bytes):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        with self._dev():
+            _ck(_lib.snn_load_state(self.h, buf, len(blob)), "snn_load_state")
+
+    def reset(self, reupload: bool = False):
+        with self._dev():
+            _ck(_lib.snn_sim_reset(self.h, int(bool(reupload))), "snn_sim_reset")
+
+    def profile_phases(self, T: int) -> np.ndarray:
+        """Advance T steps from an event-instrumented graph; summed ms per phase
+        (update, level 1, level 2, delivery)."""
+        out = np.zeros(4, np.float64)
+        with self._dev():
+            _ck(_lib.snn_profile_phases(self.h, int(T), out.ctypes.data), "snn_profile_phases")
+        return out
+
+    @property
+    def launches_per_step(self) -> int:
+        return int(_lib.snn_launches_per_step(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.snn_sim_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()

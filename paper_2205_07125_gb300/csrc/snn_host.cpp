@@ -1,0 +1,635 @@
+// Host side of the library: neuron partitioning (Algorithm 1), partition
+// grouping (Algorithm 2) and the two-level routing tables in the device
+// layout.  Setup work, run once before a simulation; nothing here is timed
+// in a step.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <mutex>
+#include <new>
+#include <queue>
+
+#include "snn_internal.h"
+
+namespace snn {
+
+int resolve_threads(int requested)
+{
+    int hw = (int)std::thread::hardware_concurrency();
+    if (hw < 1) hw = 1;
+    if (requested <= 0 || requested > hw) return hw;
+    return requested;
+}
+
+void parallel_for(int64_t n, int nthreads, const std::function<void(int64_t, int64_t, int)> &f)
+{
+    if (n <= 0) return;
+    int nt = resolve_threads(nthreads);
+    if ((int64_t)nt > n) nt = (int)n;
+    if (nt <= 1) {
+        f(0, n, 0);
+        return;
+    }
+    std::vector<std::thread> th;
+    th.reserve((size_t)nt);
+    for (int k = 0; k < nt; ++k) {
+        int64_t lo = n * k / nt, hi = n * (k + 1) / nt;
+        th.emplace_back([&f, lo, hi, k] { f(lo, hi, k); });
+    }
+    for (auto &t : th) t.join();
+}
+
+// Philox4x32-10 (Salmon et al., SC 2011), host copy for the random choices
+// of Algorithms 1 and 2; word 0 of the output block.
+static uint32_t philox_w0(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2)
+{
+    uint32_t x0 = c0, x1 = c1, x2 = c2, x3 = 0;
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        uint64_t a = (uint64_t)0xD2511F53u * x0, b = (uint64_t)0xCD9E8D57u * x2;
+        uint32_t y0 = (uint32_t)(b >> 32) ^ x1 ^ k0, y2 = (uint32_t)(a >> 32) ^ x3 ^ k1;
+        x1 = (uint32_t)b;
+        x3 = (uint32_t)a;
+        x0 = y0;
+        x2 = y2;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return x0;
+}
+
+static int check_network(const snn_network *net)
+{
+    if (!net || net->n_neurons <= 0 || !net->syn_ptr || !net->v0) return SNN_E_ARG;
+    const int64_t M = net->n_neurons;
+    if (net->syn_ptr[0] != 0) return SNN_E_ARG;
+    for (int64_t i = 0; i < M; ++i)
+        if (net->syn_ptr[i + 1] < net->syn_ptr[i]) return SNN_E_ARG;
+    if (net->syn_ptr[M] > 0 && (!net->syn_tgt || !net->syn_w || !net->syn_d)) return SNN_E_ARG;
+    return SNN_OK;
+}
+
+}  // namespace snn
+
+using namespace snn;
+
+extern "C" const char *snn_strerror(int code)
+{
+    switch (code) {
+    case SNN_OK: return "ok";
+    case SNN_E_ARG: return "invalid argument";
+    case SNN_E_NOMEM: return "out of memory or workspace too small";
+    case SNN_E_CAPACITY: return "device buffer capacity exceeded";
+    case SNN_E_CUDA: return "CUDA runtime error";
+    case SNN_E_RANGE: return "network exceeds a layout limit";
+    case SNN_E_STATE: return "invalid state for this call";
+    case SNN_E_NODEV: return "no usable CUDA device";
+    default: return "unknown error";
+    }
+}
+
+// ------------------------------------------------------------ Algorithm 1
+namespace {
+
+struct GreedyAlg1 {
+    int64_t M;
+    const int64_t *ptr;
+    const uint32_t *tgt;
+    std::vector<int64_t> in_ptr;
+    std::vector<uint32_t> in_src;
+    std::vector<int64_t> W;  // out-degree
+
+    explicit GreedyAlg1(const snn_network *net) : M(net->n_neurons), ptr(net->syn_ptr), tgt(net->syn_tgt)
+    {
+        const int64_t E = ptr[M];
+        in_ptr.assign((size_t)M + 1, 0);
+        in_src.resize((size_t)E);
+        for (int64_t e = 0; e < E; ++e) in_ptr[tgt[e] + 1]++;
+        for (int64_t i = 0; i < M; ++i) in_ptr[i + 1] += in_ptr[i];
+        std::vector<int64_t> fill(in_ptr.begin(), in_ptr.end() - 1);
+        for (int64_t i = 0; i < M; ++i)
+            for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e) in_src[(size_t)fill[tgt[e]]++] = (uint32_t)i;
+        W.resize((size_t)M);
+        for (int64_t i = 0; i < M; ++i) W[i] = ptr[i + 1] - ptr[i];
+    }
+
+    int64_t objective(const int32_t *lab) const
+    {
+        int64_t c = 0;
+        for (int64_t i = 0; i < M; ++i)
+            for (int64_t e = ptr[i]; e < ptr[i + 1]; ++e)
+                if (lab[i] != lab[tgt[e]]) c += W[i] * W[tgt[e]];
+        return c;
+    }
+
+    // One greedy pass t; heap keyed by (gain desc, id asc) over unassigned
+    // neurons with positive gain; zero-gain picks fall back to the lowest
+    // unassigned id, which is what a full scan with ties to the lowest id gives.
+    void pass(int32_t P, int32_t t, uint64_t seed, std::vector<int32_t> &lab) const
+    {
+        lab.assign((size_t)M, -1);
+        std::vector<int64_t> gain((size_t)M, 0);
+        std::vector<int64_t> touched;
+        int64_t Wtot = 0;
+        for (int64_t i = 0; i < M; ++i) Wtot += W[i];
+        int64_t n_un = M;
+        int64_t low = 0;  // lowest possibly unassigned id
+        typedef std::pair<int64_t, int64_t> Item;  // (gain, -id): max-heap => max gain, min id
+        for (int32_t k = 0; k < P; ++k) {
+            if (k == P - 1) {
+                for (int64_t i = 0; i < M; ++i)
+                    if (lab[i] < 0) lab[i] = k;
+                break;
+            }
+            if (n_un == 0) break;
+            while (low < M && lab[low] >= 0) ++low;
+            int64_t s;
+            if (t == 1) {
+                s = low;
+            } else {
+                int64_t r = (int64_t)(philox_w0(seed, (uint32_t)t, (uint32_t)k, 0xA1u) % (uint64_t)n_un);
+                s = -1;
+                for (int64_t i = low; i < M; ++i)
+                    if (lab[i] < 0) {
+                        if (r == 0) { s = i; break; }
+                        --r;
+                    }
+            }
+            for (int64_t j : touched) gain[j] = 0;
+            touched.clear();
+            std::priority_queue<Item> heap;
+            int64_t wk = 0, add = s;
+            while (add >= 0) {
+                lab[add] = k;
+                --n_un;
+                const int64_t wa = W[add];
+                wk += wa;
+                auto bump = [&](int64_t j) {
+                    int64_t inc = wa * W[j];
+                    if (gain[j] == 0) touched.push_back(j);
+                    gain[j] += inc;
+                    if (lab[j] < 0 && gain[j] > 0) heap.push(Item(gain[j], -j));
+                };
+                for (int64_t e = ptr[add]; e < ptr[add + 1]; ++e) bump(tgt[e]);
+                for (int64_t e = in_ptr[add]; e < in_ptr[add + 1]; ++e) bump(in_src[e]);
+                if (!(wk * (int64_t)P < Wtot) || n_un == 0) break;
+                add = -1;
+                while (!heap.empty()) {
+                    Item it = heap.top();
+                    int64_t j = -it.second;
+                    if (lab[j] >= 0 || gain[j] != it.first) {
+                        heap.pop();
+                        continue;
+                    }
+                    add = j;
+                    break;
+                }
+                if (add < 0) {
+                    while (low < M && lab[low] >= 0) ++low;
+                    add = low;
+                }
+            }
+        }
+    }
+};
+
+}  // namespace
+
+extern "C" int snn_partition(const snn_network *net, int32_t P, const snn_partition_params *prm,
+                             int32_t *part_of, snn_partition_stats *stats)
+{
+    if (check_network(net) != SNN_OK || !prm || !part_of) return SNN_E_ARG;
+    const int64_t M = net->n_neurons;
+    if (P < 1 || P > M) return SNN_E_ARG;
+    try {
+        if (prm->mode == SNN_PART_PLANTED) {
+            for (int32_t p = 0; p < P; ++p)
+                for (int64_t i = (int64_t)p * M / P; i < (int64_t)(p + 1) * M / P; ++i) part_of[i] = p;
+        } else if (prm->mode == SNN_PART_RANDOM) {
+            // balanced random: a seeded shuffle of the ids cut into P runs
+            std::vector<uint32_t> ids((size_t)M);
+            for (int64_t i = 0; i < M; ++i) ids[i] = (uint32_t)i;
+            uint64_t st = prm->seed ^ 0x5DEECE66DULL;
+            for (int64_t i = M - 1; i > 0; --i) {
+                st += 0x9E3779B97F4A7C15ULL;
+                uint64_t z = st;
+                z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+                z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+                z ^= z >> 31;
+                int64_t j = (int64_t)(((unsigned __int128)z * (uint64_t)(i + 1)) >> 64);
+                std::swap(ids[i], ids[j]);
+            }
+            for (int32_t p = 0; p < P; ++p)
+                for (int64_t x = (int64_t)p * M / P; x < (int64_t)(p + 1) * M / P; ++x) part_of[ids[x]] = p;
+        } else if (prm->mode == SNN_PART_GREEDY) {
+            if (prm->iters < 1) return SNN_E_ARG;
+            for (int64_t i = 0; i < M; ++i)
+                if (net->syn_ptr[i + 1] > net->syn_ptr[i])
+                    for (int64_t e = net->syn_ptr[i]; e < net->syn_ptr[i + 1]; ++e)
+                        if (net->syn_tgt[e] >= (uint64_t)M) return SNN_E_ARG;
+            GreedyAlg1 g(net);
+            std::vector<int32_t> lab;
+            int64_t best = -1;
+            for (int32_t t = 1; t <= prm->iters; ++t) {
+                g.pass(P, t, prm->seed, lab);
+                int64_t c = g.objective(lab.data());
+                if (best < 0 || c < best) {
+                    best = c;
+                    std::memcpy(part_of, lab.data(), sizeof(int32_t) * (size_t)M);
+                }
+            }
+        } else {
+            return SNN_E_ARG;
+        }
+        if (stats) {
+            std::vector<int64_t> wsum((size_t)P, 0);
+            int64_t obj = 0;
+            for (int64_t i = 0; i < M; ++i) {
+                int64_t wi = net->syn_ptr[i + 1] - net->syn_ptr[i];
+                wsum[part_of[i]] += wi;
+                for (int64_t e = net->syn_ptr[i]; e < net->syn_ptr[i + 1]; ++e) {
+                    uint32_t j = net->syn_tgt[e];
+                    if (part_of[i] != part_of[j]) obj += wi * (net->syn_ptr[j + 1] - net->syn_ptr[j]);
+                }
+            }
+            stats->objective = obj;
+            stats->min_weight = *std::min_element(wsum.begin(), wsum.end());
+            stats->max_weight = *std::max_element(wsum.begin(), wsum.end());
+        }
+    } catch (const std::bad_alloc &) {
+        return SNN_E_NOMEM;
+    }
+    return SNN_OK;
+}
+
+// ------------------------------------------------------------ Algorithm 2
+namespace {
+
+typedef unsigned __int128 u128;
+
+// Greedy grouping of P partitions into n_vn groups of size s.
+static void group_greedy(int32_t P, int32_t n_vn, int32_t iters, uint64_t seed,
+                         const std::vector<int64_t> &PG, const std::vector<int64_t> &WG,
+                         std::vector<int32_t> &best_grp, u128 &best_cost)
+{
+    const int32_t s = P / n_vn;
+    std::vector<int32_t> grp((size_t)P);
+    bool have = false;
+    for (int32_t t = 1; t <= iters; ++t) {
+        std::fill(grp.begin(), grp.end(), -1);
+        int32_t n_un = P;
+        for (int32_t g = 0; g < n_vn; ++g) {
+            if (g == n_vn - 1) {
+                for (int32_t p = 0; p < P; ++p)
+                    if (grp[p] < 0) grp[p] = g;
+                break;
+            }
+            int32_t seedp = -1;
+            if (t == 1) {
+                for (int32_t p = 0; p < P; ++p)
+                    if (grp[p] < 0 && (seedp < 0 || WG[p] > WG[seedp])) seedp = p;
+            } else {
+                uint32_t r = philox_w0(seed, (uint32_t)t, (uint32_t)g, 0xA2u) % (uint32_t)n_un;
+                for (int32_t p = 0; p < P; ++p)
+                    if (grp[p] < 0) {
+                        if (r == 0) { seedp = p; break; }
+                        --r;
+                    }
+            }
+            grp[seedp] = g;
+            --n_un;
+            std::vector<int32_t> members(1, seedp);
+            while ((int32_t)members.size() < s) {
+                int32_t bq = -1;
+                u128 bg = 0;
+                for (int32_t q = 0; q < P; ++q) {
+                    if (grp[q] >= 0) continue;
+                    u128 gq = 0;
+                    for (int32_t m : members)
+                        gq += (u128)(PG[(size_t)m * P + q] + PG[(size_t)q * P + m]) * (u128)WG[m] * (u128)WG[q];
+                    if (bq < 0 || gq > bg) { bq = q; bg = gq; }
+                }
+                grp[bq] = g;
+                --n_un;
+                members.push_back(bq);
+            }
+        }
+        u128 cost = 0;
+        for (int32_t p = 0; p < P; ++p)
+            for (int32_t q = 0; q < P; ++q)
+                if (grp[p] != grp[q]) cost += (u128)PG[(size_t)p * P + q] * (u128)WG[p] * (u128)WG[q];
+        if (!have || cost < best_cost) {
+            best_cost = cost;
+            best_grp = grp;
+            have = true;
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" int snn_routing_build(const snn_network *net, const int32_t *part_of, int32_t P,
+                                 int32_t n_vn, const snn_routing_params *prm, snn_routing **out)
+{
+    if (!out) return SNN_E_ARG;
+    *out = nullptr;
+    if (check_network(net) != SNN_OK || !part_of || !prm) return SNN_E_ARG;
+    const int64_t M = net->n_neurons, E = net->syn_ptr[M];
+    if (P < 1 || n_vn < 1 || P % n_vn || P > M) return SNN_E_ARG;
+    if (P > 4096) return SNN_E_RANGE;
+    if (prm->grouping != SNN_GROUP_CONTIGUOUS && prm->grouping != SNN_GROUP_GREEDY) return SNN_E_ARG;
+    if (prm->grouping == SNN_GROUP_GREEDY && prm->iters < 1) return SNN_E_ARG;
+    if (M >= (int64_t)1 << kTgtBits) return SNN_E_RANGE;
+    if (E >= (int64_t)1 << 40) return SNN_E_RANGE;
+    const int nt = resolve_threads(prm->n_threads);
+    const int64_t *sp = net->syn_ptr;
+    const uint32_t *tg = net->syn_tgt;
+    const uint8_t *dd = net->syn_d;
+
+    snn_routing *rt = nullptr;
+    try {
+        rt = new snn_routing();
+        rt->M = M;
+        rt->E = E;
+        rt->P = P;
+        rt->n_vn = n_vn;
+        rt->vn_size = P / n_vn;
+        const int32_t s = rt->vn_size;
+
+        // ---- validation and per-thread partition graph
+        std::vector<int64_t> sizes((size_t)P, 0);
+        for (int64_t i = 0; i < M; ++i) {
+            if (part_of[i] < 0 || part_of[i] >= P) { delete rt; return SNN_E_ARG; }
+            sizes[part_of[i]]++;
+        }
+        for (int32_t p = 0; p < P; ++p)
+            if (sizes[p] == 0) { delete rt; return SNN_E_ARG; }
+        std::vector<std::vector<int64_t>> pg_t((size_t)nt);
+        std::vector<int> bad((size_t)nt, 0), maxd((size_t)nt, 1);
+        std::vector<int64_t> WG((size_t)P, 0);
+        parallel_for(M, nt, [&](int64_t lo, int64_t hi, int k) {
+            std::vector<int64_t> &pg = pg_t[k];
+            pg.assign((size_t)P * P, 0);
+            for (int64_t i = lo; i < hi; ++i) {
+                int64_t deg = sp[i + 1] - sp[i];
+                if (deg >= ((int64_t)1 << kLenBits)) bad[k] = SNN_E_RANGE;
+                int32_t p = part_of[i];
+                for (int64_t e = sp[i]; e < sp[i + 1]; ++e) {
+                    if (tg[e] >= (uint64_t)M) { bad[k] = SNN_E_ARG; continue; }
+                    if (dd[e] < 1 || dd[e] > kMaxDelay) { bad[k] = SNN_E_RANGE; continue; }
+                    if (dd[e] > maxd[k]) maxd[k] = dd[e];
+                    int32_t q = part_of[tg[e]];
+                    if (q != p) pg[(size_t)p * P + q]++;
+                }
+            }
+        });
+        for (int k = 0; k < nt; ++k)
+            if (bad[k]) { int rc = bad[k]; delete rt; return rc; }
+        std::vector<int64_t> PG((size_t)P * P, 0);
+        for (int k = 0; k < nt; ++k) {
+            if (pg_t[k].empty()) continue;
+            for (size_t x = 0; x < PG.size(); ++x) PG[x] += pg_t[k][x];
+            rt->max_delay = std::max(rt->max_delay, maxd[k]);
+        }
+        pg_t.clear();
+        for (int64_t i = 0; i < M; ++i) WG[part_of[i]] += sp[i + 1] - sp[i];
+
+        // ---- Algorithm 2: groups
+        rt->vn_of_part.assign((size_t)P, 0);
+        if (prm->grouping == SNN_GROUP_CONTIGUOUS) {
+            for (int32_t p = 0; p < P; ++p) rt->vn_of_part[p] = p / s;
+            u128 c = 0;
+            for (int32_t p = 0; p < P; ++p)
+                for (int32_t q = 0; q < P; ++q)
+                    if (p / s != q / s) c += (u128)PG[(size_t)p * P + q] * (u128)WG[p] * (u128)WG[q];
+            rt->group_cost = c;
+        } else {
+            group_greedy(P, n_vn, prm->iters, prm->seed, PG, WG, rt->vn_of_part, rt->group_cost);
+        }
+        // internal partition order: by (VN, label)
+        rt->part_of_ip.resize((size_t)P);
+        rt->ip_of_part.resize((size_t)P);
+        {
+            std::vector<int32_t> fill((size_t)n_vn, 0);
+            for (int32_t p = 0; p < P; ++p) {
+                int32_t g = rt->vn_of_part[p];
+                int32_t ip = g * s + fill[g]++;
+                rt->ip_of_part[p] = ip;
+                rt->part_of_ip[ip] = p;
+            }
+        }
+        // relay of VN g for source VN h: (h mod s)-th member of g in label order,
+        // which is internal partition g*s + h % s
+        rt->relay.resize((size_t)n_vn * n_vn);
+        for (int32_t g = 0; g < n_vn; ++g)
+            for (int32_t h = 0; h < n_vn; ++h) rt->relay[(size_t)g * n_vn + h] = rt->part_of_ip[g * s + h % s];
+
+        // ---- internal neuron order: partition-major, ascending global id
+        rt->pbase.assign((size_t)P + 1, 0);
+        for (int32_t p = 0; p < P; ++p) rt->pbase[rt->ip_of_part[p] + 1] = sizes[p];
+        for (int32_t ip = 0; ip < P; ++ip) rt->pbase[ip + 1] += rt->pbase[ip];
+        rt->perm_inv.resize((size_t)M);
+        rt->perm_fwd.resize((size_t)M);
+        {
+            std::vector<int64_t> fill(rt->pbase.begin(), rt->pbase.end() - 1);
+            for (int64_t i = 0; i < M; ++i) {
+                int64_t k = fill[rt->ip_of_part[part_of[i]]]++;
+                rt->perm_inv[k] = (uint32_t)i;
+                rt->perm_fwd[i] = (uint32_t)k;
+            }
+        }
+        rt->identity = true;
+        for (int64_t i = 0; i < M; ++i)
+            if (rt->perm_fwd[i] != (uint32_t)i) { rt->identity = false; break; }
+        rt->v0.resize((size_t)M);
+        for (int64_t k = 0; k < M; ++k) rt->v0[k] = net->v0[rt->perm_inv[k]];
+
+        // ---- pass 1: per internal neuron, segment and VN counts
+        std::vector<int64_t> csr((size_t)M + 1, 0), l2p((size_t)M + 1, 0);
+        std::vector<uint32_t> nl1((size_t)M + 1, 0);
+        std::vector<std::vector<uint64_t>> bcap_t((size_t)nt), icap_t((size_t)nt);
+        std::vector<std::vector<uint8_t>> conn_t((size_t)nt);
+        parallel_for(M, nt, [&](int64_t lo, int64_t hi, int k) {
+            std::vector<int32_t> cnt((size_t)P, 0);
+            std::vector<uint8_t> gm((size_t)n_vn, 0);
+            bcap_t[k].assign((size_t)n_vn, 0);
+            icap_t[k].assign((size_t)P, 0);
+            conn_t[k].assign((size_t)P * P, 0);
+            for (int64_t kk = lo; kk < hi; ++kk) {
+                int64_t i = rt->perm_inv[kk];
+                int32_t ps = rt->ip_of_part[part_of[i]];
+                int64_t nseg = 0, nvn = 0;
+                for (int64_t e = sp[i]; e < sp[i + 1]; ++e) {
+                    int32_t q = rt->ip_of_part[part_of[tg[e]]];
+                    if (cnt[q]++ == 0) {
+                        ++nseg;
+                        icap_t[k][q]++;
+                        conn_t[k][(size_t)ps * P + q] = 1;
+                        int32_t g = q / s;
+                        if (!gm[g]) { gm[g] = 1; ++nvn; bcap_t[k][g]++; }
+                    }
+                }
+                for (int64_t e = sp[i]; e < sp[i + 1]; ++e) {
+                    int32_t q = rt->ip_of_part[part_of[tg[e]]];
+                    cnt[q] = 0;
+                    gm[q / s] = 0;
+                }
+                csr[kk + 1] = sp[i + 1] - sp[i];
+                l2p[kk + 1] = nseg;
+                nl1[kk + 1] = (uint32_t)nvn;
+            }
+        });
+        for (int64_t k = 0; k < M; ++k) {
+            csr[k + 1] += csr[k];
+            l2p[k + 1] += l2p[k];
+        }
+        int64_t n_l1 = 0;
+        rt->l1_ptr.alloc(M + 1);
+        rt->l1_ptr[0] = 0;
+        for (int64_t k = 0; k < M; ++k) {
+            n_l1 += nl1[k + 1];
+            if (n_l1 >= ((int64_t)1 << 32)) { delete rt; return SNN_E_RANGE; }
+            rt->l1_ptr[k + 1] = (uint32_t)n_l1;
+        }
+        const int64_t n_l2 = l2p[M];
+        if (n_l2 >= ((int64_t)1 << 32)) { delete rt; return SNN_E_RANGE; }
+        rt->n_l1 = n_l1;
+        rt->n_l2 = n_l2;
+        rt->src_vn.resize((size_t)M);
+        for (int32_t ip = 0; ip < P; ++ip)
+            for (int64_t k = rt->pbase[ip]; k < rt->pbase[ip + 1]; ++k) rt->src_vn[k] = (uint16_t)(ip / s);
+        rt->bucket_cap.assign((size_t)n_vn, 0);
+        rt->inbox_cap.assign((size_t)P, 0);
+        std::vector<uint8_t> conn((size_t)P * P, 0);
+        for (int k = 0; k < nt; ++k) {
+            if (bcap_t[k].empty()) continue;
+            for (int32_t g = 0; g < n_vn; ++g) rt->bucket_cap[g] += bcap_t[k][g];
+            for (int32_t q = 0; q < P; ++q) rt->inbox_cap[q] += icap_t[k][q];
+            for (size_t x = 0; x < conn.size(); ++x) conn[x] |= conn_t[k][x];
+        }
+        bcap_t.clear();
+        icap_t.clear();
+        conn_t.clear();
+
+        // ---- static connections per partition (label order)
+        rt->conn_direct.assign((size_t)P, 0);
+        rt->conn_two.assign((size_t)P, 0);
+        for (int32_t p = 0; p < P; ++p) {
+            int32_t ip = rt->ip_of_part[p], h = ip / s;
+            std::vector<uint8_t> gr((size_t)n_vn, 0);
+            for (int32_t q = 0; q < P; ++q) {
+                if (q == ip || !conn[(size_t)ip * P + q]) continue;
+                rt->conn_direct[p]++;
+                if (q / s == h) rt->conn_two[p]++;
+                else gr[q / s] = 1;
+            }
+            for (int32_t g = 0; g < n_vn; ++g) rt->conn_two[p] += gr[g];
+        }
+
+        // ---- pass 2: fill the CSR and the level-1 / level-2 tables
+        rt->syn_td.alloc(E);
+        rt->syn_w.alloc(E);
+        rt->l1_vn.alloc(n_l1);
+        rt->l1_l2.alloc(n_l1 + 1);
+        rt->l2.alloc(n_l2);
+        rt->l1_l2[n_l1] = (uint32_t)n_l2;
+        rt->csr = csr;
+        parallel_for(M, nt, [&](int64_t lo, int64_t hi, int) {
+            std::vector<int32_t> cnt((size_t)P, 0), pos((size_t)P, 0);
+            std::vector<int32_t> qs;
+            for (int64_t kk = lo; kk < hi; ++kk) {
+                int64_t i = rt->perm_inv[kk];
+                int32_t ps = rt->ip_of_part[part_of[i]], hs = ps / s;
+                qs.clear();
+                for (int64_t e = sp[i]; e < sp[i + 1]; ++e) {
+                    int32_t q = rt->ip_of_part[part_of[tg[e]]];
+                    if (cnt[q]++ == 0) qs.push_back(q);
+                }
+                std::sort(qs.begin(), qs.end());
+                int64_t base = csr[kk];
+                int32_t run = 0;
+                for (int32_t q : qs) {
+                    pos[q] = run;
+                    run += cnt[q];
+                }
+                int64_t f = l2p[kk];
+                uint32_t e1 = rt->l1_ptr[kk];
+                int32_t lastg = -1;
+                for (int32_t q : qs) {
+                    int32_t g = q / s;
+                    if (g != lastg) {
+                        rt->l1_vn[e1] = (uint16_t)g;
+                        rt->l1_l2[e1] = (uint32_t)f;
+                        ++e1;
+                        lastg = g;
+                    }
+                    L2Entry &l = rt->l2[f++];
+                    l.off = (uint64_t)(base + pos[q]);
+                    l.len = (uint32_t)cnt[q];
+                    l.q = (uint16_t)q;
+                    l.pad = 0;
+                    if (g == hs) l.cls = (q == ps) ? kClsLocal : kClsPeer;
+                    else l.cls = (q == g * s + hs % s) ? kClsRelayLocal : kClsRelayRemote;
+                }
+                for (int64_t e = sp[i]; e < sp[i + 1]; ++e) {
+                    int32_t q = rt->ip_of_part[part_of[tg[e]]];
+                    int64_t o = base + pos[q]++;
+                    rt->syn_td[o] = rt->perm_fwd[tg[e]] | ((uint32_t)(dd[e] - 1) << kTgtBits);
+                    rt->syn_w[o] = net->syn_w[e];
+                }
+                for (int32_t q : qs) cnt[q] = 0;
+            }
+        });
+    } catch (const std::bad_alloc &) {
+        delete rt;
+        return SNN_E_NOMEM;
+    }
+    *out = rt;
+    return SNN_OK;
+}
+
+extern "C" int snn_routing_info_get(const snn_routing *rt, snn_routing_info *o)
+{
+    if (!rt || !o) return SNN_E_ARG;
+    std::memset(o, 0, sizeof(*o));
+    o->n_neurons = rt->M;
+    o->n_synapses = rt->E;
+    o->n_parts = rt->P;
+    o->n_vn = rt->n_vn;
+    o->vn_size = rt->vn_size;
+    o->max_delay = rt->max_delay;
+    o->n_l1 = rt->n_l1;
+    o->n_l2 = rt->n_l2;
+    o->group_cost_lo = (uint64_t)rt->group_cost;
+    o->group_cost_hi = (uint64_t)(rt->group_cost >> 64);
+    for (int32_t p = 0; p < rt->P; ++p) {
+        o->conn_direct_sum += rt->conn_direct[p];
+        o->conn_two_level_sum += rt->conn_two[p];
+        o->conn_direct_max = std::max(o->conn_direct_max, rt->conn_direct[p]);
+        o->conn_two_level_max = std::max(o->conn_two_level_max, rt->conn_two[p]);
+    }
+    o->identity_order = rt->identity ? 1 : 0;
+    return SNN_OK;
+}
+
+extern "C" int snn_routing_groups(const snn_routing *rt, int32_t *vn_of_part, int32_t *relay)
+{
+    if (!rt) return SNN_E_ARG;
+    if (vn_of_part) std::memcpy(vn_of_part, rt->vn_of_part.data(), sizeof(int32_t) * (size_t)rt->P);
+    if (relay) std::memcpy(relay, rt->relay.data(), sizeof(int32_t) * rt->relay.size());
+    return SNN_OK;
+}
+
+extern "C" int snn_routing_connections(const snn_routing *rt, int32_t *direct, int32_t *two_level)
+{
+    if (!rt) return SNN_E_ARG;
+    if (direct) std::memcpy(direct, rt->conn_direct.data(), sizeof(int32_t) * (size_t)rt->P);
+    if (two_level) std::memcpy(two_level, rt->conn_two.data(), sizeof(int32_t) * (size_t)rt->P);
+    return SNN_OK;
+}
+
+extern "C" void snn_routing_destroy(snn_routing *rt)
+{
+    delete rt;
+}

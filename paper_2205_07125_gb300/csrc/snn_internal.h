@@ -1,0 +1,92 @@
+// Internal structures shared by the host routing build (snn_host.cpp) and
+// the device simulation (snn_sim.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cstring>
+#include <functional>
+#include <memory>
+#include <thread>
+#include <vector>
+
+#include "../../include/snn.h"
+
+namespace snn {
+
+// Packed synapse target word: internal target index (28 bits) | (delay-1) << 28.
+constexpr uint32_t kTgtBits = 28;
+constexpr uint32_t kTgtMask = (1u << kTgtBits) - 1u;
+constexpr int kMaxDelay = 16;
+// Level-2 inbox entry: synapse offset << 24 | segment length.
+constexpr int kLenBits = 24;
+constexpr uint64_t kLenMask = (1ull << kLenBits) - 1ull;
+
+// Level-2 entry classes (message accounting of the two-level route).
+enum : uint8_t {
+    kClsLocal = 0,        // destination is the source partition
+    kClsPeer = 1,         // other partition of the source's VN: direct message
+    kClsRelayLocal = 2,   // destination VN != source VN, destination is the relay
+    kClsRelayRemote = 3,  // destination VN != source VN, forwarded by the relay
+};
+
+// One (neuron, destination partition) entry of the level-2 table.
+struct L2Entry {
+    uint64_t off;   // first synapse of the segment in the internal CSR
+    uint32_t len;   // synapses in the segment
+    uint16_t q;     // internal destination partition
+    uint8_t cls;    // kCls*
+    uint8_t pad;
+};
+static_assert(sizeof(L2Entry) == 16, "L2Entry layout");
+
+template <class T>
+struct HostArray {
+    std::unique_ptr<T[]> p;
+    int64_t n = 0;
+    void alloc(int64_t count) {
+        p.reset(count > 0 ? new T[(size_t)count] : nullptr);
+        n = count;
+    }
+    T *data() { return p.get(); }
+    const T *data() const { return p.get(); }
+    T &operator[](int64_t i) { return p[(size_t)i]; }
+    const T &operator[](int64_t i) const { return p[(size_t)i]; }
+};
+
+}  // namespace snn
+
+struct snn_routing {
+    int64_t M = 0, E = 0;
+    int32_t P = 0, n_vn = 0, vn_size = 0, max_delay = 1;
+    bool identity = true;
+    unsigned __int128 group_cost = 0;
+
+    std::vector<int32_t> vn_of_part;  // label -> VN
+    std::vector<int32_t> ip_of_part;  // label -> internal partition
+    std::vector<int32_t> part_of_ip;  // internal partition -> label
+    std::vector<int32_t> relay;       // [g*n_vn + h] -> label
+    std::vector<int64_t> pbase;       // [P+1] first internal neuron of each internal partition
+    std::vector<uint32_t> perm_inv;   // internal -> global
+    std::vector<uint32_t> perm_fwd;   // global -> internal
+    std::vector<int32_t> conn_direct, conn_two;  // per label
+
+    // device-layout tables, host copies (internal order)
+    snn::HostArray<uint32_t> syn_td;   // [E]
+    snn::HostArray<int16_t> syn_w;     // [E]
+    snn::HostArray<uint32_t> l1_ptr;   // [M+1]
+    snn::HostArray<uint16_t> l1_vn;    // [n_l1]
+    snn::HostArray<uint32_t> l1_l2;    // [n_l1+1]
+    snn::HostArray<snn::L2Entry> l2;   // [n_l2]
+    std::vector<uint64_t> bucket_cap;  // [n_vn] exact worst case
+    std::vector<uint64_t> inbox_cap;   // [P] (internal partitions)
+    std::vector<float> v0;             // [M] internal order
+    std::vector<int64_t> csr;          // [M+1] first synapse of each internal neuron
+    std::vector<uint16_t> src_vn;      // [M] VN of each internal neuron
+    int64_t n_l1 = 0, n_l2 = 0;
+};
+
+namespace snn {
+// Run f(lo, hi) over [0, n) split into contiguous chunks on up to nthreads threads.
+void parallel_for(int64_t n, int nthreads, const std::function<void(int64_t, int64_t, int)> &f);
+int resolve_threads(int requested);
+}  // namespace snn

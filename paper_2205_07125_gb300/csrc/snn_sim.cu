@@ -1,0 +1,1027 @@
+// Device side: the per-step hot path as sm_103a kernels, CUDA-graph replay,
+// and the simulation lifecycle of the C ABI.
+//
+// One step t (arXiv 2205.07125 gives the routing, Sec. IV.B; the neuron
+// model is LIF, Table I; the step's arithmetic is fixed by the library's
+// documented readings):
+//   k_update   a1 consume ring slot t mod D, Poisson drive (Philox4x32-10,
+//                 inverse CDF), a2 FP32 LIF update + threshold (no FMA,
+//                 fixed order), a3 warp-ballot + block prefix-sum spike
+//                 compaction into the step's spike list; the last block to
+//                 finish closes the step's bookkeeping.
+//   k_level1   a4 every spike i appended to the bucket of every destination
+//                 VN in its level-1 row (one entry per VN: deduplicated).
+//   k_level2   a5 every bucket entry (i, g) expanded by the relay of g into
+//                 the inboxes of the destination partitions of g that hold
+//                 targets of i.
+//   k_deliver  a6 every inbox segment fanned out: int16 weight added with a
+//                 32-bit atomic into ring[(t+d) mod D][target].
+// The ring has D = max delay + 1 slots, so the slot consumed at step t is
+// never a slot written by the deliveries of step t.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <new>
+#include <vector>
+
+#include "snn_internal.h"
+
+using namespace snn;
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kPTab = 32;
+
+// status bits
+constexpr uint32_t kStBucket = 1u, kStInbox = 2u, kStRaster = 4u;
+
+// counter slots
+enum { C_STEPS = 0, C_SPIKES, C_EVENTS, C_L1_LOCAL, C_L1_XVN, C_L2_BASE /* + cls (4) */, C_N = 16 };
+
+struct Ctrl {
+    long long t;          // next step to update
+    long long t_cur;      // step being routed and delivered
+    long long head;       // raster write head
+    long long spk_base;   // first spike of step t_cur in spk[]
+    long long rec_steps;  // steps whose raster offsets are valid
+    unsigned int S_acc;   // spikes found so far in the running update
+    unsigned int S_cur;   // spikes of step t_cur
+    unsigned int blocks_done;
+    unsigned int status;
+    int rec_on;
+    int pad;
+};
+
+struct __align__(16) DevL2 {
+    unsigned long long off;
+    unsigned int len;
+    unsigned short q;
+    unsigned char cls;
+    unsigned char pad;
+};
+
+struct Dev {
+    // state
+    float *V;
+    uint8_t *ref;
+    int32_t *ring;
+    const uint32_t *gid;  // internal -> global id (nullptr when identical)
+    const uint16_t *src_vn;
+    // synapses and routing tables
+    const uint32_t *syn_td;
+    const int16_t *syn_w;
+    const uint32_t *l1_ptr;
+    const uint16_t *l1_vn;
+    const uint32_t *l1_l2;
+    const DevL2 *l2;
+    // exchange buffers
+    uint32_t *bucket;
+    const unsigned long long *bucket_base;
+    const uint32_t *bucket_capv;
+    uint32_t *bucket_cnt;
+    unsigned long long *inbox;
+    const unsigned long long *inbox_base;
+    const uint32_t *inbox_capv;
+    uint32_t *inbox_cnt;
+    // records
+    uint32_t *spk;
+    long long *raster_off;
+    unsigned long long *hash;
+    int32_t *cur_rec;
+    unsigned long long *counters;
+    Ctrl *ctrl;
+    // scalars
+    long long M;
+    int P, n_vn, D;
+    float alpha, e_l, v_th, v_reset;
+    int t_ref, w_ext, i_bias, th_len;
+    uint32_t key0, key1;
+    long long raster_cap, raster_steps, hash_steps;
+    int cur_every, cur_slots;
+    unsigned long long th[kPTab];
+};
+
+__device__ __forceinline__ uint32_t philox_w0(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1)
+{
+    uint32_t x0 = c0, x1 = c1, x2 = 0u, x3 = 0u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, x0), lo0 = 0xD2511F53u * x0;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, x2), lo1 = 0xCD9E8D57u * x2;
+        const uint32_t y0 = hi1 ^ x1 ^ k0, y2 = hi0 ^ x3 ^ k1;
+        x0 = y0;
+        x1 = lo1;
+        x2 = y2;
+        x3 = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return x0;
+}
+
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+template <class T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    return v;
+}
+
+// ---------------------------------------------------------------- a1-a3
+__global__ void __launch_bounds__(kThreads) k_update(const Dev d)
+{
+    __shared__ unsigned int s_wcnt[kThreads / 32];
+    __shared__ unsigned int s_base;
+    __shared__ unsigned long long s_h[2][kThreads / 32];
+    __shared__ int s_last;
+
+    Ctrl *c = d.ctrl;
+    const long long t = c->t;
+    const long long head = c->head;
+    const int slot = (int)(t % d.D);
+    const long long j = (long long)blockIdx.x * kThreads + threadIdx.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const bool do_hash = t < d.hash_steps;
+    const bool do_cur = d.cur_every > 0 && (t % d.cur_every) == 0 && (t / d.cur_every) < d.cur_slots;
+
+    bool spike = false;
+    unsigned long long hc = 0, hv = 0;
+    if (j < d.M) {
+        int32_t *rp = d.ring + (long long)slot * d.M + j;
+        const int32_t irec = *rp;
+        *rp = 0;
+        if (do_cur) d.cur_rec[(t / d.cur_every) * d.M + j] = irec;
+        const uint32_t g = d.gid ? d.gid[j] : (uint32_t)j;
+        const uint32_t u = philox_w0(d.key0, d.key1, g, (uint32_t)t);
+        int k = 0;
+        for (int m = 0; m < d.th_len; ++m) k += (d.th[m] <= (unsigned long long)u) ? 1 : 0;
+        const int32_t I = (int32_t)((uint32_t)irec + (uint32_t)k * (uint32_t)d.w_ext + (uint32_t)d.i_bias);
+        float v = d.V[j];
+        uint8_t r = d.ref[j];
+        if (r > 0) {
+            r = (uint8_t)(r - 1);
+            v = d.v_reset;
+        } else {
+            const float uu = __fsub_rn(v, d.e_l);
+            const float au = __fmul_rn(d.alpha, uu);
+            v = __fadd_rn(d.e_l, au);
+            const float x = __fmul_rn(__int2float_rn(I), 0.0009765625f);
+            v = __fadd_rn(v, x);
+            if (v >= d.v_th) {
+                spike = true;
+                v = d.v_reset;
+                r = (uint8_t)d.t_ref;
+            }
+        }
+        d.V[j] = v;
+        d.ref[j] = r;
+        if (do_hash) {
+            hc = mix64(((unsigned long long)g << 32) | (uint32_t)irec);
+            hv = mix64(((unsigned long long)g << 32) | __float_as_uint(v));
+        }
+    }
+    // a3: warp ballot, block prefix sum, one atomic per block
+    const unsigned int ballot = __ballot_sync(0xFFFFFFFFu, spike);
+    if (lane == 0) s_wcnt[wid] = __popc(ballot);
+    if (do_hash) {
+        hc = warp_sum(hc);
+        hv = warp_sum(hv);
+        if (lane == 0) {
+            s_h[0][wid] = hc;
+            s_h[1][wid] = hv;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned int tot = 0;
+        for (int w = 0; w < kThreads / 32; ++w) {
+            const unsigned int cw = s_wcnt[w];
+            s_wcnt[w] = tot;
+            tot += cw;
+        }
+        s_base = tot ? atomicAdd(&c->S_acc, tot) : 0u;
+        if (do_hash) {
+            unsigned long long a = 0, b = 0;
+            for (int w = 0; w < kThreads / 32; ++w) {
+                a += s_h[0][w];
+                b += s_h[1][w];
+            }
+            atomicAdd(&d.hash[2 * t], a);
+            atomicAdd(&d.hash[2 * t + 1], b);
+        }
+    }
+    __syncthreads();
+    if (spike) {
+        const unsigned int pos = s_base + s_wcnt[wid] + __popc(ballot & ((1u << lane) - 1u));
+        d.spk[head + pos] = (uint32_t)j;
+    }
+    // the last block to finish closes the step
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(&c->blocks_done, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    for (int x = threadIdx.x; x < d.n_vn; x += kThreads) d.bucket_cnt[x] = 0;
+    for (int x = threadIdx.x; x < d.P; x += kThreads) d.inbox_cnt[x] = 0;
+    if (threadIdx.x == 0) {
+        const unsigned int S = atomicAdd(&c->S_acc, 0u);
+        c->t_cur = t;
+        c->S_cur = S;
+        c->spk_base = head;
+        long long h = head;
+        if (c->rec_on) {
+            if (t < d.raster_steps && head + S <= d.raster_cap) {
+                h = head + S;
+                d.raster_off[t + 1] = h;
+                c->rec_steps = t + 1;
+            } else {
+                c->rec_on = 0;
+                c->status |= kStRaster;
+            }
+        }
+        c->head = h;
+        c->t = t + 1;
+        c->S_acc = 0;
+        c->blocks_done = 0;
+        d.counters[C_STEPS] += 1ull;
+        d.counters[C_SPIKES] += S;
+    }
+}
+
+// ---------------------------------------------------------------- a4
+__global__ void __launch_bounds__(kThreads) k_level1(const Dev d)
+{
+    __shared__ unsigned long long s_c[2];
+    if (threadIdx.x < 2) s_c[threadIdx.x] = 0;
+    __syncthreads();
+    const Ctrl *c = d.ctrl;
+    const unsigned int S = c->S_cur;
+    const long long base = c->spk_base;
+    unsigned int loc = 0, xvn = 0;
+    unsigned int ovf = 0;
+    for (unsigned int s = blockIdx.x * kThreads + threadIdx.x; s < S; s += gridDim.x * kThreads) {
+        const uint32_t i = d.spk[base + s];
+        const uint16_t h = d.src_vn[i];
+        for (uint32_t e = d.l1_ptr[i]; e < d.l1_ptr[i + 1]; ++e) {
+            const uint16_t g = d.l1_vn[e];
+            const unsigned int pos = atomicAdd(&d.bucket_cnt[g], 1u);
+            if (pos < d.bucket_capv[g]) d.bucket[d.bucket_base[g] + pos] = e;
+            else ovf = 1;
+            if (g == h) ++loc; else ++xvn;
+        }
+    }
+    loc = warp_sum(loc);
+    xvn = warp_sum(xvn);
+    if ((threadIdx.x & 31) == 0 && (loc | xvn)) {
+        atomicAdd(&s_c[0], (unsigned long long)loc);
+        atomicAdd(&s_c[1], (unsigned long long)xvn);
+    }
+    if (ovf) atomicOr(&d.ctrl->status, kStBucket);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (s_c[0]) atomicAdd(&d.counters[C_L1_LOCAL], s_c[0]);
+        if (s_c[1]) atomicAdd(&d.counters[C_L1_XVN], s_c[1]);
+    }
+}
+
+// ---------------------------------------------------------------- a5
+__global__ void __launch_bounds__(kThreads) k_level2(const Dev d)
+{
+    __shared__ unsigned long long s_c[4];
+    if (threadIdx.x < 4) s_c[threadIdx.x] = 0;
+    __syncthreads();
+    unsigned int cls[4] = {0, 0, 0, 0};
+    unsigned int ovf = 0;
+    const unsigned int gt = blockIdx.x * kThreads + threadIdx.x, gs = gridDim.x * kThreads;
+    for (int g = 0; g < d.n_vn; ++g) {
+        const unsigned int n = min(d.bucket_cnt[g], d.bucket_capv[g]);
+        const unsigned long long bb = d.bucket_base[g];
+        for (unsigned int x = gt; x < n; x += gs) {
+            const uint32_t e = d.bucket[bb + x];
+            for (uint32_t f = d.l1_l2[e]; f < d.l1_l2[e + 1]; ++f) {
+                const DevL2 l = d.l2[f];
+                const unsigned int pos = atomicAdd(&d.inbox_cnt[l.q], 1u);
+                if (pos < d.inbox_capv[l.q])
+                    d.inbox[d.inbox_base[l.q] + pos] = (l.off << kLenBits) | (unsigned long long)l.len;
+                else
+                    ovf = 1;
+                cls[l.cls & 3]++;
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const unsigned int v = warp_sum(cls[k]);
+        if ((threadIdx.x & 31) == 0 && v) atomicAdd(&s_c[k], (unsigned long long)v);
+    }
+    if (ovf) atomicOr(&d.ctrl->status, kStInbox);
+    __syncthreads();
+    if (threadIdx.x < 4 && s_c[threadIdx.x]) atomicAdd(&d.counters[C_L2_BASE + threadIdx.x], s_c[threadIdx.x]);
+}
+
+// ---------------------------------------------------------------- a6
+__global__ void __launch_bounds__(kThreads) k_deliver(const Dev d)
+{
+    __shared__ unsigned long long s_ev;
+    if (threadIdx.x == 0) s_ev = 0;
+    __syncthreads();
+    const long long t = d.ctrl->t_cur;
+    const int tm = (int)(t % d.D);
+    const int lane = threadIdx.x & 31;
+    const unsigned int gw = (blockIdx.x * kThreads + threadIdx.x) >> 5, nw = (gridDim.x * kThreads) >> 5;
+    unsigned long long ev = 0;
+    for (int q = 0; q < d.P; ++q) {
+        const unsigned int n = min(d.inbox_cnt[q], d.inbox_capv[q]);
+        const unsigned long long ib = d.inbox_base[q];
+        for (unsigned int x = gw; x < n; x += nw) {
+            const unsigned long long ent = d.inbox[ib + x];
+            const unsigned long long off = ent >> kLenBits;
+            const unsigned int len = (unsigned int)(ent & kLenMask);
+            for (unsigned int l = lane; l < len; l += 32) {
+                const uint32_t td = d.syn_td[off + l];
+                const int32_t w = d.syn_w[off + l];
+                int sl = tm + (int)(td >> kTgtBits) + 1;
+                if (sl >= d.D) sl -= d.D;
+                atomicAdd(&d.ring[(long long)sl * d.M + (td & kTgtMask)], w);
+            }
+            ev += len;
+        }
+    }
+    if (lane == 0 && ev) atomicAdd(&s_ev, ev);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_ev) atomicAdd(&d.counters[C_EVENTS], s_ev);
+}
+
+// ---------------------------------------------------------------- host helpers
+struct Region {
+    size_t off = 0, bytes = 0;
+};
+
+struct Layout {
+    Region V, ref, ring, gid, src_vn, syn_td, syn_w, l1_ptr, l1_vn, l1_l2, l2;
+    Region bucket, bucket_base, bucket_capv, bucket_cnt, inbox, inbox_base, inbox_capv, inbox_cnt;
+    Region spk, raster_off, hash, cur_rec, counters, ctrl;
+    size_t total = 0;
+    std::vector<uint64_t> bucket_base_h, inbox_base_h;
+    std::vector<uint32_t> bucket_cap_h, inbox_cap_h;
+    int D = 2;
+};
+
+static void place(Layout &L, Region &r, size_t bytes)
+{
+    r.off = L.total;
+    r.bytes = bytes;
+    L.total += (bytes + 255) & ~(size_t)255;
+}
+
+static int make_layout(const snn_routing *rt, const snn_sim_params *p, Layout &L)
+{
+    const int64_t M = rt->M, E = rt->E;
+    L = Layout();
+    L.D = rt->max_delay + 1;
+    auto cap = [](uint64_t exact, float frac) -> uint64_t {
+        double c = std::ceil((double)exact * (double)frac);
+        if (c < 0) c = 0;
+        if (c > (double)exact) c = (double)exact;
+        return (uint64_t)c;
+    };
+    uint64_t nb = 0, ni = 0;
+    L.bucket_base_h.resize((size_t)rt->n_vn + 1);
+    L.bucket_cap_h.resize((size_t)rt->n_vn);
+    for (int32_t g = 0; g < rt->n_vn; ++g) {
+        uint64_t c = cap(rt->bucket_cap[g], p->bucket_frac);
+        if (c > 0xFFFFFFFFull) return SNN_E_RANGE;
+        L.bucket_base_h[g] = nb;
+        L.bucket_cap_h[g] = (uint32_t)c;
+        nb += c;
+    }
+    L.bucket_base_h[rt->n_vn] = nb;
+    L.inbox_base_h.resize((size_t)rt->P + 1);
+    L.inbox_cap_h.resize((size_t)rt->P);
+    for (int32_t q = 0; q < rt->P; ++q) {
+        uint64_t c = cap(rt->inbox_cap[q], p->inbox_frac);
+        if (c > 0xFFFFFFFFull) return SNN_E_RANGE;
+        L.inbox_base_h[q] = ni;
+        L.inbox_cap_h[q] = (uint32_t)c;
+        ni += c;
+    }
+    L.inbox_base_h[rt->P] = ni;
+    place(L, L.ctrl, sizeof(Ctrl));
+    place(L, L.counters, sizeof(unsigned long long) * C_N);
+    place(L, L.V, sizeof(float) * (size_t)M);
+    place(L, L.ref, (size_t)M);
+    place(L, L.ring, sizeof(int32_t) * (size_t)M * (size_t)L.D);
+    place(L, L.gid, rt->identity ? 0 : sizeof(uint32_t) * (size_t)M);
+    place(L, L.src_vn, sizeof(uint16_t) * (size_t)M);
+    place(L, L.syn_td, sizeof(uint32_t) * (size_t)E);
+    place(L, L.syn_w, sizeof(int16_t) * (size_t)E);
+    place(L, L.l1_ptr, sizeof(uint32_t) * (size_t)(M + 1));
+    place(L, L.l1_vn, sizeof(uint16_t) * (size_t)rt->n_l1);
+    place(L, L.l1_l2, sizeof(uint32_t) * (size_t)(rt->n_l1 + 1));
+    place(L, L.l2, sizeof(L2Entry) * (size_t)rt->n_l2);
+    place(L, L.bucket, sizeof(uint32_t) * (size_t)nb);
+    place(L, L.bucket_base, sizeof(uint64_t) * (size_t)(rt->n_vn + 1));
+    place(L, L.bucket_capv, sizeof(uint32_t) * (size_t)rt->n_vn);
+    place(L, L.bucket_cnt, sizeof(uint32_t) * (size_t)rt->n_vn);
+    place(L, L.inbox, sizeof(uint64_t) * (size_t)ni);
+    place(L, L.inbox_base, sizeof(uint64_t) * (size_t)(rt->P + 1));
+    place(L, L.inbox_capv, sizeof(uint32_t) * (size_t)rt->P);
+    place(L, L.inbox_cnt, sizeof(uint32_t) * (size_t)rt->P);
+    place(L, L.spk, sizeof(uint32_t) * (size_t)(p->raster_cap + M));
+    place(L, L.raster_off, sizeof(long long) * (size_t)(p->raster_steps + 1));
+    place(L, L.hash, sizeof(unsigned long long) * 2 * (size_t)p->hash_steps);
+    place(L, L.cur_rec, sizeof(int32_t) * (size_t)M * (size_t)p->cur_slots);
+    return SNN_OK;
+}
+
+static bool params_ok(const snn_sim_params *p)
+{
+    if (!p) return false;
+    if (!(p->dt_ms > 0) || !(p->tau_ms > 0)) return false;
+    if (p->t_ref < 0 || p->t_ref > 255) return false;
+    if (!(p->drive_lambda >= 0.0) || p->drive_lambda > 16.0) return false;
+    if (p->raster_cap < 0 || p->raster_steps < 0 || p->hash_steps < 0) return false;
+    if (p->cur_every < 0 || p->cur_slots < 0) return false;
+    if (!(p->bucket_frac >= 0.0f) || !(p->inbox_frac >= 0.0f)) return false;
+    if (p->steps_per_graph < 1 || p->steps_per_graph > 256) return false;
+    return true;
+}
+
+// Poisson inverse-CDF thresholds floor(2^32 * CDF(k)), closed by 2^32 at the
+// first threshold that reaches 2^32 - 1 (pmf by p_k = p_{k-1} lambda / k).
+static int poisson_thresholds(double lambda, unsigned long long *th, int *len)
+{
+    double pmf = std::exp(-lambda), cdf = pmf;
+    int n = 0;
+    for (int k = 0; k < kPTab; ++k) {
+        if (k > 0) {
+            pmf = pmf * lambda / (double)k;
+            cdf = cdf + pmf;
+        }
+        double x = std::floor(cdf * 4294967296.0);
+        unsigned long long v = x >= 4294967295.0 ? 4294967296ULL : (unsigned long long)x;
+        th[k] = v;
+        n = k + 1;
+        if (v >= 4294967296ULL) break;
+    }
+    for (int k = n; k < kPTab; ++k) th[k] = 4294967296ULL;
+    *len = n;
+    return SNN_OK;
+}
+
+}  // namespace
+
+struct snn_sim {
+    const snn_routing *rt = nullptr;
+    snn_sim_params prm;
+    Layout L;
+    Dev dev;
+    char *ws = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t g1 = nullptr, gU = nullptr;
+    int U = 32;
+    int device = 0;
+    cudaGraphExec_t gP = nullptr;  // instrumented graph (snn_profile_phases)
+    int UP = 0;
+    std::vector<cudaEvent_t> pev;
+    unsigned grid_update = 1, grid_route = 1;
+    std::vector<void *> pinned;
+};
+
+#define CK(x)                                     \
+    do {                                          \
+        cudaError_t e_ = (x);                     \
+        if (e_ != cudaSuccess) return SNN_E_CUDA; \
+    } while (0)
+
+extern "C" void snn_sim_params_default(snn_sim_params *p)
+{
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->dt_ms = 0.1;
+    p->tau_ms = 20.0;
+    p->e_l = -65.0f;
+    p->v_th = -50.0f;
+    p->v_reset = -65.0f;
+    p->t_ref = 20;
+    p->drive_lambda = 0.8;
+    p->w_ext = 96;
+    p->i_bias = 0;
+    p->drive_seed = 2000;
+    p->bucket_frac = 1.0f;
+    p->inbox_frac = 1.0f;
+    p->steps_per_graph = 32;
+}
+
+extern "C" int snn_sim_workspace_bytes(const snn_routing *rt, const snn_sim_params *p, size_t *bytes)
+{
+    if (!rt || !bytes || !params_ok(p)) return SNN_E_ARG;
+    Layout L;
+    int rc = make_layout(rt, p, L);
+    if (rc) return rc;
+    *bytes = L.total;
+    return SNN_OK;
+}
+
+static int upload_tables(snn_sim *s)
+{
+    const snn_routing *rt = s->rt;
+    const Layout &L = s->L;
+    char *w = s->ws;
+    cudaStream_t st = s->stream;
+    auto up = [&](const Region &r, const void *src) -> cudaError_t {
+        if (!r.bytes) return cudaSuccess;
+        return cudaMemcpyAsync(w + r.off, src, r.bytes, cudaMemcpyHostToDevice, st);
+    };
+    CK(up(L.syn_td, rt->syn_td.data()));
+    CK(up(L.syn_w, rt->syn_w.data()));
+    CK(up(L.l1_ptr, rt->l1_ptr.data()));
+    CK(up(L.l1_vn, rt->l1_vn.data()));
+    CK(up(L.l1_l2, rt->l1_l2.data()));
+    CK(up(L.l2, rt->l2.data()));
+    CK(up(L.src_vn, rt->src_vn.data()));
+    if (!rt->identity) CK(up(L.gid, rt->perm_inv.data()));
+    CK(up(L.bucket_base, L.bucket_base_h.data()));
+    CK(up(L.bucket_capv, L.bucket_cap_h.data()));
+    CK(up(L.inbox_base, L.inbox_base_h.data()));
+    CK(up(L.inbox_capv, L.inbox_cap_h.data()));
+    return SNN_OK;
+}
+
+static int reset_state(snn_sim *s)
+{
+    const Layout &L = s->L;
+    char *w = s->ws;
+    cudaStream_t st = s->stream;
+    CK(cudaMemcpyAsync(w + L.V.off, s->rt->v0.data(), L.V.bytes, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(w + L.ref.off, 0, L.ref.bytes, st));
+    CK(cudaMemsetAsync(w + L.ring.off, 0, L.ring.bytes, st));
+    CK(cudaMemsetAsync(w + L.counters.off, 0, L.counters.bytes, st));
+    CK(cudaMemsetAsync(w + L.bucket_cnt.off, 0, L.bucket_cnt.bytes, st));
+    CK(cudaMemsetAsync(w + L.inbox_cnt.off, 0, L.inbox_cnt.bytes, st));
+    if (L.raster_off.bytes) CK(cudaMemsetAsync(w + L.raster_off.off, 0, L.raster_off.bytes, st));
+    if (L.hash.bytes) CK(cudaMemsetAsync(w + L.hash.off, 0, L.hash.bytes, st));
+    if (L.cur_rec.bytes) CK(cudaMemsetAsync(w + L.cur_rec.off, 0, L.cur_rec.bytes, st));
+    Ctrl c;
+    std::memset(&c, 0, sizeof(c));
+    c.rec_on = s->prm.raster_cap > 0 && s->prm.raster_steps > 0;
+    CK(cudaMemcpyAsync(w + L.ctrl.off, &c, sizeof(c), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    return SNN_OK;
+}
+
+static cudaError_t launch_step(snn_sim *s, cudaStream_t st)
+{
+    k_update<<<s->grid_update, kThreads, 0, st>>>(s->dev);
+    k_level1<<<s->grid_route, kThreads, 0, st>>>(s->dev);
+    k_level2<<<s->grid_route, kThreads, 0, st>>>(s->dev);
+    k_deliver<<<s->grid_route, kThreads, 0, st>>>(s->dev);
+    return cudaGetLastError();
+}
+
+static int capture(snn_sim *s, int steps, cudaGraphExec_t *out)
+{
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t le = cudaSuccess;
+    for (int k = 0; k < steps && le == cudaSuccess; ++k) le = launch_step(s, s->cap_stream);
+    cudaError_t ce = cudaStreamEndCapture(s->cap_stream, &g);
+    if (le != cudaSuccess || ce != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return SNN_E_CUDA;
+    }
+    cudaError_t ie = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    return ie == cudaSuccess ? SNN_OK : SNN_E_CUDA;
+}
+
+extern "C" void snn_sim_destroy(snn_sim *s)
+{
+    if (!s) return;
+    if (s->g1) cudaGraphExecDestroy(s->g1);
+    if (s->gU) cudaGraphExecDestroy(s->gU);
+    if (s->gP) cudaGraphExecDestroy(s->gP);
+    for (cudaEvent_t e : s->pev) cudaEventDestroy(e);
+    if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
+    for (void *p : s->pinned) cudaHostUnregister(p);
+    delete s;
+}
+
+extern "C" int snn_sim_create(const snn_network *net, const snn_routing *rt, const snn_sim_params *p,
+                              void *workspace, size_t ws_bytes, void *stream, snn_sim **out)
+{
+    if (!out) return SNN_E_ARG;
+    *out = nullptr;
+    if (!net || !rt || !params_ok(p) || !workspace) return SNN_E_ARG;
+    if (net->n_neurons != rt->M || net->syn_ptr[net->n_neurons] != rt->E) return SNN_E_ARG;
+    if (((uintptr_t)workspace) & 255) return SNN_E_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) return SNN_E_NODEV;
+    snn_sim *s = new (std::nothrow) snn_sim();
+    if (!s) return SNN_E_NOMEM;
+    s->rt = rt;
+    s->prm = *p;
+    int rc = make_layout(rt, p, s->L);
+    if (rc) { delete s; return rc; }
+    if (ws_bytes < s->L.total) { delete s; return SNN_E_NOMEM; }
+    s->ws = (char *)workspace;
+    s->stream = (cudaStream_t)stream;
+    s->U = p->steps_per_graph;
+    if (cudaGetDevice(&s->device) != cudaSuccess) { delete s; return SNN_E_CUDA; }
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device) != cudaSuccess) {
+        delete s;
+        return SNN_E_CUDA;
+    }
+    s->grid_update = (unsigned)((rt->M + kThreads - 1) / kThreads);
+    s->grid_route = (unsigned)(2 * sms);
+    if (cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete s;
+        return SNN_E_CUDA;
+    }
+    if (p->pin_host_tables) {
+        auto pin = [&](const void *ptr, size_t bytes) {
+            if (ptr && bytes && cudaHostRegister((void *)ptr, bytes, cudaHostRegisterDefault) == cudaSuccess)
+                s->pinned.push_back((void *)ptr);
+            else
+                cudaGetLastError();
+        };
+        pin(rt->syn_td.data(), s->L.syn_td.bytes);
+        pin(rt->syn_w.data(), s->L.syn_w.bytes);
+        pin(rt->l2.data(), s->L.l2.bytes);
+    }
+    // device view
+    const Layout &L = s->L;
+    char *w = s->ws;
+    Dev &d = s->dev;
+    std::memset(&d, 0, sizeof(d));
+    d.V = (float *)(w + L.V.off);
+    d.ref = (uint8_t *)(w + L.ref.off);
+    d.ring = (int32_t *)(w + L.ring.off);
+    d.gid = rt->identity ? nullptr : (const uint32_t *)(w + L.gid.off);
+    d.src_vn = (const uint16_t *)(w + L.src_vn.off);
+    d.syn_td = (const uint32_t *)(w + L.syn_td.off);
+    d.syn_w = (const int16_t *)(w + L.syn_w.off);
+    d.l1_ptr = (const uint32_t *)(w + L.l1_ptr.off);
+    d.l1_vn = (const uint16_t *)(w + L.l1_vn.off);
+    d.l1_l2 = (const uint32_t *)(w + L.l1_l2.off);
+    d.l2 = (const DevL2 *)(w + L.l2.off);
+    d.bucket = (uint32_t *)(w + L.bucket.off);
+    d.bucket_base = (const unsigned long long *)(w + L.bucket_base.off);
+    d.bucket_capv = (const uint32_t *)(w + L.bucket_capv.off);
+    d.bucket_cnt = (uint32_t *)(w + L.bucket_cnt.off);
+    d.inbox = (unsigned long long *)(w + L.inbox.off);
+    d.inbox_base = (const unsigned long long *)(w + L.inbox_base.off);
+    d.inbox_capv = (const uint32_t *)(w + L.inbox_capv.off);
+    d.inbox_cnt = (uint32_t *)(w + L.inbox_cnt.off);
+    d.spk = (uint32_t *)(w + L.spk.off);
+    d.raster_off = (long long *)(w + L.raster_off.off);
+    d.hash = (unsigned long long *)(w + L.hash.off);
+    d.cur_rec = (int32_t *)(w + L.cur_rec.off);
+    d.counters = (unsigned long long *)(w + L.counters.off);
+    d.ctrl = (Ctrl *)(w + L.ctrl.off);
+    d.M = rt->M;
+    d.P = rt->P;
+    d.n_vn = rt->n_vn;
+    d.D = L.D;
+    d.alpha = (float)std::exp(-p->dt_ms / p->tau_ms);
+    d.e_l = p->e_l;
+    d.v_th = p->v_th;
+    d.v_reset = p->v_reset;
+    d.t_ref = p->t_ref;
+    d.w_ext = p->w_ext;
+    d.i_bias = p->i_bias;
+    d.key0 = (uint32_t)p->drive_seed;
+    d.key1 = (uint32_t)(p->drive_seed >> 32);
+    d.raster_cap = p->raster_cap;
+    d.raster_steps = p->raster_steps;
+    d.hash_steps = p->hash_steps;
+    d.cur_every = p->cur_every;
+    d.cur_slots = p->cur_slots;
+    poisson_thresholds(p->drive_lambda, d.th, &d.th_len);
+
+    rc = upload_tables(s);
+    if (!rc) rc = reset_state(s);
+    if (rc) {
+        snn_sim_destroy(s);
+        return rc;
+    }
+    *out = s;
+    return SNN_OK;
+}
+
+extern "C" int snn_step(snn_sim *s, int32_t T)
+{
+    if (!s || T < 0) return SNN_E_ARG;
+    if (!s->g1) {
+        int rc = capture(s, 1, &s->g1);
+        if (!rc && s->U > 1) rc = capture(s, s->U, &s->gU);
+        if (rc) return rc;
+    }
+    int32_t n = T;
+    if (s->gU)
+        for (; n >= s->U; n -= s->U) CK(cudaGraphLaunch(s->gU, s->stream));
+    for (; n > 0; --n) CK(cudaGraphLaunch(s->g1, s->stream));
+    return SNN_OK;
+}
+
+extern "C" int snn_profile_phases(snn_sim *s, int32_t T, double *phase_ms)
+{
+    if (!s || T < 0 || !phase_ms) return SNN_E_ARG;
+    for (int k = 0; k < 4; ++k) phase_ms[k] = 0.0;
+    if (!s->gP) {
+        const int U = 16;
+        s->pev.resize((size_t)U * 5);
+        for (auto &e : s->pev) CK(cudaEventCreate(&e));
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t le = cudaSuccess;
+        for (int k = 0; k < U && le == cudaSuccess; ++k) {
+            cudaEvent_t *ev = &s->pev[(size_t)k * 5];
+            cudaStream_t st = s->cap_stream;
+            le = cudaEventRecord(ev[0], st);
+            if (le == cudaSuccess) { k_update<<<s->grid_update, kThreads, 0, st>>>(s->dev); le = cudaEventRecord(ev[1], st); }
+            if (le == cudaSuccess) { k_level1<<<s->grid_route, kThreads, 0, st>>>(s->dev); le = cudaEventRecord(ev[2], st); }
+            if (le == cudaSuccess) { k_level2<<<s->grid_route, kThreads, 0, st>>>(s->dev); le = cudaEventRecord(ev[3], st); }
+            if (le == cudaSuccess) { k_deliver<<<s->grid_route, kThreads, 0, st>>>(s->dev); le = cudaEventRecord(ev[4], st); }
+            if (le == cudaSuccess) le = cudaGetLastError();
+        }
+        cudaError_t ce = cudaStreamEndCapture(s->cap_stream, &g);
+        if (le != cudaSuccess || ce != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return SNN_E_CUDA;
+        }
+        cudaError_t ie = cudaGraphInstantiate(&s->gP, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) return SNN_E_CUDA;
+        s->UP = U;
+    }
+    int32_t left = T;
+    while (left > 0) {
+        // whole instrumented graphs, then plain single steps for the remainder
+        if (left >= s->UP) {
+            CK(cudaGraphLaunch(s->gP, s->stream));
+            CK(cudaStreamSynchronize(s->stream));
+            for (int k = 0; k < s->UP; ++k)
+                for (int ph = 0; ph < 4; ++ph) {
+                    float ms = 0.f;
+                    CK(cudaEventElapsedTime(&ms, s->pev[(size_t)k * 5 + ph], s->pev[(size_t)k * 5 + ph + 1]));
+                    phase_ms[ph] += ms;
+                }
+            left -= s->UP;
+        } else {
+            int rc = snn_step(s, left);
+            if (rc) return rc;
+            CK(cudaStreamSynchronize(s->stream));
+            left = 0;
+        }
+    }
+    return SNN_OK;
+}
+
+extern "C" int64_t snn_launches_per_step(const snn_sim *s)
+{
+    return s ? 4 : 0;
+}
+
+static int read_ctrl(snn_sim *s, Ctrl *c)
+{
+    CK(cudaMemcpyAsync(c, s->dev.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return SNN_OK;
+}
+
+extern "C" int snn_sync_status(snn_sim *s)
+{
+    if (!s) return SNN_E_ARG;
+    CK(cudaStreamSynchronize(s->stream));
+    CK(cudaGetLastError());
+    Ctrl c;
+    int rc = read_ctrl(s, &c);
+    if (rc) return rc;
+    if (c.status & (kStBucket | kStInbox)) return SNN_E_CAPACITY;
+    return SNN_OK;
+}
+
+extern "C" int snn_read_raster(snn_sim *s, int64_t t0, int64_t t1, uint32_t *ids, int64_t cap,
+                               int64_t *step_off, int64_t *n)
+{
+    if (!s || t0 < 0 || t1 < t0 || !step_off || !n) return SNN_E_ARG;
+    *n = -1;
+    Ctrl c;
+    int rc = read_ctrl(s, &c);
+    if (rc) return rc;
+    if (t1 > c.rec_steps) return SNN_E_CAPACITY;
+    const int64_t nst = t1 - t0;
+    std::vector<long long> off((size_t)nst + 1);
+    CK(cudaMemcpy(off.data(), s->dev.raster_off + t0, sizeof(long long) * (size_t)(nst + 1),
+                  cudaMemcpyDeviceToHost));
+    const int64_t tot = off[nst] - off[0];
+    *n = tot;
+    for (int64_t k = 0; k <= nst; ++k) step_off[k] = off[k] - off[0];
+    if (tot > cap || (tot > 0 && !ids)) return tot > cap ? SNN_E_CAPACITY : SNN_E_ARG;
+    if (tot > 0) {
+        CK(cudaMemcpy(ids, s->dev.spk + off[0], sizeof(uint32_t) * (size_t)tot, cudaMemcpyDeviceToHost));
+        const uint32_t *inv = s->rt->perm_inv.data();
+        for (int64_t k = 0; k < nst; ++k) {
+            uint32_t *b = ids + step_off[k], *e = ids + step_off[k + 1];
+            for (uint32_t *x = b; x < e; ++x) *x = inv[*x];
+            std::sort(b, e);
+        }
+    }
+    return SNN_OK;
+}
+
+extern "C" int snn_read_currents(snn_sim *s, int64_t t, int32_t *out)
+{
+    if (!s || !out || t < 0) return SNN_E_ARG;
+    const snn_sim_params &p = s->prm;
+    if (p.cur_every <= 0 || t % p.cur_every || t / p.cur_every >= p.cur_slots) return SNN_E_ARG;
+    Ctrl c;
+    int rc = read_ctrl(s, &c);
+    if (rc) return rc;
+    if (t >= c.t) return SNN_E_STATE;
+    const int64_t M = s->rt->M;
+    std::vector<int32_t> buf((size_t)M);
+    CK(cudaMemcpy(buf.data(), s->dev.cur_rec + (t / p.cur_every) * M, sizeof(int32_t) * (size_t)M,
+                  cudaMemcpyDeviceToHost));
+    const uint32_t *inv = s->rt->perm_inv.data();
+    for (int64_t k = 0; k < M; ++k) out[inv[k]] = buf[k];
+    return SNN_OK;
+}
+
+extern "C" int snn_read_hashes(snn_sim *s, int64_t t0, int64_t t1, uint64_t *cur, uint64_t *v)
+{
+    if (!s || t0 < 0 || t1 < t0) return SNN_E_ARG;
+    if (t1 > s->prm.hash_steps) return SNN_E_CAPACITY;
+    std::vector<unsigned long long> h((size_t)(2 * (t1 - t0)));
+    if (t1 > t0) {
+        CK(cudaStreamSynchronize(s->stream));
+        CK(cudaMemcpy(h.data(), s->dev.hash + 2 * t0, sizeof(unsigned long long) * h.size(),
+                      cudaMemcpyDeviceToHost));
+    }
+    for (int64_t k = 0; k < t1 - t0; ++k) {
+        if (cur) cur[k] = h[2 * k];
+        if (v) v[k] = h[2 * k + 1];
+    }
+    return SNN_OK;
+}
+
+extern "C" int snn_read_counts(snn_sim *s, snn_counts *o)
+{
+    if (!s || !o) return SNN_E_ARG;
+    unsigned long long c[C_N];
+    CK(cudaMemcpyAsync(c, s->dev.counters, sizeof(c), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    o->steps = c[C_STEPS];
+    o->spikes = c[C_SPIKES];
+    o->events = c[C_EVENTS];
+    o->l1_local = c[C_L1_LOCAL];
+    o->l1_xvn = c[C_L1_XVN];
+    o->l2_local = c[C_L2_BASE + kClsLocal];
+    o->l2_peer = c[C_L2_BASE + kClsPeer];
+    o->l2_relay_local = c[C_L2_BASE + kClsRelayLocal];
+    o->l2_relay_remote = c[C_L2_BASE + kClsRelayRemote];
+    o->direct = o->l2_peer + o->l2_relay_local + o->l2_relay_remote;
+    o->direct_xvn = o->l2_relay_local + o->l2_relay_remote;
+    return SNN_OK;
+}
+
+extern "C" int snn_read_state(snn_sim *s, float *V, uint8_t *ref, int64_t *t)
+{
+    if (!s) return SNN_E_ARG;
+    const int64_t M = s->rt->M;
+    const uint32_t *inv = s->rt->perm_inv.data();
+    CK(cudaStreamSynchronize(s->stream));
+    if (V) {
+        std::vector<float> b((size_t)M);
+        CK(cudaMemcpy(b.data(), s->dev.V, sizeof(float) * (size_t)M, cudaMemcpyDeviceToHost));
+        for (int64_t k = 0; k < M; ++k) V[inv[k]] = b[k];
+    }
+    if (ref) {
+        std::vector<uint8_t> b((size_t)M);
+        CK(cudaMemcpy(b.data(), s->dev.ref, (size_t)M, cudaMemcpyDeviceToHost));
+        for (int64_t k = 0; k < M; ++k) ref[inv[k]] = b[k];
+    }
+    if (t) {
+        Ctrl c;
+        int rc = read_ctrl(s, &c);
+        if (rc) return rc;
+        *t = c.t;
+    }
+    return SNN_OK;
+}
+
+extern "C" int snn_read_inbox_pairs(snn_sim *s, uint64_t *pairs, int64_t cap, int64_t *n)
+{
+    if (!s || !n) return SNN_E_ARG;
+    const snn_routing *rt = s->rt;
+    const Layout &L = s->L;
+    CK(cudaStreamSynchronize(s->stream));
+    std::vector<uint32_t> cnt((size_t)rt->P);
+    CK(cudaMemcpy(cnt.data(), s->dev.inbox_cnt, sizeof(uint32_t) * cnt.size(), cudaMemcpyDeviceToHost));
+    int64_t tot = 0;
+    for (int32_t q = 0; q < rt->P; ++q) {
+        uint32_t m = std::min(cnt[q], L.inbox_cap_h[q]);
+        if (m == 0) continue;
+        std::vector<unsigned long long> ent(m);
+        CK(cudaMemcpy(ent.data(), s->dev.inbox + L.inbox_base_h[q], sizeof(unsigned long long) * m,
+                      cudaMemcpyDeviceToHost));
+        for (uint32_t x = 0; x < m; ++x) {
+            const int64_t off = (int64_t)(ent[x] >> kLenBits);
+            const int64_t k = std::upper_bound(rt->csr.begin(), rt->csr.end(), off) - rt->csr.begin() - 1;
+            if (pairs && tot < cap)
+                pairs[tot] = ((uint64_t)rt->perm_inv[k] << 32) | (uint32_t)rt->part_of_ip[q];
+            ++tot;
+        }
+    }
+    *n = tot;
+    return SNN_OK;
+}
+
+// checkpoint image: header, V, ref, ring, counters
+namespace {
+struct CkptHeader {
+    uint64_t magic;
+    int64_t M;
+    int32_t D, pad;
+    long long t;
+};
+constexpr uint64_t kCkptMagic = 0x534E4E434B505431ULL;
+}  // namespace
+
+extern "C" int snn_state_bytes(snn_sim *s, size_t *bytes)
+{
+    if (!s || !bytes) return SNN_E_ARG;
+    const Layout &L = s->L;
+    *bytes = sizeof(CkptHeader) + L.V.bytes + L.ref.bytes + L.ring.bytes + L.counters.bytes;
+    return SNN_OK;
+}
+
+extern "C" int snn_save_state(snn_sim *s, void *buf, size_t capb)
+{
+    size_t need = 0;
+    if (snn_state_bytes(s, &need) || !buf || capb < need) return SNN_E_ARG;
+    Ctrl c;
+    int rc = read_ctrl(s, &c);
+    if (rc) return rc;
+    const Layout &L = s->L;
+    char *b = (char *)buf;
+    CkptHeader h{kCkptMagic, s->rt->M, L.D, 0, c.t};
+    std::memcpy(b, &h, sizeof(h));
+    b += sizeof(h);
+    for (const Region *r : {&L.V, &L.ref, &L.ring, &L.counters}) {
+        CK(cudaMemcpy(b, s->ws + r->off, r->bytes, cudaMemcpyDeviceToHost));
+        b += r->bytes;
+    }
+    return SNN_OK;
+}
+
+extern "C" int snn_load_state(snn_sim *s, const void *buf, size_t bytes)
+{
+    size_t need = 0;
+    if (snn_state_bytes(s, &need) || !buf || bytes < need) return SNN_E_ARG;
+    const Layout &L = s->L;
+    const char *b = (const char *)buf;
+    CkptHeader h;
+    std::memcpy(&h, b, sizeof(h));
+    if (h.magic != kCkptMagic || h.M != s->rt->M || h.D != L.D) return SNN_E_ARG;
+    b += sizeof(h);
+    CK(cudaStreamSynchronize(s->stream));
+    for (const Region *r : {&L.V, &L.ref, &L.ring, &L.counters}) {
+        CK(cudaMemcpy(s->ws + r->off, b, r->bytes, cudaMemcpyHostToDevice));
+        b += r->bytes;
+    }
+    Ctrl c;
+    std::memset(&c, 0, sizeof(c));
+    c.t = h.t;
+    c.rec_on = 0;  // records restart empty and stay off after a restore
+    CK(cudaMemcpy(s->dev.ctrl, &c, sizeof(c), cudaMemcpyHostToDevice));
+    if (h.t < s->prm.hash_steps)
+        CK(cudaMemset(s->dev.hash + 2 * h.t, 0, sizeof(unsigned long long) * 2 * (size_t)(s->prm.hash_steps - h.t)));
+    CK(cudaMemset(s->dev.bucket_cnt, 0, L.bucket_cnt.bytes));
+    CK(cudaMemset(s->dev.inbox_cnt, 0, L.inbox_cnt.bytes));
+    return SNN_OK;
+}
+
+extern "C" int snn_sim_reset(snn_sim *s, int32_t reupload)
+{
+    if (!s) return SNN_E_ARG;
+    if (reupload) {
+        int rc = upload_tables(s);
+        if (rc) return rc;
+    }
+    return reset_state(s);
+}

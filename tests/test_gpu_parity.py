@@ -1,0 +1,209 @@
+"""GPU parity: the CUDA step (through the C ABI) against the CPU oracle.
+
+Integer work (rasters, routes, message counts, int32 currents) must match
+bit for bit, and so must the FP32 membrane (both sides use the same fixed
+operation order with no fused multiply-add).  Where several results are
+valid (the order of spikes inside a step, of bucket and inbox entries), the
+comparison is on sorted multisets.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def snn():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2205_07125_gb300 as m
+    return m
+
+
+def _oracle_mapping(g, cfg, part_mode, group_mode, P, n_vn, iters=3, seed=5):
+    if part_mode == "planted":
+        po = oracle.partition_planted(g.M, P)
+    elif part_mode == "greedy":
+        po, _ = oracle.partition_greedy(g, P, iters=iters, seed=seed)
+    else:
+        raise ValueError(part_mode)
+    if group_mode == "contiguous":
+        vn = oracle.group_contiguous(P, n_vn)
+    else:
+        vn, _ = oracle.group_greedy(g, po, P, n_vn, iters=iters, seed=seed)
+    return po, vn
+
+
+def _run_pair(snn, g, cfg, T, P, n_vn, part_mode="planted", group_mode="contiguous", cur_every=None,
+              steps_per_graph=32, iters=3, seed=5, **prm_kw):
+    net = snn.Network.from_synth(g)
+    if part_mode == "planted":
+        part, _ = snn.snn_partition(net, P, "planted")
+    else:
+        part, _ = snn.snn_partition(net, P, part_mode, iters=iters, seed=seed)
+    rt = snn.Routing(net, part, P, n_vn, group_mode, iters=iters, seed=seed)
+    ce = cur_every if cur_every is not None else max(1, T // 8)
+    prm = snn.sim_params(cfg.dyn, raster_cap=max(4096, g.M * T // 10), raster_steps=T, hash_steps=T,
+                         cur_every=ce, cur_slots=T // ce + 1, steps_per_graph=steps_per_graph,
+                         **prm_kw)
+    sim = snn.Sim(net, rt, prm, device="cuda:0")
+    po, vn = _oracle_mapping(g, cfg, part_mode, group_mode, P, n_vn, iters, seed)
+    assert np.array_equal(part, po)
+    assert np.array_equal(rt.groups()[0], vn)
+    o = oracle.Oracle(g, P, po, n_vn, vn, cfg.dyn)
+    rec = list(range(0, T, ce))
+    return sim, o, rec, rt
+
+
+def _compare(sim, o, T, rec, t0=0):
+    r = o.run(T, rec_steps=[t0 + s for s in rec], pairs=True)
+    ids, off = sim.read_raster(t0, t0 + T)
+    assert np.array_equal(off, r["raster_off"]), "raster offsets"
+    assert np.array_equal(ids, r["raster_ids"]), "raster ids"
+    ch, vh = sim.read_hashes(t0, t0 + T)
+    assert np.array_equal(ch, r["cur_hash"]), "current hashes"
+    assert np.array_equal(vh, r["v_hash"]), "membrane hashes"
+    for s in rec:
+        assert np.array_equal(sim.read_currents(t0 + s), r["currents"][t0 + s]), "currents at %d" % s
+    V, ref, t = sim.read_state()
+    assert t == o.t
+    assert np.array_equal(V.view(np.uint32), o.V.view(np.uint32)), "membrane bits"
+    assert np.array_equal(ref, o.ref), "refractory counters"
+    c = sim.read_counts()
+    oc = o.count_dict()
+    for k in c:
+        assert c[k] == oc[k], (k, c[k], oc[k])
+    pairs = np.sort(sim.read_inbox_pairs())
+    assert np.array_equal(pairs, r["pairs"]), "two-level inbox multiset vs direct route"
+    return c, r
+
+
+def test_tiny_full_run(snn):
+    """4,096 neurons, 4 partitions over 2 VNs, 1,000 steps: everything bit-exact."""
+    cfg = synth.TINY
+    g = synth.make_network(cfg)
+    sim, o, rec, _ = _run_pair(snn, g, cfg, cfg.steps, cfg.P, cfg.n_vn, cur_every=50)
+    sim.step(cfg.steps)
+    c, _ = _compare(sim, o, cfg.steps, rec)
+    assert sim.sync_status() == 0
+    assert c["spikes"] > 1000 and c["events"] == c["spikes"] * cfg.K
+    st = o.fp64_stats()
+    assert st["max_rel_err"] <= 1e-5
+
+
+def test_tiny_greedy_partition_and_grouping(snn):
+    """Algorithm 1 + Algorithm 2 mapping: neurons reordered internally, ids stay global."""
+    cfg = synth.TINY
+    g = synth.make_network(cfg)
+    sim, o, rec, rt = _run_pair(snn, g, cfg, 300, cfg.P, cfg.n_vn, "greedy", "greedy")
+    assert rt.info()["identity_order"] == 0
+    sim.step(300)
+    _compare(sim, o, 300, rec)
+
+
+@pytest.mark.parametrize("spg", [1, 7, 32])
+def test_locality_delays_several_tiles(snn, spg):
+    """Locality mix and delays 1..8 over 64 partitions / 16 VNs, several graph unrollings."""
+    cfg = synth.SCALE.scaled(M=1 << 16, seed=41)
+    g = synth.make_network(cfg)
+    sim, o, rec, _ = _run_pair(snn, g, cfg, 150, cfg.P, cfg.n_vn, steps_per_graph=spg)
+    sim.step(150)
+    _compare(sim, o, 150, rec)
+
+
+def test_ragged_sizes_and_uneven_partitions(snn):
+    """M not a multiple of the block size, uneven greedy partitions, 3 VNs of 1."""
+    cfg = synth.NetConfig(name="ragged", M=1000 + 7, P=3, n_vn=3, K=37, uniform_all=True, dmax=4,
+                          seed=99, dyn=synth.Dynamics(drive_lambda=1.1, w_ext=120, drive_seed=9))
+    g = synth.make_network(cfg)
+    sim, o, rec, _ = _run_pair(snn, g, cfg, 200, 3, 3, "greedy", "contiguous")
+    sim.step(200)
+    _compare(sim, o, 200, rec)
+
+
+def test_degenerate_networks(snn):
+    """No synapses at all; one partition and one VN; a silent network."""
+    g = synth.make_edges(300, [], v0=np.linspace(-70, -45, 300).astype(np.float32))
+    cfg = synth.NetConfig(name="iso", M=300, P=1, n_vn=1, K=0, uniform_all=True,
+                          dyn=synth.Dynamics(drive_lambda=0.5, w_ext=200))
+    sim, o, rec, _ = _run_pair(snn, g, cfg, 64, 1, 1)
+    sim.step(64)
+    c, _ = _compare(sim, o, 64, rec)
+    assert c["events"] == 0 and c["spikes"] > 0
+    silent = synth.TINY.scaled(dyn=synth.Dynamics(drive_lambda=0.0))
+    g2 = synth.make_network(silent.scaled(M=512, seed=3))
+    g2.v0[:] = -65.0
+    sim2, o2, rec2, _ = _run_pair(snn, g2, silent, 40, 4, 2)
+    sim2.step(40)
+    c2, _ = _compare(sim2, o2, 40, rec2)
+    assert c2["spikes"] == 0
+
+
+def test_step_in_chunks_equals_one_call(snn):
+    cfg = synth.TINY
+    g = synth.make_network(cfg)
+    sim, o, rec, _ = _run_pair(snn, g, cfg, 200, cfg.P, cfg.n_vn, steps_per_graph=16)
+    for T in (1, 15, 16, 33, 135):
+        sim.step(T)
+    _compare(sim, o, 200, rec)
+
+
+def test_capacity_overflow_is_reported(snn):
+    """Buckets far below their worst case overflow; the status says so, nothing faults."""
+    cfg = synth.TINY
+    g = synth.make_network(cfg)
+    net = snn.Network.from_synth(g)
+    rt = snn.Routing(net, oracle.partition_planted(g.M, 4), 4, 2)
+    prm = snn.sim_params(cfg.dyn, bucket_frac=0.0005, inbox_frac=1.0)
+    sim = snn.Sim(net, rt, prm, device="cuda:0")
+    sim.step(100)
+    assert sim.sync_status() == snn.SNN_E_CAPACITY
+    prm = snn.sim_params(cfg.dyn, bucket_frac=1.0, inbox_frac=0.0005)
+    sim = snn.Sim(net, rt, prm, device="cuda:0")
+    sim.step(100)
+    assert sim.sync_status() == snn.SNN_E_CAPACITY
+    prm = snn.sim_params(cfg.dyn)
+    sim = snn.Sim(net, rt, prm, device="cuda:0")
+    sim.step(100)
+    assert sim.sync_status() == 0
+
+
+def test_checkpoint_resume_bit_exact(snn):
+    cfg = synth.SCALE.scaled(M=1 << 15, seed=17)
+    g = synth.make_network(cfg)
+    net = snn.Network.from_synth(g)
+    rt = snn.Routing(net, oracle.partition_planted(g.M, cfg.P), cfg.P, cfg.n_vn)
+    prm = snn.sim_params(cfg.dyn, hash_steps=400)
+    sim = snn.Sim(net, rt, prm, device="cuda:0")
+    sim.step(150)
+    blob = sim.save_state()
+    sim.step(200)
+    a = sim.read_hashes(150, 350)
+    ca = sim.read_counts()
+    Va, _, _ = sim.read_state()
+    sim.load_state(blob)
+    sim.step(200)
+    b = sim.read_hashes(150, 350)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    Vb, _, t = sim.read_state()
+    assert t == 350 and np.array_equal(Va.view(np.uint32), Vb.view(np.uint32))
+    assert sim.read_counts() == ca
+
+
+def test_reset_replays_identically(snn):
+    cfg = synth.TINY
+    g = synth.make_network(cfg)
+    net = snn.Network.from_synth(g)
+    rt = snn.Routing(net, oracle.partition_planted(g.M, 4), 4, 2)
+    prm = snn.sim_params(cfg.dyn, raster_cap=100000, raster_steps=300, hash_steps=300)
+    sim = snn.Sim(net, rt, prm, device="cuda:0")
+    sim.step(300)
+    a = sim.read_raster(0, 300), sim.read_hashes(0, 300), sim.read_counts()
+    sim.reset(reupload=True)
+    sim.step(300)
+    b = sim.read_raster(0, 300), sim.read_hashes(0, 300), sim.read_counts()
+    assert np.array_equal(a[0][0], b[0][0]) and np.array_equal(a[1][0], b[1][0]) and a[2] == b[2]

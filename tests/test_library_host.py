@@ -1,0 +1,194 @@
+"""CPU tests of the library: the C ABI loads and exports every declared call,
+and the host-side setup (Algorithm 1 partition, Algorithm 2 grouping, relay
+map, routing-table sizes, static connections, argument checks) agrees with
+the oracle's independent readings and with brute force."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def snn():
+    import __graft_entry__
+    __graft_entry__._load_builder().build()
+    import paper_2205_07125_gb300 as m
+    return m
+
+
+def test_library_exports_every_declared_call(snn):
+    hdr = open(os.path.join(ROOT, "include", "snn.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    names = set(re.findall(r"\b(snn_[a-z0-9_]+)\s*\(", hdr))
+    assert len(names) >= 20
+    lib = ctypes.CDLL(snn.library_path())
+    for n in sorted(names):
+        assert hasattr(lib, n), n
+    assert set(snn.EXPORTS) == names
+
+
+def test_strerror_names_codes(snn):
+    for code in range(0, -8, -1):
+        s = snn._lib_strerror(code).decode()
+        assert s and s != "unknown error"
+
+
+@pytest.mark.parametrize("kind", ["cliques", "planted", "uniform"])
+def test_greedy_partition_equals_oracle(snn, kind):
+    if kind == "cliques":
+        edges = [(b + i, b + j, 1, 1) for b in (0, 6, 12) for i in range(6) for j in range(6) if i != j]
+        edges += [(2, 9, 1, 1), (10, 15, 1, 1)]
+        g = synth.make_edges(18, edges)
+        P = 3
+    elif kind == "planted":
+        g = synth.make_network(synth.NetConfig(name="t", M=1536, P=6, n_vn=3, K=20, uniform_all=False,
+                                               n_part=14, n_vn_t=4, n_remote=2, seed=5))
+        P = 6
+    else:
+        g = synth.make_network(synth.NetConfig(name="t", M=700, P=4, n_vn=2, K=9, uniform_all=True,
+                                               seed=8))
+        P = 5
+    net = snn.Network.from_synth(g)
+    for iters, seed in ((1, 3), (4, 11)):
+        mine, st = snn.snn_partition(net, P, "greedy", iters=iters, seed=seed)
+        ref, obj = oracle.partition_greedy(g, P, iters=iters, seed=seed)
+        assert np.array_equal(mine, ref)
+        assert st["objective"] == obj
+
+
+def test_planted_and_random_partitions(snn):
+    g = synth.make_network(synth.NetConfig(name="t", M=1003, P=7, n_vn=7, K=5, uniform_all=True))
+    net = snn.Network.from_synth(g)
+    pl, _ = snn.snn_partition(net, 7, "planted")
+    assert np.array_equal(pl, oracle.partition_planted(1003, 7))
+    rnd, st = snn.snn_partition(net, 7, "random", seed=3)
+    sizes = np.bincount(rnd, minlength=7)
+    assert sizes.max() - sizes.min() <= 1
+    assert not np.array_equal(rnd, pl)
+    assert st["objective"] == oracle.cut(g, rnd)
+
+
+def _brute_tables(g, part, vn):
+    """Distinct destination VNs / partitions per neuron and static connections."""
+    P = int(part.max()) + 1
+    n_vn = int(vn.max()) + 1
+    n_l1 = n_l2 = 0
+    bcap = np.zeros(n_vn, np.int64)
+    icap = np.zeros(P, np.int64)
+    conn = np.zeros((P, P), bool)
+    for i in range(g.M):
+        Q = {int(part[j]) for j in g.tgt[g.syn_ptr[i]:g.syn_ptr[i + 1]]}
+        G = {int(vn[q]) for q in Q}
+        n_l1 += len(G)
+        n_l2 += len(Q)
+        for q in Q:
+            icap[q] += 1
+            conn[part[i], q] = True
+        for x in G:
+            bcap[x] += 1
+    direct = np.zeros(P, np.int64)
+    two = np.zeros(P, np.int64)
+    for p in range(P):
+        qs = [q for q in range(P) if q != p and conn[p, q]]
+        direct[p] = len(qs)
+        two[p] = sum(1 for q in qs if vn[q] == vn[p]) + len({int(vn[q]) for q in qs if vn[q] != vn[p]})
+    return n_l1, n_l2, direct, two
+
+
+@pytest.mark.parametrize("grouping", ["contiguous", "greedy"])
+def test_routing_tables_and_groups(snn, grouping):
+    cfg = synth.NetConfig(name="t", M=2048, P=8, n_vn=4, K=24, uniform_all=False, n_part=12,
+                          n_vn_t=8, n_remote=4, dmax=5, seed=31)
+    g = synth.make_network(cfg)
+    net = snn.Network.from_synth(g)
+    part = oracle.partition_planted(g.M, 8)
+    perm = np.array([5, 2, 7, 0, 3, 6, 1, 4], np.int32)
+    part = perm[part]  # labels not aligned with the planted groups
+    rt = snn.Routing(net, part, 8, 4, grouping, iters=3, seed=9, n_threads=3)
+    vn, relay = rt.groups()
+    if grouping == "greedy":
+        ovn, ocost = oracle.group_greedy(g, part, 8, 4, iters=3, seed=9)
+        assert np.array_equal(vn, ovn)
+        assert rt.info()["group_cost"] == ocost
+    else:
+        assert np.array_equal(vn, oracle.group_contiguous(8, 4))
+    # relay: (h mod s)-th member of group g in ascending label order
+    s = 2
+    for gg in range(4):
+        members = sorted(q for q in range(8) if vn[q] == gg)
+        for h in range(4):
+            assert relay[gg, h] == members[h % s]
+    info = rt.info()
+    n_l1, n_l2, direct, two = _brute_tables(g, part, vn)
+    assert info["n_l1"] == n_l1 and info["n_l2"] == n_l2
+    assert info["max_delay"] == 5 and info["n_synapses"] == g.E
+    cd, ct = rt.connections()
+    assert np.array_equal(cd, direct) and np.array_equal(ct, two)
+    assert info["conn_direct_sum"] == direct.sum() and info["conn_two_level_sum"] == two.sum()
+    assert info["identity_order"] == 0  # relabelled partitions reorder the neurons
+
+
+def test_routing_thread_count_does_not_change_tables(snn):
+    cfg = synth.NetConfig(name="t", M=3000, P=6, n_vn=2, K=15, uniform_all=False, n_part=9,
+                          n_vn_t=4, n_remote=2, dmax=3, seed=4)
+    g = synth.make_network(cfg)
+    net = snn.Network.from_synth(g)
+    part = oracle.partition_planted(g.M, 6)
+    a = snn.Routing(net, part, 6, 2, "greedy", n_threads=1).info()
+    b = snn.Routing(net, part, 6, 2, "greedy", n_threads=5).info()
+    assert a == b
+
+
+def test_argument_errors(snn):
+    g = synth.make_network(synth.NetConfig(name="t", M=64, P=4, n_vn=2, K=4, uniform_all=True, dmax=2))
+    net = snn.Network.from_synth(g)
+    part = oracle.partition_planted(64, 4)
+    with pytest.raises(snn.SnnError) as e:
+        snn.Routing(net, part, 4, 3)          # 4 % 3 != 0
+    assert e.value.code == -1
+    bad = part.copy()
+    bad[5] = 9
+    with pytest.raises(snn.SnnError):
+        snn.Routing(net, bad, 4, 2)
+    d = g.d.copy()
+    d[3] = 0
+    with pytest.raises(snn.SnnError) as e:
+        snn.Routing(snn.Network(g.syn_ptr, g.tgt, g.w, d, g.v0), part, 4, 2)
+    assert e.value.code == -5
+    d[3] = 17
+    with pytest.raises(snn.SnnError) as e:
+        snn.Routing(snn.Network(g.syn_ptr, g.tgt, g.w, d, g.v0), part, 4, 2)
+    assert e.value.code == -5
+    empty = part.copy()
+    empty[empty == 2] = 1
+    with pytest.raises(snn.SnnError):
+        snn.Routing(net, empty, 4, 2)         # partition 2 empty
+    with pytest.raises(snn.SnnError):
+        snn.snn_partition(net, 0, "planted")
+
+
+def test_workspace_size_and_no_device(snn):
+    g = synth.make_network(synth.TINY)
+    net = snn.Network.from_synth(g)
+    rt = snn.Routing(net, oracle.partition_planted(g.M, 4), 4, 2)
+    p = snn.sim_params(synth.TINY.dyn)
+    nb = ctypes.c_size_t(0)
+    assert snn._lib.snn_sim_workspace_bytes(rt.h, ctypes.byref(p), ctypes.byref(nb)) == 0
+    # synapse arrays (6 B/synapse) dominate the tiny workspace
+    assert nb.value >= g.E * 6 and nb.value % 256 == 0
+    p.steps_per_graph = 0
+    assert snn._lib.snn_sim_workspace_bytes(rt.h, ctypes.byref(p), ctypes.byref(nb)) == -1
+    import torch
+    if not torch.cuda.is_available():
+        p = snn.sim_params(synth.TINY.dyn)
+        h = ctypes.c_void_p()
+        rc = snn._lib.snn_sim_create(ctypes.byref(net.s), rt.h, ctypes.byref(p),
+                                     ctypes.c_void_p(1 << 20), nb.value, None, ctypes.byref(h))
+        assert rc == -7 and not h.value
