@@ -177,6 +177,8 @@ def run_ours(args):
                          pin_host_tables=1)
     sim = snn.Sim(net, rt, prm, device=dev)
     setup_s = time.time() - t_setup
+    print("[bench] setup %.1f s (generate + partition + routing + upload)" % setup_s,
+          file=sys.stderr, flush=True)
     stream = sim.stream
 
     # warm-up, then EXACTLY K timed steps from graph replays
@@ -223,6 +225,8 @@ def run_ours(args):
         phases[n] = {"kernel": kn, "ms_per_step": t_ms / NP, "bytes_per_step": b / NP,
                      "gbs": (b / (t_ms * 1e-3) / 1e9) if t_ms > 0 else None,
                      "share": t_ms / max(1e-12, sum(phase_ms))}
+    print("[bench] timed %.3f ms for %d steps; phases ms/step %s" % (
+        ms, K, [round(x / NP, 5) for x in phase_ms]), file=sys.stderr, flush=True)
     dom = max(phases, key=lambda n: phases[n]["ms_per_step"])
     peak, peak_kind = _peaks()
     traffic = load_traffic(phases[dom]["kernel"])

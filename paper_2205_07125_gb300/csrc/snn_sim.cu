@@ -749,13 +749,16 @@ extern "C" int snn_profile_phases(snn_sim *s, int32_t T, double *phase_ms)
         CK(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
         cudaError_t le = cudaSuccess;
         for (int k = 0; k < U && le == cudaSuccess; ++k) {
+            // cudaEventRecordExternal: a real event-record node in the graph
+            // (a plain record inside a capture only orders streams)
             cudaEvent_t *ev = &s->pev[(size_t)k * 5];
             cudaStream_t st = s->cap_stream;
-            le = cudaEventRecord(ev[0], st);
-            if (le == cudaSuccess) { k_update<<<s->grid_update, kThreads, 0, st>>>(s->dev); le = cudaEventRecord(ev[1], st); }
-            if (le == cudaSuccess) { k_level1<<<s->grid_route, kThreads, 0, st>>>(s->dev); le = cudaEventRecord(ev[2], st); }
-            if (le == cudaSuccess) { k_level2<<<s->grid_route, kThreads, 0, st>>>(s->dev); le = cudaEventRecord(ev[3], st); }
-            if (le == cudaSuccess) { k_deliver<<<s->grid_route, kThreads, 0, st>>>(s->dev); le = cudaEventRecord(ev[4], st); }
+            const unsigned fl = cudaEventRecordExternal;
+            le = cudaEventRecordWithFlags(ev[0], st, fl);
+            if (le == cudaSuccess) { k_update<<<s->grid_update, kThreads, 0, st>>>(s->dev); le = cudaEventRecordWithFlags(ev[1], st, fl); }
+            if (le == cudaSuccess) { k_level1<<<s->grid_route, kThreads, 0, st>>>(s->dev); le = cudaEventRecordWithFlags(ev[2], st, fl); }
+            if (le == cudaSuccess) { k_level2<<<s->grid_route, kThreads, 0, st>>>(s->dev); le = cudaEventRecordWithFlags(ev[3], st, fl); }
+            if (le == cudaSuccess) { k_deliver<<<s->grid_route, kThreads, 0, st>>>(s->dev); le = cudaEventRecordWithFlags(ev[4], st, fl); }
             if (le == cudaSuccess) le = cudaGetLastError();
         }
         cudaError_t ce = cudaStreamEndCapture(s->cap_stream, &g);

@@ -1,0 +1,76 @@
+"""Multi-rank host logic of bench.py on CPU: two gloo ranks, replicas with
+summed work and the maximum time over ranks (no data-path collective)."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), SNN_BENCH_BACKEND="gloo")
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    dist, r, w = bench.dist_init()
+    assert (r, w) == (rank, world)
+    bench.barrier(dist)
+    ev, ms, extra = bench.reduce_over_ranks(dist, events=1000.0 * (rank + 1), ms=10.0 + rank,
+                                            extra=rank + 0.5)
+    q.put((rank, ev, ms, extra))
+    dist.destroy_process_group()
+
+
+def test_two_rank_aggregation():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in ps:
+        p.start()
+    for p in ps:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    got = sorted(q.get(timeout=10) for _ in range(2))
+    for rank, ev, ms, extra in got:
+        assert ev == 3000.0 and ms == 11.0 and extra == 2.0
+
+
+def test_single_rank_passthrough():
+    import bench
+    assert bench.reduce_over_ranks(None, 5.0, 2.0, 1.0) == (5.0, 2.0, 1.0)
+
+
+def test_phase_bytes_formula():
+    import bench
+    d = dict(spikes=10, l1_local=10, l1_xvn=20, l2_local=10, l2_peer=30, l2_relay_local=5,
+             l2_relay_remote=15, events=10000)
+    b = bench.phase_bytes(M=100, d_steps=2, d=d, gid=False)
+    assert b[0] == 18 * 100 * 2 + 40
+    assert b[1] == 12 * 10 + 6 * 30
+    assert b[2] == 12 * 30 + 24 * 60
+    assert b[3] == 8 * 60 + 6 * 10000
+
+
+def test_reference_arm_ranks_other_than_zero_exit_quietly(capsys, monkeypatch):
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    bench.main(["--impl", "reference"])
+    assert capsys.readouterr().out == ""
+
+
+@pytest.mark.parametrize("argv", [["--warmup", "2"]])
+def test_bench_rejects_short_warmup(argv):
+    import bench
+    with pytest.raises(SystemExit):
+        bench.main(argv)
