@@ -284,6 +284,29 @@ int64_t snn_launches_per_step(const snn_sim *sim);
  */
 int snn_profile_phases(snn_sim *sim, int32_t T, double *phase_ms);
 
+/*
+ * Route a caller-given set of spikes through the two-level route (level-1
+ * entries per destination VN, level-2 relay expansion into partition
+ * segments, Sec. IV.B) and fan them out:
+ *     out[(d-1)*M + j] += sum of w over synapses i -> j with delay d,
+ * summed over the listed source neurons i (global ids; a repeated id is
+ * delivered once per occurrence).  Use: external stimulation, or the
+ * synaptic input a spike pattern produces, without advancing the sim.
+ *   ids: device uint32 [n]; out: device int32 [max_delay * M], global
+ *   neuron order, accumulated into (the call does not clear it); both
+ *   caller-owned.  counts (host uint64 [3], may be NULL) receives the
+ *   level-1 entries, level-2 entries and synaptic events of this call.
+ * Scratch: the level-1 bucket and level-2 inbox regions of the sim's
+ * workspace, so the call must not overlap snn_step on the same sim.
+ * Runs on the sim's stream and synchronises it before returning.
+ * Errors: SNN_E_ARG (n < 0, NULL pointers with n > 0, an id >= M),
+ * SNN_E_CAPACITY (the spikes need more bucket/inbox room than the
+ * workspace holds), SNN_E_CUDA.
+ */
+int snn_deliver_spikes(snn_sim *sim, const uint32_t *ids, int64_t n, int32_t *out,
+                       uint64_t *counts);
+
+
 void snn_sim_destroy(snn_sim *sim);
 
 #ifdef __cplusplus

@@ -115,6 +115,7 @@ _sig("snn_load_state", ctypes.c_int, [_vp, _vp, ctypes.c_size_t])
 _sig("snn_sim_reset", ctypes.c_int, [_vp, _i32])
 _sig("snn_launches_per_step", _i64, [_vp])
 _sig("snn_profile_phases", ctypes.c_int, [_vp, _i32, _vp])
+_sig("snn_deliver_spikes", ctypes.c_int, [_vp, _vp, _i64, _vp, _vp])
 _sig("snn_sim_destroy", None, [_vp])
 
 EXPORTS = ("snn_strerror", "snn_partition", "snn_routing_build", "snn_routing_info_get",
@@ -123,7 +124,7 @@ EXPORTS = ("snn_strerror", "snn_partition", "snn_routing_build", "snn_routing_in
            "snn_sync_status", "snn_read_raster", "snn_read_currents", "snn_read_hashes",
            "snn_read_counts", "snn_read_state", "snn_read_inbox_pairs", "snn_state_bytes",
            "snn_save_state", "snn_load_state", "snn_sim_reset", "snn_launches_per_step",
-           "snn_profile_phases", "snn_sim_destroy")
+           "snn_profile_phases", "snn_deliver_spikes", "snn_sim_destroy")
 
 
 class SnnError(RuntimeError):
@@ -344,6 +345,19 @@ class Sim:
         with self._dev():
             _ck(_lib.snn_profile_phases(self.h, int(T), out.ctypes.data), "snn_profile_phases")
         return out
+
+    def deliver_spikes(self, ids, out):
+        """Route and fan out global spike ids (a torch int32/uint32-compatible CUDA
+        tensor of int32) into out (CUDA int32 tensor [max_delay, M], accumulated).
+        Returns (level-1 entries, level-2 entries, events)."""
+        import torch
+        assert ids.is_cuda and out.is_cuda and out.dtype == torch.int32 and ids.dtype == torch.int32
+        assert ids.is_contiguous() and out.is_contiguous()
+        c = np.zeros(3, np.uint64)
+        with self._dev():
+            _ck(_lib.snn_deliver_spikes(self.h, ids.data_ptr(), ids.numel(), out.data_ptr(),
+                                        c.ctypes.data), "snn_deliver_spikes")
+        return tuple(int(x) for x in c)
 
     @property
     def launches_per_step(self) -> int:

@@ -363,6 +363,91 @@ __global__ void __launch_bounds__(kThreads) k_deliver(const Dev d)
     if (threadIdx.x == 0 && s_ev) atomicAdd(&d.counters[C_EVENTS], s_ev);
 }
 
+// ---------------------------------------------------------------- spike fan-out
+// Route and fan out a caller-given spike list (snn_deliver_spikes): the same
+// level-1 -> level-2 -> segment path as a step, with flat scratch lists and
+// the result accumulated into a caller buffer out[d-1][global id].
+struct FoArgs {
+    const uint32_t *ids;
+    long long n;
+    const uint32_t *fwd;  // global -> internal (nullptr when identical)
+    const uint32_t *gid;  // internal -> global (nullptr when identical)
+    const uint32_t *l1_ptr;
+    const uint32_t *l1_l2;
+    const DevL2 *l2;
+    const uint32_t *syn_td;
+    const int16_t *syn_w;
+    uint32_t *bucket;              // scratch: level-1 entry ids
+    unsigned long long cap1;
+    unsigned long long *inbox;     // scratch: packed segments
+    unsigned long long cap2;
+    unsigned int *cnt;             // scratch: [0] bucket fill, [1] inbox fill, [2] status
+    unsigned long long *ev;        // scratch: events delivered
+    int32_t *out;
+    long long M;
+};
+
+constexpr unsigned int kFoStBucket = 1u, kFoStInbox = 2u, kFoStId = 4u;
+
+__global__ void __launch_bounds__(kThreads) k_fo_level1(const FoArgs a)
+{
+    unsigned int st = 0;
+    for (long long s = (long long)blockIdx.x * kThreads + threadIdx.x; s < a.n;
+         s += (long long)gridDim.x * kThreads) {
+        const uint32_t g = a.ids[s];
+        if ((long long)g >= a.M) {
+            st |= kFoStId;
+            continue;
+        }
+        const uint32_t i = a.fwd ? a.fwd[g] : g;
+        for (uint32_t e = a.l1_ptr[i]; e < a.l1_ptr[i + 1]; ++e) {
+            const unsigned int pos = atomicAdd(&a.cnt[0], 1u);
+            if (pos < a.cap1) a.bucket[pos] = e;
+            else st |= kFoStBucket;
+        }
+    }
+    if (st) atomicOr(&a.cnt[2], st);
+}
+
+__global__ void __launch_bounds__(kThreads) k_fo_level2(const FoArgs a)
+{
+    unsigned int st = 0;
+    const unsigned long long n1 = min((unsigned long long)a.cnt[0], a.cap1);
+    for (unsigned long long x = (unsigned long long)blockIdx.x * kThreads + threadIdx.x; x < n1;
+         x += (unsigned long long)gridDim.x * kThreads) {
+        const uint32_t e = a.bucket[x];
+        for (uint32_t f = a.l1_l2[e]; f < a.l1_l2[e + 1]; ++f) {
+            const DevL2 l = a.l2[f];
+            const unsigned int pos = atomicAdd(&a.cnt[1], 1u);
+            if (pos < a.cap2) a.inbox[pos] = (l.off << kLenBits) | (unsigned long long)l.len;
+            else st |= kFoStInbox;
+        }
+    }
+    if (st) atomicOr(&a.cnt[2], st);
+}
+
+__global__ void __launch_bounds__(kThreads) k_fo_deliver(const FoArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned long long n2 = min((unsigned long long)a.cnt[1], a.cap2);
+    const unsigned long long nw = ((unsigned long long)gridDim.x * kThreads) >> 5;
+    unsigned long long ev = 0;
+    for (unsigned long long x = ((unsigned long long)blockIdx.x * kThreads + threadIdx.x) >> 5; x < n2;
+         x += nw) {
+        const unsigned long long ent = a.inbox[x];
+        const unsigned long long off = ent >> kLenBits;
+        const unsigned int len = (unsigned int)(ent & kLenMask);
+        for (unsigned int l = lane; l < len; l += 32) {
+            const uint32_t td = a.syn_td[off + l];
+            const uint32_t tgt = td & kTgtMask;
+            const long long j = a.gid ? (long long)a.gid[tgt] : (long long)tgt;
+            atomicAdd(&a.out[(long long)(td >> kTgtBits) * a.M + j], (int32_t)a.syn_w[off + l]);
+        }
+        ev += len;
+    }
+    if (lane == 0 && ev) atomicAdd(a.ev, ev);
+}
+
 // ---------------------------------------------------------------- host helpers
 struct Region {
     size_t off = 0, bytes = 0;
@@ -372,6 +457,7 @@ struct Layout {
     Region V, ref, ring, gid, src_vn, syn_td, syn_w, l1_ptr, l1_vn, l1_l2, l2;
     Region bucket, bucket_base, bucket_capv, bucket_cnt, inbox, inbox_base, inbox_capv, inbox_cnt;
     Region spk, raster_off, hash, cur_rec, counters, ctrl;
+    Region fwd, fo_cnt;  // snn_deliver_spikes: global -> internal map, scratch counters
     size_t total = 0;
     std::vector<uint64_t> bucket_base_h, inbox_base_h;
     std::vector<uint32_t> bucket_cap_h, inbox_cap_h;
@@ -442,6 +528,8 @@ static int make_layout(const snn_routing *rt, const snn_sim_params *p, Layout &L
     place(L, L.raster_off, sizeof(long long) * (size_t)(p->raster_steps + 1));
     place(L, L.hash, sizeof(unsigned long long) * 2 * (size_t)p->hash_steps);
     place(L, L.cur_rec, sizeof(int32_t) * (size_t)M * (size_t)p->cur_slots);
+    place(L, L.fwd, rt->identity ? 0 : sizeof(uint32_t) * (size_t)M);
+    place(L, L.fo_cnt, 64);
     return SNN_OK;
 }
 
@@ -553,6 +641,7 @@ static int upload_tables(snn_sim *s)
     CK(up(L.l2, rt->l2.data()));
     CK(up(L.src_vn, rt->src_vn.data()));
     if (!rt->identity) CK(up(L.gid, rt->perm_inv.data()));
+    if (!rt->identity) CK(up(L.fwd, rt->perm_fwd.data()));
     CK(up(L.bucket_base, L.bucket_base_h.data()));
     CK(up(L.bucket_capv, L.bucket_cap_h.data()));
     CK(up(L.inbox_base, L.inbox_base_h.data()));
@@ -792,6 +881,69 @@ extern "C" int snn_profile_phases(snn_sim *s, int32_t T, double *phase_ms)
         }
     }
     return SNN_OK;
+}
+
+// Fill the table pointers of a fan-out from the sim's device view.
+static FoArgs fanout_tables(const snn_sim *s, const uint32_t *ids, int64_t n, int32_t *out)
+{
+    FoArgs a;
+    std::memset(&a, 0, sizeof(a));
+    const Dev &d = s->dev;
+    a.ids = ids;
+    a.n = n;
+    a.fwd = s->rt->identity ? nullptr : (const uint32_t *)(s->ws + s->L.fwd.off);
+    a.gid = d.gid;
+    a.l1_ptr = d.l1_ptr;
+    a.l1_l2 = d.l1_l2;
+    a.l2 = d.l2;
+    a.syn_td = d.syn_td;
+    a.syn_w = d.syn_w;
+    a.out = out;
+    a.M = d.M;
+    return a;
+}
+
+// Clear the scratch counters, run the three fan-out kernels on the sim's
+// stream, wait, and map the scratch status to an error code.
+static int run_fanout(snn_sim *s, const FoArgs &a, uint64_t *counts)
+{
+    cudaStream_t st = s->stream;
+    CK(cudaMemsetAsync(a.cnt, 0, 4 * sizeof(unsigned int), st));
+    CK(cudaMemsetAsync(a.ev, 0, sizeof(unsigned long long), st));
+    if (a.n > 0) {
+        const unsigned g = s->grid_route;
+        k_fo_level1<<<g, kThreads, 0, st>>>(a);
+        k_fo_level2<<<g, kThreads, 0, st>>>(a);
+        k_fo_deliver<<<g, kThreads, 0, st>>>(a);
+        CK(cudaGetLastError());
+    }
+    unsigned int c[4];
+    unsigned long long ev = 0;
+    CK(cudaMemcpyAsync(c, a.cnt, sizeof(c), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&ev, a.ev, sizeof(ev), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (counts) {
+        counts[0] = c[0];
+        counts[1] = c[1];
+        counts[2] = ev;
+    }
+    if (c[2] & kFoStId) return SNN_E_ARG;
+    if (c[2] & (kFoStBucket | kFoStInbox)) return SNN_E_CAPACITY;
+    return SNN_OK;
+}
+
+extern "C" int snn_deliver_spikes(snn_sim *s, const uint32_t *ids, int64_t n, int32_t *out,
+                                  uint64_t *counts)
+{
+    if (!s || n < 0 || (n > 0 && (!ids || !out))) return SNN_E_ARG;
+    FoArgs a = fanout_tables(s, ids, n, out);
+    a.bucket = s->dev.bucket;
+    a.cap1 = s->L.bucket.bytes / sizeof(uint32_t);
+    a.inbox = s->dev.inbox;
+    a.cap2 = s->L.inbox.bytes / sizeof(unsigned long long);
+    a.cnt = (unsigned int *)(s->ws + s->L.fo_cnt.off);
+    a.ev = (unsigned long long *)(s->ws + s->L.fo_cnt.off + 16);
+    return run_fanout(s, a, counts);
 }
 
 extern "C" int64_t snn_launches_per_step(const snn_sim *s)
