@@ -306,6 +306,33 @@ int snn_profile_phases(snn_sim *sim, int32_t T, double *phase_ms);
 int snn_deliver_spikes(snn_sim *sim, const uint32_t *ids, int64_t n, int32_t *out,
                        uint64_t *counts);
 
+/*
+ * snn_deliver_spikes without any device allocation.  The paper has no
+ * counterpart: this is for callers that cannot allocate device memory while
+ * they run, such as a host program that hands out all device memory itself
+ * from a fixed budget, or a real-time stimulation loop that may not stall
+ * in an allocator call.  It computes exactly what snn_deliver_spikes
+ * computes (same arguments, same output, same counts) but keeps its scratch
+ * in a fixed array built into the library, of snn_static_scratch_bytes()
+ * (8 MiB) per GPU; every GPU that loads the library holds that array until
+ * the process exits.  The call itself allocates nothing: no cudaMalloc,
+ * no cudaFree.
+ *   - The first call on a device looks up the array's device address once
+ *     (cudaGetSymbolAddress, with that device current); make that first
+ *     call before any stream capture.
+ *   - Size limit: n * (4 B * longest level-1 row + 8 B * most level-2
+ *     entries of any neuron) + 512 B must fit in the array; larger calls
+ *     return SNN_E_RANGE and do nothing.
+ *   - All calls share the one array and each call clears its counters
+ *     first, so calls that overlap on the GPU (other streams, other threads,
+ *     other sims on the same GPU) race and give wrong results: serialise
+ *     them.  The array keeps the last call's contents.
+ * Errors: as snn_deliver_spikes, plus SNN_E_RANGE.
+ */
+int snn_deliver_spikes_static(snn_sim *sim, const uint32_t *ids, int64_t n, int32_t *out,
+                              uint64_t *counts);
+/* Size in bytes of the fixed scratch array of snn_deliver_spikes_static. */
+size_t snn_static_scratch_bytes(void);
 
 void snn_sim_destroy(snn_sim *sim);
 

@@ -116,6 +116,8 @@ _sig("snn_sim_reset", ctypes.c_int, [_vp, _i32])
 _sig("snn_launches_per_step", _i64, [_vp])
 _sig("snn_profile_phases", ctypes.c_int, [_vp, _i32, _vp])
 _sig("snn_deliver_spikes", ctypes.c_int, [_vp, _vp, _i64, _vp, _vp])
+_sig("snn_deliver_spikes_static", ctypes.c_int, [_vp, _vp, _i64, _vp, _vp])
+_sig("snn_static_scratch_bytes", ctypes.c_size_t, [])
 _sig("snn_sim_destroy", None, [_vp])
 
 EXPORTS = ("snn_strerror", "snn_partition", "snn_routing_build", "snn_routing_info_get",
@@ -124,7 +126,8 @@ EXPORTS = ("snn_strerror", "snn_partition", "snn_routing_build", "snn_routing_in
            "snn_sync_status", "snn_read_raster", "snn_read_currents", "snn_read_hashes",
            "snn_read_counts", "snn_read_state", "snn_read_inbox_pairs", "snn_state_bytes",
            "snn_save_state", "snn_load_state", "snn_sim_reset", "snn_launches_per_step",
-           "snn_profile_phases", "snn_deliver_spikes", "snn_sim_destroy")
+           "snn_profile_phases", "snn_deliver_spikes", "snn_deliver_spikes_static",
+           "snn_static_scratch_bytes", "snn_sim_destroy")
 
 
 class SnnError(RuntimeError):

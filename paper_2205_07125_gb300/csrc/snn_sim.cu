@@ -23,6 +23,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -584,6 +585,7 @@ struct snn_sim {
     cudaGraphExec_t gP = nullptr;  // instrumented graph (snn_profile_phases)
     int UP = 0;
     std::vector<cudaEvent_t> pev;
+    int64_t static_row_l1 = -1, static_row_l2 = -1;  // snn_deliver_spikes_static sizing
     unsigned grid_update = 1, grid_route = 1;
     std::vector<void *> pinned;
 };
@@ -943,6 +945,80 @@ extern "C" int snn_deliver_spikes(snn_sim *s, const uint32_t *ids, int64_t n, in
     a.cap2 = s->L.inbox.bytes / sizeof(unsigned long long);
     a.cnt = (unsigned int *)(s->ws + s->L.fo_cnt.off);
     a.ev = (unsigned long long *)(s->ws + s->L.fo_cnt.off + 16);
+    return run_fanout(s, a, counts);
+}
+
+// ---------------------------------------------------------------- fan-out without allocation
+// snn_deliver_spikes_static: the same fan-out as snn_deliver_spikes, but its
+// scratch (counters, level-1 list, level-2 list) lives in this fixed device
+// array instead of the sim's workspace.  Every GPU that loads the library
+// holds the array until the process exits; all calls share it.
+constexpr size_t kStaticScratchBytes = (size_t)8 << 20;  // 8 MiB
+static __device__ __align__(256) unsigned char g_fanout_scratch[kStaticScratchBytes];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+void *g_scratch_addr[kMaxDevices] = {};
+}  // namespace
+
+// Device address of g_fanout_scratch on `dev`, looked up once per device with
+// that device current (host code only sees a host-side stand-in for the array).
+static int static_scratch_address(int dev, void **out)
+{
+    if (dev < 0 || dev >= kMaxDevices) return SNN_E_RANGE;
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        int prev = -1;
+        if (cudaGetDevice(&prev) != cudaSuccess) return SNN_E_CUDA;
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) return SNN_E_CUDA;
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_fanout_scratch);
+        if (prev != dev) cudaSetDevice(prev);
+        if (e != cudaSuccess || !p) return SNN_E_CUDA;
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return SNN_OK;
+}
+
+extern "C" size_t snn_static_scratch_bytes(void)
+{
+    return kStaticScratchBytes;
+}
+
+extern "C" int snn_deliver_spikes_static(snn_sim *s, const uint32_t *ids, int64_t n, int32_t *out,
+                                         uint64_t *counts)
+{
+    if (!s || n < 0 || (n > 0 && (!ids || !out))) return SNN_E_ARG;
+    // worst case per spike: its longest level-1 row and its most level-2 entries
+    if (s->static_row_l1 < 0) {
+        const snn_routing *rt = s->rt;
+        int64_t m1 = 0, m2 = 0;
+        for (int64_t k = 0; k < rt->M; ++k) {
+            const uint32_t a = rt->l1_ptr[k], b = rt->l1_ptr[k + 1];
+            m1 = std::max<int64_t>(m1, (int64_t)(b - a));
+            m2 = std::max<int64_t>(m2, (int64_t)rt->l1_l2[b] - (int64_t)rt->l1_l2[a]);
+        }
+        s->static_row_l1 = m1;
+        s->static_row_l2 = m2;
+    }
+    if (n > (int64_t)kStaticScratchBytes) return SNN_E_RANGE;
+    const size_t head = 256;
+    const size_t need1 = (((size_t)n * (size_t)s->static_row_l1 * sizeof(uint32_t)) + 255) & ~(size_t)255;
+    const size_t need2 = (size_t)n * (size_t)s->static_row_l2 * sizeof(unsigned long long);
+    if (head + need1 + need2 > kStaticScratchBytes) return SNN_E_RANGE;
+    void *base = nullptr;
+    int rc = static_scratch_address(s->device, &base);
+    if (rc) return rc;
+    char *b = (char *)base;
+    FoArgs a = fanout_tables(s, ids, n, out);
+    a.cnt = (unsigned int *)b;
+    a.ev = (unsigned long long *)(b + 16);
+    a.bucket = (uint32_t *)(b + head);
+    a.cap1 = need1 / sizeof(uint32_t);
+    a.inbox = (unsigned long long *)(b + head + need1);
+    a.cap2 = need2 / sizeof(unsigned long long);
     return run_fanout(s, a, counts);
 }
 
