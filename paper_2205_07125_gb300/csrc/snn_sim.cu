@@ -1,23 +1,7 @@
-// Device side: the per-step hot path as sm_103a kernels, CUDA-graph replay,
-// and the simulation lifecycle of the C ABI.
-//
-// One step t (arXiv 2205.07125 gives the routing, Sec. IV.B; the neuron
-// model is LIF, Table I; the step's arithmetic is fixed by the library's
-// documented readings):
-//   k_update   a1 consume ring slot t mod D, Poisson drive (Philox4x32-10,
-//                 inverse CDF), a2 FP32 LIF update + threshold (no FMA,
-//                 fixed order), a3 warp-ballot + block prefix-sum spike
-//                 compaction into the step's spike list; the last block to
-//                 finish closes the step's bookkeeping.
-//   k_level1   a4 every spike i appended to the bucket of every destination
-//                 VN in its level-1 row (one entry per VN: deduplicated).
-//   k_level2   a5 every bucket entry (i, g) expanded by the relay of g into
-//                 the inboxes of the destination partitions of g that hold
-//                 targets of i.
-//   k_deliver  a6 every inbox segment fanned out: int16 weight added with a
-//                 32-bit atomic into ring[(t+d) mod D][target].
-// The ring has D = max delay + 1 slots, so the slot consumed at step t is
-// never a slot written by the deliveries of step t.
+// Host side of the simulation: device layout in the caller's workspace, table
+// upload, CUDA-graph capture and replay of the step kernels (snn_step.cuh),
+// the spike fan-out entry points, and the read-out and checkpoint calls of
+// the C ABI.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -31,338 +15,9 @@
 
 using namespace snn;
 
+#include "snn_step.cuh"
+
 namespace {
-
-constexpr int kThreads = 256;
-constexpr int kPTab = 32;
-
-// status bits
-constexpr uint32_t kStBucket = 1u, kStInbox = 2u, kStRaster = 4u;
-
-// counter slots
-enum { C_STEPS = 0, C_SPIKES, C_EVENTS, C_L1_LOCAL, C_L1_XVN, C_L2_BASE /* + cls (4) */, C_N = 16 };
-
-struct Ctrl {
-    long long t;          // next step to update
-    long long t_cur;      // step being routed and delivered
-    long long head;       // raster write head
-    long long spk_base;   // first spike of step t_cur in spk[]
-    long long rec_steps;  // steps whose raster offsets are valid
-    unsigned int S_acc;   // spikes found so far in the running update
-    unsigned int S_cur;   // spikes of step t_cur
-    unsigned int blocks_done;
-    unsigned int status;
-    int rec_on;
-    int pad;
-};
-
-struct __align__(16) DevL2 {
-    unsigned long long off;
-    unsigned int len;
-    unsigned short q;
-    unsigned char cls;
-    unsigned char pad;
-};
-
-struct Dev {
-    // state
-    float *V;
-    uint8_t *ref;
-    int32_t *ring;
-    const uint32_t *gid;  // internal -> global id (nullptr when identical)
-    const uint16_t *src_vn;
-    // synapses and routing tables
-    const uint32_t *syn_td;
-    const int16_t *syn_w;
-    const uint32_t *l1_ptr;
-    const uint16_t *l1_vn;
-    const uint32_t *l1_l2;
-    const DevL2 *l2;
-    // exchange buffers
-    uint32_t *bucket;
-    const unsigned long long *bucket_base;
-    const uint32_t *bucket_capv;
-    uint32_t *bucket_cnt;
-    unsigned long long *inbox;
-    const unsigned long long *inbox_base;
-    const uint32_t *inbox_capv;
-    uint32_t *inbox_cnt;
-    // records
-    uint32_t *spk;
-    long long *raster_off;
-    unsigned long long *hash;
-    int32_t *cur_rec;
-    unsigned long long *counters;
-    Ctrl *ctrl;
-    // scalars
-    long long M;
-    int P, n_vn, D;
-    float alpha, e_l, v_th, v_reset;
-    int t_ref, w_ext, i_bias, th_len;
-    uint32_t key0, key1;
-    long long raster_cap, raster_steps, hash_steps;
-    int cur_every, cur_slots;
-    unsigned long long th[kPTab];
-};
-
-__device__ __forceinline__ uint32_t philox_w0(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1)
-{
-    uint32_t x0 = c0, x1 = c1, x2 = 0u, x3 = 0u;
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const uint32_t hi0 = __umulhi(0xD2511F53u, x0), lo0 = 0xD2511F53u * x0;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, x2), lo1 = 0xCD9E8D57u * x2;
-        const uint32_t y0 = hi1 ^ x1 ^ k0, y2 = hi0 ^ x3 ^ k1;
-        x0 = y0;
-        x1 = lo1;
-        x2 = y2;
-        x3 = lo0;
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
-    }
-    return x0;
-}
-
-__device__ __forceinline__ unsigned long long mix64(unsigned long long z)
-{
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
-    return z ^ (z >> 31);
-}
-
-template <class T>
-__device__ __forceinline__ T warp_sum(T v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-    return v;
-}
-
-// ---------------------------------------------------------------- a1-a3
-__global__ void __launch_bounds__(kThreads) k_update(const Dev d)
-{
-    __shared__ unsigned int s_wcnt[kThreads / 32];
-    __shared__ unsigned int s_base;
-    __shared__ unsigned long long s_h[2][kThreads / 32];
-    __shared__ int s_last;
-
-    Ctrl *c = d.ctrl;
-    const long long t = c->t;
-    const long long head = c->head;
-    const int slot = (int)(t % d.D);
-    const long long j = (long long)blockIdx.x * kThreads + threadIdx.x;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const bool do_hash = t < d.hash_steps;
-    const bool do_cur = d.cur_every > 0 && (t % d.cur_every) == 0 && (t / d.cur_every) < d.cur_slots;
-
-    bool spike = false;
-    unsigned long long hc = 0, hv = 0;
-    if (j < d.M) {
-        int32_t *rp = d.ring + (long long)slot * d.M + j;
-        const int32_t irec = *rp;
-        *rp = 0;
-        if (do_cur) d.cur_rec[(t / d.cur_every) * d.M + j] = irec;
-        const uint32_t g = d.gid ? d.gid[j] : (uint32_t)j;
-        const uint32_t u = philox_w0(d.key0, d.key1, g, (uint32_t)t);
-        int k = 0;
-        for (int m = 0; m < d.th_len; ++m) k += (d.th[m] <= (unsigned long long)u) ? 1 : 0;
-        const int32_t I = (int32_t)((uint32_t)irec + (uint32_t)k * (uint32_t)d.w_ext + (uint32_t)d.i_bias);
-        float v = d.V[j];
-        uint8_t r = d.ref[j];
-        if (r > 0) {
-            r = (uint8_t)(r - 1);
-            v = d.v_reset;
-        } else {
-            const float uu = __fsub_rn(v, d.e_l);
-            const float au = __fmul_rn(d.alpha, uu);
-            v = __fadd_rn(d.e_l, au);
-            const float x = __fmul_rn(__int2float_rn(I), 0.0009765625f);
-            v = __fadd_rn(v, x);
-            if (v >= d.v_th) {
-                spike = true;
-                v = d.v_reset;
-                r = (uint8_t)d.t_ref;
-            }
-        }
-        d.V[j] = v;
-        d.ref[j] = r;
-        if (do_hash) {
-            hc = mix64(((unsigned long long)g << 32) | (uint32_t)irec);
-            hv = mix64(((unsigned long long)g << 32) | __float_as_uint(v));
-        }
-    }
-    // a3: warp ballot, block prefix sum, one atomic per block
-    const unsigned int ballot = __ballot_sync(0xFFFFFFFFu, spike);
-    if (lane == 0) s_wcnt[wid] = __popc(ballot);
-    if (do_hash) {
-        hc = warp_sum(hc);
-        hv = warp_sum(hv);
-        if (lane == 0) {
-            s_h[0][wid] = hc;
-            s_h[1][wid] = hv;
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned int tot = 0;
-        for (int w = 0; w < kThreads / 32; ++w) {
-            const unsigned int cw = s_wcnt[w];
-            s_wcnt[w] = tot;
-            tot += cw;
-        }
-        s_base = tot ? atomicAdd(&c->S_acc, tot) : 0u;
-        if (do_hash) {
-            unsigned long long a = 0, b = 0;
-            for (int w = 0; w < kThreads / 32; ++w) {
-                a += s_h[0][w];
-                b += s_h[1][w];
-            }
-            atomicAdd(&d.hash[2 * t], a);
-            atomicAdd(&d.hash[2 * t + 1], b);
-        }
-    }
-    __syncthreads();
-    if (spike) {
-        const unsigned int pos = s_base + s_wcnt[wid] + __popc(ballot & ((1u << lane) - 1u));
-        d.spk[head + pos] = (uint32_t)j;
-    }
-    // the last block to finish closes the step
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = (atomicAdd(&c->blocks_done, 1u) == gridDim.x - 1);
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    for (int x = threadIdx.x; x < d.n_vn; x += kThreads) d.bucket_cnt[x] = 0;
-    for (int x = threadIdx.x; x < d.P; x += kThreads) d.inbox_cnt[x] = 0;
-    if (threadIdx.x == 0) {
-        const unsigned int S = atomicAdd(&c->S_acc, 0u);
-        c->t_cur = t;
-        c->S_cur = S;
-        c->spk_base = head;
-        long long h = head;
-        if (c->rec_on) {
-            if (t < d.raster_steps && head + S <= d.raster_cap) {
-                h = head + S;
-                d.raster_off[t + 1] = h;
-                c->rec_steps = t + 1;
-            } else {
-                c->rec_on = 0;
-                c->status |= kStRaster;
-            }
-        }
-        c->head = h;
-        c->t = t + 1;
-        c->S_acc = 0;
-        c->blocks_done = 0;
-        d.counters[C_STEPS] += 1ull;
-        d.counters[C_SPIKES] += S;
-    }
-}
-
-// ---------------------------------------------------------------- a4
-__global__ void __launch_bounds__(kThreads) k_level1(const Dev d)
-{
-    __shared__ unsigned long long s_c[2];
-    if (threadIdx.x < 2) s_c[threadIdx.x] = 0;
-    __syncthreads();
-    const Ctrl *c = d.ctrl;
-    const unsigned int S = c->S_cur;
-    const long long base = c->spk_base;
-    unsigned int loc = 0, xvn = 0;
-    unsigned int ovf = 0;
-    for (unsigned int s = blockIdx.x * kThreads + threadIdx.x; s < S; s += gridDim.x * kThreads) {
-        const uint32_t i = d.spk[base + s];
-        const uint16_t h = d.src_vn[i];
-        for (uint32_t e = d.l1_ptr[i]; e < d.l1_ptr[i + 1]; ++e) {
-            const uint16_t g = d.l1_vn[e];
-            const unsigned int pos = atomicAdd(&d.bucket_cnt[g], 1u);
-            if (pos < d.bucket_capv[g]) d.bucket[d.bucket_base[g] + pos] = e;
-            else ovf = 1;
-            if (g == h) ++loc; else ++xvn;
-        }
-    }
-    loc = warp_sum(loc);
-    xvn = warp_sum(xvn);
-    if ((threadIdx.x & 31) == 0 && (loc | xvn)) {
-        atomicAdd(&s_c[0], (unsigned long long)loc);
-        atomicAdd(&s_c[1], (unsigned long long)xvn);
-    }
-    if (ovf) atomicOr(&d.ctrl->status, kStBucket);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        if (s_c[0]) atomicAdd(&d.counters[C_L1_LOCAL], s_c[0]);
-        if (s_c[1]) atomicAdd(&d.counters[C_L1_XVN], s_c[1]);
-    }
-}
-
-// ---------------------------------------------------------------- a5
-__global__ void __launch_bounds__(kThreads) k_level2(const Dev d)
-{
-    __shared__ unsigned long long s_c[4];
-    if (threadIdx.x < 4) s_c[threadIdx.x] = 0;
-    __syncthreads();
-    unsigned int cls[4] = {0, 0, 0, 0};
-    unsigned int ovf = 0;
-    const unsigned int gt = blockIdx.x * kThreads + threadIdx.x, gs = gridDim.x * kThreads;
-    for (int g = 0; g < d.n_vn; ++g) {
-        const unsigned int n = min(d.bucket_cnt[g], d.bucket_capv[g]);
-        const unsigned long long bb = d.bucket_base[g];
-        for (unsigned int x = gt; x < n; x += gs) {
-            const uint32_t e = d.bucket[bb + x];
-            for (uint32_t f = d.l1_l2[e]; f < d.l1_l2[e + 1]; ++f) {
-                const DevL2 l = d.l2[f];
-                const unsigned int pos = atomicAdd(&d.inbox_cnt[l.q], 1u);
-                if (pos < d.inbox_capv[l.q])
-                    d.inbox[d.inbox_base[l.q] + pos] = (l.off << kLenBits) | (unsigned long long)l.len;
-                else
-                    ovf = 1;
-                cls[l.cls & 3]++;
-            }
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const unsigned int v = warp_sum(cls[k]);
-        if ((threadIdx.x & 31) == 0 && v) atomicAdd(&s_c[k], (unsigned long long)v);
-    }
-    if (ovf) atomicOr(&d.ctrl->status, kStInbox);
-    __syncthreads();
-    if (threadIdx.x < 4 && s_c[threadIdx.x]) atomicAdd(&d.counters[C_L2_BASE + threadIdx.x], s_c[threadIdx.x]);
-}
-
-// ---------------------------------------------------------------- a6
-__global__ void __launch_bounds__(kThreads) k_deliver(const Dev d)
-{
-    __shared__ unsigned long long s_ev;
-    if (threadIdx.x == 0) s_ev = 0;
-    __syncthreads();
-    const long long t = d.ctrl->t_cur;
-    const int tm = (int)(t % d.D);
-    const int lane = threadIdx.x & 31;
-    const unsigned int gw = (blockIdx.x * kThreads + threadIdx.x) >> 5, nw = (gridDim.x * kThreads) >> 5;
-    unsigned long long ev = 0;
-    for (int q = 0; q < d.P; ++q) {
-        const unsigned int n = min(d.inbox_cnt[q], d.inbox_capv[q]);
-        const unsigned long long ib = d.inbox_base[q];
-        for (unsigned int x = gw; x < n; x += nw) {
-            const unsigned long long ent = d.inbox[ib + x];
-            const unsigned long long off = ent >> kLenBits;
-            const unsigned int len = (unsigned int)(ent & kLenMask);
-            for (unsigned int l = lane; l < len; l += 32) {
-                const uint32_t td = d.syn_td[off + l];
-                const int32_t w = d.syn_w[off + l];
-                int sl = tm + (int)(td >> kTgtBits) + 1;
-                if (sl >= d.D) sl -= d.D;
-                atomicAdd(&d.ring[(long long)sl * d.M + (td & kTgtMask)], w);
-            }
-            ev += len;
-        }
-    }
-    if (lane == 0 && ev) atomicAdd(&s_ev, ev);
-    __syncthreads();
-    if (threadIdx.x == 0 && s_ev) atomicAdd(&d.counters[C_EVENTS], s_ev);
-}
 
 // ---------------------------------------------------------------- spike fan-out
 // Route and fan out a caller-given spike list (snn_deliver_spikes): the same
@@ -459,6 +114,7 @@ struct Layout {
     Region bucket, bucket_base, bucket_capv, bucket_cnt, inbox, inbox_base, inbox_capv, inbox_cnt;
     Region spk, raster_off, hash, cur_rec, counters, ctrl;
     Region fwd, fo_cnt;  // snn_deliver_spikes: global -> internal map, scratch counters
+    Region bucket_pre, inbox_pre;
     size_t total = 0;
     std::vector<uint64_t> bucket_base_h, inbox_base_h;
     std::vector<uint32_t> bucket_cap_h, inbox_cap_h;
@@ -521,10 +177,12 @@ static int make_layout(const snn_routing *rt, const snn_sim_params *p, Layout &L
     place(L, L.bucket_base, sizeof(uint64_t) * (size_t)(rt->n_vn + 1));
     place(L, L.bucket_capv, sizeof(uint32_t) * (size_t)rt->n_vn);
     place(L, L.bucket_cnt, sizeof(uint32_t) * (size_t)rt->n_vn);
+    place(L, L.bucket_pre, sizeof(uint32_t) * (size_t)(rt->n_vn + 1));
     place(L, L.inbox, sizeof(uint64_t) * (size_t)ni);
     place(L, L.inbox_base, sizeof(uint64_t) * (size_t)(rt->P + 1));
     place(L, L.inbox_capv, sizeof(uint32_t) * (size_t)rt->P);
     place(L, L.inbox_cnt, sizeof(uint32_t) * (size_t)rt->P);
+    place(L, L.inbox_pre, sizeof(uint32_t) * (size_t)(rt->P + 1));
     place(L, L.spk, sizeof(uint32_t) * (size_t)(p->raster_cap + M));
     place(L, L.raster_off, sizeof(long long) * (size_t)(p->raster_steps + 1));
     place(L, L.hash, sizeof(unsigned long long) * 2 * (size_t)p->hash_steps);
@@ -586,7 +244,8 @@ struct snn_sim {
     int UP = 0;
     std::vector<cudaEvent_t> pev;
     int64_t static_row_l1 = -1, static_row_l2 = -1;  // snn_deliver_spikes_static sizing
-    unsigned grid_update = 1, grid_route = 1;
+    unsigned grid_update = 1, grid_l1 = 1, grid_route = 1;
+    bool vec = false;  // 4 neurons per thread with 16-byte loads (M % 4 == 0)
     std::vector<void *> pinned;
 };
 
@@ -673,12 +332,26 @@ static int reset_state(snn_sim *s)
     return SNN_OK;
 }
 
+// Launch phase 0..3 of a step (update, level 1, level 2, delivery).
+static void launch_phase(snn_sim *s, int ph, cudaStream_t st)
+{
+    switch (ph) {
+    case 0:
+        if (s->vec) k_update<true><<<s->grid_update, kThreads, 0, st>>>(s->dev);
+        else k_update<false><<<s->grid_update, kThreads, 0, st>>>(s->dev);
+        break;
+    case 1: k_level1<<<s->grid_l1, kThreads, 0, st>>>(s->dev); break;
+    case 2: k_level2<<<s->grid_route, kThreads, 0, st>>>(s->dev); break;
+    default: k_deliver<<<s->grid_route, kThreads, 0, st>>>(s->dev); break;
+    }
+}
+
 static cudaError_t launch_step(snn_sim *s, cudaStream_t st)
 {
-    k_update<<<s->grid_update, kThreads, 0, st>>>(s->dev);
-    k_level1<<<s->grid_route, kThreads, 0, st>>>(s->dev);
-    k_level2<<<s->grid_route, kThreads, 0, st>>>(s->dev);
-    k_deliver<<<s->grid_route, kThreads, 0, st>>>(s->dev);
+    launch_phase(s, 0, st);
+    launch_phase(s, 1, st);
+    launch_phase(s, 2, st);
+    launch_phase(s, 3, st);
     return cudaGetLastError();
 }
 
@@ -736,8 +409,24 @@ extern "C" int snn_sim_create(const snn_network *net, const snn_routing *rt, con
         delete s;
         return SNN_E_CUDA;
     }
-    s->grid_update = (unsigned)((rt->M + kThreads - 1) / kThreads);
-    s->grid_route = (unsigned)(2 * sms);
+    s->vec = (rt->M % 4) == 0;
+    {
+        // persistent grids: as many blocks as stay resident together
+        int ou = 0, o2 = 0, o3 = 0;
+        cudaError_t oe = s->vec ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ou, k_update<true>, kThreads, 0)
+                                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ou, k_update<false>, kThreads, 0);
+        if (oe == cudaSuccess) oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, k_level2, kThreads, 0);
+        if (oe == cudaSuccess) oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o3, k_deliver, kThreads, 0);
+        if (oe != cudaSuccess) {
+            snn_sim_destroy(s);
+            return SNN_E_CUDA;
+        }
+        const int64_t items = s->vec ? rt->M / 4 : rt->M;
+        const int64_t blocks = (items + kThreads - 1) / kThreads;
+        s->grid_update = (unsigned)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)sms * std::max(1, ou)));
+        s->grid_l1 = (unsigned)(4 * sms);
+        s->grid_route = (unsigned)(sms * std::max(1, std::min(o2, o3)));
+    }
     if (cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
         delete s;
         return SNN_E_CUDA;
@@ -773,10 +462,12 @@ extern "C" int snn_sim_create(const snn_network *net, const snn_routing *rt, con
     d.bucket_base = (const unsigned long long *)(w + L.bucket_base.off);
     d.bucket_capv = (const uint32_t *)(w + L.bucket_capv.off);
     d.bucket_cnt = (uint32_t *)(w + L.bucket_cnt.off);
+    d.bucket_pre = (uint32_t *)(w + L.bucket_pre.off);
     d.inbox = (unsigned long long *)(w + L.inbox.off);
     d.inbox_base = (const unsigned long long *)(w + L.inbox_base.off);
     d.inbox_capv = (const uint32_t *)(w + L.inbox_capv.off);
     d.inbox_cnt = (uint32_t *)(w + L.inbox_cnt.off);
+    d.inbox_pre = (uint32_t *)(w + L.inbox_pre.off);
     d.spk = (uint32_t *)(w + L.spk.off);
     d.raster_off = (long long *)(w + L.raster_off.off);
     d.hash = (unsigned long long *)(w + L.hash.off);
@@ -801,7 +492,13 @@ extern "C" int snn_sim_create(const snn_network *net, const snn_routing *rt, con
     d.hash_steps = p->hash_steps;
     d.cur_every = p->cur_every;
     d.cur_slots = p->cur_slots;
-    poisson_thresholds(p->drive_lambda, d.th, &d.th_len);
+    {
+        unsigned long long th[kPTab];
+        int len = 0;
+        poisson_thresholds(p->drive_lambda, th, &len);
+        d.th_fin = len - 1;  // every threshold but the closing 2^32 fits in 32 bits
+        for (int k = 0; k < kPTab; ++k) d.th32[k] = k < len - 1 ? (uint32_t)th[k] : 0xFFFFFFFFu;
+    }
 
     rc = upload_tables(s);
     if (!rc) rc = reset_state(s);
@@ -846,10 +543,10 @@ extern "C" int snn_profile_phases(snn_sim *s, int32_t T, double *phase_ms)
             cudaStream_t st = s->cap_stream;
             const unsigned fl = cudaEventRecordExternal;
             le = cudaEventRecordWithFlags(ev[0], st, fl);
-            if (le == cudaSuccess) { k_update<<<s->grid_update, kThreads, 0, st>>>(s->dev); le = cudaEventRecordWithFlags(ev[1], st, fl); }
-            if (le == cudaSuccess) { k_level1<<<s->grid_route, kThreads, 0, st>>>(s->dev); le = cudaEventRecordWithFlags(ev[2], st, fl); }
-            if (le == cudaSuccess) { k_level2<<<s->grid_route, kThreads, 0, st>>>(s->dev); le = cudaEventRecordWithFlags(ev[3], st, fl); }
-            if (le == cudaSuccess) { k_deliver<<<s->grid_route, kThreads, 0, st>>>(s->dev); le = cudaEventRecordWithFlags(ev[4], st, fl); }
+            for (int ph = 0; ph < 4 && le == cudaSuccess; ++ph) {
+                launch_phase(s, ph, st);
+                le = cudaEventRecordWithFlags(ev[ph + 1], st, fl);
+            }
             if (le == cudaSuccess) le = cudaGetLastError();
         }
         cudaError_t ce = cudaStreamEndCapture(s->cap_stream, &g);
