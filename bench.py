@@ -132,9 +132,12 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ workload
-def workload(seed_offset: int = 0):
+def workload(seed_offset: int = 0, neurons: int = 0):
     import synth
     cfg = synth.SCALE
+    if neurons and neurons != cfg.M:
+        # same per-neuron statistics on a smaller or larger network (profiling cases)
+        cfg = cfg.scaled(M=neurons, name="scale-%dn-%dp-%dvn-k%d" % (neurons, cfg.P, cfg.n_vn, cfg.K))
     dyn = cfg.dyn
     if seed_offset:
         import dataclasses
@@ -163,7 +166,7 @@ def run_ours(args):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    cfg = workload(rank)
+    cfg = workload(rank, args.neurons)
     K, W = args.steps, args.warmup
 
     t_setup = time.time()
@@ -217,9 +220,10 @@ def run_ours(args):
     phase_ms = sim.profile_phases(NP)
     cb = sim.read_counts()
     dp = {k: cb[k] - ca[k] for k in cb}
-    pbytes = phase_bytes(cfg.M, dp["steps"], dp, not info["identity_order"])
-    names = ["update", "level1", "level2", "deliver"]
-    kernel_names = ["k_update", "k_level1", "k_level2", "k_deliver"]
+    pb4 = phase_bytes(cfg.M, dp["steps"], dp, not info["identity_order"])
+    pbytes = [pb4[0] + pb4[1] + pb4[2], pb4[3]]  # the update kernel also routes (a4, a5)
+    names = ["update_route", "deliver"]
+    kernel_names = ["k_update", "k_deliver"]
     phases = {}
     for n, kn, t_ms, b in zip(names, kernel_names, phase_ms, pbytes):
         phases[n] = {"kernel": kn, "ms_per_step": t_ms / NP, "bytes_per_step": b / NP,
@@ -239,23 +243,25 @@ def run_ours(args):
 
     # end to end through the C ABI: upload of every table from pinned host
     # memory, K steps, read-back of the raster and the counters
-    t_e2e0 = time.time()
-    torch.cuda.synchronize()
-    e2 = torch.cuda.Event(enable_timing=True)
-    e3 = torch.cuda.Event(enable_timing=True)
-    barrier(dist)
-    h0 = time.perf_counter()
-    sim.reset(reupload=True)
-    sim.step(K)
-    ids, off = sim.read_raster(0, K)
-    ce = sim.read_counts()
-    h1 = time.perf_counter()
-    e2e_ms = (h1 - h0) * 1e3
-    e2e_events, e2e_ms_max, _ = reduce_over_ranks(dist, float(ce["events"]), e2e_ms)
-    h2d = (info["n_synapses"] * 6 + info["n_l2"] * 16 + info["n_l1"] * 6 + (cfg.M + 1) * 4
-           + cfg.M * 6)
-    d2h = ids.nbytes + off.nbytes + 88
-    del e2, e3, t_e2e0
+    e2e = None
+    if not args.no_e2e:
+        torch.cuda.synchronize()
+        barrier(dist)
+        h0 = time.perf_counter()
+        sim.reset(reupload=True)
+        sim.step(K)
+        ids, off = sim.read_raster(0, K)
+        ce = sim.read_counts()
+        h1 = time.perf_counter()
+        e2e_ms = (h1 - h0) * 1e3
+        e2e_events, e2e_ms_max, _ = reduce_over_ranks(dist, float(ce["events"]), e2e_ms)
+        h2d = (info["n_synapses"] * 6 + info["n_l2"] * 16 + info["n_l1"] * 6 + (cfg.M + 1) * 4
+               + cfg.M * 6)
+        d2h = ids.nbytes + off.nbytes + 88
+        e2e = {"value": e2e_events / (e2e_ms_max * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K,
+               "what": "snn_sim_reset(reupload) from pinned host tables + snn_step(K) + "
+                       "snn_read_raster + snn_read_counts, host wall clock"}
 
     result = {
         "metric": METRIC, "value": events_all / (ms_max * 1e-3), "unit": UNIT, "n_gpus": world,
@@ -282,10 +288,7 @@ def run_ours(args):
         "phases": phases,
         "gpu_launches": int(sim.launches_per_step * K),
         "clocks": clocks.summary(wall0, wall1),
-        "e2e": {"value": e2e_events / (e2e_ms_max * 1e-3), "unit": UNIT,
-                "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K,
-                "what": "snn_sim_reset(reupload) from pinned host tables + snn_step(K) + "
-                        "snn_read_raster + snn_read_counts, host wall clock"},
+        "e2e": e2e,
         "routing": routing_report(dc, info, rt),
         "setup_s": setup_s,
     }
@@ -315,6 +318,16 @@ def routing_report(dc, info, rt):
     }
 
 
+def kernel_source_sha() -> str:
+    """Hash of the step-kernel sources (a capture taken on other sources is stale)."""
+    import hashlib
+    hs = hashlib.sha256()
+    for f in ("snn_step.cuh", "snn_sim.cu"):
+        with open(os.path.join(ROOT, "paper_2205_07125_gb300", "csrc", f), "rb") as fh:
+            hs.update(fh.read())
+    return hs.hexdigest()[:16]
+
+
 def load_traffic(kernel: str):
     """dram bytes per launch of `kernel` from the committed ncu summary, if it
     was taken on the current kernel source (else null)."""
@@ -327,9 +340,7 @@ def load_traffic(kernel: str):
     ent = t.get(kernel)
     if not ent:
         return None
-    import hashlib
-    src = os.path.join(ROOT, "paper_2205_07125_gb300", "csrc", "snn_sim.cu")
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    h = kernel_source_sha()
     if ent.get("source_sha") != h:
         return None
     return ent.get("dram_bytes_per_launch")
@@ -406,6 +417,10 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-steps", type=int, default=400)
+    ap.add_argument("--neurons", type=int, default=0,
+                    help="network size with the scale workload's per-neuron statistics "
+                         "(default: the 1,048,576-neuron workload)")
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

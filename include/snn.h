@@ -277,9 +277,10 @@ int64_t snn_launches_per_step(const snn_sim *sim);
 /*
  * Advance T steps like snn_step, but from a CUDA graph that records a CUDA
  * event before and after every kernel, and return the summed event time of
- * each step phase in phase_ms[0..3] (update+compaction, level-1 bucketing,
- * level-2 relay expansion, delivery), milliseconds.  For measurement; the
- * event nodes add a little time to each step.  Synchronises the stream.
+ * each kernel of a step in phase_ms[0 .. snn_launches_per_step(sim)-1],
+ * milliseconds: [0] update + compaction + level-1 bucketing + level-2 relay
+ * expansion, [1] delivery.  For measurement; the event nodes add a little
+ * time to each step.  Synchronises the stream.
  * Errors: SNN_E_ARG, SNN_E_CUDA.
  */
 int snn_profile_phases(snn_sim *sim, int32_t T, double *phase_ms);

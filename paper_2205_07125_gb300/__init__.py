@@ -342,9 +342,9 @@ class Sim:
             _ck(_lib.snn_sim_reset(self.h, int(bool(reupload))), "snn_sim_reset")
 
     def profile_phases(self, T: int) -> np.ndarray:
-        """Advance T steps from an event-instrumented graph; summed ms per phase
-        (update, level 1, level 2, delivery)."""
-        out = np.zeros(4, np.float64)
+        """Advance T steps from an event-instrumented graph; summed ms per kernel
+        of a step ([0] update + compaction + level 1 + level 2, [1] delivery)."""
+        out = np.zeros(self.launches_per_step, np.float64)
         with self._dev():
             _ck(_lib.snn_profile_phases(self.h, int(T), out.ctypes.data), "snn_profile_phases")
         return out

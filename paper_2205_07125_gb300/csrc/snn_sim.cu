@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -114,7 +115,8 @@ struct Layout {
     Region bucket, bucket_base, bucket_capv, bucket_cnt, inbox, inbox_base, inbox_capv, inbox_cnt;
     Region spk, raster_off, hash, cur_rec, counters, ctrl;
     Region fwd, fo_cnt;  // snn_deliver_spikes: global -> internal map, scratch counters
-    Region bucket_pre, inbox_pre;
+    Region inbox_pre, piece;
+    uint32_t piece_cap = 0;
     size_t total = 0;
     std::vector<uint64_t> bucket_base_h, inbox_base_h;
     std::vector<uint32_t> bucket_cap_h, inbox_cap_h;
@@ -160,6 +162,15 @@ static int make_layout(const snn_routing *rt, const snn_sim_params *p, Layout &L
         ni += c;
     }
     L.inbox_base_h[rt->P] = ni;
+    // pieces of long segments, worst case: every neuron spiking
+    uint64_t pe = 0;
+    for (int64_t f = 0; f < rt->n_l2; ++f) {
+        const uint32_t len = rt->l2[f].len;
+        if (len > (uint32_t)kShortSeg) pe += (len + kPiece - 1) / kPiece;
+    }
+    const uint64_t pc = cap(pe, p->inbox_frac);
+    if (pc > 0xFFFFFFFFull) return SNN_E_RANGE;
+    L.piece_cap = (uint32_t)pc;
     place(L, L.ctrl, sizeof(Ctrl));
     place(L, L.counters, sizeof(unsigned long long) * C_N);
     place(L, L.V, sizeof(float) * (size_t)M);
@@ -176,13 +187,13 @@ static int make_layout(const snn_routing *rt, const snn_sim_params *p, Layout &L
     place(L, L.bucket, sizeof(uint32_t) * (size_t)nb);
     place(L, L.bucket_base, sizeof(uint64_t) * (size_t)(rt->n_vn + 1));
     place(L, L.bucket_capv, sizeof(uint32_t) * (size_t)rt->n_vn);
-    place(L, L.bucket_cnt, sizeof(uint32_t) * (size_t)rt->n_vn);
-    place(L, L.bucket_pre, sizeof(uint32_t) * (size_t)(rt->n_vn + 1));
+    place(L, L.bucket_cnt, sizeof(uint32_t) * kCntStride * (size_t)rt->n_vn);
     place(L, L.inbox, sizeof(uint64_t) * (size_t)ni);
     place(L, L.inbox_base, sizeof(uint64_t) * (size_t)(rt->P + 1));
     place(L, L.inbox_capv, sizeof(uint32_t) * (size_t)rt->P);
-    place(L, L.inbox_cnt, sizeof(uint32_t) * (size_t)rt->P);
+    place(L, L.inbox_cnt, sizeof(uint32_t) * kCntStride * (size_t)rt->P);
     place(L, L.inbox_pre, sizeof(uint32_t) * (size_t)(rt->P + 1));
+    place(L, L.piece, sizeof(unsigned long long) * (size_t)L.piece_cap);
     place(L, L.spk, sizeof(uint32_t) * (size_t)(p->raster_cap + M));
     place(L, L.raster_off, sizeof(long long) * (size_t)(p->raster_steps + 1));
     place(L, L.hash, sizeof(unsigned long long) * 2 * (size_t)p->hash_steps);
@@ -244,8 +255,9 @@ struct snn_sim {
     int UP = 0;
     std::vector<cudaEvent_t> pev;
     int64_t static_row_l1 = -1, static_row_l2 = -1;  // snn_deliver_spikes_static sizing
-    unsigned grid_update = 1, grid_l1 = 1, grid_route = 1;
+    unsigned grid_update = 1, grid_route = 1;
     bool vec = false;  // 4 neurons per thread with 16-byte loads (M % 4 == 0)
+    bool pdl = true;   // programmatic dependent launch between step kernels
     std::vector<void *> pinned;
 };
 
@@ -321,6 +333,7 @@ static int reset_state(snn_sim *s)
     CK(cudaMemsetAsync(w + L.counters.off, 0, L.counters.bytes, st));
     CK(cudaMemsetAsync(w + L.bucket_cnt.off, 0, L.bucket_cnt.bytes, st));
     CK(cudaMemsetAsync(w + L.inbox_cnt.off, 0, L.inbox_cnt.bytes, st));
+    CK(cudaMemsetAsync(w + L.inbox_pre.off, 0, L.inbox_pre.bytes, st));
     if (L.raster_off.bytes) CK(cudaMemsetAsync(w + L.raster_off.off, 0, L.raster_off.bytes, st));
     if (L.hash.bytes) CK(cudaMemsetAsync(w + L.hash.off, 0, L.hash.bytes, st));
     if (L.cur_rec.bytes) CK(cudaMemsetAsync(w + L.cur_rec.off, 0, L.cur_rec.bytes, st));
@@ -332,26 +345,41 @@ static int reset_state(snn_sim *s)
     return SNN_OK;
 }
 
-// Launch phase 0..3 of a step (update, level 1, level 2, delivery).
+// Kernels per step: 0 = update + compaction + level 1 + level 2, 1 = delivery.
+constexpr int kPhases = 2;
+
+// Launch phase ph of a step.  With programmatic dependent launch each kernel
+// may be scheduled while the one before it drains; the kernels wait
+// (griddepcontrol.wait) before reading.
 static void launch_phase(snn_sim *s, int ph, cudaStream_t st)
 {
-    switch (ph) {
-    case 0:
-        if (s->vec) k_update<true><<<s->grid_update, kThreads, 0, st>>>(s->dev);
-        else k_update<false><<<s->grid_update, kThreads, 0, st>>>(s->dev);
-        break;
-    case 1: k_level1<<<s->grid_l1, kThreads, 0, st>>>(s->dev); break;
-    case 2: k_level2<<<s->grid_route, kThreads, 0, st>>>(s->dev); break;
-    default: k_deliver<<<s->grid_route, kThreads, 0, st>>>(s->dev); break;
+    void (*fn)(const Dev) = nullptr;
+    unsigned grid = 1;
+    if (ph == 0) {
+        fn = s->vec ? k_update<true> : k_update<false>;
+        grid = s->grid_update;
+    } else {
+        fn = k_deliver;
+        grid = s->grid_route;
     }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    if (s->pdl) {
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+    }
+    cudaLaunchKernelEx(&cfg, fn, s->dev);
 }
 
 static cudaError_t launch_step(snn_sim *s, cudaStream_t st)
 {
-    launch_phase(s, 0, st);
-    launch_phase(s, 1, st);
-    launch_phase(s, 2, st);
-    launch_phase(s, 3, st);
+    for (int ph = 0; ph < kPhases; ++ph) launch_phase(s, ph, st);
     return cudaGetLastError();
 }
 
@@ -411,21 +439,21 @@ extern "C" int snn_sim_create(const snn_network *net, const snn_routing *rt, con
     }
     s->vec = (rt->M % 4) == 0;
     {
+        // SNN_PDL=0 launches the step kernels with plain stream order
+        const char *e = std::getenv("SNN_PDL");
+        s->pdl = !(e && e[0] == '0');
+    }
+    {
         // persistent grids: as many blocks as stay resident together
-        int ou = 0, o2 = 0, o3 = 0;
-        cudaError_t oe = s->vec ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ou, k_update<true>, kThreads, 0)
-                                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ou, k_update<false>, kThreads, 0);
-        if (oe == cudaSuccess) oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, k_level2, kThreads, 0);
-        if (oe == cudaSuccess) oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o3, k_deliver, kThreads, 0);
-        if (oe != cudaSuccess) {
+        int o3 = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o3, k_deliver, kThreads, 0) != cudaSuccess) {
             snn_sim_destroy(s);
             return SNN_E_CUDA;
         }
         const int64_t items = s->vec ? rt->M / 4 : rt->M;
         const int64_t blocks = (items + kThreads - 1) / kThreads;
-        s->grid_update = (unsigned)std::max<int64_t>(1, std::min<int64_t>(blocks, (int64_t)sms * std::max(1, ou)));
-        s->grid_l1 = (unsigned)(4 * sms);
-        s->grid_route = (unsigned)(sms * std::max(1, std::min(o2, o3)));
+        s->grid_update = (unsigned)std::max<int64_t>(1, blocks);  // one pass over the neurons
+        s->grid_route = (unsigned)(sms * std::max(1, o3));
     }
     if (cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
         delete s;
@@ -462,12 +490,13 @@ extern "C" int snn_sim_create(const snn_network *net, const snn_routing *rt, con
     d.bucket_base = (const unsigned long long *)(w + L.bucket_base.off);
     d.bucket_capv = (const uint32_t *)(w + L.bucket_capv.off);
     d.bucket_cnt = (uint32_t *)(w + L.bucket_cnt.off);
-    d.bucket_pre = (uint32_t *)(w + L.bucket_pre.off);
     d.inbox = (unsigned long long *)(w + L.inbox.off);
     d.inbox_base = (const unsigned long long *)(w + L.inbox_base.off);
     d.inbox_capv = (const uint32_t *)(w + L.inbox_capv.off);
     d.inbox_cnt = (uint32_t *)(w + L.inbox_cnt.off);
     d.inbox_pre = (uint32_t *)(w + L.inbox_pre.off);
+    d.piece = (unsigned long long *)(w + L.piece.off);
+    d.piece_cap = L.piece_cap;
     d.spk = (uint32_t *)(w + L.spk.off);
     d.raster_off = (long long *)(w + L.raster_off.off);
     d.hash = (unsigned long long *)(w + L.hash.off);
@@ -528,10 +557,10 @@ extern "C" int snn_step(snn_sim *s, int32_t T)
 extern "C" int snn_profile_phases(snn_sim *s, int32_t T, double *phase_ms)
 {
     if (!s || T < 0 || !phase_ms) return SNN_E_ARG;
-    for (int k = 0; k < 4; ++k) phase_ms[k] = 0.0;
+    for (int k = 0; k < kPhases; ++k) phase_ms[k] = 0.0;
     if (!s->gP) {
         const int U = 16;
-        s->pev.resize((size_t)U * 5);
+        s->pev.resize((size_t)U * (kPhases + 1));
         for (auto &e : s->pev) CK(cudaEventCreate(&e));
         cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
@@ -539,11 +568,11 @@ extern "C" int snn_profile_phases(snn_sim *s, int32_t T, double *phase_ms)
         for (int k = 0; k < U && le == cudaSuccess; ++k) {
             // cudaEventRecordExternal: a real event-record node in the graph
             // (a plain record inside a capture only orders streams)
-            cudaEvent_t *ev = &s->pev[(size_t)k * 5];
+            cudaEvent_t *ev = &s->pev[(size_t)k * (kPhases + 1)];
             cudaStream_t st = s->cap_stream;
             const unsigned fl = cudaEventRecordExternal;
             le = cudaEventRecordWithFlags(ev[0], st, fl);
-            for (int ph = 0; ph < 4 && le == cudaSuccess; ++ph) {
+            for (int ph = 0; ph < kPhases && le == cudaSuccess; ++ph) {
                 launch_phase(s, ph, st);
                 le = cudaEventRecordWithFlags(ev[ph + 1], st, fl);
             }
@@ -566,9 +595,9 @@ extern "C" int snn_profile_phases(snn_sim *s, int32_t T, double *phase_ms)
             CK(cudaGraphLaunch(s->gP, s->stream));
             CK(cudaStreamSynchronize(s->stream));
             for (int k = 0; k < s->UP; ++k)
-                for (int ph = 0; ph < 4; ++ph) {
+                for (int ph = 0; ph < kPhases; ++ph) {
                     float ms = 0.f;
-                    CK(cudaEventElapsedTime(&ms, s->pev[(size_t)k * 5 + ph], s->pev[(size_t)k * 5 + ph + 1]));
+                    CK(cudaEventElapsedTime(&ms, s->pev[(size_t)k * (kPhases + 1) + ph], s->pev[(size_t)k * (kPhases + 1) + ph + 1]));
                     phase_ms[ph] += ms;
                 }
             left -= s->UP;
@@ -721,7 +750,7 @@ extern "C" int snn_deliver_spikes_static(snn_sim *s, const uint32_t *ids, int64_
 
 extern "C" int64_t snn_launches_per_step(const snn_sim *s)
 {
-    return s ? 4 : 0;
+    return s ? kPhases : 0;
 }
 
 static int read_ctrl(snn_sim *s, Ctrl *c)
@@ -858,11 +887,12 @@ extern "C" int snn_read_inbox_pairs(snn_sim *s, uint64_t *pairs, int64_t cap, in
     const snn_routing *rt = s->rt;
     const Layout &L = s->L;
     CK(cudaStreamSynchronize(s->stream));
-    std::vector<uint32_t> cnt((size_t)rt->P);
-    CK(cudaMemcpy(cnt.data(), s->dev.inbox_cnt, sizeof(uint32_t) * cnt.size(), cudaMemcpyDeviceToHost));
+    // filled inbox lengths of the last step, from its prefix sums
+    std::vector<uint32_t> pre((size_t)rt->P + 1);
+    CK(cudaMemcpy(pre.data(), s->dev.inbox_pre, sizeof(uint32_t) * pre.size(), cudaMemcpyDeviceToHost));
     int64_t tot = 0;
     for (int32_t q = 0; q < rt->P; ++q) {
-        uint32_t m = std::min(cnt[q], L.inbox_cap_h[q]);
+        uint32_t m = pre[q + 1] - pre[q];
         if (m == 0) continue;
         std::vector<unsigned long long> ent(m);
         CK(cudaMemcpy(ent.data(), s->dev.inbox + L.inbox_base_h[q], sizeof(unsigned long long) * m,

@@ -5,24 +5,23 @@
 // documented readings (include/snn.h).
 //   k_update   a1 consume ring slot t mod D, Poisson drive (Philox4x32-10,
 //                 inverse CDF); a2 FP32 LIF update + threshold (no FMA,
-//                 fixed order); a3 warp-ballot / warp-scan / block-scan
-//                 spike compaction into the step's spike list.  Persistent
-//                 grid, 4 neurons per thread with 16-byte loads; the last
-//                 block to finish closes the step's bookkeeping.
-//   k_level1   a4 one warp per spike, one lane per level-1 entry: the spike
-//                 is appended to the bucket of every destination VN in its
-//                 level-1 row (one entry per VN: deduplicated).  The last
-//                 block writes the bucket prefix sums.
-//   k_level2   a5 one thread per bucket entry (flattened over all VNs): the
-//                 relay of VN g expands entry (i, g) into the inboxes of the
-//                 partitions of g holding targets of i; inbox slots are
-//                 reserved with warp-aggregated atomics (one per distinct
-//                 partition and warp).  The last block writes the inbox
-//                 prefix sums.
-//   k_deliver  a6 warps take 32 inbox entries (flattened over partitions):
-//                 short segments are walked by their lane, long ones by the
-//                 whole warp with 4-deep unrolled streaming loads; every
-//                 synapse adds its int16 weight with a 32-bit reduction into
+//                 fixed order); a3 warp-scan / block-scan spike compaction
+//                 into a block buffer and the step's spike list (4 neurons
+//                 per thread with 16-byte loads).  The block that found the
+//                 spikes then routes them, one warp per spike:
+//              a4 level-1 bucketing: the spike is appended to the bucket of
+//                 every destination VN in its level-1 row (one entry per VN:
+//                 deduplicated);
+//              a5 level-2 relay expansion: every (spike, VN) entry becomes an
+//                 inbox entry of each partition of that VN holding targets;
+//                 long segments are also queued as 128-synapse pieces.
+//                 The last block to finish writes the inbox prefix sums and
+//                 closes the step's bookkeeping.
+//   k_deliver  a6 long segments arrive cut into 128-synapse pieces, one
+//                 warp per piece with 4 streaming loads in flight per lane;
+//                 short segments (<= 8 synapses) are walked by one lane per
+//                 inbox entry (flattened over partitions); every synapse adds
+//                 its int16 weight with a 32-bit reduction into
 //                 ring[(t+d) mod D][target].
 // The ring has D = max delay + 1 slots, so the slot consumed at step t is
 // never written by the deliveries of step t.
@@ -38,7 +37,11 @@ constexpr int kThreads = 256;
 constexpr int kPTab = 32;
 constexpr int kSpkBuf = 1024;   // spikes a k_update block buffers before flushing
 constexpr int kShortSeg = 8;    // segments up to this length are walked by one lane
+constexpr int kPiece = 128;     // longer segments are cut into pieces of this many synapses
 constexpr int kPreMax = 4097;   // staged prefix entries (P <= 4096)
+// Per-VN and per-partition fill counters sit one 128-byte line apart, so
+// that their atomics spread over L2 slices instead of queueing on one line.
+constexpr int kCntStride = 32;
 
 // status bits
 constexpr uint32_t kStBucket = 1u, kStInbox = 2u, kStRaster = 4u;
@@ -57,8 +60,8 @@ struct Ctrl {
     unsigned int blocks_done;
     unsigned int status;
     int rec_on;
-    unsigned int done1;   // k_level1 blocks finished
-    unsigned int done2;   // k_level2 blocks finished
+    unsigned int n_piece;      // long-segment pieces queued so far in the running update
+    unsigned int n_piece_cur;  // pieces of step t_cur, for k_deliver
     unsigned int pad;
 };
 
@@ -89,12 +92,13 @@ struct Dev {
     const unsigned long long *bucket_base;
     const uint32_t *bucket_capv;
     uint32_t *bucket_cnt;
-    uint32_t *bucket_pre;   // [n_vn+1] prefix of the filled bucket lengths
     unsigned long long *inbox;
     const unsigned long long *inbox_base;
     const uint32_t *inbox_capv;
     uint32_t *inbox_cnt;
     uint32_t *inbox_pre;    // [P+1] prefix of the filled inbox lengths
+    unsigned long long *piece;  // pieces of long segments: offset << 8 | length
+    unsigned int piece_cap;
     // records
     uint32_t *spk;
     long long *raster_off;
@@ -146,6 +150,15 @@ __device__ __forceinline__ T warp_sum(T v)
     return v;
 }
 
+// Programmatic dependent launch: every step kernel waits for the grid before
+// it (all of its writes visible) before touching shared state, and lets the
+// next grid be scheduled early.  Both are no-ops for a plain launch.
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Index k with pre[k] <= x < pre[k+1] (pre nondecreasing, pre[0] = 0 <= x < pre[n]).
 __device__ __forceinline__ int prefix_find(const uint32_t *pre, int n, uint32_t x)
 {
@@ -159,12 +172,14 @@ __device__ __forceinline__ int prefix_find(const uint32_t *pre, int n, uint32_t 
 }
 
 // a1 + a2 for one neuron: returns true on a spike.
-__device__ __forceinline__ bool lif_neuron(const Dev &d, uint32_t g, uint32_t t, int32_t irec, float &v,
-                                           uint32_t &r)
+// th: the Poisson thresholds staged in shared memory (lanes index them
+// divergently, which the kernel-parameter bank would serialise).
+__device__ __forceinline__ bool lif_neuron(const Dev &d, const uint32_t *th, uint32_t g, uint32_t t, int32_t irec,
+                                           float &v, uint32_t &r)
 {
     const uint32_t u = philox_w0(d.key0, d.key1, g, t);
     int k = 0;
-    while (k < d.th_fin && u >= d.th32[k]) ++k;
+    while (k < d.th_fin && u >= th[k]) ++k;
     const int32_t I = (int32_t)((uint32_t)irec + (uint32_t)k * (uint32_t)d.w_ext + (uint32_t)d.i_bias);
     if (r > 0) {
         r -= 1;
@@ -184,30 +199,136 @@ __device__ __forceinline__ bool lif_neuron(const Dev &d, uint32_t g, uint32_t t,
     return false;
 }
 
-// Move the block's buffered spikes to the step's spike list (all threads call).
+// Exclusive prefix of min(cnt[k * kCntStride], cap[k]) into pre[0..n] by one block.
+__device__ __forceinline__ void block_prefix(const uint32_t *cnt, const uint32_t *cap, uint32_t *pre, int n)
+{
+    __shared__ uint32_t s_carry;
+    __shared__ uint32_t s_w[kThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (int b = 0; b < n; b += kThreads) {
+        const int k = b + threadIdx.x;
+        const uint32_t v = k < n ? min(__ldcg(cnt + (size_t)k * kCntStride), cap[k]) : 0u;
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_w[wid] = x;
+        __syncthreads();
+        uint32_t wb = 0;
+        for (int w = 0; w < wid; ++w) wb += s_w[w];
+        if (k < n) pre[k] = s_carry + wb + x - v;
+        __syncthreads();
+        if (threadIdx.x == kThreads - 1) s_carry += wb + x;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) pre[n] = s_carry;
+    __syncthreads();
+}
+
+// Per-thread tallies of the routing done by one block.
+struct RouteTally {
+    unsigned int l1_loc = 0, l1_xvn = 0, ovf = 0;
+    unsigned int cls[4] = {0, 0, 0, 0};
+};
+
+// a4 + a5 for the n spikes buffered in s_spk, one warp per spike (all
+// threads of the block call this).
+__device__ __forceinline__ void route_spikes(const Dev &d, const uint32_t *s_spk, unsigned int n, RouteTally &rt)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (unsigned int s = wid; s < n; s += kThreads / 32) {
+        const uint32_t i = s_spk[s];
+        const uint16_t h = d.src_vn[i];
+        const uint32_t e0 = d.l1_ptr[i], e1 = d.l1_ptr[i + 1];
+        // a4: one level-1 entry per destination VN, appended to that VN's bucket
+        for (uint32_t e = e0 + lane; e < e1; e += 32u) {
+            const uint16_t g = d.l1_vn[e];
+            const unsigned int pos = atomicAdd(&d.bucket_cnt[(int)g * kCntStride], 1u);
+            if (pos < d.bucket_capv[g]) d.bucket[d.bucket_base[g] + pos] = e;
+            else rt.ovf |= kStBucket;
+            if (g == h) ++rt.l1_loc;
+            else ++rt.l1_xvn;
+        }
+        // a5: the relay of each destination VN expands the spike's entry into
+        // the inboxes of the VN's partitions that hold targets; the level-2
+        // rows of one spike's VNs are contiguous
+        const uint32_t f0 = d.l1_l2[e0], f1 = d.l1_l2[e1];
+        for (uint32_t fb = f0; fb < f1; fb += 32u) {
+            const uint32_t f = fb + lane;
+            DevL2 l;
+            l.off = 0;
+            l.len = 0;
+            if (f < f1) {
+                l = d.l2[f];
+                const unsigned int pos = atomicAdd(&d.inbox_cnt[(int)l.q * kCntStride], 1u);
+                if (pos < d.inbox_capv[l.q])
+                    d.inbox[d.inbox_base[l.q] + pos] = (l.off << kLenBits) | (unsigned long long)l.len;
+                else
+                    rt.ovf |= kStInbox;
+                rt.cls[l.cls & 3]++;
+            }
+            // long segments are also cut into pieces for an even delivery
+            const unsigned int np = l.len > (unsigned int)kShortSeg ? (l.len + kPiece - 1) / kPiece : 0u;
+            unsigned int incl = np;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const unsigned int ptot = __shfl_sync(0xFFFFFFFFu, incl, 31);
+            if (ptot) {
+                unsigned int pb = 0;
+                if (lane == 0) pb = atomicAdd(&d.ctrl->n_piece, ptot);
+                pb = __shfl_sync(0xFFFFFFFFu, pb, 0) + incl - np;
+                for (unsigned int k = 0; k < np; ++k, ++pb) {
+                    const unsigned int len = min((unsigned int)kPiece, l.len - k * kPiece);
+                    if (pb < d.piece_cap) d.piece[pb] = ((l.off + (unsigned long long)k * kPiece) << 8) | len;
+                    else rt.ovf |= kStInbox;
+                }
+            }
+        }
+    }
+}
+
+// Route the block's buffered spikes and move them to the step's spike list
+// (all threads call).
 __device__ __forceinline__ void flush_spikes(const Dev &d, long long head, uint32_t *s_spk, unsigned int &s_n,
-                                             unsigned int &s_gbase)
+                                             unsigned int &s_gbase, int &s_routed, RouteTally &rt)
 {
     __syncthreads();
-    if (threadIdx.x == 0) s_gbase = s_n ? atomicAdd(&d.ctrl->S_acc, s_n) : 0u;
+    const unsigned int n = s_n;
+    if (n == 0) return;
+    route_spikes(d, s_spk, n, rt);
+    if (threadIdx.x == 0) {
+        s_gbase = atomicAdd(&d.ctrl->S_acc, n);
+        s_routed = 1;
+    }
     __syncthreads();
-    const unsigned int n = s_n, gb = s_gbase;
+    const unsigned int gb = s_gbase;
     for (unsigned int k = threadIdx.x; k < n; k += kThreads) d.spk[head + gb + k] = s_spk[k];
     __syncthreads();
     if (threadIdx.x == 0) s_n = 0;
     __syncthreads();
 }
 
-// ---------------------------------------------------------------- a1-a3
+// ---------------------------------------------------------------- a1-a5
 template <bool VEC>
 __global__ void __launch_bounds__(kThreads) k_update(const Dev d)
 {
     __shared__ uint32_t s_spk[kSpkBuf];
     __shared__ unsigned int s_wsum[kThreads / 32];
     __shared__ unsigned int s_n, s_tot, s_gbase;
-    __shared__ int s_flush, s_last;
+    __shared__ int s_flush, s_last, s_routed;
     __shared__ unsigned long long s_h[2][kThreads / 32];
+    __shared__ unsigned int s_tally[kThreads / 32][6];
+    __shared__ uint32_t s_th[kPTab];
+    if (threadIdx.x < kPTab) s_th[threadIdx.x] = d.th32[threadIdx.x];
 
+    pdl_enter();
     Ctrl *c = d.ctrl;
     const long long t = c->t;
     const long long head = c->head;
@@ -219,9 +340,13 @@ __global__ void __launch_bounds__(kThreads) k_update(const Dev d)
     int32_t *cur = do_cur ? d.cur_rec + (t / d.cur_every) * d.M : nullptr;
     constexpr int NPT = VEC ? 4 : 1;
     const long long nitem = VEC ? d.M / 4 : d.M;
-    if (threadIdx.x == 0) s_n = 0;
+    if (threadIdx.x == 0) {
+        s_n = 0;
+        s_routed = 0;
+    }
     __syncthreads();
 
+    RouteTally rt;
     unsigned long long hc = 0, hv = 0;
     for (long long b0 = (long long)blockIdx.x * kThreads; b0 < nitem; b0 += (long long)gridDim.x * kThreads) {
         const long long q = b0 + threadIdx.x;
@@ -257,7 +382,7 @@ __global__ void __launch_bounds__(kThreads) k_update(const Dev d)
             for (int k = 0; k < NPT; ++k) {
                 const uint32_t g = d.gid ? d.gid[j0 + k] : (uint32_t)(j0 + k);
                 uint32_t r = (r4 >> (8 * k)) & 0xFFu;
-                if (lif_neuron(d, g, (uint32_t)t, ii[k], vv[k], r)) m |= 1u << k;
+                if (lif_neuron(d, s_th, g, (uint32_t)t, ii[k], vv[k], r)) m |= 1u << k;
                 r_out |= r << (8 * k);
                 if (do_hash) {
                     hc += mix64(((unsigned long long)g << 32) | (uint32_t)ii[k]);
@@ -294,14 +419,14 @@ __global__ void __launch_bounds__(kThreads) k_update(const Dev d)
                 s_flush = (s_n + tot > (unsigned int)kSpkBuf);
             }
             __syncthreads();
-            if (s_flush) flush_spikes(d, head, s_spk, s_n, s_gbase);
+            if (s_flush) flush_spikes(d, head, s_spk, s_n, s_gbase, s_routed, rt);
             unsigned int pos = s_n + s_wsum[wid] + x - cnt;
             for (unsigned int mm = m; mm; mm &= mm - 1u) s_spk[pos++] = (uint32_t)(j0 + __ffs(mm) - 1);
             __syncthreads();
             if (threadIdx.x == 0) s_n += s_tot;
         }
     }
-    flush_spikes(d, head, s_spk, s_n, s_gbase);
+    flush_spikes(d, head, s_spk, s_n, s_gbase, s_routed, rt);
     if (do_hash) {
         hc = warp_sum(hc);
         hv = warp_sum(hv);
@@ -320,15 +445,39 @@ __global__ void __launch_bounds__(kThreads) k_update(const Dev d)
             atomicAdd(&d.hash[2 * t + 1], b);
         }
     }
-    // the last block to finish closes the step
-    __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) s_last = (atomicAdd(&c->blocks_done, 1u) == gridDim.x - 1);
+    if (s_routed) {
+        // message tallies of the routed spikes; every routing thread fences its
+        // atomics before the block reports done
+        unsigned int v[6] = {rt.l1_loc, rt.l1_xvn, rt.cls[0], rt.cls[1], rt.cls[2], rt.cls[3]};
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            v[k] = warp_sum(v[k]);
+            if (lane == 0) s_tally[wid][k] = v[k];
+        }
+        if (rt.ovf) atomicOr(&c->status, rt.ovf);
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x < 6) {
+            unsigned long long a = 0;
+            for (int w = 0; w < kThreads / 32; ++w) a += s_tally[w][threadIdx.x];
+            const int slot6[6] = {C_L1_LOCAL, C_L1_XVN, C_L2_BASE, C_L2_BASE + 1, C_L2_BASE + 2, C_L2_BASE + 3};
+            if (a) atomicAdd(&d.counters[slot6[threadIdx.x]], a);
+        }
+    }
+    // the last block to finish closes the step: inbox prefix sums for
+    // k_deliver, counters reset for the next step
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = (atomicAdd(&c->blocks_done, 1u) == gridDim.x - 1);
+    }
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    for (int x = threadIdx.x; x < d.n_vn; x += kThreads) d.bucket_cnt[x] = 0;
-    for (int x = threadIdx.x; x < d.P; x += kThreads) d.inbox_cnt[x] = 0;
+    block_prefix(d.inbox_cnt, d.inbox_capv, d.inbox_pre, d.P);
+    for (int x = threadIdx.x; x < d.n_vn; x += kThreads) d.bucket_cnt[x * kCntStride] = 0;
+    for (int x = threadIdx.x; x < d.P; x += kThreads) d.inbox_cnt[x * kCntStride] = 0;
     if (threadIdx.x == 0) {
         const unsigned int S = atomicAdd(&c->S_acc, 0u);
         c->t_cur = t;
@@ -349,155 +498,11 @@ __global__ void __launch_bounds__(kThreads) k_update(const Dev d)
         c->t = t + 1;
         c->S_acc = 0;
         c->blocks_done = 0;
+        c->n_piece_cur = atomicAdd(&c->n_piece, 0u);
+        c->n_piece = 0;
         d.counters[C_STEPS] += 1ull;
         d.counters[C_SPIKES] += S;
     }
-}
-
-// Exclusive prefix of min(cnt[k], cap[k]) into pre[0..n] by one block.
-__device__ __forceinline__ void block_prefix(const uint32_t *cnt, const uint32_t *cap, uint32_t *pre, int n)
-{
-    __shared__ uint32_t s_carry;
-    __shared__ uint32_t s_w[kThreads / 32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (threadIdx.x == 0) s_carry = 0;
-    __syncthreads();
-    for (int b = 0; b < n; b += kThreads) {
-        const int k = b + threadIdx.x;
-        const uint32_t v = k < n ? min(__ldcg(cnt + k), cap[k]) : 0u;
-        uint32_t x = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) s_w[wid] = x;
-        __syncthreads();
-        uint32_t wb = 0;
-        for (int w = 0; w < wid; ++w) wb += s_w[w];
-        if (k < n) pre[k] = s_carry + wb + x - v;
-        __syncthreads();
-        if (threadIdx.x == kThreads - 1) s_carry += wb + x;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) pre[n] = s_carry;
-}
-
-// ---------------------------------------------------------------- a4
-__global__ void __launch_bounds__(kThreads) k_level1(const Dev d)
-{
-    __shared__ unsigned long long s_c[2];
-    __shared__ int s_last;
-    if (threadIdx.x < 2) s_c[threadIdx.x] = 0;
-    __syncthreads();
-    Ctrl *c = d.ctrl;
-    const unsigned int S = c->S_cur;
-    const long long base = c->spk_base;
-    const int lane = threadIdx.x & 31;
-    const unsigned int nw = (gridDim.x * kThreads) >> 5;
-    unsigned int loc = 0, xvn = 0, ovf = 0;
-    for (unsigned int s = (blockIdx.x * kThreads + threadIdx.x) >> 5; s < S; s += nw) {
-        const uint32_t i = d.spk[base + s];
-        const uint16_t h = d.src_vn[i];
-        const uint32_t e1 = d.l1_ptr[i + 1];
-        for (uint32_t e = d.l1_ptr[i] + lane; e < e1; e += 32) {
-            const uint16_t g = d.l1_vn[e];
-            const unsigned int pos = atomicAdd(&d.bucket_cnt[g], 1u);
-            if (pos < d.bucket_capv[g]) d.bucket[d.bucket_base[g] + pos] = e;
-            else ovf = 1;
-            if (g == h) ++loc;
-            else ++xvn;
-        }
-    }
-    loc = warp_sum(loc);
-    xvn = warp_sum(xvn);
-    if (lane == 0 && (loc | xvn)) {
-        atomicAdd(&s_c[0], (unsigned long long)loc);
-        atomicAdd(&s_c[1], (unsigned long long)xvn);
-    }
-    if (ovf) atomicOr(&c->status, kStBucket);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        if (s_c[0]) atomicAdd(&d.counters[C_L1_LOCAL], s_c[0]);
-        if (s_c[1]) atomicAdd(&d.counters[C_L1_XVN], s_c[1]);
-    }
-    // the last block writes the bucket prefix sums for k_level2
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = (atomicAdd(&c->done1, 1u) == gridDim.x - 1);
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    block_prefix(d.bucket_cnt, d.bucket_capv, d.bucket_pre, d.n_vn);
-    if (threadIdx.x == 0) c->done1 = 0;
-}
-
-// ---------------------------------------------------------------- a5
-__global__ void __launch_bounds__(kThreads) k_level2(const Dev d)
-{
-    __shared__ uint32_t s_pre[kPreMax];
-    __shared__ unsigned long long s_c[4];
-    __shared__ int s_last;
-    Ctrl *c = d.ctrl;
-    const int nb = d.n_vn + 1;
-    for (int k = threadIdx.x; k < nb; k += kThreads) s_pre[k] = d.bucket_pre[k];
-    if (threadIdx.x < 4) s_c[threadIdx.x] = 0;
-    __syncthreads();
-    const uint32_t n1 = s_pre[d.n_vn];
-    const int lane = threadIdx.x & 31;
-    const unsigned int lt = (1u << lane) - 1u;
-    unsigned int cls[4] = {0, 0, 0, 0};
-    unsigned int ovf = 0;
-    for (uint32_t b0 = blockIdx.x * kThreads; b0 < n1; b0 += gridDim.x * kThreads) {
-        const uint32_t x = b0 + threadIdx.x;
-        uint32_t f = 0, f1 = 0;
-        if (x < n1) {
-            const int g = prefix_find(s_pre, nb, x);
-            const uint32_t e = d.bucket[d.bucket_base[g] + (x - s_pre[g])];
-            f = d.l1_l2[e];
-            f1 = d.l1_l2[e + 1];
-        }
-        // one level-2 entry per lane and round; slots reserved once per
-        // distinct destination partition in the warp
-        while (__any_sync(0xFFFFFFFFu, f < f1)) {
-            const bool a = f < f1;
-            DevL2 l;
-            l.q = 0;
-            if (a) l = d.l2[f];
-            const unsigned int key = a ? (unsigned int)l.q : 0x10000u + lane;
-            const unsigned int grp = __match_any_sync(0xFFFFFFFFu, key);
-            const int leader = __ffs(grp) - 1;
-            unsigned int pos0 = 0;
-            if (a && lane == leader) pos0 = atomicAdd(&d.inbox_cnt[l.q], (unsigned int)__popc(grp));
-            pos0 = __shfl_sync(0xFFFFFFFFu, pos0, leader);
-            if (a) {
-                const unsigned int pos = pos0 + __popc(grp & lt);
-                if (pos < d.inbox_capv[l.q])
-                    d.inbox[d.inbox_base[l.q] + pos] = (l.off << kLenBits) | (unsigned long long)l.len;
-                else
-                    ovf = 1;
-                cls[l.cls & 3]++;
-                ++f;
-            }
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const unsigned int v = warp_sum(cls[k]);
-        if (lane == 0 && v) atomicAdd(&s_c[k], (unsigned long long)v);
-    }
-    if (ovf) atomicOr(&c->status, kStInbox);
-    __syncthreads();
-    if (threadIdx.x < 4 && s_c[threadIdx.x]) atomicAdd(&d.counters[C_L2_BASE + threadIdx.x], s_c[threadIdx.x]);
-    // the last block writes the inbox prefix sums for k_deliver
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) s_last = (atomicAdd(&c->done2, 1u) == gridDim.x - 1);
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    block_prefix(d.inbox_cnt, d.inbox_capv, d.inbox_pre, d.P);
-    if (threadIdx.x == 0) c->done2 = 0;
 }
 
 __device__ __forceinline__ void deliver_one(const Dev &d, int tm, unsigned long long o)
@@ -510,59 +515,60 @@ __device__ __forceinline__ void deliver_one(const Dev &d, int tm, unsigned long 
 }
 
 // ---------------------------------------------------------------- a6
+// Work items: the pieces of long segments (one warp each, 4 synapses per
+// lane, all loads in flight before the reductions), then chunks of 32 inbox
+// entries whose short segments are walked by their lane.
 __global__ void __launch_bounds__(kThreads) k_deliver(const Dev d)
 {
     __shared__ uint32_t s_pre[kPreMax];
     __shared__ unsigned long long s_ev;
+    pdl_enter();
     const int np = d.P + 1;
     for (int k = threadIdx.x; k < np; k += kThreads) s_pre[k] = d.inbox_pre[k];
     if (threadIdx.x == 0) s_ev = 0;
     __syncthreads();
     const uint32_t n2 = s_pre[d.P];
+    const unsigned int npc = min(d.ctrl->n_piece_cur, d.piece_cap);
+    const uint32_t items = npc + (n2 + 31u) / 32u;
     const int tm = (int)(d.ctrl->t_cur % d.D);
     const int lane = threadIdx.x & 31;
     const uint32_t nw = (gridDim.x * kThreads) >> 5;
     unsigned long long ev = 0;
-    for (uint32_t cb = ((blockIdx.x * kThreads + threadIdx.x) >> 5) * 32u; cb < n2; cb += nw * 32u) {
-        const uint32_t x = cb + lane;
-        unsigned long long off = 0;
-        unsigned int len = 0;
-        if (x < n2) {
-            const int q = prefix_find(s_pre, np, x);
-            const unsigned long long ent = d.inbox[d.inbox_base[q] + (x - s_pre[q])];
-            off = ent >> kLenBits;
-            len = (unsigned int)(ent & kLenMask);
-        }
-        ev += len;
-        if (len <= (unsigned int)kShortSeg) {
-            for (unsigned int l = 0; l < len; ++l) deliver_one(d, tm, off + l);
-        }
-        // long segments: the whole warp, 4 loads in flight per lane
-        unsigned int lm = __ballot_sync(0xFFFFFFFFu, len > (unsigned int)kShortSeg);
-        while (lm) {
-            const int src = __ffs(lm) - 1;
-            lm &= lm - 1u;
-            const unsigned long long o = __shfl_sync(0xFFFFFFFFu, off, src);
-            const unsigned int n = __shfl_sync(0xFFFFFFFFu, len, src);
-            for (unsigned int b = 0; b < n; b += 128u) {
-                uint32_t td[4];
-                int32_t w[4];
+    for (uint32_t it = (blockIdx.x * kThreads + threadIdx.x) >> 5; it < items; it += nw) {
+        if (it < npc) {
+            const unsigned long long e = d.piece[it];
+            const unsigned long long o = e >> 8;
+            const unsigned int n = (unsigned int)(e & 0xFFu);
+            uint32_t td[kPiece / 32];
+            int32_t w[kPiece / 32];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const unsigned int k = b + (unsigned int)u * 32u + (unsigned int)lane;
-                    if (k < n) {
-                        td[u] = __ldcs(d.syn_td + o + k);
-                        w[u] = __ldcs(d.syn_w + o + k);
-                    }
+            for (int u = 0; u < kPiece / 32; ++u) {
+                const unsigned int k = (unsigned int)u * 32u + (unsigned int)lane;
+                if (k < n) {
+                    td[u] = __ldcs(d.syn_td + o + k);
+                    w[u] = __ldcs(d.syn_w + o + k);
                 }
+            }
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const unsigned int k = b + (unsigned int)u * 32u + (unsigned int)lane;
-                    if (k < n) {
-                        int sl = tm + (int)(td[u] >> kTgtBits) + 1;
-                        if (sl >= d.D) sl -= d.D;
-                        atomicAdd(&d.ring[(long long)sl * d.M + (td[u] & kTgtMask)], w[u]);
-                    }
+            for (int u = 0; u < kPiece / 32; ++u) {
+                const unsigned int k = (unsigned int)u * 32u + (unsigned int)lane;
+                if (k < n) {
+                    int sl = tm + (int)(td[u] >> kTgtBits) + 1;
+                    if (sl >= d.D) sl -= d.D;
+                    atomicAdd(&d.ring[(long long)sl * d.M + (td[u] & kTgtMask)], w[u]);
+                }
+            }
+            if (lane == 0) ev += n;
+        } else {
+            const uint32_t x = (it - npc) * 32u + lane;
+            if (x < n2) {
+                const int q = prefix_find(s_pre, np, x);
+                const unsigned long long ent = d.inbox[d.inbox_base[q] + (x - s_pre[q])];
+                const unsigned long long off = ent >> kLenBits;
+                const unsigned int len = (unsigned int)(ent & kLenMask);
+                if (len <= (unsigned int)kShortSeg) {
+                    ev += len;
+                    for (unsigned int l = 0; l < len; ++l) deliver_one(d, tm, off + l);
                 }
             }
         }
