@@ -42,9 +42,10 @@
  *     ref = t_ref; while ref > 0 the neuron is clamped to V_reset, ref
  *     decreases by one, and its input is consumed and discarded.
  *   - Poisson drive: k ~ Poisson(lambda) by inverse CDF on one 32-bit
- *     Philox4x32-10 word (Salmon et al., SC'11) with key = drive seed and
- *     counter = (neuron id, step, 0, 0); thresholds floor(2^32 * CDF(k)) in
- *     double.
+ *     Philox4x32-10 word (Salmon et al., SC'11): neuron j at step t takes word
+ *     (j mod 4) of the block with key = drive seed and counter =
+ *     (j div 4, step, 0, 0), so one block serves four consecutive neurons;
+ *     thresholds floor(2^32 * CDF(k)) in double.
  *   - relay of destination group g for source group h: the
  *     (h mod |g|)-th partition of g in ascending partition index; for the
  *     own group the source partition sends directly.
@@ -82,6 +83,16 @@ void or_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32
         c0 = n0; c1 = n1; c2 = n2; c3 = n3;
     }
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Drive word of neuron j at step t: word j mod 4 of block (j div 4, t, 0, 0). */
+static uint32_t drive_word(uint64_t seed, uint32_t j, uint32_t t)
+{
+    uint32_t ctr[4] = {j >> 2, t, 0u, 0u};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t out[4];
+    or_philox4x32_10(ctr, key, out);
+    return out[j & 3u];
 }
 
 static uint32_t philox_word(uint64_t seed, uint32_t a, uint32_t b, uint32_t c)
@@ -548,7 +559,7 @@ int or_run(void *hv, int64_t t0, int32_t T, int32_t D,
                 rs[j] = 0;
                 if (rec) rec[j] = irec;
                 ch += mix64(((uint64_t)j << 32) | (uint32_t)irec);
-                uint32_t u = philox_word(dy->drive_seed, (uint32_t)j, (uint32_t)t, 0u);
+                uint32_t u = drive_word(dy->drive_seed, (uint32_t)j, (uint32_t)t);
                 int32_t kd = poisson_draw(h->th, h->th_len, u);
                 int32_t I = (int32_t)((uint32_t)irec + (uint32_t)kd * (uint32_t)dy->w_ext
                                       + (uint32_t)dy->i_bias);
@@ -706,6 +717,6 @@ int or_drive_draws(uint64_t seed, double lambda, int64_t j0, int64_t n, int64_t 
     int32_t len;
     if (or_poisson_table(lambda, th, &len)) return -1;
     for (int64_t a = 0; a < n; ++a)
-        out[a] = poisson_draw(th, len, philox_word(seed, (uint32_t)(j0 + a), (uint32_t)t, 0u));
+        out[a] = poisson_draw(th, len, drive_word(seed, (uint32_t)(j0 + a), (uint32_t)t));
     return 0;
 }

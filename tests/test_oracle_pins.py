@@ -63,6 +63,11 @@ def test_drive_draw_distribution():
     exp = np.array([poisson.pmf(k, lam) for k in range(kmax)] + [poisson.sf(kmax - 1, lam)]) * n
     stat = ((obs - exp) ** 2 / exp).sum()
     assert stat < chi2.ppf(0.999, len(obs) - 1)
+    # one Philox4x32-10 block (pinned by the known answers) serves four
+    # consecutive neurons: neuron j takes word j mod 4 of block (j div 4, t)
+    th = oracle.poisson_table(lam)
+    words = oracle.philox4x32_10([25, 7, 0, 0], [2000, 0])
+    assert list(oracle.drive_draws(2000, lam, 100, 4, 7)) == [int((th <= int(w)).sum()) for w in words]
     # counter-based: a draw depends only on (seed, neuron, step)
     a = oracle.drive_draws(2000, lam, 100, 10, 7)
     b = oracle.drive_draws(2000, lam, 95, 20, 7)[5:15]
