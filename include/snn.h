@@ -46,6 +46,7 @@ extern "C" {
 #define SNN_E_RANGE    -5   /* network exceeds a layout limit (ids, delays, lengths) */
 #define SNN_E_STATE    -6   /* call not valid in the object's current state */
 #define SNN_E_NODEV    -7   /* no usable CUDA device */
+#define SNN_E_TIMEOUT  -8   /* a bounded device-side wait gave up; the sim state is inconsistent */
 
 const char *snn_strerror(int code);
 
@@ -167,8 +168,8 @@ typedef struct {
     float e_l, v_th, v_reset;
     int32_t t_ref;               /* 0..255 */
     /* input I = recurrent int32 input + k*w_ext + i_bias, k ~ Poisson(lambda)
-     * drawn by inverse CDF from Philox4x32-10 word 0 with key = drive_seed,
-     * counter = (global neuron id, step, 0, 0) */
+     * drawn by inverse CDF from word (j mod 4) of the Philox4x32-10 block
+     * with key = drive_seed, counter = (j div 4, step, 0, 0), j = global id */
     double drive_lambda;         /* 0..16 */
     int32_t w_ext, i_bias;
     uint64_t drive_seed;
@@ -223,16 +224,22 @@ int snn_sim_create(const snn_network *net, const snn_routing *rt, const snn_sim_
  * Poisson drive; (a2) LIF update and threshold; (a3) warp-ballot/prefix-sum
  * spike compaction; (a4) level-1 bucketing by destination VN; (a5) level-2
  * relay expansion into per-partition inboxes; (a6) CSR fan-out of int16
- * weights into int32 ring accumulators.  Asynchronous on the sim's stream
- * (replays of captured CUDA graphs); errors raised on the device are
- * reported by snn_sync_status.  Errors: SNN_E_ARG, SNN_E_CUDA.
+ * weights into int32 ring accumulators.  Asynchronous on the sim's stream.
+ * On a GPU with cooperative launch the T steps run in one persistent
+ * kernel (every block resident, a grid barrier after each phase, each
+ * barrier wait bounded by one second); otherwise, or with the environment
+ * variable SNN_PERSIST=0 at snn_sim_create, as replays of captured CUDA
+ * graphs of two kernels per step.  Both give the same results bit for bit.
+ * Errors raised on the device are reported by snn_sync_status.
+ * Errors: SNN_E_ARG, SNN_E_CUDA.
  */
 int snn_step(snn_sim *sim, int32_t T);
 
 /* Wait for the sim's stream and return the device status:
  * SNN_OK, SNN_E_CAPACITY (bucket/inbox overflow; the affected steps are
- * wrong, the raster overflow alone is reported by snn_read_raster), or
- * SNN_E_CUDA. */
+ * wrong, the raster overflow alone is reported by snn_read_raster),
+ * SNN_E_TIMEOUT (a grid barrier of the persistent step kernel waited past its
+ * one-second bound and the run stopped), or SNN_E_CUDA. */
 int snn_sync_status(snn_sim *sim);
 
 /*
@@ -271,16 +278,20 @@ int snn_load_state(snn_sim *sim, const void *host_buf, size_t bytes);
  * reupload != 0 the routing tables are copied to the device again. */
 int snn_sim_reset(snn_sim *sim, int32_t reupload);
 
-/* Number of kernel launches one snn_step(sim, T) issues. */
+/* Kernels (phases) of one step: 2 (update + routing, delivery). */
 int64_t snn_launches_per_step(const snn_sim *sim);
+/* Kernel launches one snn_step(sim, T) issues: 1 on the persistent path,
+ * 2 per step plus one per replayed graph on the graph path. */
+int64_t snn_launches(const snn_sim *sim, int32_t T);
 
 /*
- * Advance T steps like snn_step, but from a CUDA graph that records a CUDA
- * event before and after every kernel, and return the summed event time of
- * each kernel of a step in phase_ms[0 .. snn_launches_per_step(sim)-1],
- * milliseconds: [0] update + compaction + level-1 bucketing + level-2 relay
- * expansion, [1] delivery.  For measurement; the event nodes add a little
- * time to each step.  Synchronises the stream.
+ * Advance T steps like snn_step and return the summed time of each phase of
+ * a step in phase_ms[0 .. snn_launches_per_step(sim)-1], milliseconds:
+ * [0] update + compaction + level-1 bucketing + level-2 relay expansion,
+ * [1] delivery.  Persistent path: block 0 reads the GPU's global timer at
+ * the start of each phase and after the grid barrier that ends it.  Graph
+ * path: CUDA events recorded before and after every kernel (the event
+ * nodes add a little time to each step).  Synchronises the stream.
  * Errors: SNN_E_ARG, SNN_E_CUDA.
  */
 int snn_profile_phases(snn_sim *sim, int32_t T, double *phase_ms);

@@ -114,6 +114,7 @@ _sig("snn_save_state", ctypes.c_int, [_vp, _vp, ctypes.c_size_t])
 _sig("snn_load_state", ctypes.c_int, [_vp, _vp, ctypes.c_size_t])
 _sig("snn_sim_reset", ctypes.c_int, [_vp, _i32])
 _sig("snn_launches_per_step", _i64, [_vp])
+_sig("snn_launches", _i64, [_vp, _i32])
 _sig("snn_profile_phases", ctypes.c_int, [_vp, _i32, _vp])
 _sig("snn_deliver_spikes", ctypes.c_int, [_vp, _vp, _i64, _vp, _vp])
 _sig("snn_deliver_spikes_static", ctypes.c_int, [_vp, _vp, _i64, _vp, _vp])
@@ -125,7 +126,7 @@ EXPORTS = ("snn_strerror", "snn_partition", "snn_routing_build", "snn_routing_in
            "snn_sim_params_default", "snn_sim_workspace_bytes", "snn_sim_create", "snn_step",
            "snn_sync_status", "snn_read_raster", "snn_read_currents", "snn_read_hashes",
            "snn_read_counts", "snn_read_state", "snn_read_inbox_pairs", "snn_state_bytes",
-           "snn_save_state", "snn_load_state", "snn_sim_reset", "snn_launches_per_step",
+           "snn_save_state", "snn_load_state", "snn_sim_reset", "snn_launches_per_step", "snn_launches",
            "snn_profile_phases", "snn_deliver_spikes", "snn_deliver_spikes_static",
            "snn_static_scratch_bytes", "snn_sim_destroy")
 
@@ -361,6 +362,10 @@ class Sim:
             _ck(_lib.snn_deliver_spikes(self.h, ids.data_ptr(), ids.numel(), out.data_ptr(),
                                         c.ctypes.data), "snn_deliver_spikes")
         return tuple(int(x) for x in c)
+
+    def launches(self, T: int) -> int:
+        """Kernel launches one step(T) issues."""
+        return int(_lib.snn_launches(self.h, int(T)))
 
     @property
     def launches_per_step(self) -> int:

@@ -85,6 +85,7 @@ extern "C" const char *snn_strerror(int code)
     case SNN_E_RANGE: return "network exceeds a layout limit";
     case SNN_E_STATE: return "invalid state for this call";
     case SNN_E_NODEV: return "no usable CUDA device";
+    case SNN_E_TIMEOUT: return "a bounded device-side wait gave up";
     default: return "unknown error";
     }
 }

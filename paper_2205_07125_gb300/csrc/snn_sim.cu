@@ -115,7 +115,7 @@ struct Layout {
     Region bucket, bucket_base, bucket_capv, bucket_cnt, inbox, inbox_base, inbox_capv, inbox_cnt;
     Region spk, raster_off, hash, cur_rec, counters, ctrl;
     Region fwd, fo_cnt;  // snn_deliver_spikes: global -> internal map, scratch counters
-    Region inbox_pre, piece;
+    Region piece, phase_ns;
     uint32_t piece_cap = 0;
     size_t total = 0;
     std::vector<uint64_t> bucket_base_h, inbox_base_h;
@@ -187,12 +187,11 @@ static int make_layout(const snn_routing *rt, const snn_sim_params *p, Layout &L
     place(L, L.bucket, sizeof(uint32_t) * (size_t)nb);
     place(L, L.bucket_base, sizeof(uint64_t) * (size_t)(rt->n_vn + 1));
     place(L, L.bucket_capv, sizeof(uint32_t) * (size_t)rt->n_vn);
-    place(L, L.bucket_cnt, sizeof(uint32_t) * kCntStride * (size_t)rt->n_vn);
+    place(L, L.bucket_cnt, 2 * sizeof(uint32_t) * kCntStride * (size_t)rt->n_vn);  // by step parity
     place(L, L.inbox, sizeof(uint64_t) * (size_t)ni);
     place(L, L.inbox_base, sizeof(uint64_t) * (size_t)(rt->P + 1));
     place(L, L.inbox_capv, sizeof(uint32_t) * (size_t)rt->P);
-    place(L, L.inbox_cnt, sizeof(uint32_t) * kCntStride * (size_t)rt->P);
-    place(L, L.inbox_pre, sizeof(uint32_t) * (size_t)(rt->P + 1));
+    place(L, L.inbox_cnt, 2 * sizeof(uint32_t) * kCntStride * (size_t)rt->P);  // by step parity
     place(L, L.piece, sizeof(unsigned long long) * (size_t)L.piece_cap);
     place(L, L.spk, sizeof(uint32_t) * (size_t)(p->raster_cap + M));
     place(L, L.raster_off, sizeof(long long) * (size_t)(p->raster_steps + 1));
@@ -200,6 +199,7 @@ static int make_layout(const snn_routing *rt, const snn_sim_params *p, Layout &L
     place(L, L.cur_rec, sizeof(int32_t) * (size_t)M * (size_t)p->cur_slots);
     place(L, L.fwd, rt->identity ? 0 : sizeof(uint32_t) * (size_t)M);
     place(L, L.fo_cnt, 64);
+    place(L, L.phase_ns, 2 * sizeof(unsigned long long));
     return SNN_OK;
 }
 
@@ -257,7 +257,13 @@ struct snn_sim {
     int64_t static_row_l1 = -1, static_row_l2 = -1;  // snn_deliver_spikes_static sizing
     unsigned grid_update = 1, grid_route = 1;
     bool vec = false;  // 4 neurons per thread with 16-byte loads (M % 4 == 0)
-    bool pdl = true;   // programmatic dependent launch between step kernels
+    bool pdl = true;       // programmatic dependent launch between step kernels
+    bool persist = false;  // one cooperative launch per snn_step (k_persist)
+    unsigned grid_persist = 1;
+    // bound on one grid-barrier wait of k_persist: a healthy barrier takes
+    // microseconds; past this the kernel records a timeout and returns
+    unsigned long long barrier_limit_ns = 1000000000ull;
+    int test_skip_arrival = 0;  // tests of the bounded wait (SNN_TEST_SKIP_BARRIER)
     std::vector<void *> pinned;
 };
 
@@ -333,7 +339,6 @@ static int reset_state(snn_sim *s)
     CK(cudaMemsetAsync(w + L.counters.off, 0, L.counters.bytes, st));
     CK(cudaMemsetAsync(w + L.bucket_cnt.off, 0, L.bucket_cnt.bytes, st));
     CK(cudaMemsetAsync(w + L.inbox_cnt.off, 0, L.inbox_cnt.bytes, st));
-    CK(cudaMemsetAsync(w + L.inbox_pre.off, 0, L.inbox_pre.bytes, st));
     if (L.raster_off.bytes) CK(cudaMemsetAsync(w + L.raster_off.off, 0, L.raster_off.bytes, st));
     if (L.hash.bytes) CK(cudaMemsetAsync(w + L.hash.off, 0, L.hash.bytes, st));
     if (L.cur_rec.bytes) CK(cudaMemsetAsync(w + L.cur_rec.off, 0, L.cur_rec.bytes, st));
@@ -351,9 +356,9 @@ constexpr int kPhases = 2;
 // Launch phase ph of a step.  With programmatic dependent launch each kernel
 // may be scheduled while the one before it drains; the kernels wait
 // (griddepcontrol.wait) before reading.
-static void launch_phase(snn_sim *s, int ph, cudaStream_t st)
+static void launch_phase(snn_sim *s, int ph, int k, cudaStream_t st)
 {
-    void (*fn)(const Dev) = nullptr;
+    void (*fn)(const Dev, int) = nullptr;
     unsigned grid = 1;
     if (ph == 0) {
         fn = s->vec ? k_update<true> : k_update<false>;
@@ -374,12 +379,12 @@ static void launch_phase(snn_sim *s, int ph, cudaStream_t st)
         cfg.attrs = attr;
         cfg.numAttrs = 1;
     }
-    cudaLaunchKernelEx(&cfg, fn, s->dev);
+    cudaLaunchKernelEx(&cfg, fn, s->dev, k);
 }
 
-static cudaError_t launch_step(snn_sim *s, cudaStream_t st)
+static cudaError_t launch_step(snn_sim *s, int k, cudaStream_t st)
 {
-    for (int ph = 0; ph < kPhases; ++ph) launch_phase(s, ph, st);
+    for (int ph = 0; ph < kPhases; ++ph) launch_phase(s, ph, k, st);
     return cudaGetLastError();
 }
 
@@ -388,7 +393,11 @@ static int capture(snn_sim *s, int steps, cudaGraphExec_t *out)
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t le = cudaSuccess;
-    for (int k = 0; k < steps && le == cudaSuccess; ++k) le = launch_step(s, s->cap_stream);
+    for (int k = 0; k < steps && le == cudaSuccess; ++k) le = launch_step(s, k, s->cap_stream);
+    if (le == cudaSuccess) {
+        k_advance<<<1, 1, 0, s->cap_stream>>>(s->dev.ctrl, steps);
+        le = cudaGetLastError();
+    }
     cudaError_t ce = cudaStreamEndCapture(s->cap_stream, &g);
     if (le != cudaSuccess || ce != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -454,6 +463,30 @@ extern "C" int snn_sim_create(const snn_network *net, const snn_routing *rt, con
         const int64_t blocks = (items + kThreads - 1) / kThreads;
         s->grid_update = (unsigned)std::max<int64_t>(1, blocks);  // one pass over the neurons
         s->grid_route = (unsigned)(sms * std::max(1, o3));
+        // persistent path: one cooperative launch, every block resident
+        // (SNN_PERSIST=0 selects the CUDA-graph path)
+        int coop = 0, op = 0;
+        const char *e = std::getenv("SNN_PERSIST");
+        if (!(e && e[0] == '0') &&
+            cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, s->device) == cudaSuccess && coop) {
+            const cudaError_t oe =
+                s->vec ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&op, k_persist<true>, kThreads, 0)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&op, k_persist<false>, kThreads, 0);
+            // SNN_PERSIST_BLOCKS_PER_SM lowers the resident blocks per SM (tuning)
+            const char *bps = std::getenv("SNN_PERSIST_BLOCKS_PER_SM");
+            if (bps && std::atoi(bps) > 0 && std::atoi(bps) < op) op = std::atoi(bps);
+            if (oe == cudaSuccess && op > 0) {
+                s->persist = true;
+                s->grid_persist = (unsigned)(sms * op);
+            }
+        }
+        cudaGetLastError();
+        // tests of the bounded barrier wait: a shorter bound, and block 0
+        // skipping its first arrival so that the others' wait runs out
+        const char *lim = std::getenv("SNN_BARRIER_LIMIT_NS");
+        if (lim && std::strtoull(lim, nullptr, 10) > 0) s->barrier_limit_ns = std::strtoull(lim, nullptr, 10);
+        const char *skip = std::getenv("SNN_TEST_SKIP_BARRIER");
+        s->test_skip_arrival = (skip && skip[0] == '1') ? 1 : 0;
     }
     if (cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
         delete s;
@@ -494,7 +527,6 @@ extern "C" int snn_sim_create(const snn_network *net, const snn_routing *rt, con
     d.inbox_base = (const unsigned long long *)(w + L.inbox_base.off);
     d.inbox_capv = (const uint32_t *)(w + L.inbox_capv.off);
     d.inbox_cnt = (uint32_t *)(w + L.inbox_cnt.off);
-    d.inbox_pre = (uint32_t *)(w + L.inbox_pre.off);
     d.piece = (unsigned long long *)(w + L.piece.off);
     d.piece_cap = L.piece_cap;
     d.spk = (uint32_t *)(w + L.spk.off);
@@ -539,9 +571,23 @@ extern "C" int snn_sim_create(const snn_network *net, const snn_routing *rt, con
     return SNN_OK;
 }
 
+static int launch_persist(snn_sim *s, int32_t T, const Dev &d)
+{
+    if (T <= 0) return SNN_OK;
+    int tt = T;
+    unsigned long long lim = s->barrier_limit_ns;
+    int skip = s->test_skip_arrival;
+    s->test_skip_arrival = 0;  // once: the test checks the first launch's status
+    void *args[] = {(void *)&d, (void *)&tt, (void *)&lim, (void *)&skip};
+    const void *fn = s->vec ? (const void *)k_persist<true> : (const void *)k_persist<false>;
+    CK(cudaLaunchCooperativeKernel(fn, dim3(s->grid_persist), dim3(kThreads), args, 0, s->stream));
+    return SNN_OK;
+}
+
 extern "C" int snn_step(snn_sim *s, int32_t T)
 {
     if (!s || T < 0) return SNN_E_ARG;
+    if (s->persist) return launch_persist(s, T, s->dev);
     if (!s->g1) {
         int rc = capture(s, 1, &s->g1);
         if (!rc && s->U > 1) rc = capture(s, s->U, &s->gU);
@@ -558,6 +604,21 @@ extern "C" int snn_profile_phases(snn_sim *s, int32_t T, double *phase_ms)
 {
     if (!s || T < 0 || !phase_ms) return SNN_E_ARG;
     for (int k = 0; k < kPhases; ++k) phase_ms[k] = 0.0;
+    if (s->persist) {
+        // block 0 sums each phase's span (phase start to the end of the grid
+        // barrier after it) with the GPU's global timer
+        Dev dp = s->dev;
+        dp.phase_ns = (unsigned long long *)(s->ws + s->L.phase_ns.off);
+        CK(cudaMemsetAsync(dp.phase_ns, 0, 2 * sizeof(unsigned long long), s->stream));
+        int rc = launch_persist(s, T, dp);
+        if (rc) return rc;
+        unsigned long long ns[2];
+        CK(cudaMemcpyAsync(ns, dp.phase_ns, sizeof(ns), cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+        phase_ms[0] = ns[0] * 1e-6;
+        phase_ms[1] = ns[1] * 1e-6;
+        return SNN_OK;
+    }
     if (!s->gP) {
         const int U = 16;
         s->pev.resize((size_t)U * (kPhases + 1));
@@ -573,10 +634,14 @@ extern "C" int snn_profile_phases(snn_sim *s, int32_t T, double *phase_ms)
             const unsigned fl = cudaEventRecordExternal;
             le = cudaEventRecordWithFlags(ev[0], st, fl);
             for (int ph = 0; ph < kPhases && le == cudaSuccess; ++ph) {
-                launch_phase(s, ph, st);
+                launch_phase(s, ph, k, st);
                 le = cudaEventRecordWithFlags(ev[ph + 1], st, fl);
             }
             if (le == cudaSuccess) le = cudaGetLastError();
+        }
+        if (le == cudaSuccess) {
+            k_advance<<<1, 1, 0, s->cap_stream>>>(s->dev.ctrl, U);
+            le = cudaGetLastError();
         }
         cudaError_t ce = cudaStreamEndCapture(s->cap_stream, &g);
         if (le != cudaSuccess || ce != cudaSuccess) {
@@ -748,6 +813,14 @@ extern "C" int snn_deliver_spikes_static(snn_sim *s, const uint32_t *ids, int64_
     return run_fanout(s, a, counts);
 }
 
+extern "C" int64_t snn_launches(const snn_sim *s, int32_t T)
+{
+    if (!s || T <= 0) return 0;
+    if (s->persist) return 1;
+    const int64_t graphs = (s->U > 1 ? T / s->U : 0) + (s->U > 1 ? T % s->U : T);
+    return (int64_t)kPhases * T + graphs;  // step kernels + one k_advance per graph
+}
+
 extern "C" int64_t snn_launches_per_step(const snn_sim *s)
 {
     return s ? kPhases : 0;
@@ -768,6 +841,7 @@ extern "C" int snn_sync_status(snn_sim *s)
     Ctrl c;
     int rc = read_ctrl(s, &c);
     if (rc) return rc;
+    if (c.status & kStTimeout) return SNN_E_TIMEOUT;
     if (c.status & (kStBucket | kStInbox)) return SNN_E_CAPACITY;
     return SNN_OK;
 }
@@ -889,7 +963,19 @@ extern "C" int snn_read_inbox_pairs(snn_sim *s, uint64_t *pairs, int64_t cap, in
     CK(cudaStreamSynchronize(s->stream));
     // filled inbox lengths of the last step, from its prefix sums
     std::vector<uint32_t> pre((size_t)rt->P + 1);
-    CK(cudaMemcpy(pre.data(), s->dev.inbox_pre, sizeof(uint32_t) * pre.size(), cudaMemcpyDeviceToHost));
+    {
+        // the last step's inbox fill counts (its step parity) and capacities
+        Ctrl c;
+        int rc = read_ctrl(s, &c);
+        if (rc) return rc;
+        const int pl = (int)((c.t + 1) & 1);  // parity of step t - 1
+        std::vector<uint32_t> cnt((size_t)rt->P * kCntStride);
+        CK(cudaMemcpy(cnt.data(), s->dev.inbox_cnt + (size_t)pl * rt->P * kCntStride,
+                      sizeof(uint32_t) * cnt.size(), cudaMemcpyDeviceToHost));
+        pre[0] = 0;
+        for (int32_t q = 0; q < rt->P; ++q)
+            pre[q + 1] = pre[q] + std::min(cnt[(size_t)q * kCntStride], L.inbox_cap_h[q]);
+    }
     int64_t tot = 0;
     for (int32_t q = 0; q < rt->P; ++q) {
         uint32_t m = pre[q + 1] - pre[q];

@@ -2,29 +2,36 @@
 //
 // The routing is the paper's two-level route (arXiv 2205.07125, Sec. IV.B);
 // the neuron model is LIF (Table I); the arithmetic follows the library's
-// documented readings (include/snn.h).
-//   k_update   a1 consume ring slot t mod D, Poisson drive (Philox4x32-10,
-//                 inverse CDF); a2 FP32 LIF update + threshold (no FMA,
-//                 fixed order); a3 warp-scan / block-scan spike compaction
-//                 into a block buffer and the step's spike list (4 neurons
-//                 per thread with 16-byte loads).  The block that found the
-//                 spikes then routes them, one warp per spike:
-//              a4 level-1 bucketing: the spike is appended to the bucket of
-//                 every destination VN in its level-1 row (one entry per VN:
-//                 deduplicated);
-//              a5 level-2 relay expansion: every (spike, VN) entry becomes an
-//                 inbox entry of each partition of that VN holding targets;
-//                 long segments are also queued as 128-synapse pieces.
-//                 The last block to finish writes the inbox prefix sums and
-//                 closes the step's bookkeeping.
-//   k_deliver  a6 long segments arrive cut into 128-synapse pieces, one
-//                 warp per piece with 4 streaming loads in flight per lane;
-//                 short segments (<= 8 synapses) are walked by one lane per
-//                 inbox entry (flattened over partitions); every synapse adds
-//                 its int16 weight with a 32-bit reduction into
-//                 ring[(t+d) mod D][target].
+// documented readings (include/snn.h).  A step has two phases:
+//   update_route  a1 consume ring slot t mod D, Poisson drive (Philox4x32-10,
+//                    inverse CDF); a2 FP32 LIF update + threshold (no FMA,
+//                    fixed order); a3 warp-scan / block-scan compaction of
+//                    the spikes into a block buffer and the step's spike
+//                    list (4 neurons per thread with 16-byte loads).  The
+//                    block that found the spikes routes them, one warp each:
+//                 a4 level-1 bucketing: the spike is appended to the bucket of
+//                    every destination VN in its level-1 row (one entry per
+//                    VN: deduplicated);
+//                 a5 level-2 relay expansion: every (spike, VN) entry becomes
+//                    an inbox entry of each partition of that VN holding
+//                    targets; long segments are also queued as 128-synapse
+//                    pieces.
+//   deliver       a6 every block takes the inbox prefix sums; pieces of long
+//                    segments go one warp per piece with 4 streaming loads in
+//                    flight per lane; short segments (<= 8 synapses) are
+//                    walked by one lane per inbox entry; every synapse adds
+//                    its int16 weight with a 32-bit reduction into
+//                    ring[(t+d) mod D][target].  Block 0 closes the step's
+//                    bookkeeping (raster offsets, counters).
 // The ring has D = max delay + 1 slots, so the slot consumed at step t is
-// never written by the deliveries of step t.
+// never written by the deliveries of step t.  Per-step counters are kept
+// twice, by step parity: step t fills parity t & 1 and clears the other
+// one, which step t - 1 used and step t + 1 will fill, so no block has to
+// close a phase.
+//
+// Two ways to run the phases: k_persist, one cooperative launch for T steps
+// with a grid barrier after each phase (bounded waits), and the CUDA-graph
+// path, k_update / k_deliver per step with programmatic dependent launch.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -35,7 +42,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kPTab = 32;
-constexpr int kSpkBuf = 1024;   // spikes a k_update block buffers before flushing
+constexpr int kSpkBuf = 1024;   // spikes a block buffers before flushing
 constexpr int kShortSeg = 8;    // segments up to this length are walked by one lane
 constexpr int kPiece = 128;     // longer segments are cut into pieces of this many synapses
 constexpr int kPreMax = 4097;   // staged prefix entries (P <= 4096)
@@ -44,25 +51,23 @@ constexpr int kPreMax = 4097;   // staged prefix entries (P <= 4096)
 constexpr int kCntStride = 32;
 
 // status bits
-constexpr uint32_t kStBucket = 1u, kStInbox = 2u, kStRaster = 4u;
+constexpr uint32_t kStBucket = 1u, kStInbox = 2u, kStRaster = 4u, kStTimeout = 8u;
 
 // counter slots
 enum { C_STEPS = 0, C_SPIKES, C_EVENTS, C_L1_LOCAL, C_L1_XVN, C_L2_BASE /* + cls (4) */, C_N = 16 };
 
+// The atomically updated words each own a 128-byte line: blocks spinning on
+// the barrier generation must not share a line with the hot counters.
 struct Ctrl {
-    long long t;          // next step to update
-    long long t_cur;      // step being routed and delivered
-    long long head;       // raster write head
-    long long spk_base;   // first spike of step t_cur in spk[]
-    long long rec_steps;  // steps whose raster offsets are valid
-    unsigned int S_acc;   // spikes found so far in the running update
-    unsigned int S_cur;   // spikes of step t_cur
-    unsigned int blocks_done;
+    long long t;              // next step to run
+    long long head[2];        // raster write head at the start of a step, by step parity
+    long long rec_steps;      // steps whose raster offsets are valid
     unsigned int status;
     int rec_on;
-    unsigned int n_piece;      // long-segment pieces queued so far in the running update
-    unsigned int n_piece_cur;  // pieces of step t_cur, for k_deliver
-    unsigned int pad;
+    alignas(128) unsigned int S_acc[2];    // spikes of a step, by parity
+    alignas(128) unsigned int n_piece[2];  // long-segment pieces queued in a step, by parity
+    alignas(128) unsigned int bar_count;   // grid barrier arrivals (k_persist)
+    alignas(128) unsigned int bar_gen;     // grid barrier generation (k_persist)
 };
 
 struct __align__(16) DevL2 {
@@ -91,12 +96,11 @@ struct Dev {
     uint32_t *bucket;
     const unsigned long long *bucket_base;
     const uint32_t *bucket_capv;
-    uint32_t *bucket_cnt;
+    uint32_t *bucket_cnt;       // [2][n_vn * kCntStride], by step parity
     unsigned long long *inbox;
     const unsigned long long *inbox_base;
     const uint32_t *inbox_capv;
-    uint32_t *inbox_cnt;
-    uint32_t *inbox_pre;    // [P+1] prefix of the filled inbox lengths
+    uint32_t *inbox_cnt;        // [2][P * kCntStride], by step parity
     unsigned long long *piece;  // pieces of long segments: offset << 8 | length
     unsigned int piece_cap;
     // records
@@ -105,6 +109,7 @@ struct Dev {
     unsigned long long *hash;
     int32_t *cur_rec;
     unsigned long long *counters;
+    unsigned long long *phase_ns;  // [2] summed phase times of k_persist (profiling)
     Ctrl *ctrl;
     // scalars
     long long M;
@@ -117,7 +122,19 @@ struct Dev {
     uint32_t th32[kPTab];   // finite Poisson thresholds (the closing 2^32 is implied)
 };
 
-__device__ __forceinline__ uint32_t philox_w0(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1)
+__device__ __forceinline__ uint32_t *bucket_cnt_of(const Dev &d, int p)
+{
+    return d.bucket_cnt + (size_t)p * (size_t)d.n_vn * kCntStride;
+}
+
+__device__ __forceinline__ uint32_t *inbox_cnt_of(const Dev &d, int p)
+{
+    return d.inbox_cnt + (size_t)p * (size_t)d.P * kCntStride;
+}
+
+// Philox4x32-10 block of counter (c0, c1, 0, 0): the drive word of neuron j
+// at step t is word (j mod 4) of the block (j div 4, t).
+__device__ __forceinline__ uint4 philox4(uint32_t k0, uint32_t k1, uint32_t c0, uint32_t c1)
 {
     uint32_t x0 = c0, x1 = c1, x2 = 0u, x3 = 0u;
 #pragma unroll
@@ -132,7 +149,12 @@ __device__ __forceinline__ uint32_t philox_w0(uint32_t k0, uint32_t k1, uint32_t
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
     }
-    return x0;
+    return make_uint4(x0, x1, x2, x3);
+}
+
+__device__ __forceinline__ uint32_t uint4_word(const uint4 &w, uint32_t k)
+{
+    return k == 0 ? w.x : k == 1 ? w.y : k == 2 ? w.z : w.w;
 }
 
 __device__ __forceinline__ unsigned long long mix64(unsigned long long z)
@@ -150,13 +172,56 @@ __device__ __forceinline__ T warp_sum(T v)
     return v;
 }
 
-// Programmatic dependent launch: every step kernel waits for the grid before
-// it (all of its writes visible) before touching shared state, and lets the
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Programmatic dependent launch (graph path): wait for the grid before this
+// one (all of its writes visible) before touching shared state, and let the
 // next grid be scheduled early.  Both are no-ops for a plain launch.
 __device__ __forceinline__ void pdl_enter()
 {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Grid-wide barrier of k_persist (all blocks co-resident: cooperative
+// launch).  The wait is bounded: past `limit_ns` the block records
+// kStTimeout and gives up.  Returns false when this or any other block gave
+// up, after which every block leaves the kernel.
+__device__ __forceinline__ bool grid_sync(Ctrl *c, unsigned long long limit_ns, bool arrive = true)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int *gen = &c->bar_gen;
+        const unsigned int g = *gen;
+        __threadfence();
+        int ok = 1;
+        if (arrive && atomicAdd(&c->bar_count, 1u) == gridDim.x - 1) {
+            c->bar_count = 0;
+            __threadfence();
+            atomicAdd(&c->bar_gen, 1u);
+        } else {
+            const unsigned long long deadline = global_ns() + limit_ns;
+            while (*gen == g) {
+                if (global_ns() > deadline) {
+                    atomicOr(&c->status, kStTimeout);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        if (*(volatile unsigned int *)&c->status & kStTimeout) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
 }
 
 // Index k with pre[k] <= x < pre[k+1] (pre nondecreasing, pre[0] = 0 <= x < pre[n]).
@@ -169,34 +234,6 @@ __device__ __forceinline__ int prefix_find(const uint32_t *pre, int n, uint32_t 
         else hi = mid - 1;
     }
     return lo;
-}
-
-// a1 + a2 for one neuron: returns true on a spike.
-// th: the Poisson thresholds staged in shared memory (lanes index them
-// divergently, which the kernel-parameter bank would serialise).
-__device__ __forceinline__ bool lif_neuron(const Dev &d, const uint32_t *th, uint32_t g, uint32_t t, int32_t irec,
-                                           float &v, uint32_t &r)
-{
-    const uint32_t u = philox_w0(d.key0, d.key1, g, t);
-    int k = 0;
-    while (k < d.th_fin && u >= th[k]) ++k;
-    const int32_t I = (int32_t)((uint32_t)irec + (uint32_t)k * (uint32_t)d.w_ext + (uint32_t)d.i_bias);
-    if (r > 0) {
-        r -= 1;
-        v = d.v_reset;
-        return false;
-    }
-    const float uu = __fsub_rn(v, d.e_l);
-    const float au = __fmul_rn(d.alpha, uu);
-    v = __fadd_rn(d.e_l, au);
-    const float x = __fmul_rn(__int2float_rn(I), 0.0009765625f);
-    v = __fadd_rn(v, x);
-    if (v >= d.v_th) {
-        v = d.v_reset;
-        r = (uint32_t)d.t_ref;
-        return true;
-    }
-    return false;
 }
 
 // Exclusive prefix of min(cnt[k * kCntStride], cap[k]) into pre[0..n] by one block.
@@ -229,6 +266,34 @@ __device__ __forceinline__ void block_prefix(const uint32_t *cnt, const uint32_t
     __syncthreads();
 }
 
+// a1 + a2 for one neuron: returns true on a spike.
+// th: the Poisson thresholds staged in shared memory (lanes index them
+// divergently, which the kernel-parameter bank would serialise).
+// u: the neuron's drive word.
+__device__ __forceinline__ bool lif_neuron(const Dev &d, const uint32_t *th, uint32_t u, int32_t irec, float &v,
+                                           uint32_t &r)
+{
+    int k = 0;
+    while (k < d.th_fin && u >= th[k]) ++k;
+    const int32_t I = (int32_t)((uint32_t)irec + (uint32_t)k * (uint32_t)d.w_ext + (uint32_t)d.i_bias);
+    if (r > 0) {
+        r -= 1;
+        v = d.v_reset;
+        return false;
+    }
+    const float uu = __fsub_rn(v, d.e_l);
+    const float au = __fmul_rn(d.alpha, uu);
+    v = __fadd_rn(d.e_l, au);
+    const float x = __fmul_rn(__int2float_rn(I), 0.0009765625f);
+    v = __fadd_rn(v, x);
+    if (v >= d.v_th) {
+        v = d.v_reset;
+        r = (uint32_t)d.t_ref;
+        return true;
+    }
+    return false;
+}
+
 // Per-thread tallies of the routing done by one block.
 struct RouteTally {
     unsigned int l1_loc = 0, l1_xvn = 0, ovf = 0;
@@ -236,10 +301,13 @@ struct RouteTally {
 };
 
 // a4 + a5 for the n spikes buffered in s_spk, one warp per spike (all
-// threads of the block call this).
-__device__ __forceinline__ void route_spikes(const Dev &d, const uint32_t *s_spk, unsigned int n, RouteTally &rt)
+// threads of the block call this); counters of step parity p.
+__device__ __forceinline__ void route_spikes(const Dev &d, int p, const uint32_t *s_spk, unsigned int n,
+                                             RouteTally &rt)
 {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t *bcnt = bucket_cnt_of(d, p);
+    uint32_t *icnt = inbox_cnt_of(d, p);
     for (unsigned int s = wid; s < n; s += kThreads / 32) {
         const uint32_t i = s_spk[s];
         const uint16_t h = d.src_vn[i];
@@ -247,7 +315,7 @@ __device__ __forceinline__ void route_spikes(const Dev &d, const uint32_t *s_spk
         // a4: one level-1 entry per destination VN, appended to that VN's bucket
         for (uint32_t e = e0 + lane; e < e1; e += 32u) {
             const uint16_t g = d.l1_vn[e];
-            const unsigned int pos = atomicAdd(&d.bucket_cnt[(int)g * kCntStride], 1u);
+            const unsigned int pos = atomicAdd(&bcnt[(int)g * kCntStride], 1u);
             if (pos < d.bucket_capv[g]) d.bucket[d.bucket_base[g] + pos] = e;
             else rt.ovf |= kStBucket;
             if (g == h) ++rt.l1_loc;
@@ -262,16 +330,10 @@ __device__ __forceinline__ void route_spikes(const Dev &d, const uint32_t *s_spk
             DevL2 l;
             l.off = 0;
             l.len = 0;
-            if (f < f1) {
-                l = d.l2[f];
-                const unsigned int pos = atomicAdd(&d.inbox_cnt[(int)l.q * kCntStride], 1u);
-                if (pos < d.inbox_capv[l.q])
-                    d.inbox[d.inbox_base[l.q] + pos] = (l.off << kLenBits) | (unsigned long long)l.len;
-                else
-                    rt.ovf |= kStInbox;
-                rt.cls[l.cls & 3]++;
-            }
-            // long segments are also cut into pieces for an even delivery
+            l.q = 0;
+            if (f < f1) l = d.l2[f];
+            // long segments are also cut into pieces for an even delivery;
+            // their reservation is issued next to the inbox one
             const unsigned int np = l.len > (unsigned int)kShortSeg ? (l.len + kPiece - 1) / kPiece : 0u;
             unsigned int incl = np;
 #pragma unroll
@@ -280,9 +342,21 @@ __device__ __forceinline__ void route_spikes(const Dev &d, const uint32_t *s_spk
                 if (lane >= o) incl += y;
             }
             const unsigned int ptot = __shfl_sync(0xFFFFFFFFu, incl, 31);
+            unsigned int pos = 0, pb = 0;
+            if (f < f1) pos = atomicAdd(&icnt[(int)l.q * kCntStride], 1u);
+            if (ptot && lane == 0) pb = atomicAdd(&d.ctrl->n_piece[p], ptot);
+            if (f < f1) {
+                if (pos < d.inbox_capv[l.q])
+                    d.inbox[d.inbox_base[l.q] + pos] = (l.off << kLenBits) | (unsigned long long)l.len;
+                else
+                    rt.ovf |= kStInbox;
+                // per-class tallies without a dynamically indexed (local-memory) array
+                rt.cls[0] += l.cls == 0;
+                rt.cls[1] += l.cls == 1;
+                rt.cls[2] += l.cls == 2;
+                rt.cls[3] += l.cls == 3;
+            }
             if (ptot) {
-                unsigned int pb = 0;
-                if (lane == 0) pb = atomicAdd(&d.ctrl->n_piece, ptot);
                 pb = __shfl_sync(0xFFFFFFFFu, pb, 0) + incl - np;
                 for (unsigned int k = 0; k < np; ++k, ++pb) {
                     const unsigned int len = min((unsigned int)kPiece, l.len - k * kPiece);
@@ -294,17 +368,18 @@ __device__ __forceinline__ void route_spikes(const Dev &d, const uint32_t *s_spk
     }
 }
 
-// Route the block's buffered spikes and move them to the step's spike list
-// (all threads call).
-__device__ __forceinline__ void flush_spikes(const Dev &d, long long head, uint32_t *s_spk, unsigned int &s_n,
-                                             unsigned int &s_gbase, int &s_routed, RouteTally &rt)
+// Route the block's buffered spikes and append them to the step's spike
+// list (all threads call).
+__device__ __forceinline__ void flush_spikes(const Dev &d, int p, long long head, uint32_t *s_spk,
+                                             unsigned int &s_n, unsigned int &s_gbase, int &s_routed,
+                                             RouteTally &rt)
 {
     __syncthreads();
     const unsigned int n = s_n;
     if (n == 0) return;
-    route_spikes(d, s_spk, n, rt);
+    route_spikes(d, p, s_spk, n, rt);
     if (threadIdx.x == 0) {
-        s_gbase = atomicAdd(&d.ctrl->S_acc, n);
+        s_gbase = atomicAdd(&d.ctrl->S_acc[p], n);
         s_routed = 1;
     }
     __syncthreads();
@@ -317,21 +392,19 @@ __device__ __forceinline__ void flush_spikes(const Dev &d, long long head, uint3
 
 // ---------------------------------------------------------------- a1-a5
 template <bool VEC>
-__global__ void __launch_bounds__(kThreads) k_update(const Dev d)
+__device__ __forceinline__ void update_route(const Dev &d, long long t)
 {
     __shared__ uint32_t s_spk[kSpkBuf];
     __shared__ unsigned int s_wsum[kThreads / 32];
     __shared__ unsigned int s_n, s_tot, s_gbase;
-    __shared__ int s_flush, s_last, s_routed;
+    __shared__ int s_flush, s_routed;
     __shared__ unsigned long long s_h[2][kThreads / 32];
     __shared__ unsigned int s_tally[kThreads / 32][6];
     __shared__ uint32_t s_th[kPTab];
-    if (threadIdx.x < kPTab) s_th[threadIdx.x] = d.th32[threadIdx.x];
 
-    pdl_enter();
     Ctrl *c = d.ctrl;
-    const long long t = c->t;
-    const long long head = c->head;
+    const int p = (int)(t & 1);
+    const long long head = c->head[p];
     const int slot = (int)(t % d.D);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const bool do_hash = t < d.hash_steps;
@@ -340,6 +413,17 @@ __global__ void __launch_bounds__(kThreads) k_update(const Dev d)
     int32_t *cur = do_cur ? d.cur_rec + (t / d.cur_every) * d.M : nullptr;
     constexpr int NPT = VEC ? 4 : 1;
     const long long nitem = VEC ? d.M / 4 : d.M;
+    if (blockIdx.x == 0) {
+        // clear the other parity: step t - 1 is done with it, step t + 1 fills it
+        uint32_t *b1 = bucket_cnt_of(d, p ^ 1), *i1 = inbox_cnt_of(d, p ^ 1);
+        for (int x = threadIdx.x; x < d.n_vn; x += kThreads) b1[x * kCntStride] = 0;
+        for (int x = threadIdx.x; x < d.P; x += kThreads) i1[x * kCntStride] = 0;
+        if (threadIdx.x == 0) {
+            c->S_acc[p ^ 1] = 0;
+            c->n_piece[p ^ 1] = 0;
+        }
+    }
+    if (threadIdx.x < kPTab) s_th[threadIdx.x] = d.th32[threadIdx.x];
     if (threadIdx.x == 0) {
         s_n = 0;
         s_routed = 0;
@@ -379,10 +463,17 @@ __global__ void __launch_bounds__(kThreads) k_update(const Dev d)
             }
             uint32_t r_out = 0;
 #pragma unroll
+            // one Philox block serves the four neurons of a quad in the
+            // global order; a reordering map needs a block per neuron
+            uint4 wq = make_uint4(0u, 0u, 0u, 0u);
+            if (VEC && !d.gid) wq = philox4(d.key0, d.key1, (uint32_t)(j0 >> 2), (uint32_t)t);
             for (int k = 0; k < NPT; ++k) {
                 const uint32_t g = d.gid ? d.gid[j0 + k] : (uint32_t)(j0 + k);
+                uint32_t u;
+                if (VEC && !d.gid) u = uint4_word(wq, (uint32_t)k);
+                else u = uint4_word(philox4(d.key0, d.key1, g >> 2, (uint32_t)t), g & 3u);
                 uint32_t r = (r4 >> (8 * k)) & 0xFFu;
-                if (lif_neuron(d, s_th, g, (uint32_t)t, ii[k], vv[k], r)) m |= 1u << k;
+                if (lif_neuron(d, s_th, u, ii[k], vv[k], r)) m |= 1u << k;
                 r_out |= r << (8 * k);
                 if (do_hash) {
                     hc += mix64(((unsigned long long)g << 32) | (uint32_t)ii[k]);
@@ -419,14 +510,14 @@ __global__ void __launch_bounds__(kThreads) k_update(const Dev d)
                 s_flush = (s_n + tot > (unsigned int)kSpkBuf);
             }
             __syncthreads();
-            if (s_flush) flush_spikes(d, head, s_spk, s_n, s_gbase, s_routed, rt);
+            if (s_flush) flush_spikes(d, p, head, s_spk, s_n, s_gbase, s_routed, rt);
             unsigned int pos = s_n + s_wsum[wid] + x - cnt;
             for (unsigned int mm = m; mm; mm &= mm - 1u) s_spk[pos++] = (uint32_t)(j0 + __ffs(mm) - 1);
             __syncthreads();
             if (threadIdx.x == 0) s_n += s_tot;
         }
     }
-    flush_spikes(d, head, s_spk, s_n, s_gbase, s_routed, rt);
+    flush_spikes(d, p, head, s_spk, s_n, s_gbase, s_routed, rt);
     if (do_hash) {
         hc = warp_sum(hc);
         hv = warp_sum(hv);
@@ -447,8 +538,7 @@ __global__ void __launch_bounds__(kThreads) k_update(const Dev d)
     }
     __syncthreads();
     if (s_routed) {
-        // message tallies of the routed spikes; every routing thread fences its
-        // atomics before the block reports done
+        // message tallies of the routed spikes
         unsigned int v[6] = {rt.l1_loc, rt.l1_xvn, rt.cls[0], rt.cls[1], rt.cls[2], rt.cls[3]};
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
@@ -456,52 +546,13 @@ __global__ void __launch_bounds__(kThreads) k_update(const Dev d)
             if (lane == 0) s_tally[wid][k] = v[k];
         }
         if (rt.ovf) atomicOr(&c->status, rt.ovf);
-        __threadfence();
         __syncthreads();
         if (threadIdx.x < 6) {
             unsigned long long a = 0;
             for (int w = 0; w < kThreads / 32; ++w) a += s_tally[w][threadIdx.x];
-            const int slot6[6] = {C_L1_LOCAL, C_L1_XVN, C_L2_BASE, C_L2_BASE + 1, C_L2_BASE + 2, C_L2_BASE + 3};
-            if (a) atomicAdd(&d.counters[slot6[threadIdx.x]], a);
+            // slots C_L1_LOCAL, C_L1_XVN, C_L2_BASE + 0..3 are consecutive
+            if (a) atomicAdd(&d.counters[C_L1_LOCAL + threadIdx.x], a);
         }
-    }
-    // the last block to finish closes the step: inbox prefix sums for
-    // k_deliver, counters reset for the next step
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        s_last = (atomicAdd(&c->blocks_done, 1u) == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    block_prefix(d.inbox_cnt, d.inbox_capv, d.inbox_pre, d.P);
-    for (int x = threadIdx.x; x < d.n_vn; x += kThreads) d.bucket_cnt[x * kCntStride] = 0;
-    for (int x = threadIdx.x; x < d.P; x += kThreads) d.inbox_cnt[x * kCntStride] = 0;
-    if (threadIdx.x == 0) {
-        const unsigned int S = atomicAdd(&c->S_acc, 0u);
-        c->t_cur = t;
-        c->S_cur = S;
-        c->spk_base = head;
-        long long h = head;
-        if (c->rec_on) {
-            if (t < d.raster_steps && head + S <= d.raster_cap) {
-                h = head + S;
-                d.raster_off[t + 1] = h;
-                c->rec_steps = t + 1;
-            } else {
-                c->rec_on = 0;
-                c->status |= kStRaster;
-            }
-        }
-        c->head = h;
-        c->t = t + 1;
-        c->S_acc = 0;
-        c->blocks_done = 0;
-        c->n_piece_cur = atomicAdd(&c->n_piece, 0u);
-        c->n_piece = 0;
-        d.counters[C_STEPS] += 1ull;
-        d.counters[C_SPIKES] += S;
     }
 }
 
@@ -514,23 +565,47 @@ __device__ __forceinline__ void deliver_one(const Dev &d, int tm, unsigned long 
     atomicAdd(&d.ring[(long long)sl * d.M + (td & kTgtMask)], w);
 }
 
+// Close step t (one thread): raster offsets, the next step's write head,
+// step and spike counters.
+__device__ __forceinline__ void close_step(const Dev &d, long long t)
+{
+    Ctrl *c = d.ctrl;
+    const int p = (int)(t & 1);
+    const unsigned int S = *(volatile unsigned int *)&c->S_acc[p];
+    long long h = c->head[p];
+    if (c->rec_on) {
+        if (t < d.raster_steps && h + S <= d.raster_cap) {
+            h += S;
+            d.raster_off[t + 1] = h;
+            c->rec_steps = t + 1;
+        } else {
+            c->rec_on = 0;
+            c->status |= kStRaster;
+        }
+    }
+    c->head[p ^ 1] = h;
+    d.counters[C_STEPS] += 1ull;
+    d.counters[C_SPIKES] += S;
+}
+
 // ---------------------------------------------------------------- a6
 // Work items: the pieces of long segments (one warp each, 4 synapses per
 // lane, all loads in flight before the reductions), then chunks of 32 inbox
 // entries whose short segments are walked by their lane.
-__global__ void __launch_bounds__(kThreads) k_deliver(const Dev d)
+__device__ __forceinline__ void deliver(const Dev &d, long long t)
 {
     __shared__ uint32_t s_pre[kPreMax];
     __shared__ unsigned long long s_ev;
-    pdl_enter();
-    const int np = d.P + 1;
-    for (int k = threadIdx.x; k < np; k += kThreads) s_pre[k] = d.inbox_pre[k];
+    const int p = (int)(t & 1);
+    block_prefix(inbox_cnt_of(d, p), d.inbox_capv, s_pre, d.P);
     if (threadIdx.x == 0) s_ev = 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) close_step(d, t);
     __syncthreads();
+    const int np = d.P + 1;
     const uint32_t n2 = s_pre[d.P];
-    const unsigned int npc = min(d.ctrl->n_piece_cur, d.piece_cap);
+    const unsigned int npc = min(*(volatile unsigned int *)&d.ctrl->n_piece[p], d.piece_cap);
     const uint32_t items = npc + (n2 + 31u) / 32u;
-    const int tm = (int)(d.ctrl->t_cur % d.D);
+    const int tm = (int)(t % d.D);
     const int lane = threadIdx.x & 31;
     const uint32_t nw = (gridDim.x * kThreads) >> 5;
     unsigned long long ev = 0;
@@ -577,6 +652,67 @@ __global__ void __launch_bounds__(kThreads) k_deliver(const Dev d)
     if (lane == 0 && ev) atomicAdd(&s_ev, ev);
     __syncthreads();
     if (threadIdx.x == 0 && s_ev) atomicAdd(&d.counters[C_EVENTS], s_ev);
+}
+
+// ---------------------------------------------------------------- graph path
+// Step t = ctrl->t + k of a captured graph; k_advance moves ctrl->t past the
+// graph's steps at its end.
+template <bool VEC>
+__global__ void __launch_bounds__(kThreads) k_update(const Dev d, int k)
+{
+    pdl_enter();
+    update_route<VEC>(d, d.ctrl->t + k);
+}
+
+__global__ void __launch_bounds__(kThreads) k_deliver(const Dev d, int k)
+{
+    pdl_enter();
+    deliver(d, d.ctrl->t + k);
+}
+
+__global__ void k_advance(Ctrl *c, int steps)
+{
+    c->t += steps;
+}
+
+// ---------------------------------------------------------------- persistent
+// T steps in one cooperative launch: update_route, barrier, deliver, barrier.
+// Every wait is bounded (limit_ns per barrier); a timeout ends the run with
+// kStTimeout in the status word.  With phase_ns set, block 0 sums the time of
+// each phase (from the start of a phase to the end of the barrier after it).
+// skip_arrival (tests of the bounded wait only): block 0 waits at the first
+// barrier without arriving, so every block's wait runs out.
+template <bool VEC>
+__global__ void __launch_bounds__(kThreads, 4) k_persist(const Dev d, int T, unsigned long long limit_ns,
+                                                         int skip_arrival)
+{
+    Ctrl *c = d.ctrl;
+    const long long t0 = c->t;
+    int done = 0;
+    unsigned long long ns[2] = {0, 0};
+    const bool prof = d.phase_ns != nullptr && blockIdx.x == 0 && threadIdx.x == 0;
+    for (int s = 0; s < T; ++s) {
+        const long long t = t0 + s;
+        const unsigned long long a = prof ? global_ns() : 0;
+        update_route<VEC>(d, t);
+        if (!grid_sync(c, limit_ns, !(skip_arrival && s == 0 && blockIdx.x == 0))) break;
+        const unsigned long long b = prof ? global_ns() : 0;
+        deliver(d, t);
+        if (!grid_sync(c, limit_ns)) break;
+        if (prof) {
+            const unsigned long long e = global_ns();
+            ns[0] += b - a;
+            ns[1] += e - b;
+        }
+        ++done;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        c->t = t0 + done;
+        if (prof) {
+            d.phase_ns[0] += ns[0];
+            d.phase_ns[1] += ns[1];
+        }
+    }
 }
 
 }  // namespace

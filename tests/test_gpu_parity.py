@@ -82,11 +82,19 @@ def _compare(sim, o, T, rec, t0=0):
     return c, r
 
 
-def test_tiny_full_run(snn):
+@pytest.fixture(params=["persistent", "graph"])
+def path(request, monkeypatch):
+    """Run a test on the persistent kernel and on the CUDA-graph path."""
+    monkeypatch.setenv("SNN_PERSIST", "1" if request.param == "persistent" else "0")
+    return request.param
+
+
+def test_tiny_full_run(snn, path):
     """4,096 neurons, 4 partitions over 2 VNs, 1,000 steps: everything bit-exact."""
     cfg = synth.TINY
     g = synth.make_network(cfg)
     sim, o, rec, _ = _run_pair(snn, g, cfg, cfg.steps, cfg.P, cfg.n_vn, cur_every=50)
+    assert (sim.launches(10) == 1) == (path == "persistent")
     sim.step(cfg.steps)
     c, _ = _compare(sim, o, cfg.steps, rec)
     assert sim.sync_status() == 0
@@ -95,7 +103,7 @@ def test_tiny_full_run(snn):
     assert st["max_rel_err"] <= 1e-5
 
 
-def test_tiny_greedy_partition_and_grouping(snn):
+def test_tiny_greedy_partition_and_grouping(snn, path):
     """Algorithm 1 + Algorithm 2 mapping: neurons reordered internally, ids stay global."""
     cfg = synth.TINY
     g = synth.make_network(cfg)
@@ -106,7 +114,7 @@ def test_tiny_greedy_partition_and_grouping(snn):
 
 
 @pytest.mark.parametrize("spg", [1, 7, 32])
-def test_locality_delays_several_tiles(snn, spg):
+def test_locality_delays_several_tiles(snn, spg, path):
     """Locality mix and delays 1..8 over 64 partitions / 16 VNs, several graph unrollings."""
     cfg = synth.SCALE.scaled(M=1 << 16, seed=41)
     g = synth.make_network(cfg)
@@ -115,7 +123,7 @@ def test_locality_delays_several_tiles(snn, spg):
     _compare(sim, o, 150, rec)
 
 
-def test_ragged_sizes_and_uneven_partitions(snn):
+def test_ragged_sizes_and_uneven_partitions(snn, path):
     """M not a multiple of the block size, uneven greedy partitions, 3 VNs of 1."""
     cfg = synth.NetConfig(name="ragged", M=1000 + 7, P=3, n_vn=3, K=37, uniform_all=True, dmax=4,
                           seed=99, dyn=synth.Dynamics(drive_lambda=1.1, w_ext=120, drive_seed=9))
@@ -143,7 +151,7 @@ def test_degenerate_networks(snn):
     assert c2["spikes"] == 0
 
 
-def test_step_in_chunks_equals_one_call(snn):
+def test_step_in_chunks_equals_one_call(snn, path):
     cfg = synth.TINY
     g = synth.make_network(cfg)
     sim, o, rec, _ = _run_pair(snn, g, cfg, 200, cfg.P, cfg.n_vn, steps_per_graph=16)
@@ -172,7 +180,7 @@ def test_capacity_overflow_is_reported(snn):
     assert sim.sync_status() == 0
 
 
-def test_checkpoint_resume_bit_exact(snn):
+def test_checkpoint_resume_bit_exact(snn, path):
     cfg = synth.SCALE.scaled(M=1 << 15, seed=17)
     g = synth.make_network(cfg)
     net = snn.Network.from_synth(g)
@@ -207,3 +215,32 @@ def test_reset_replays_identically(snn):
     sim.step(300)
     b = sim.read_raster(0, 300), sim.read_hashes(0, 300), sim.read_counts()
     assert np.array_equal(a[0][0], b[0][0]) and np.array_equal(a[1][0], b[1][0]) and a[2] == b[2]
+
+
+def test_barrier_wait_is_bounded(snn, monkeypatch):
+    """A grid barrier whose wait cannot complete gives up and reports a timeout.
+
+    Block 0 skips its first arrival (test switch), so the other blocks' wait
+    runs out after the shortened bound; the host reads SNN_E_TIMEOUT and the
+    context stays usable: a reset sim steps correctly afterwards.
+    """
+    monkeypatch.setenv("SNN_PERSIST", "1")
+    monkeypatch.setenv("SNN_BARRIER_LIMIT_NS", "20000000")  # 20 ms
+    monkeypatch.setenv("SNN_TEST_SKIP_BARRIER", "1")
+    cfg = synth.TINY
+    g = synth.make_network(cfg)
+    net = snn.Network.from_synth(g)
+    rt = snn.Routing(net, oracle.partition_planted(g.M, 4), 4, 2)
+    sim = snn.Sim(net, rt, snn.sim_params(cfg.dyn), device="cuda:0")
+    if sim.launches(10) != 1:
+        pytest.skip("no cooperative launch on this device")
+    sim.step(50)
+    assert sim.sync_status() == -8  # SNN_E_TIMEOUT
+    _, _, t = sim.read_state()
+    assert t < 50
+    monkeypatch.delenv("SNN_TEST_SKIP_BARRIER")
+    sim.reset()
+    sim.step(20)
+    assert sim.sync_status() == 0
+    _, _, t = sim.read_state()
+    assert t == 20

@@ -35,7 +35,7 @@ def test_library_exports_every_declared_call(snn):
 
 
 def test_strerror_names_codes(snn):
-    for code in range(0, -8, -1):
+    for code in range(0, -9, -1):
         s = snn._lib_strerror(code).decode()
         assert s and s != "unknown error"
 
