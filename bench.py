@@ -214,27 +214,28 @@ def run_ours(args):
     assert dc["steps"] == K
     events_all, ms_max, spikes_all = reduce_over_ranks(dist, float(dc["events"]), ms, float(dc["spikes"]))
 
-    # per-phase CUDA-event times from an instrumented graph over more steps
+    # time split of a step over more steps: the step's work and the wait for
+    # the other blocks (persistent path: block 0's global-timer stamps; graph
+    # path: CUDA events around every step kernel, no separate wait)
     NP = min(K, 2048)
     ca = sim.read_counts()
     phase_ms = sim.profile_phases(NP)
     cb = sim.read_counts()
     dp = {k: cb[k] - ca[k] for k in cb}
     pb4 = phase_bytes(cfg.M, dp["steps"], dp, not info["identity_order"])
-    pbytes = [pb4[0] + pb4[1] + pb4[2], pb4[3]]  # the update kernel also routes (a4, a5)
-    names = ["update_route", "deliver"]
-    kernel_names = ["k_update", "k_deliver"]
-    phases = {}
-    for n, kn, t_ms, b in zip(names, kernel_names, phase_ms, pbytes):
-        phases[n] = {"kernel": kn, "ms_per_step": t_ms / NP, "bytes_per_step": b / NP,
-                     "gbs": (b / (t_ms * 1e-3) / 1e9) if t_ms > 0 else None,
-                     "share": t_ms / max(1e-12, sum(phase_ms))}
-    print("[bench] timed %.3f ms for %d steps; phases ms/step %s" % (
+    persistent = sim.launches(2) == 1
+    phases = {
+        "work": {"what": "update, compaction, level-1 bucketing, level-2 expansion, delivery"
+                         + (" (block 0)" if persistent else " (k_step kernel)"),
+                 "ms_per_step": phase_ms[0] / NP},
+        "sync": {"what": "block 0's wait at the grid barrier" if persistent else "none (kernel boundary)",
+                 "ms_per_step": phase_ms[1] / NP},
+        "bytes_per_step": dict(zip(["update", "level1", "level2", "deliver"], [x / NP for x in pb4])),
+    }
+    print("[bench] timed %.3f ms for %d steps; work/sync ms per step %s" % (
         ms, K, [round(x / NP, 5) for x in phase_ms]), file=sys.stderr, flush=True)
     peak, peak_kind = _peaks()
-    step_bytes = sum(pbytes) / NP
-    delivery = phases["deliver"]
-    persistent = sim.launches(2) == 1
+    step_bytes = sum(pb4) / NP
     if persistent:
         # one cooperative launch runs every timed step: the kernel's launch
         # duration is the timed region, its algorithmic bytes those of K steps
@@ -242,10 +243,9 @@ def run_ours(args):
         achieved = step_bytes * K / (ms * 1e-3) / 1e9
         per_launch = step_bytes * K
     else:
-        dom = max(phases, key=lambda n: phases[n]["ms_per_step"])
-        kern = phases[dom]["kernel"]
-        achieved = phases[dom]["gbs"]
-        per_launch = phases[dom]["bytes_per_step"]
+        kern = "k_step"
+        achieved = step_bytes / (phase_ms[0] / NP * 1e-3) / 1e9
+        per_launch = step_bytes
     traffic = load_traffic(kern)
     roof = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak,
@@ -297,8 +297,6 @@ def run_ours(args):
         "step_roofline": {"bytes_per_step": step_bytes,
                           "achieved_gbs": step_bytes / (ms_max / K * 1e-3) / 1e9,
                           "frac": step_bytes / (ms_max / K * 1e-3) / 1e9 / peak},
-        "delivery_roofline": {"kernel": "k_deliver", "achieved": delivery["gbs"], "peak": peak,
-                              "frac": (delivery["gbs"] or 0) / peak},
         "phases": phases,
         "gpu_launches": sim.launches(K),
         "clocks": clocks.summary(wall0, wall1),

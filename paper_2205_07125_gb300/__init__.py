@@ -343,9 +343,10 @@ class Sim:
             _ck(_lib.snn_sim_reset(self.h, int(bool(reupload))), "snn_sim_reset")
 
     def profile_phases(self, T: int) -> np.ndarray:
-        """Advance T steps from an event-instrumented graph; summed ms per kernel
-        of a step ([0] update + compaction + level 1 + level 2, [1] delivery)."""
-        out = np.zeros(self.launches_per_step, np.float64)
+        """Advance T steps and return the summed ms of [0] the steps' work
+        (update, compaction, level 1, level 2, delivery) and [1] the wait at
+        the grid barrier between steps (persistent path; 0 on the graph path)."""
+        out = np.zeros(2, np.float64)
         with self._dev():
             _ck(_lib.snn_profile_phases(self.h, int(T), out.ctypes.data), "snn_profile_phases")
         return out

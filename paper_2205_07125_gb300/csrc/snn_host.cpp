@@ -497,9 +497,9 @@ extern "C" int snn_routing_build(const snn_network *net, const int32_t *part_of,
         if (n_l2 >= ((int64_t)1 << 32)) { delete rt; return SNN_E_RANGE; }
         rt->n_l1 = n_l1;
         rt->n_l2 = n_l2;
-        rt->src_vn.resize((size_t)M);
+        rt->src_part.resize((size_t)M);
         for (int32_t ip = 0; ip < P; ++ip)
-            for (int64_t k = rt->pbase[ip]; k < rt->pbase[ip + 1]; ++k) rt->src_vn[k] = (uint16_t)(ip / s);
+            for (int64_t k = rt->pbase[ip]; k < rt->pbase[ip + 1]; ++k) rt->src_part[k] = (uint16_t)ip;
         rt->bucket_cap.assign((size_t)n_vn, 0);
         rt->inbox_cap.assign((size_t)P, 0);
         std::vector<uint8_t> conn((size_t)P * P, 0);
@@ -581,6 +581,49 @@ extern "C" int snn_routing_build(const snn_network *net, const int32_t *part_of,
                 }
                 for (int32_t q : qs) cnt[q] = 0;
             }
+        });
+
+        // ---- exchange pairs and their exact worst cases by source partition
+        // (each partition's neurons are contiguous in the internal order)
+        std::vector<uint32_t> bc((size_t)P * n_vn, 0), ic((size_t)P * P, 0);
+        parallel_for(P, nt, [&](int64_t plo, int64_t phi, int) {
+            for (int64_t ip = plo; ip < phi; ++ip) {
+                uint32_t *b = &bc[(size_t)ip * n_vn];
+                uint32_t *c = &ic[(size_t)ip * P];
+                for (int64_t k = rt->pbase[ip]; k < rt->pbase[ip + 1]; ++k) {
+                    for (uint32_t e = rt->l1_ptr[k]; e < rt->l1_ptr[k + 1]; ++e) b[rt->l1_vn[e]]++;
+                    const uint32_t f0 = rt->l1_l2[rt->l1_ptr[k]], f1 = rt->l1_l2[rt->l1_ptr[k + 1]];
+                    for (uint32_t f = f0; f < f1; ++f) c[rt->l2[f].q]++;
+                }
+            }
+        });
+        // number the pairs; the dense tables then hold each pair's id
+        auto number = [P](std::vector<uint32_t> &dense, int32_t n_dst, std::vector<uint32_t> &ptr,
+                          std::vector<uint16_t> &dst, std::vector<uint32_t> &cap) {
+            ptr.assign((size_t)P + 1, 0);
+            for (int32_t ip = 0; ip < P; ++ip) {
+                for (int32_t x = 0; x < n_dst; ++x) {
+                    uint32_t &v = dense[(size_t)ip * n_dst + x];
+                    if (!v) continue;
+                    dst.push_back((uint16_t)x);
+                    cap.push_back(v);
+                    v = (uint32_t)(cap.size() - 1);
+                }
+                ptr[ip + 1] = (uint32_t)cap.size();
+            }
+        };
+        number(bc, n_vn, rt->bpair_ptr, rt->bpair_dst, rt->bpair_cap);
+        number(ic, P, rt->ipair_ptr, rt->ipair_dst, rt->ipair_cap);
+        rt->l1_pair.alloc(n_l1);
+        rt->l2_pair.alloc(n_l2);
+        parallel_for(P, nt, [&](int64_t plo, int64_t phi, int) {
+            for (int64_t ip = plo; ip < phi; ++ip)
+                for (int64_t k = rt->pbase[ip]; k < rt->pbase[ip + 1]; ++k)
+                    for (uint32_t e = rt->l1_ptr[k]; e < rt->l1_ptr[k + 1]; ++e) {
+                        rt->l1_pair[e] = bc[(size_t)ip * n_vn + rt->l1_vn[e]];
+                        for (uint32_t f = rt->l1_l2[e]; f < rt->l1_l2[e + 1]; ++f)
+                            rt->l2_pair[f] = ic[(size_t)ip * P + rt->l2[f].q];
+                    }
         });
     } catch (const std::bad_alloc &) {
         delete rt;

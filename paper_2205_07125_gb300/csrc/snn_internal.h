@@ -20,6 +20,10 @@ constexpr int kMaxDelay = 16;
 // Level-2 inbox entry: synapse offset << 24 | segment length.
 constexpr int kLenBits = 24;
 constexpr uint64_t kLenMask = (1ull << kLenBits) - 1ull;
+// Delivery work: segments of up to kShortSeg synapses are walked by one
+// lane; longer segments are cut into pieces of kPiece synapses, one warp each.
+constexpr uint32_t kShortSeg = 8;
+constexpr uint32_t kPiece = 128;
 
 // Level-2 entry classes (message accounting of the two-level route).
 enum : uint8_t {
@@ -79,9 +83,21 @@ struct snn_routing {
     snn::HostArray<snn::L2Entry> l2;   // [n_l2]
     std::vector<uint64_t> bucket_cap;  // [n_vn] exact worst case
     std::vector<uint64_t> inbox_cap;   // [P] (internal partitions)
+    // Exchange pairs: (internal source partition p, destination VN g) of
+    // level 1 and (p, destination partition q) of level 2 that carry at least
+    // one entry, numbered by p then destination, each with its exact worst
+    // case (every neuron of p spiking).
+    std::vector<uint32_t> bpair_ptr;      // [P+1] level-1 pairs of p
+    std::vector<uint16_t> bpair_dst;      // [n_bpair] g
+    std::vector<uint32_t> bpair_cap;      // [n_bpair]
+    std::vector<uint32_t> ipair_ptr;      // [P+1] level-2 pairs of p
+    std::vector<uint16_t> ipair_dst;      // [n_ipair] q
+    std::vector<uint32_t> ipair_cap;      // [n_ipair]
+    snn::HostArray<uint32_t> l1_pair;     // [n_l1] level-1 pair of each entry
+    snn::HostArray<uint32_t> l2_pair;     // [n_l2] level-2 pair of each entry
     std::vector<float> v0;             // [M] internal order
     std::vector<int64_t> csr;          // [M+1] first synapse of each internal neuron
-    std::vector<uint16_t> src_vn;      // [M] VN of each internal neuron
+    std::vector<uint16_t> src_part;    // [M] internal partition of each internal neuron
     int64_t n_l1 = 0, n_l2 = 0;
 };
 

@@ -111,15 +111,16 @@ struct Region {
 };
 
 struct Layout {
-    Region V, ref, ring, gid, src_vn, syn_td, syn_w, l1_ptr, l1_vn, l1_l2, l2;
+    Region V, ref, ring, gid, src_part, syn_td, syn_w, l1_ptr, l1_vn, l1_l2, l2, l1_pair, l2_pair;
     Region bucket, bucket_base, bucket_capv, bucket_cnt, inbox, inbox_base, inbox_capv, inbox_cnt;
+    Region tally;  // per-block tally rows
     Region spk, raster_off, hash, cur_rec, counters, ctrl;
     Region fwd, fo_cnt;  // snn_deliver_spikes: global -> internal map, scratch counters
-    Region piece, phase_ns;
-    uint32_t piece_cap = 0;
+    Region phase_ns;
     size_t total = 0;
     std::vector<uint64_t> bucket_base_h, inbox_base_h;
     std::vector<uint32_t> bucket_cap_h, inbox_cap_h;
+    int64_t tally_rows = 0;
     int D = 2;
 };
 
@@ -129,6 +130,18 @@ static void place(Layout &L, Region &r, size_t bytes)
     r.bytes = bytes;
     L.total += (bytes + 255) & ~(size_t)255;
 }
+
+// Blocks of one k_step launch: one pass over the neurons, 4 per thread when
+// M % 4 == 0.
+static int64_t step_grid(int64_t M)
+{
+    const int64_t items = (M % 4) == 0 ? M / 4 : M;
+    return std::max<int64_t>(1, (items + kThreads - 1) / kThreads);
+}
+
+// Tally rows: one per block of either launch shape (a persistent grid is
+// capped to the rows there are).
+constexpr int64_t kMinTallyRows = 2048;
 
 static int make_layout(const snn_routing *rt, const snn_sim_params *p, Layout &L)
 {
@@ -141,58 +154,54 @@ static int make_layout(const snn_routing *rt, const snn_sim_params *p, Layout &L
         if (c > (double)exact) c = (double)exact;
         return (uint64_t)c;
     };
+    // one region per exchange pair and per source partition's work list,
+    // each sized by its exact worst case times the capacity fraction
+    auto regions = [&](const uint64_t *exact, size_t n, float frac, std::vector<uint64_t> &base,
+                       std::vector<uint32_t> *capv, uint64_t &tot) -> bool {
+        base.resize(n);
+        tot = 0;
+        for (size_t k = 0; k < n; ++k) {
+            const uint64_t c = cap(exact[k], frac);
+            if (c > 0xFFFFFFFFull) return false;
+            base[k] = tot;
+            if (capv) capv->push_back((uint32_t)c);
+            tot += c;
+        }
+        return true;
+    };
+    const int32_t P = rt->P;
+    const size_t n_bp = rt->bpair_cap.size(), n_ip = rt->ipair_cap.size();
+    std::vector<uint64_t> ex(rt->bpair_cap.begin(), rt->bpair_cap.end());
     uint64_t nb = 0, ni = 0;
-    L.bucket_base_h.resize((size_t)rt->n_vn + 1);
-    L.bucket_cap_h.resize((size_t)rt->n_vn);
-    for (int32_t g = 0; g < rt->n_vn; ++g) {
-        uint64_t c = cap(rt->bucket_cap[g], p->bucket_frac);
-        if (c > 0xFFFFFFFFull) return SNN_E_RANGE;
-        L.bucket_base_h[g] = nb;
-        L.bucket_cap_h[g] = (uint32_t)c;
-        nb += c;
-    }
-    L.bucket_base_h[rt->n_vn] = nb;
-    L.inbox_base_h.resize((size_t)rt->P + 1);
-    L.inbox_cap_h.resize((size_t)rt->P);
-    for (int32_t q = 0; q < rt->P; ++q) {
-        uint64_t c = cap(rt->inbox_cap[q], p->inbox_frac);
-        if (c > 0xFFFFFFFFull) return SNN_E_RANGE;
-        L.inbox_base_h[q] = ni;
-        L.inbox_cap_h[q] = (uint32_t)c;
-        ni += c;
-    }
-    L.inbox_base_h[rt->P] = ni;
-    // pieces of long segments, worst case: every neuron spiking
-    uint64_t pe = 0;
-    for (int64_t f = 0; f < rt->n_l2; ++f) {
-        const uint32_t len = rt->l2[f].len;
-        if (len > (uint32_t)kShortSeg) pe += (len + kPiece - 1) / kPiece;
-    }
-    const uint64_t pc = cap(pe, p->inbox_frac);
-    if (pc > 0xFFFFFFFFull) return SNN_E_RANGE;
-    L.piece_cap = (uint32_t)pc;
+    if (!regions(ex.data(), n_bp, p->bucket_frac, L.bucket_base_h, &L.bucket_cap_h, nb)) return SNN_E_RANGE;
+    ex.assign(rt->ipair_cap.begin(), rt->ipair_cap.end());
+    if (!regions(ex.data(), n_ip, p->inbox_frac, L.inbox_base_h, &L.inbox_cap_h, ni)) return SNN_E_RANGE;
+    (void)P;
+    L.tally_rows = std::max<int64_t>(step_grid(rt->M), kMinTallyRows);
     place(L, L.ctrl, sizeof(Ctrl));
     place(L, L.counters, sizeof(unsigned long long) * C_N);
     place(L, L.V, sizeof(float) * (size_t)M);
     place(L, L.ref, (size_t)M);
     place(L, L.ring, sizeof(int32_t) * (size_t)M * (size_t)L.D);
     place(L, L.gid, rt->identity ? 0 : sizeof(uint32_t) * (size_t)M);
-    place(L, L.src_vn, sizeof(uint16_t) * (size_t)M);
+    place(L, L.src_part, sizeof(uint16_t) * (size_t)M);
     place(L, L.syn_td, sizeof(uint32_t) * (size_t)E);
     place(L, L.syn_w, sizeof(int16_t) * (size_t)E);
     place(L, L.l1_ptr, sizeof(uint32_t) * (size_t)(M + 1));
     place(L, L.l1_vn, sizeof(uint16_t) * (size_t)rt->n_l1);
     place(L, L.l1_l2, sizeof(uint32_t) * (size_t)(rt->n_l1 + 1));
     place(L, L.l2, sizeof(L2Entry) * (size_t)rt->n_l2);
+    place(L, L.l1_pair, sizeof(uint32_t) * (size_t)rt->n_l1);
+    place(L, L.l2_pair, sizeof(uint32_t) * (size_t)rt->n_l2);
     place(L, L.bucket, sizeof(uint32_t) * (size_t)nb);
-    place(L, L.bucket_base, sizeof(uint64_t) * (size_t)(rt->n_vn + 1));
-    place(L, L.bucket_capv, sizeof(uint32_t) * (size_t)rt->n_vn);
-    place(L, L.bucket_cnt, 2 * sizeof(uint32_t) * kCntStride * (size_t)rt->n_vn);  // by step parity
+    place(L, L.bucket_base, sizeof(uint64_t) * n_bp);
+    place(L, L.bucket_capv, sizeof(uint32_t) * n_bp);
+    place(L, L.bucket_cnt, 2 * sizeof(uint32_t) * kPairStride * n_bp);  // by step parity
     place(L, L.inbox, sizeof(uint64_t) * (size_t)ni);
-    place(L, L.inbox_base, sizeof(uint64_t) * (size_t)(rt->P + 1));
-    place(L, L.inbox_capv, sizeof(uint32_t) * (size_t)rt->P);
-    place(L, L.inbox_cnt, 2 * sizeof(uint32_t) * kCntStride * (size_t)rt->P);  // by step parity
-    place(L, L.piece, sizeof(unsigned long long) * (size_t)L.piece_cap);
+    place(L, L.inbox_base, sizeof(uint64_t) * n_ip);
+    place(L, L.inbox_capv, sizeof(uint32_t) * n_ip);
+    place(L, L.inbox_cnt, 2 * sizeof(uint32_t) * kPairStride * n_ip);  // by step parity
+    place(L, L.tally, sizeof(unsigned long long) * C_N * (size_t)L.tally_rows);
     place(L, L.spk, sizeof(uint32_t) * (size_t)(p->raster_cap + M));
     place(L, L.raster_off, sizeof(long long) * (size_t)(p->raster_steps + 1));
     place(L, L.hash, sizeof(unsigned long long) * 2 * (size_t)p->hash_steps);
@@ -318,7 +327,9 @@ static int upload_tables(snn_sim *s)
     CK(up(L.l1_vn, rt->l1_vn.data()));
     CK(up(L.l1_l2, rt->l1_l2.data()));
     CK(up(L.l2, rt->l2.data()));
-    CK(up(L.src_vn, rt->src_vn.data()));
+    CK(up(L.src_part, rt->src_part.data()));
+    CK(up(L.l1_pair, rt->l1_pair.data()));
+    CK(up(L.l2_pair, rt->l2_pair.data()));
     if (!rt->identity) CK(up(L.gid, rt->perm_inv.data()));
     if (!rt->identity) CK(up(L.fwd, rt->perm_fwd.data()));
     CK(up(L.bucket_base, L.bucket_base_h.data()));
@@ -339,37 +350,27 @@ static int reset_state(snn_sim *s)
     CK(cudaMemsetAsync(w + L.counters.off, 0, L.counters.bytes, st));
     CK(cudaMemsetAsync(w + L.bucket_cnt.off, 0, L.bucket_cnt.bytes, st));
     CK(cudaMemsetAsync(w + L.inbox_cnt.off, 0, L.inbox_cnt.bytes, st));
+    CK(cudaMemsetAsync(w + L.tally.off, 0, L.tally.bytes, st));
     if (L.raster_off.bytes) CK(cudaMemsetAsync(w + L.raster_off.off, 0, L.raster_off.bytes, st));
     if (L.hash.bytes) CK(cudaMemsetAsync(w + L.hash.off, 0, L.hash.bytes, st));
     if (L.cur_rec.bytes) CK(cudaMemsetAsync(w + L.cur_rec.off, 0, L.cur_rec.bytes, st));
     Ctrl c;
     std::memset(&c, 0, sizeof(c));
-    c.rec_on = s->prm.raster_cap > 0 && s->prm.raster_steps > 0;
+    const bool rec = s->prm.raster_cap > 0 && s->prm.raster_steps > 0;
+    for (int k = 0; k < 3; ++k) c.head[k] = rec ? 0 : -1;  // step 0 (and the step before it) write at 0
     CK(cudaMemcpyAsync(w + L.ctrl.off, &c, sizeof(c), cudaMemcpyHostToDevice, st));
     CK(cudaStreamSynchronize(st));
     return SNN_OK;
 }
 
-// Kernels per step: 0 = update + compaction + level 1 + level 2, 1 = delivery.
-constexpr int kPhases = 2;
-
-// Launch phase ph of a step.  With programmatic dependent launch each kernel
-// may be scheduled while the one before it drains; the kernels wait
-// (griddepcontrol.wait) before reading.
-static void launch_phase(snn_sim *s, int ph, int k, cudaStream_t st)
+// Launch the step kernel for step ctrl->t + k.  With programmatic dependent
+// launch each kernel may be scheduled while the one before it drains; it
+// waits (griddepcontrol.wait) before reading.
+static cudaError_t launch_step(snn_sim *s, int k, cudaStream_t st)
 {
-    void (*fn)(const Dev, int) = nullptr;
-    unsigned grid = 1;
-    if (ph == 0) {
-        fn = s->vec ? k_update<true> : k_update<false>;
-        grid = s->grid_update;
-    } else {
-        fn = k_deliver;
-        grid = s->grid_route;
-    }
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
-    cfg.gridDim = dim3(grid);
+    cfg.gridDim = dim3(s->grid_update);
     cfg.blockDim = dim3(kThreads);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = st;
@@ -379,12 +380,7 @@ static void launch_phase(snn_sim *s, int ph, int k, cudaStream_t st)
         cfg.attrs = attr;
         cfg.numAttrs = 1;
     }
-    cudaLaunchKernelEx(&cfg, fn, s->dev, k);
-}
-
-static cudaError_t launch_step(snn_sim *s, int k, cudaStream_t st)
-{
-    for (int ph = 0; ph < kPhases; ++ph) launch_phase(s, ph, k, st);
+    cudaLaunchKernelEx(&cfg, s->vec ? k_step<true> : k_step<false>, s->dev, k);
     return cudaGetLastError();
 }
 
@@ -395,7 +391,7 @@ static int capture(snn_sim *s, int steps, cudaGraphExec_t *out)
     cudaError_t le = cudaSuccess;
     for (int k = 0; k < steps && le == cudaSuccess; ++k) le = launch_step(s, k, s->cap_stream);
     if (le == cudaSuccess) {
-        k_advance<<<1, 1, 0, s->cap_stream>>>(s->dev.ctrl, steps);
+        k_advance<<<1, 1, 0, s->cap_stream>>>(s->dev, steps);
         le = cudaGetLastError();
     }
     cudaError_t ce = cudaStreamEndCapture(s->cap_stream, &g);
@@ -453,15 +449,13 @@ extern "C" int snn_sim_create(const snn_network *net, const snn_routing *rt, con
         s->pdl = !(e && e[0] == '0');
     }
     {
-        // persistent grids: as many blocks as stay resident together
+        // fan-out grids: as many blocks as stay resident together
         int o3 = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o3, k_deliver, kThreads, 0) != cudaSuccess) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o3, k_fo_deliver, kThreads, 0) != cudaSuccess) {
             snn_sim_destroy(s);
             return SNN_E_CUDA;
         }
-        const int64_t items = s->vec ? rt->M / 4 : rt->M;
-        const int64_t blocks = (items + kThreads - 1) / kThreads;
-        s->grid_update = (unsigned)std::max<int64_t>(1, blocks);  // one pass over the neurons
+        s->grid_update = (unsigned)step_grid(rt->M);  // one pass over the neurons
         s->grid_route = (unsigned)(sms * std::max(1, o3));
         // persistent path: one cooperative launch, every block resident
         // (SNN_PERSIST=0 selects the CUDA-graph path)
@@ -477,7 +471,7 @@ extern "C" int snn_sim_create(const snn_network *net, const snn_routing *rt, con
             if (bps && std::atoi(bps) > 0 && std::atoi(bps) < op) op = std::atoi(bps);
             if (oe == cudaSuccess && op > 0) {
                 s->persist = true;
-                s->grid_persist = (unsigned)(sms * op);
+                s->grid_persist = (unsigned)std::min<int64_t>((int64_t)sms * op, s->L.tally_rows);
             }
         }
         cudaGetLastError();
@@ -512,7 +506,9 @@ extern "C" int snn_sim_create(const snn_network *net, const snn_routing *rt, con
     d.ref = (uint8_t *)(w + L.ref.off);
     d.ring = (int32_t *)(w + L.ring.off);
     d.gid = rt->identity ? nullptr : (const uint32_t *)(w + L.gid.off);
-    d.src_vn = (const uint16_t *)(w + L.src_vn.off);
+    d.src_part = (const uint16_t *)(w + L.src_part.off);
+    d.l1_pair = (const uint32_t *)(w + L.l1_pair.off);
+    d.l2_pair = (const uint32_t *)(w + L.l2_pair.off);
     d.syn_td = (const uint32_t *)(w + L.syn_td.off);
     d.syn_w = (const int16_t *)(w + L.syn_w.off);
     d.l1_ptr = (const uint32_t *)(w + L.l1_ptr.off);
@@ -527,8 +523,7 @@ extern "C" int snn_sim_create(const snn_network *net, const snn_routing *rt, con
     d.inbox_base = (const unsigned long long *)(w + L.inbox_base.off);
     d.inbox_capv = (const uint32_t *)(w + L.inbox_capv.off);
     d.inbox_cnt = (uint32_t *)(w + L.inbox_cnt.off);
-    d.piece = (unsigned long long *)(w + L.piece.off);
-    d.piece_cap = L.piece_cap;
+    d.tally = (unsigned long long *)(w + L.tally.off);
     d.spk = (uint32_t *)(w + L.spk.off);
     d.raster_off = (long long *)(w + L.raster_off.off);
     d.hash = (unsigned long long *)(w + L.hash.off);
@@ -538,6 +533,9 @@ extern "C" int snn_sim_create(const snn_network *net, const snn_routing *rt, con
     d.M = rt->M;
     d.P = rt->P;
     d.n_vn = rt->n_vn;
+    d.vn_size = rt->P / rt->n_vn;
+    d.n_bpair = (int)rt->bpair_cap.size();
+    d.n_ipair = (int)rt->ipair_cap.size();
     d.D = L.D;
     d.alpha = (float)std::exp(-p->dt_ms / p->tau_ms);
     d.e_l = p->e_l;
@@ -580,6 +578,8 @@ static int launch_persist(snn_sim *s, int32_t T, const Dev &d)
     s->test_skip_arrival = 0;  // once: the test checks the first launch's status
     void *args[] = {(void *)&d, (void *)&tt, (void *)&lim, (void *)&skip};
     const void *fn = s->vec ? (const void *)k_persist<true> : (const void *)k_persist<false>;
+    // the grid barrier counts arrivals from zero in every launch
+    CK(cudaMemsetAsync(s->ws + s->L.ctrl.off + offsetof(Ctrl, bar), 0, sizeof(unsigned long long), s->stream));
     CK(cudaLaunchCooperativeKernel(fn, dim3(s->grid_persist), dim3(kThreads), args, 0, s->stream));
     return SNN_OK;
 }
@@ -603,10 +603,10 @@ extern "C" int snn_step(snn_sim *s, int32_t T)
 extern "C" int snn_profile_phases(snn_sim *s, int32_t T, double *phase_ms)
 {
     if (!s || T < 0 || !phase_ms) return SNN_E_ARG;
-    for (int k = 0; k < kPhases; ++k) phase_ms[k] = 0.0;
+    phase_ms[0] = phase_ms[1] = 0.0;
     if (s->persist) {
-        // block 0 sums each phase's span (phase start to the end of the grid
-        // barrier after it) with the GPU's global timer
+        // block 0 sums its work of each step and its wait at the grid barrier
+        // after it, with the GPU's global timer
         Dev dp = s->dev;
         dp.phase_ns = (unsigned long long *)(s->ws + s->L.phase_ns.off);
         CK(cudaMemsetAsync(dp.phase_ns, 0, 2 * sizeof(unsigned long long), s->stream));
@@ -620,27 +620,23 @@ extern "C" int snn_profile_phases(snn_sim *s, int32_t T, double *phase_ms)
         return SNN_OK;
     }
     if (!s->gP) {
+        // a graph of U steps with an event-record node before and after every
+        // step kernel (cudaEventRecordExternal: a plain record inside a
+        // capture only orders streams)
         const int U = 16;
-        s->pev.resize((size_t)U * (kPhases + 1));
+        s->pev.resize((size_t)U * 2);
         for (auto &e : s->pev) CK(cudaEventCreate(&e));
         cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
         cudaError_t le = cudaSuccess;
+        const unsigned fl = cudaEventRecordExternal;
         for (int k = 0; k < U && le == cudaSuccess; ++k) {
-            // cudaEventRecordExternal: a real event-record node in the graph
-            // (a plain record inside a capture only orders streams)
-            cudaEvent_t *ev = &s->pev[(size_t)k * (kPhases + 1)];
-            cudaStream_t st = s->cap_stream;
-            const unsigned fl = cudaEventRecordExternal;
-            le = cudaEventRecordWithFlags(ev[0], st, fl);
-            for (int ph = 0; ph < kPhases && le == cudaSuccess; ++ph) {
-                launch_phase(s, ph, k, st);
-                le = cudaEventRecordWithFlags(ev[ph + 1], st, fl);
-            }
-            if (le == cudaSuccess) le = cudaGetLastError();
+            le = cudaEventRecordWithFlags(s->pev[2 * k], s->cap_stream, fl);
+            if (le == cudaSuccess) le = launch_step(s, k, s->cap_stream);
+            if (le == cudaSuccess) le = cudaEventRecordWithFlags(s->pev[2 * k + 1], s->cap_stream, fl);
         }
         if (le == cudaSuccess) {
-            k_advance<<<1, 1, 0, s->cap_stream>>>(s->dev.ctrl, U);
+            k_advance<<<1, 1, 0, s->cap_stream>>>(s->dev, U);
             le = cudaGetLastError();
         }
         cudaError_t ce = cudaStreamEndCapture(s->cap_stream, &g);
@@ -659,12 +655,11 @@ extern "C" int snn_profile_phases(snn_sim *s, int32_t T, double *phase_ms)
         if (left >= s->UP) {
             CK(cudaGraphLaunch(s->gP, s->stream));
             CK(cudaStreamSynchronize(s->stream));
-            for (int k = 0; k < s->UP; ++k)
-                for (int ph = 0; ph < kPhases; ++ph) {
-                    float ms = 0.f;
-                    CK(cudaEventElapsedTime(&ms, s->pev[(size_t)k * (kPhases + 1) + ph], s->pev[(size_t)k * (kPhases + 1) + ph + 1]));
-                    phase_ms[ph] += ms;
-                }
+            for (int k = 0; k < s->UP; ++k) {
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, s->pev[2 * k], s->pev[2 * k + 1]));
+                phase_ms[0] += ms;
+            }
             left -= s->UP;
         } else {
             int rc = snn_step(s, left);
@@ -818,12 +813,12 @@ extern "C" int64_t snn_launches(const snn_sim *s, int32_t T)
     if (!s || T <= 0) return 0;
     if (s->persist) return 1;
     const int64_t graphs = (s->U > 1 ? T / s->U : 0) + (s->U > 1 ? T % s->U : T);
-    return (int64_t)kPhases * T + graphs;  // step kernels + one k_advance per graph
+    return (int64_t)T + graphs;  // step kernels + one k_advance per graph
 }
 
 extern "C" int64_t snn_launches_per_step(const snn_sim *s)
 {
-    return s ? kPhases : 0;
+    return s ? 1 : 0;
 }
 
 static int read_ctrl(snn_sim *s, Ctrl *c)
@@ -910,12 +905,27 @@ extern "C" int snn_read_hashes(snn_sim *s, int64_t t0, int64_t t1, uint64_t *cur
     return SNN_OK;
 }
 
+// Totals of the counters: the closing thread's slots plus every block's
+// tally row.
+static int read_counters(snn_sim *s, unsigned long long *c)
+{
+    const Layout &L = s->L;
+    std::vector<unsigned long long> rows((size_t)L.tally_rows * C_N);
+    CK(cudaMemcpyAsync(c, s->dev.counters, sizeof(unsigned long long) * C_N, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(rows.data(), s->dev.tally, sizeof(unsigned long long) * rows.size(), cudaMemcpyDeviceToHost,
+                       s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    for (int64_t r = 0; r < L.tally_rows; ++r)
+        for (int k = 0; k < C_N; ++k) c[k] += rows[(size_t)r * C_N + k];
+    return SNN_OK;
+}
+
 extern "C" int snn_read_counts(snn_sim *s, snn_counts *o)
 {
     if (!s || !o) return SNN_E_ARG;
     unsigned long long c[C_N];
-    CK(cudaMemcpyAsync(c, s->dev.counters, sizeof(c), cudaMemcpyDeviceToHost, s->stream));
-    CK(cudaStreamSynchronize(s->stream));
+    int rc = read_counters(s, c);
+    if (rc) return rc;
     o->steps = c[C_STEPS];
     o->spikes = c[C_SPIKES];
     o->events = c[C_EVENTS];
@@ -961,34 +971,32 @@ extern "C" int snn_read_inbox_pairs(snn_sim *s, uint64_t *pairs, int64_t cap, in
     const snn_routing *rt = s->rt;
     const Layout &L = s->L;
     CK(cudaStreamSynchronize(s->stream));
-    // filled inbox lengths of the last step, from its prefix sums
-    std::vector<uint32_t> pre((size_t)rt->P + 1);
-    {
-        // the last step's inbox fill counts (its step parity) and capacities
-        Ctrl c;
-        int rc = read_ctrl(s, &c);
-        if (rc) return rc;
-        const int pl = (int)((c.t + 1) & 1);  // parity of step t - 1
-        std::vector<uint32_t> cnt((size_t)rt->P * kCntStride);
-        CK(cudaMemcpy(cnt.data(), s->dev.inbox_cnt + (size_t)pl * rt->P * kCntStride,
-                      sizeof(uint32_t) * cnt.size(), cudaMemcpyDeviceToHost));
-        pre[0] = 0;
-        for (int32_t q = 0; q < rt->P; ++q)
-            pre[q + 1] = pre[q] + std::min(cnt[(size_t)q * kCntStride], L.inbox_cap_h[q]);
-    }
-    int64_t tot = 0;
-    for (int32_t q = 0; q < rt->P; ++q) {
-        uint32_t m = pre[q + 1] - pre[q];
-        if (m == 0) continue;
-        std::vector<unsigned long long> ent(m);
-        CK(cudaMemcpy(ent.data(), s->dev.inbox + L.inbox_base_h[q], sizeof(unsigned long long) * m,
+    // the last step's inbox fill counts (its step parity), one per exchange pair
+    Ctrl c;
+    int rc = read_ctrl(s, &c);
+    if (rc) return rc;
+    const int pl = (int)((c.t + 1) & 1);  // parity of step t - 1
+    const size_t n_ip = rt->ipair_cap.size();
+    std::vector<uint32_t> cnt(n_ip * kPairStride);
+    if (n_ip)
+        CK(cudaMemcpy(cnt.data(), s->dev.inbox_cnt + (size_t)pl * n_ip * kPairStride, sizeof(uint32_t) * cnt.size(),
                       cudaMemcpyDeviceToHost));
-        for (uint32_t x = 0; x < m; ++x) {
-            const int64_t off = (int64_t)(ent[x] >> kLenBits);
-            const int64_t k = std::upper_bound(rt->csr.begin(), rt->csr.end(), off) - rt->csr.begin() - 1;
-            if (pairs && tot < cap)
-                pairs[tot] = ((uint64_t)rt->perm_inv[k] << 32) | (uint32_t)rt->part_of_ip[q];
-            ++tot;
+    int64_t tot = 0;
+    for (int32_t ip = 0; ip < rt->P; ++ip) {
+        for (uint32_t k = rt->ipair_ptr[ip]; k < rt->ipair_ptr[ip + 1]; ++k) {
+            const uint32_t m = std::min(cnt[(size_t)k * kPairStride], L.inbox_cap_h[k]);
+            if (m == 0) continue;
+            const int32_t q = rt->ipair_dst[k];
+            std::vector<unsigned long long> ent(m);
+            CK(cudaMemcpy(ent.data(), s->dev.inbox + L.inbox_base_h[k], sizeof(unsigned long long) * m,
+                          cudaMemcpyDeviceToHost));
+            for (uint32_t x = 0; x < m; ++x) {
+                const int64_t off = (int64_t)(ent[x] >> kLenBits);
+                const int64_t i = std::upper_bound(rt->csr.begin(), rt->csr.end(), off) - rt->csr.begin() - 1;
+                if (pairs && tot < cap)
+                    pairs[tot] = ((uint64_t)rt->perm_inv[i] << 32) | (uint32_t)rt->part_of_ip[q];
+                ++tot;
+            }
         }
     }
     *n = tot;
@@ -1026,10 +1034,14 @@ extern "C" int snn_save_state(snn_sim *s, void *buf, size_t capb)
     CkptHeader h{kCkptMagic, s->rt->M, L.D, 0, c.t};
     std::memcpy(b, &h, sizeof(h));
     b += sizeof(h);
-    for (const Region *r : {&L.V, &L.ref, &L.ring, &L.counters}) {
+    for (const Region *r : {&L.V, &L.ref, &L.ring}) {
         CK(cudaMemcpy(b, s->ws + r->off, r->bytes, cudaMemcpyDeviceToHost));
         b += r->bytes;
     }
+    unsigned long long tot[C_N];
+    rc = read_counters(s, tot);
+    if (rc) return rc;
+    std::memcpy(b, tot, sizeof(tot));
     return SNN_OK;
 }
 
@@ -1048,10 +1060,11 @@ extern "C" int snn_load_state(snn_sim *s, const void *buf, size_t bytes)
         CK(cudaMemcpy(s->ws + r->off, b, r->bytes, cudaMemcpyHostToDevice));
         b += r->bytes;
     }
+    CK(cudaMemset(s->dev.tally, 0, L.tally.bytes));
     Ctrl c;
     std::memset(&c, 0, sizeof(c));
     c.t = h.t;
-    c.rec_on = 0;  // records restart empty and stay off after a restore
+    for (int k = 0; k < 3; ++k) c.head[k] = -1;  // records restart empty and stay off after a restore
     CK(cudaMemcpy(s->dev.ctrl, &c, sizeof(c), cudaMemcpyHostToDevice));
     if (h.t < s->prm.hash_steps)
         CK(cudaMemset(s->dev.hash + 2 * h.t, 0, sizeof(unsigned long long) * 2 * (size_t)(s->prm.hash_steps - h.t)));
