@@ -111,8 +111,8 @@ struct Region {
 };
 
 struct Layout {
-    Region V, ref, ring, gid, src_part, syn_td, syn_w, l1_ptr, l1_vn, l1_l2, l2, l1_pair, l2_pair;
-    Region bucket, bucket_base, bucket_capv, bucket_cnt, inbox, inbox_base, inbox_capv, inbox_cnt;
+    Region V, ref, ring, gid, src_part, syn_td, syn_w, l1_ptr, l1_vn, l1_l2, l2, row, l1_pair, l2_pair;
+    Region bucket, bucket_slot, bucket_cnt, inbox, inbox_slot, inbox_cnt;
     Region tally;  // per-block tally rows
     Region spk, raster_off, hash, cur_rec, counters, ctrl;
     Region fwd, fo_cnt;  // snn_deliver_spikes: global -> internal map, scratch counters
@@ -191,15 +191,14 @@ static int make_layout(const snn_routing *rt, const snn_sim_params *p, Layout &L
     place(L, L.l1_vn, sizeof(uint16_t) * (size_t)rt->n_l1);
     place(L, L.l1_l2, sizeof(uint32_t) * (size_t)(rt->n_l1 + 1));
     place(L, L.l2, sizeof(L2Entry) * (size_t)rt->n_l2);
+    place(L, L.row, sizeof(uint2) * (size_t)(M + 1));
     place(L, L.l1_pair, sizeof(uint32_t) * (size_t)rt->n_l1);
     place(L, L.l2_pair, sizeof(uint32_t) * (size_t)rt->n_l2);
     place(L, L.bucket, sizeof(uint32_t) * (size_t)nb);
-    place(L, L.bucket_base, sizeof(uint64_t) * n_bp);
-    place(L, L.bucket_capv, sizeof(uint32_t) * n_bp);
+    place(L, L.bucket_slot, sizeof(ulonglong2) * n_bp);
     place(L, L.bucket_cnt, 2 * sizeof(uint32_t) * kPairStride * n_bp);  // by step parity
     place(L, L.inbox, sizeof(uint64_t) * (size_t)ni);
-    place(L, L.inbox_base, sizeof(uint64_t) * n_ip);
-    place(L, L.inbox_capv, sizeof(uint32_t) * n_ip);
+    place(L, L.inbox_slot, sizeof(ulonglong2) * n_ip);
     place(L, L.inbox_cnt, 2 * sizeof(uint32_t) * kPairStride * n_ip);  // by step parity
     place(L, L.tally, sizeof(unsigned long long) * C_N * (size_t)L.tally_rows);
     place(L, L.spk, sizeof(uint32_t) * (size_t)(p->raster_cap + M));
@@ -266,6 +265,9 @@ struct snn_sim {
     int64_t static_row_l1 = -1, static_row_l2 = -1;  // snn_deliver_spikes_static sizing
     unsigned grid_update = 1, grid_route = 1;
     bool vec = false;  // 4 neurons per thread with 16-byte loads (M % 4 == 0)
+    int pmode = kModeScalar;  // neuron-state access of k_persist
+    size_t persist_smem = 0;  // dynamic shared memory of k_persist (kModeSmem)
+    int64_t chunk_q = 0;      // quads per block of k_persist (kModeSmem)
     bool pdl = true;       // programmatic dependent launch between step kernels
     bool persist = false;  // one cooperative launch per snn_step (k_persist)
     unsigned grid_persist = 1;
@@ -329,13 +331,25 @@ static int upload_tables(snn_sim *s)
     CK(up(L.l2, rt->l2.data()));
     CK(up(L.src_part, rt->src_part.data()));
     CK(up(L.l1_pair, rt->l1_pair.data()));
+    {
+        // first level-1 and level-2 entry of each neuron, read together
+        std::vector<uint2> row((size_t)rt->M + 1);
+        for (int64_t i = 0; i <= rt->M; ++i) row[i] = make_uint2(rt->l1_ptr[i], rt->l1_l2[rt->l1_ptr[i]]);
+        CK(cudaMemcpy(w + L.row.off, row.data(), L.row.bytes, cudaMemcpyHostToDevice));
+    }
     CK(up(L.l2_pair, rt->l2_pair.data()));
     if (!rt->identity) CK(up(L.gid, rt->perm_inv.data()));
     if (!rt->identity) CK(up(L.fwd, rt->perm_fwd.data()));
-    CK(up(L.bucket_base, L.bucket_base_h.data()));
-    CK(up(L.bucket_capv, L.bucket_cap_h.data()));
-    CK(up(L.inbox_base, L.inbox_base_h.data()));
-    CK(up(L.inbox_capv, L.inbox_cap_h.data()));
+    {
+        // exchange regions {first entry, capacity} of every pair
+        auto slots = [&](const Region &r, const std::vector<uint64_t> &base, const std::vector<uint32_t> &cap) {
+            std::vector<ulonglong2> v(base.size());
+            for (size_t k = 0; k < v.size(); ++k) v[k] = make_ulonglong2(base[k], cap[k]);
+            return r.bytes ? cudaMemcpy(w + r.off, v.data(), r.bytes, cudaMemcpyHostToDevice) : cudaSuccess;
+        };
+        CK(slots(L.bucket_slot, L.bucket_base_h, L.bucket_cap_h));
+        CK(slots(L.inbox_slot, L.inbox_base_h, L.inbox_cap_h));
+    }
     return SNN_OK;
 }
 
@@ -380,7 +394,7 @@ static cudaError_t launch_step(snn_sim *s, int k, cudaStream_t st)
         cfg.attrs = attr;
         cfg.numAttrs = 1;
     }
-    cudaLaunchKernelEx(&cfg, s->vec ? k_step<true> : k_step<false>, s->dev, k);
+    cudaLaunchKernelEx(&cfg, s->vec ? k_step<kModeVec> : k_step<kModeScalar>, s->dev, k);
     return cudaGetLastError();
 }
 
@@ -458,20 +472,54 @@ extern "C" int snn_sim_create(const snn_network *net, const snn_routing *rt, con
         s->grid_update = (unsigned)step_grid(rt->M);  // one pass over the neurons
         s->grid_route = (unsigned)(sms * std::max(1, o3));
         // persistent path: one cooperative launch, every block resident
-        // (SNN_PERSIST=0 selects the CUDA-graph path)
-        int coop = 0, op = 0;
+        // (SNN_PERSIST=0 selects the CUDA-graph path).  With M % 4 == 0 each
+        // block keeps its quads' state in shared memory when that fits at
+        // the most blocks per SM that do (SNN_PERSIST_SMEM=0: global state).
+        int coop = 0;
         const char *e = std::getenv("SNN_PERSIST");
+        const char *esm = std::getenv("SNN_PERSIST_SMEM");
+        // SNN_PERSIST_BLOCKS_PER_SM lowers the resident blocks per SM (tuning)
+        const char *bps = std::getenv("SNN_PERSIST_BLOCKS_PER_SM");
+        const int bmax = (bps && std::atoi(bps) > 0) ? std::atoi(bps) : 1 << 30;
         if (!(e && e[0] == '0') &&
             cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, s->device) == cudaSuccess && coop) {
-            const cudaError_t oe =
-                s->vec ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&op, k_persist<true>, kThreads, 0)
-                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&op, k_persist<false>, kThreads, 0);
-            // SNN_PERSIST_BLOCKS_PER_SM lowers the resident blocks per SM (tuning)
-            const char *bps = std::getenv("SNN_PERSIST_BLOCKS_PER_SM");
-            if (bps && std::atoi(bps) > 0 && std::atoi(bps) < op) op = std::atoi(bps);
-            if (oe == cudaSuccess && op > 0) {
-                s->persist = true;
-                s->grid_persist = (unsigned)std::min<int64_t>((int64_t)sms * op, s->L.tally_rows);
+            if (s->vec && !(esm && esm[0] == '0')) {
+                int smax = 0;
+                cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device);
+                const int64_t nq = rt->M / 4;
+                for (int b = std::min(4, bmax); b >= 1 && s->pmode != kModeSmem; --b) {
+                    const int64_t grid = std::min<int64_t>((int64_t)sms * b, s->L.tally_rows);
+                    const int64_t cq = (nq + grid - 1) / grid;
+                    const size_t dyn = (size_t)cq * 36;
+                    if (dyn > (size_t)smax) continue;
+                    if (cudaFuncSetAttribute(k_persist<kModeSmem>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)dyn) != cudaSuccess)
+                        continue;
+                    int op = 0;
+                    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&op, k_persist<kModeSmem>, kThreads, dyn) !=
+                            cudaSuccess ||
+                        op < b)
+                        continue;
+                    s->persist = true;
+                    s->pmode = kModeSmem;
+                    s->grid_persist = (unsigned)grid;
+                    s->persist_smem = dyn;
+                    s->chunk_q = cq;
+                }
+                cudaGetLastError();
+            }
+            if (!s->persist) {
+                int op = 0;
+                const int mode = s->vec ? kModeVec : kModeScalar;
+                const cudaError_t oe =
+                    s->vec ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&op, k_persist<kModeVec>, kThreads, 0)
+                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&op, k_persist<kModeScalar>, kThreads, 0);
+                op = std::min(op, bmax);
+                if (oe == cudaSuccess && op > 0) {
+                    s->persist = true;
+                    s->pmode = mode;
+                    s->grid_persist = (unsigned)std::min<int64_t>((int64_t)sms * op, s->L.tally_rows);
+                }
             }
         }
         cudaGetLastError();
@@ -507,6 +555,7 @@ extern "C" int snn_sim_create(const snn_network *net, const snn_routing *rt, con
     d.ring = (int32_t *)(w + L.ring.off);
     d.gid = rt->identity ? nullptr : (const uint32_t *)(w + L.gid.off);
     d.src_part = (const uint16_t *)(w + L.src_part.off);
+    d.row = (const uint2 *)(w + L.row.off);
     d.l1_pair = (const uint32_t *)(w + L.l1_pair.off);
     d.l2_pair = (const uint32_t *)(w + L.l2_pair.off);
     d.syn_td = (const uint32_t *)(w + L.syn_td.off);
@@ -516,12 +565,10 @@ extern "C" int snn_sim_create(const snn_network *net, const snn_routing *rt, con
     d.l1_l2 = (const uint32_t *)(w + L.l1_l2.off);
     d.l2 = (const DevL2 *)(w + L.l2.off);
     d.bucket = (uint32_t *)(w + L.bucket.off);
-    d.bucket_base = (const unsigned long long *)(w + L.bucket_base.off);
-    d.bucket_capv = (const uint32_t *)(w + L.bucket_capv.off);
+    d.bucket_slot = (const ulonglong2 *)(w + L.bucket_slot.off);
     d.bucket_cnt = (uint32_t *)(w + L.bucket_cnt.off);
     d.inbox = (unsigned long long *)(w + L.inbox.off);
-    d.inbox_base = (const unsigned long long *)(w + L.inbox_base.off);
-    d.inbox_capv = (const uint32_t *)(w + L.inbox_capv.off);
+    d.inbox_slot = (const ulonglong2 *)(w + L.inbox_slot.off);
     d.inbox_cnt = (uint32_t *)(w + L.inbox_cnt.off);
     d.tally = (unsigned long long *)(w + L.tally.off);
     d.spk = (uint32_t *)(w + L.spk.off);
@@ -534,6 +581,7 @@ extern "C" int snn_sim_create(const snn_network *net, const snn_routing *rt, con
     d.P = rt->P;
     d.n_vn = rt->n_vn;
     d.vn_size = rt->P / rt->n_vn;
+    d.chunk_q = s->chunk_q;
     d.n_bpair = (int)rt->bpair_cap.size();
     d.n_ipair = (int)rt->ipair_cap.size();
     d.D = L.D;
@@ -577,10 +625,12 @@ static int launch_persist(snn_sim *s, int32_t T, const Dev &d)
     int skip = s->test_skip_arrival;
     s->test_skip_arrival = 0;  // once: the test checks the first launch's status
     void *args[] = {(void *)&d, (void *)&tt, (void *)&lim, (void *)&skip};
-    const void *fn = s->vec ? (const void *)k_persist<true> : (const void *)k_persist<false>;
+    const void *fn = s->pmode == kModeSmem  ? (const void *)k_persist<kModeSmem>
+                     : s->pmode == kModeVec ? (const void *)k_persist<kModeVec>
+                                            : (const void *)k_persist<kModeScalar>;
     // the grid barrier counts arrivals from zero in every launch
     CK(cudaMemsetAsync(s->ws + s->L.ctrl.off + offsetof(Ctrl, bar), 0, sizeof(unsigned long long), s->stream));
-    CK(cudaLaunchCooperativeKernel(fn, dim3(s->grid_persist), dim3(kThreads), args, 0, s->stream));
+    CK(cudaLaunchCooperativeKernel(fn, dim3(s->grid_persist), dim3(kThreads), args, s->persist_smem, s->stream));
     return SNN_OK;
 }
 

@@ -42,10 +42,12 @@ constexpr int kPTab = 32;
 constexpr int kSpkBuf = 1024;   // spikes a block buffers before routing them
 constexpr int kLongCap = 512;   // staged pieces of one routing round
 constexpr int kShortCap = 1024; // staged short segments of one routing round
-// Exchange fill counters are keyed by (source partition, destination) pair
-// and sit 32 bytes apart, so each sees only the spikes of one source
-// partition.
-constexpr int kPairStride = 8;
+constexpr int kRound = 16;      // spikes routed per round (<= 32)
+// Exchange fill counters are keyed by (source partition, destination) pair,
+// so each sees only the spikes of one source partition, and each owns a
+// 128-byte line: the counters of one partition then spread over many L2
+// slices instead of queueing in a few.
+constexpr int kPairStride = 32;
 
 // status bits
 constexpr uint32_t kStBucket = 1u, kStInbox = 2u, kStRaster = 4u, kStTimeout = 8u;
@@ -87,16 +89,15 @@ struct Dev {
     const uint16_t *l1_vn;
     const uint32_t *l1_l2;
     const DevL2 *l2;
+    const uint2 *row;         // [M+1] first level-1 and level-2 entry of each internal neuron
     const uint32_t *l1_pair;  // exchange pair (source partition, VN) of each level-1 entry
     const uint32_t *l2_pair;  // exchange pair (source partition, partition) of each level-2 entry
     // exchange buffers, one region per pair (source partition p, destination)
     uint32_t *bucket;                        // level-1 entry ids, region (p, VN g)
-    const unsigned long long *bucket_base;   // [n_bpair]
-    const uint32_t *bucket_capv;             // [n_bpair]
+    const ulonglong2 *bucket_slot;           // [n_bpair] region {first entry, capacity}
     uint32_t *bucket_cnt;                    // [2][n_bpair * kPairStride], by step parity
     unsigned long long *inbox;               // segments offset << 24 | length, region (p, q)
-    const unsigned long long *inbox_base;    // [n_ipair]
-    const uint32_t *inbox_capv;              // [n_ipair]
+    const ulonglong2 *inbox_slot;            // [n_ipair] region {first entry, capacity}
     uint32_t *inbox_cnt;                     // [2][n_ipair * kPairStride], by step parity
     // records
     uint32_t *spk;
@@ -111,6 +112,7 @@ struct Dev {
     long long M;
     int P, n_vn, vn_size, D;
     int n_bpair, n_ipair;
+    long long chunk_q;  // kModeSmem: quads owned by each block of k_persist
     float alpha, e_l, v_th, v_reset;
     int t_ref, w_ext, i_bias, th_fin;
     uint32_t key0, key1;
@@ -183,6 +185,23 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
+// Start moving the line holding p into L2 (no register result).
+__device__ __forceinline__ void prefetch_l2(const void *p)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
+// Row bounds of spiking neuron i are the first thing its routing reads:
+// start fetching them when the spike is found.
+__device__ __forceinline__ void prefetch_rows(const Dev &d, long long j0, unsigned int m)
+{
+    for (; m; m &= m - 1u) {
+        const long long i = j0 + __ffs(m) - 1;
+        prefetch_l2(d.row + i);
+        prefetch_l2(d.row + i + 1);
+    }
+}
+
 __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long *p)
 {
     unsigned long long v;
@@ -250,8 +269,14 @@ __device__ __forceinline__ bool grid_sync(Ctrl *c, unsigned long long k, unsigne
 __device__ __forceinline__ bool lif_neuron(const Dev &d, const uint32_t *th, uint32_t u, int32_t irec, float &v,
                                            uint32_t &r)
 {
+    // k = number of finite thresholds <= u (they ascend): the first four
+    // compared at once against the kernel parameters, the rest (rare: k >= 4
+    // has probability ~1.4 % at 0.8 arrivals per step) from shared memory
     int k = 0;
-    while (k < d.th_fin && u >= th[k]) ++k;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) k += (m < d.th_fin && u >= d.th32[m]) ? 1 : 0;
+    if (k == 4)
+        while (k < d.th_fin && u >= th[k]) ++k;
     const int32_t I = (int32_t)((uint32_t)irec + (uint32_t)k * (uint32_t)d.w_ext + (uint32_t)d.i_bias);
     if (r > 0) {
         r -= 1;
@@ -289,13 +314,29 @@ struct Stage {
     unsigned int *n, *gbase, *nl, *ns;
     int *routed;
     unsigned int (*ty)[kTally];  // [kWarps][kTally] tallies: events, l1 local, l1 cross-VN, l2 by class
+    uint32_t *e0, *f0;           // [kRound] first level-1 / level-2 entry of each spike of a round
+    uint32_t *pre1, *pre2;       // [kRound + 1] prefix of the level-1 / level-2 entry counts
+    int *part;                   // [kRound] source partition of each spike
 };
 
-// Add a warp's per-lane tally v into slot k of its shared tally row.
+// Add a warp's per-lane tally v into slot k of its shared tally row (whole
+// warp calls).
 __device__ __forceinline__ void tally_add(const Stage &sg, int k, unsigned int v)
 {
     v = warp_sum(v);
     if ((threadIdx.x & 31) == 0) sg.ty[threadIdx.x >> 5][k] += v;
+}
+
+// Index k with pre[k] <= x < pre[k+1] (pre nondecreasing, pre[0] = 0 <= x < pre[n]).
+__device__ __forceinline__ int prefix_find(const uint32_t *pre, int n, uint32_t x)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pre[mid] <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
 }
 
 // a6 for n consecutive synapses from offset o by one thread (the rare
@@ -310,92 +351,6 @@ __device__ __forceinline__ unsigned int deliver_run(const Dev &d, int tm, unsign
         atomicAdd(&d.ring[(long long)sl * d.M + (td & kTgtMask)], w);
     }
     return n;
-}
-
-// a4 + a5 for spike i by one warp, with its delivery work staged in shared
-// memory; counters of step parity par.
-__device__ __forceinline__ void route_spike(const Dev &d, int par, int tm, uint32_t i, const Stage &sg)
-{
-    unsigned int ev = 0, l1_loc = 0, l1_xvn = 0, ovf = 0;
-    unsigned int cls[4] = {0, 0, 0, 0};
-    const int lane = threadIdx.x & 31;
-    uint32_t *bcnt = bucket_cnt_of(d, par);
-    uint32_t *icnt = inbox_cnt_of(d, par);
-    const int p = d.src_part[i];
-    const int h = p / d.vn_size;
-    const uint32_t e0 = d.l1_ptr[i], e1 = d.l1_ptr[i + 1];
-    const uint32_t f0 = d.l1_l2[e0], f1 = d.l1_l2[e1];
-    // a4: one level-1 entry per destination VN, appended to bucket (p, g)
-    for (uint32_t e = e0 + lane; e < e1; e += 32u) {
-        const int g = d.l1_vn[e];
-        const uint32_t k = d.l1_pair[e];
-        const unsigned int pos = atomicAdd(&bcnt[(size_t)k * kPairStride], 1u);
-        if (pos < d.bucket_capv[k]) d.bucket[d.bucket_base[k] + pos] = e;
-        else ovf |= kStBucket;
-        if (g == h) ++l1_loc;
-        else ++l1_xvn;
-    }
-    // a5: the relay of each destination VN expands the spike's entry into
-    // inbox (p, q) of every partition q of that VN holding targets (the
-    // level-2 rows of one spike's VNs are contiguous)
-    for (uint32_t fb = f0; fb < f1; fb += 32u) {
-        const uint32_t f = fb + lane;
-        const bool a = f < f1;
-        DevL2 l;
-        l.off = 0;
-        l.len = 0;
-        l.q = 0;
-        l.cls = 0;
-        uint32_t kq = 0;
-        if (a) {
-            l = d.l2[f];
-            kq = d.l2_pair[f];
-            const unsigned int pos = atomicAdd(&icnt[(size_t)kq * kPairStride], 1u);
-            if (pos < d.inbox_capv[kq])
-                d.inbox[d.inbox_base[kq] + pos] = (l.off << kLenBits) | (unsigned long long)l.len;
-            else
-                ovf |= kStInbox;
-            // per-class tallies without a dynamically indexed (local-memory) array
-            cls[0] += l.cls == 0;
-            cls[1] += l.cls == 1;
-            cls[2] += l.cls == 2;
-            cls[3] += l.cls == 3;
-        }
-        // stage the delivery: long segments as pieces, short ones whole
-        const bool shrt = a && l.len <= kShortSeg;
-        const unsigned int np = (a && !shrt) ? (l.len + kPiece - 1u) / kPiece : 0u;
-        unsigned int incl = np;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        const unsigned int ptot = __shfl_sync(0xFFFFFFFFu, incl, 31);
-        const unsigned int sm = __ballot_sync(0xFFFFFFFFu, shrt);
-        unsigned int pb = 0, sb = 0;
-        if (lane == 0) {
-            if (ptot) pb = atomicAdd(sg.nl, ptot);
-            if (sm) sb = atomicAdd(sg.ns, (unsigned int)__popc(sm));
-        }
-        pb = __shfl_sync(0xFFFFFFFFu, pb, 0) + incl - np;
-        sb = __shfl_sync(0xFFFFFFFFu, sb, 0) + (unsigned int)__popc(sm & ((1u << lane) - 1u));
-        for (unsigned int k = 0; k < np; ++k, ++pb) {
-            const unsigned long long o = l.off + (unsigned long long)k * kPiece;
-            const unsigned int n = min(kPiece, l.len - k * kPiece);
-            if (pb < (unsigned int)kLongCap) sg.lng[pb] = (o << 8) | n;
-            else ev += deliver_run(d, tm, o, n);  // list full: this lane delivers it
-        }
-        if (shrt) {
-            if (sb < (unsigned int)kShortCap) sg.sht[sb] = (l.off << 8) | l.len;
-            else ev += deliver_run(d, tm, l.off, l.len);
-        }
-    }
-    if (ovf) atomicOr(&d.ctrl->status, ovf);
-    tally_add(sg, 0, ev);
-    tally_add(sg, 1, l1_loc);
-    tally_add(sg, 2, l1_xvn);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) tally_add(sg, 3 + k, cls[k]);
 }
 
 // a6 for the staged work of one routing round, all warps of the block: a
@@ -463,8 +418,136 @@ __device__ __forceinline__ void deliver_staged(const Dev &d, int tm, const Stage
     tally_add(sg, 0, ev);
 }
 
-// Route and deliver the block's buffered spikes in rounds of one spike per
-// warp, and append them to the step's spike list at raster head `head`
+// a4 + a5 + a6 for the nr <= kRound spikes spk[0 .. nr) by the whole block:
+// the level-1 and level-2 entries of all of them are numbered through and
+// taken a thread each, so one spike's entries go out together.  Each
+// level-2 entry's delivery is staged in shared memory as soon as the entry is
+// read; the fill-counter reservation of a thread's last entry is left in
+// flight during the delivery and its exchange write done after it.  Counters
+// of step parity par.
+__device__ __forceinline__ void route_round(const Dev &d, int par, int tm, const uint32_t *spk, unsigned int nr,
+                                            const Stage &sg)
+{
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x < nr) {
+        const uint32_t i = spk[threadIdx.x];
+        const uint2 a = d.row[i], b = d.row[i + 1];
+        sg.e0[threadIdx.x] = a.x;
+        sg.f0[threadIdx.x] = a.y;
+        sg.pre1[threadIdx.x + 1] = b.x - a.x;
+        sg.pre2[threadIdx.x + 1] = b.y - a.y;
+        sg.part[threadIdx.x] = d.src_part[i];
+    }
+    if (threadIdx.x == 0) {
+        *sg.nl = 0;
+        *sg.ns = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        // inclusive scans of the counts (kRound <= 32: one warp)
+        uint32_t v1 = (unsigned int)lane < nr ? sg.pre1[lane + 1] : 0u;
+        uint32_t v2 = (unsigned int)lane < nr ? sg.pre2[lane + 1] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y1 = __shfl_up_sync(0xFFFFFFFFu, v1, o), y2 = __shfl_up_sync(0xFFFFFFFFu, v2, o);
+            if (lane >= o) {
+                v1 += y1;
+                v2 += y2;
+            }
+        }
+        if ((unsigned int)lane < nr) {
+            sg.pre1[lane + 1] = v1;
+            sg.pre2[lane + 1] = v2;
+        }
+        if (lane == 0) {
+            sg.pre1[0] = 0;
+            sg.pre2[0] = 0;
+        }
+    }
+    __syncthreads();
+    uint32_t *bcnt = bucket_cnt_of(d, par);
+    uint32_t *icnt = inbox_cnt_of(d, par);
+    const uint32_t N1 = sg.pre1[nr], N = N1 + sg.pre2[nr];
+    unsigned int ev = 0, l1_loc = 0, l1_xvn = 0, ovf = 0;
+    unsigned int cls[4] = {0, 0, 0, 0};
+    // the exchange write still to do: kind 1 bucket, 2 inbox
+    int pk = 0;
+    unsigned int ppos = 0;
+    ulonglong2 pslot = make_ulonglong2(0ull, 0ull);
+    unsigned long long pval = 0;
+    for (uint32_t x = threadIdx.x; x < N; x += kThreads) {
+        if (pk == 1) {
+            if (ppos < pslot.y) d.bucket[pslot.x + ppos] = (uint32_t)pval;
+            else ovf |= kStBucket;
+        } else if (pk == 2) {
+            if (ppos < pslot.y) d.inbox[pslot.x + ppos] = pval;
+            else ovf |= kStInbox;
+        }
+        if (x < N1) {
+            // a4: one level-1 entry per destination VN, appended to bucket (p, g)
+            const int k = prefix_find(sg.pre1, (int)nr, x);
+            const uint32_t e = sg.e0[k] + (x - sg.pre1[k]);
+            const int g = d.l1_vn[e];
+            const uint32_t kp = d.l1_pair[e];
+            pslot = d.bucket_slot[kp];
+            ppos = atomicAdd(&bcnt[(size_t)kp * kPairStride], 1u);
+            pval = e;
+            pk = 1;
+            if (g == sg.part[k] / d.vn_size) ++l1_loc;
+            else ++l1_xvn;
+        } else {
+            // a5: the relay of the entry's VN expands it into inbox (p, q) of
+            // partition q; the segment's delivery is staged
+            const uint32_t y = x - N1;
+            const int k = prefix_find(sg.pre2, (int)nr, y);
+            const uint32_t f = sg.f0[k] + (y - sg.pre2[k]);
+            const DevL2 l = d.l2[f];
+            const uint32_t kq = d.l2_pair[f];
+            pslot = d.inbox_slot[kq];
+            ppos = atomicAdd(&icnt[(size_t)kq * kPairStride], 1u);
+            pval = (l.off << kLenBits) | (unsigned long long)l.len;
+            pk = 2;
+            if (l.len <= kShortSeg) {
+                const unsigned int sb = atomicAdd(sg.ns, 1u);
+                if (sb < (unsigned int)kShortCap) sg.sht[sb] = (l.off << 8) | l.len;
+                else ev += deliver_run(d, tm, l.off, l.len);  // list full: this thread delivers it
+            } else {
+                const unsigned int np = (l.len + kPiece - 1u) / kPiece;
+                unsigned int pb = atomicAdd(sg.nl, np);
+                for (unsigned int j = 0; j < np; ++j, ++pb) {
+                    const unsigned long long o = l.off + (unsigned long long)j * kPiece;
+                    const unsigned int n = min(kPiece, l.len - j * kPiece);
+                    if (pb < (unsigned int)kLongCap) sg.lng[pb] = (o << 8) | n;
+                    else ev += deliver_run(d, tm, o, n);
+                }
+            }
+            // per-class tallies without a dynamically indexed (local-memory) array
+            cls[0] += l.cls == 0;
+            cls[1] += l.cls == 1;
+            cls[2] += l.cls == 2;
+            cls[3] += l.cls == 3;
+        }
+    }
+    __syncthreads();
+    deliver_staged(d, tm, sg, min(*sg.nl, (unsigned int)kLongCap), min(*sg.ns, (unsigned int)kShortCap));
+    if (pk == 1) {
+        if (ppos < pslot.y) d.bucket[pslot.x + ppos] = (uint32_t)pval;
+        else ovf |= kStBucket;
+    } else if (pk == 2) {
+        if (ppos < pslot.y) d.inbox[pslot.x + ppos] = pval;
+        else ovf |= kStInbox;
+    }
+    if (ovf) atomicOr(&d.ctrl->status, ovf);
+    tally_add(sg, 0, ev);
+    tally_add(sg, 1, l1_loc);
+    tally_add(sg, 2, l1_xvn);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) tally_add(sg, 3 + k, cls[k]);
+    __syncthreads();
+}
+
+// Route and deliver the block's buffered spikes in rounds of up to kRound
+// spikes, and append them to the step's spike list at raster head `head`
 // (all threads call).
 __device__ __forceinline__ void flush_spikes(const Dev &d, long long t, long long head, const Stage &sg)
 {
@@ -473,22 +556,11 @@ __device__ __forceinline__ void flush_spikes(const Dev &d, long long t, long lon
     if (n == 0) return;
     const int par = (int)(t & 1);
     const int tm = (int)(t % d.D);
-    const int wid = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
         *sg.gbase = atomicAdd(&d.ctrl->S_acc[slot3(t)], n);
         *sg.routed = 1;
     }
-    for (unsigned int b = 0; b < n; b += kWarps) {
-        if (threadIdx.x == 0) {
-            *sg.nl = 0;
-            *sg.ns = 0;
-        }
-        __syncthreads();
-        if (b + (unsigned int)wid < n) route_spike(d, par, tm, sg.spk[b + wid], sg);
-        __syncthreads();
-        deliver_staged(d, tm, sg, min(*sg.nl, (unsigned int)kLongCap), min(*sg.ns, (unsigned int)kShortCap));
-        __syncthreads();
-    }
+    for (unsigned int b = 0; b < n; b += kRound) route_round(d, par, tm, sg.spk + b, min(n - b, (unsigned int)kRound), sg);
     if (head >= 0) {
         const unsigned int gb = *sg.gbase;
         for (unsigned int k = threadIdx.x; k < n; k += kThreads) d.spk[head + gb + k] = sg.spk[k];
@@ -499,21 +571,155 @@ __device__ __forceinline__ void flush_spikes(const Dev &d, long long t, long lon
 }
 
 // ---------------------------------------------------------------- a1-a6
-// One step t on this block's share of the neurons (all threads call).
-template <bool VEC>
-__device__ __forceinline__ void run_step(const Dev &d, long long t)
-{
-    __shared__ uint32_t s_spk[kSpkBuf];
-    __shared__ unsigned long long s_lng[kLongCap];
-    __shared__ unsigned long long s_sht[kShortCap];
-    __shared__ unsigned int s_wsum[kWarps];
-    __shared__ unsigned int s_n, s_tot, s_gbase, s_nl, s_ns;
-    __shared__ int s_flush, s_routed;
-    __shared__ unsigned long long s_h[2][kWarps];
-    __shared__ unsigned int s_tally[kWarps][kTally];
-    __shared__ uint32_t s_th[kPTab];
-    const Stage sg{s_spk, s_lng, s_sht, &s_n, &s_gbase, &s_nl, &s_ns, &s_routed, s_tally};
+// How a step reaches its neurons' state:
+//   kModeScalar  one neuron per thread, grid-stride over global memory;
+//   kModeVec     four neurons per thread with 16-byte global loads (M % 4 == 0);
+//   kModeSmem    k_persist only: each block owns a contiguous run of quads
+//                whose V and ref stay in shared memory for the whole launch;
+//                the block's part of ring slot t comes in with one bulk copy
+//                (cp.async.bulk, mbarrier completion) per step.
+enum { kModeScalar = 0, kModeVec = 1, kModeSmem = 2 };
 
+// Shared-memory state of a block in kModeSmem.
+struct Resident {
+    float4 *V;                 // [cq] membrane potentials of the block's quads
+    int4 *ring;                // [cq] this step's ring slot, staged by the bulk copy
+    uint32_t *ref;             // [cq] refractory counters, one byte per neuron
+    unsigned long long *bar;   // mbarrier of the bulk copy
+    long long q0;              // first quad of the block
+    int nq;                    // quads of the block
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned)
+// from global memory into this CTA's shared memory, completing on `bar`.
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, unsigned long long *bar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Wait until phase `parity` of `bar` completes, for at most limit_ns.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity, unsigned long long limit_ns)
+{
+    const unsigned long long deadline = global_ns() + limit_ns;
+    for (;;) {
+        uint32_t ok;
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (global_ns() > deadline) return false;
+    }
+}
+
+// a1 + a2 for the quad of neurons j0 .. j0+3 (internal ids): membrane
+// potentials vv, recurrent inputs ii, refractory counters r4 (a byte each).
+// Returns the spike bits.
+__device__ __forceinline__ unsigned int update_quad(const Dev &d, const uint32_t *th, long long t, long long j0,
+                                                    float (&vv)[4], const int32_t (&ii)[4], uint32_t &r4,
+                                                    bool do_hash, unsigned long long &hc, unsigned long long &hv)
+{
+    // one Philox block serves the four neurons of a quad in the global
+    // order; a reordering map needs a block per neuron
+    uint4 wq = make_uint4(0u, 0u, 0u, 0u);
+    if (!d.gid) wq = philox4(d.key0, d.key1, (uint32_t)(j0 >> 2), (uint32_t)t);
+    unsigned int m = 0;
+    uint32_t r_out = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const uint32_t g = d.gid ? d.gid[j0 + k] : (uint32_t)(j0 + k);
+        const uint32_t u = d.gid ? uint4_word(philox4(d.key0, d.key1, g >> 2, (uint32_t)t), g & 3u)
+                                 : uint4_word(wq, (uint32_t)k);
+        uint32_t r = (r4 >> (8 * k)) & 0xFFu;
+        if (lif_neuron(d, th, u, ii[k], vv[k], r)) m |= 1u << k;
+        r_out |= r << (8 * k);
+        if (do_hash) {
+            hc += mix64(((unsigned long long)g << 32) | (uint32_t)ii[k]);
+            hv += mix64(((unsigned long long)g << 32) | __float_as_uint(vv[k]));
+        }
+    }
+    r4 = r_out;
+    return m;
+}
+
+// Shared-memory scratch of run_step.
+struct StepShared {
+    uint32_t spk[kSpkBuf];
+    unsigned long long lng[kLongCap];
+    unsigned long long sht[kShortCap];
+    unsigned int wsum[kWarps];
+    unsigned int n, tot, gbase, nl, ns;
+    int routed;
+    long long head;
+    long long t0;
+    unsigned long long h[2][kWarps];
+    unsigned int tally[kWarps][kTally];
+    uint32_t th[kPTab];
+    uint32_t e0[kRound], f0[kRound], pre1[kRound + 1], pre2[kRound + 1];
+    int part[kRound];
+};
+
+// a3: compaction of the spikes each thread collected in `bits` (bit b is
+// neuron id_of(b)) into the block buffer, then routing and delivery of the
+// buffer.  The block's spikes are numbered by a block-wide scan and go
+// through the buffer in windows of kSpkBuf (all threads call; without spikes
+// this costs one barrier).
+template <class IdOf>
+__device__ __forceinline__ void compact_flush(const Dev &d, long long t, long long head, StepShared &sh,
+                                              const Stage &sg, uint32_t bits, IdOf id_of)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned int cnt = __popc(bits);
+    if (!__syncthreads_or(cnt)) return;
+    unsigned int x = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh.wsum[wid] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned int tot = 0;
+        for (int w = 0; w < kWarps; ++w) {
+            const unsigned int cw = sh.wsum[w];
+            sh.wsum[w] = tot;
+            tot += cw;
+        }
+        sh.tot = tot;
+    }
+    __syncthreads();
+    const unsigned int first = sh.wsum[wid] + x - cnt, tot = sh.tot;
+    for (unsigned int w0 = 0; w0 < tot; w0 += kSpkBuf) {
+        unsigned int pos = first;
+        for (uint32_t bb = bits; bb; bb &= bb - 1u, ++pos)
+            if (pos >= w0 && pos < w0 + kSpkBuf) sh.spk[pos - w0] = id_of(__ffs(bb) - 1);
+        if (threadIdx.x == 0) sh.n = min((unsigned int)kSpkBuf, tot - w0);
+        flush_spikes(d, t, head, sg);
+    }
+}
+
+// One step t on this block's share of the neurons (all threads call).  In
+// kModeSmem, rs is the block's resident state and `phase` the parity of the
+// bulk copy's mbarrier; a copy that does not complete within limit_ns
+// records kStTimeout.
+template <int MODE>
+__device__ __forceinline__ void run_step(const Dev &d, long long t, StepShared &sh, const Resident &rs,
+                                         uint32_t phase, unsigned long long limit_ns)
+{
+    const Stage sg{sh.spk, sh.lng, sh.sht, &sh.n, &sh.gbase, &sh.nl, &sh.ns, &sh.routed, sh.tally,
+                   sh.e0, sh.f0, sh.pre1, sh.pre2, sh.part};
     Ctrl *c = d.ctrl;
     const int par = (int)(t & 1);
     const int slot = (int)(t % d.D);
@@ -522,11 +728,25 @@ __device__ __forceinline__ void run_step(const Dev &d, long long t)
     const bool do_cur = d.cur_every > 0 && (t % d.cur_every) == 0 && (t / d.cur_every) < d.cur_slots;
     int32_t *ring = d.ring + (long long)slot * d.M;
     int32_t *cur = do_cur ? d.cur_rec + (t / d.cur_every) * d.M : nullptr;
-    constexpr int NPT = VEC ? 4 : 1;
-    const long long nitem = VEC ? d.M / 4 : d.M;
+    if constexpr (MODE == kModeSmem) {
+        // a1: the block's part of ring slot t, in flight while the counters
+        // are cleared.  The slot was written through the generic proxy
+        // (other blocks' reductions, ordered by the grid barrier) and the
+        // staging buffer was last read by this block's threads: both are
+        // ordered before the async-proxy copy by the proxy fences.
+        __syncthreads();
+        if (threadIdx.x == 0 && rs.nq > 0) {
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            bulk_load(rs.ring, ring + rs.q0 * 4, (uint32_t)rs.nq * 16u, rs.bar);
+        }
+    }
     // this step's raster head, from the previous step's head and spike count
-    const long long head = next_head(d, *(volatile long long *)&c->head[slot3(t - 1)],
-                                     *(volatile unsigned int *)&c->S_acc[slot3(t - 1)], t - 1);
+    // (one thread reads them: every warp loading the same words would queue
+    // thousands of requests on one L2 line)
+    if (threadIdx.x == 0)
+        sh.head = next_head(d, *(volatile long long *)&c->head[slot3(t - 1)],
+                            *(volatile unsigned int *)&c->S_acc[slot3(t - 1)], t - 1);
     {
         // clear the other parity (used by step t - 1 only; step t + 1 fills
         // it) and the spike count of step t + 1
@@ -538,126 +758,129 @@ __device__ __forceinline__ void run_step(const Dev &d, long long t)
         }
         if (blockIdx.x == 0 && threadIdx.x == 0) c->S_acc[slot3(t + 1)] = 0;
     }
-    if (threadIdx.x < kPTab) s_th[threadIdx.x] = d.th32[threadIdx.x];
+    if (threadIdx.x < kPTab) sh.th[threadIdx.x] = d.th32[threadIdx.x];
     if (threadIdx.x == 0) {
-        s_n = 0;
-        s_routed = 0;
+        sh.n = 0;
+        sh.routed = 0;
     }
-    if (threadIdx.x < kWarps * kTally) (&s_tally[0][0])[threadIdx.x] = 0u;
+    if (threadIdx.x < kWarps * kTally) (&sh.tally[0][0])[threadIdx.x] = 0u;
     __syncthreads();
+    const long long head = sh.head;
 
     unsigned long long hc = 0, hv = 0;
-    for (long long b0 = (long long)blockIdx.x * kThreads; b0 < nitem; b0 += (long long)gridDim.x * kThreads) {
-        const long long q = b0 + threadIdx.x;
-        const long long j0 = q * NPT;
-        unsigned int m = 0;
-        if (q < nitem) {
-            float vv[NPT];
-            int32_t ii[NPT];
-            uint32_t r4;
-            if constexpr (VEC) {
-                const float4 v4 = *reinterpret_cast<const float4 *>(d.V + j0);
-                const int4 i4 = *reinterpret_cast<const int4 *>(ring + j0);
-                r4 = *reinterpret_cast<const uint32_t *>(d.ref + j0);
-                *reinterpret_cast<int4 *>(ring + j0) = make_int4(0, 0, 0, 0);
-                if (cur) *reinterpret_cast<int4 *>(cur + j0) = i4;
-                vv[0] = v4.x;
-                vv[1] = v4.y;
-                vv[2] = v4.z;
-                vv[3] = v4.w;
-                ii[0] = i4.x;
-                ii[1] = i4.y;
-                ii[2] = i4.z;
-                ii[3] = i4.w;
-            } else {
-                vv[0] = d.V[j0];
-                ii[0] = ring[j0];
-                r4 = d.ref[j0];
-                ring[j0] = 0;
-                if (cur) cur[j0] = ii[0];
-            }
-            uint32_t r_out = 0;
-            // one Philox block serves the four neurons of a quad in the
-            // global order; a reordering map needs a block per neuron
-            uint4 wq = make_uint4(0u, 0u, 0u, 0u);
-            if (VEC && !d.gid) wq = philox4(d.key0, d.key1, (uint32_t)(j0 >> 2), (uint32_t)t);
-#pragma unroll
-            for (int k = 0; k < NPT; ++k) {
-                const uint32_t g = d.gid ? d.gid[j0 + k] : (uint32_t)(j0 + k);
-                uint32_t u;
-                if (VEC && !d.gid) u = uint4_word(wq, (uint32_t)k);
-                else u = uint4_word(philox4(d.key0, d.key1, g >> 2, (uint32_t)t), g & 3u);
-                uint32_t r = (r4 >> (8 * k)) & 0xFFu;
-                if (lif_neuron(d, s_th, u, ii[k], vv[k], r)) m |= 1u << k;
-                r_out |= r << (8 * k);
-                if (do_hash) {
-                    hc += mix64(((unsigned long long)g << 32) | (uint32_t)ii[k]);
-                    hv += mix64(((unsigned long long)g << 32) | __float_as_uint(vv[k]));
+    // a1 + a2 over this block's neurons; each thread collects its spikes as
+    // bits (4 per quad, 1 per neuron in kModeScalar) and a3 runs once the
+    // word is full or the neurons are done
+    if constexpr (MODE == kModeSmem) {
+        if (rs.nq > 0 && !mbar_wait(rs.bar, phase, limit_ns)) atomicOr(&c->status, kStTimeout);
+        const long long qb = rs.q0 + threadIdx.x;
+        for (int l0 = 0; l0 < rs.nq; l0 += 8 * kThreads) {
+            uint32_t bits = 0;
+#pragma unroll 2
+            for (int k = 0; k < 8; ++k) {
+                const int lq = l0 + k * kThreads + (int)threadIdx.x;
+                if (lq < rs.nq) {
+                    const long long j0 = (rs.q0 + lq) * 4;
+                    const float4 v4 = rs.V[lq];
+                    const int4 i4 = rs.ring[lq];
+                    uint32_t r4 = rs.ref[lq];
+                    *reinterpret_cast<int4 *>(ring + j0) = make_int4(0, 0, 0, 0);
+                    if (cur) *reinterpret_cast<int4 *>(cur + j0) = i4;
+                    float vv[4] = {v4.x, v4.y, v4.z, v4.w};
+                    const int32_t ii[4] = {i4.x, i4.y, i4.z, i4.w};
+                    const unsigned int m = update_quad(d, sh.th, t, j0, vv, ii, r4, do_hash, hc, hv);
+                    prefetch_rows(d, j0, m);
+                    bits |= m << (4 * k);
+                    rs.V[lq] = make_float4(vv[0], vv[1], vv[2], vv[3]);
+                    rs.ref[lq] = r4;
                 }
             }
-            if constexpr (VEC) {
-                *reinterpret_cast<float4 *>(d.V + j0) = make_float4(vv[0], vv[1], vv[2], vv[3]);
-                *reinterpret_cast<uint32_t *>(d.ref + j0) = r_out;
-            } else {
-                d.V[j0] = vv[0];
-                d.ref[j0] = (uint8_t)r_out;
-            }
+            compact_flush(d, t, head, sh, sg, bits,
+                          [&](int b) { return (uint32_t)((qb + l0 + (b >> 2) * kThreads) * 4 + (b & 3)); });
         }
-        // a3: compaction of this pass (blocks without spikes skip it)
-        const unsigned int cnt = __popc(m);
-        if (__syncthreads_or(cnt)) {
-            unsigned int x = cnt;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-                if (lane >= o) x += y;
-            }
-            if (lane == 31) s_wsum[wid] = x;
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                unsigned int tot = 0;
-                for (int w = 0; w < kWarps; ++w) {
-                    const unsigned int cw = s_wsum[w];
-                    s_wsum[w] = tot;
-                    tot += cw;
+    } else if constexpr (MODE == kModeVec) {
+        const long long nq = d.M / 4, stride = (long long)gridDim.x * kThreads;
+        const long long qb = (long long)blockIdx.x * kThreads + threadIdx.x;
+        for (long long b0 = (long long)blockIdx.x * kThreads; b0 < nq; b0 += 8 * stride) {
+            uint32_t bits = 0;
+            for (int k = 0; k < 8; ++k) {
+                const long long q = b0 + k * stride + threadIdx.x;
+                if (q < nq) {
+                    const long long j0 = q * 4;
+                    const float4 v4 = *reinterpret_cast<const float4 *>(d.V + j0);
+                    const int4 i4 = *reinterpret_cast<const int4 *>(ring + j0);
+                    uint32_t r4 = *reinterpret_cast<const uint32_t *>(d.ref + j0);
+                    *reinterpret_cast<int4 *>(ring + j0) = make_int4(0, 0, 0, 0);
+                    if (cur) *reinterpret_cast<int4 *>(cur + j0) = i4;
+                    float vv[4] = {v4.x, v4.y, v4.z, v4.w};
+                    const int32_t ii[4] = {i4.x, i4.y, i4.z, i4.w};
+                    const unsigned int m = update_quad(d, sh.th, t, j0, vv, ii, r4, do_hash, hc, hv);
+                    prefetch_rows(d, j0, m);
+                    bits |= m << (4 * k);
+                    *reinterpret_cast<float4 *>(d.V + j0) = make_float4(vv[0], vv[1], vv[2], vv[3]);
+                    *reinterpret_cast<uint32_t *>(d.ref + j0) = r4;
                 }
-                s_tot = tot;
-                s_flush = (s_n + tot > (unsigned int)kSpkBuf);
             }
-            __syncthreads();
-            if (s_flush) flush_spikes(d, t, head, sg);
-            unsigned int pos = s_n + s_wsum[wid] + x - cnt;
-            for (unsigned int mm = m; mm; mm &= mm - 1u) s_spk[pos++] = (uint32_t)(j0 + __ffs(mm) - 1);
-            __syncthreads();
-            if (threadIdx.x == 0) s_n += s_tot;
+            const long long base = b0 - (long long)blockIdx.x * kThreads;
+            compact_flush(d, t, head, sh, sg, bits,
+                          [&](int b) { return (uint32_t)((qb + base + (b >> 2) * stride) * 4 + (b & 3)); });
+        }
+    } else {
+        const long long stride = (long long)gridDim.x * kThreads;
+        const long long jb = (long long)blockIdx.x * kThreads + threadIdx.x;
+        for (long long b0 = (long long)blockIdx.x * kThreads; b0 < d.M; b0 += 32 * stride) {
+            uint32_t bits = 0;
+            for (int k = 0; k < 32; ++k) {
+                const long long j = b0 + k * stride + threadIdx.x;
+                if (j < d.M) {
+                    float v = d.V[j];
+                    const int32_t irec = ring[j];
+                    uint32_t r = d.ref[j];
+                    ring[j] = 0;
+                    if (cur) cur[j] = irec;
+                    const uint32_t g = d.gid ? d.gid[j] : (uint32_t)j;
+                    const uint32_t u = uint4_word(philox4(d.key0, d.key1, g >> 2, (uint32_t)t), g & 3u);
+                    if (lif_neuron(d, sh.th, u, irec, v, r)) {
+                        bits |= 1u << k;
+                        prefetch_rows(d, j, 1u);
+                    }
+                    if (do_hash) {
+                        hc += mix64(((unsigned long long)g << 32) | (uint32_t)irec);
+                        hv += mix64(((unsigned long long)g << 32) | __float_as_uint(v));
+                    }
+                    d.V[j] = v;
+                    d.ref[j] = (uint8_t)r;
+                }
+            }
+            const long long base = b0 - (long long)blockIdx.x * kThreads;
+            compact_flush(d, t, head, sh, sg, bits, [&](int b) { return (uint32_t)(jb + base + b * stride); });
         }
     }
-    flush_spikes(d, t, head, sg);
     if (do_hash) {
         hc = warp_sum(hc);
         hv = warp_sum(hv);
         if (lane == 0) {
-            s_h[0][wid] = hc;
-            s_h[1][wid] = hv;
+            sh.h[0][wid] = hc;
+            sh.h[1][wid] = hv;
         }
         __syncthreads();
         if (threadIdx.x == 0) {
             unsigned long long a = 0, b = 0;
             for (int w = 0; w < kWarps; ++w) {
-                a += s_h[0][w];
-                b += s_h[1][w];
+                a += sh.h[0][w];
+                b += sh.h[1][w];
             }
             atomicAdd(&d.hash[2 * t], a);
             atomicAdd(&d.hash[2 * t + 1], b);
         }
     }
     __syncthreads();
-    if (s_routed) {
+    if (sh.routed) {
         // tallies of the routed spikes into this block's row (no other block
         // writes it, so plain adds)
         if (threadIdx.x < kTally) {
             unsigned long long a = 0;
-            for (int w = 0; w < kWarps; ++w) a += s_tally[w][threadIdx.x];
+            for (int w = 0; w < kWarps; ++w) a += sh.tally[w][threadIdx.x];
             d.tally[(size_t)blockIdx.x * C_N + C_EVENTS + threadIdx.x] += a;
         }
     }
@@ -686,13 +909,16 @@ __device__ __forceinline__ void close_step(const Dev &d, long long t)
 // Step t = ctrl->t + k of a captured graph.  Block 0 closes step t - 1 (the
 // graph's first step was closed by the graph before); k_advance closes the
 // graph's last step and moves ctrl->t past its steps.
-template <bool VEC>
+template <int MODE>
 __global__ void __launch_bounds__(kThreads) k_step(const Dev d, int k)
 {
+    __shared__ StepShared sh;
     pdl_enter();
-    const long long t = *(volatile long long *)&d.ctrl->t + k;
+    if (threadIdx.x == 0) sh.t0 = *(volatile long long *)&d.ctrl->t;
+    __syncthreads();
+    const long long t = sh.t0 + k;
     if (k > 0 && blockIdx.x == 0 && threadIdx.x == 0) close_step(d, t - 1);
-    run_step<VEC>(d, t);
+    run_step<MODE>(d, t, sh, Resident{}, 0u, 0ull);
 }
 
 __global__ void k_advance(const Dev d, int steps)
@@ -706,20 +932,46 @@ __global__ void k_advance(const Dev d, int steps)
 // ---------------------------------------------------------------- persistent
 // T steps in one cooperative launch, a grid barrier after each.  Block 0
 // closes step t - 1 while step t runs and the last step after the final
-// barrier.  Every wait is bounded (limit_ns per barrier); a timeout ends the
-// run with kStTimeout in the status word.  With phase_ns set, block 0 sums
-// its own work and its wait at the barrier.  skip_arrival (tests of the
-// bounded wait only): block 0 waits at the first barrier without arriving, so
-// every block's wait runs out.
-template <bool VEC>
+// barrier.  Every wait is bounded (limit_ns per barrier and per bulk copy); a
+// timeout ends the run with kStTimeout in the status word.  With phase_ns
+// set, block 0 sums its own work and its wait at the barrier.  skip_arrival
+// (tests of the bounded wait only): block 0 waits at the first barrier
+// without arriving, so every block's wait runs out.  In kModeSmem block b
+// owns quads [b cq, (b + 1) cq) (cq = Dev::chunk_q) and keeps their V and
+// ref in dynamic shared memory from the launch's start to its end.
+template <int MODE>
 __global__ void __launch_bounds__(kThreads, 4) k_persist(const Dev d, int T, unsigned long long limit_ns,
                                                          int skip_arrival)
 {
+    __shared__ StepShared sh;
+    __shared__ __align__(8) unsigned long long s_bar;
+    extern __shared__ __align__(128) unsigned char s_dyn[];
     Ctrl *c = d.ctrl;
-    const long long t0 = *(volatile long long *)&c->t;
+    Resident rs{};
+    if constexpr (MODE == kModeSmem) {
+        const long long cq = d.chunk_q;
+        rs.V = reinterpret_cast<float4 *>(s_dyn);
+        rs.ring = reinterpret_cast<int4 *>(s_dyn + cq * 16);
+        rs.ref = reinterpret_cast<uint32_t *>(s_dyn + cq * 32);
+        rs.bar = &s_bar;
+        rs.q0 = (long long)blockIdx.x * cq;
+        rs.nq = (int)max(0ll, min(cq, d.M / 4 - rs.q0));
+        for (int lq = threadIdx.x; lq < rs.nq; lq += kThreads) {
+            rs.V[lq] = reinterpret_cast<const float4 *>(d.V)[rs.q0 + lq];
+            rs.ref[lq] = reinterpret_cast<const uint32_t *>(d.ref)[rs.q0 + lq];
+        }
+        if (threadIdx.x == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_bar)) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) sh.t0 = *(volatile long long *)&c->t;
+    __syncthreads();
+    const long long t0 = sh.t0;
     const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
     const bool prof = d.phase_ns != nullptr && lead;
-    int done = 0;
+    int done = 0, issued = 0;
     long long closed = t0 - 1;
     unsigned long long ns[2] = {0, 0};
     for (int s = 0; s < T; ++s) {
@@ -729,7 +981,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_persist(const Dev d, int T, uns
             close_step(d, t - 1);
             closed = t - 1;
         }
-        run_step<VEC>(d, t);
+        run_step<MODE>(d, t, sh, rs, (uint32_t)(s & 1), limit_ns);
+        ++issued;
         const unsigned long long b = prof ? global_ns() : 0;
         if (!grid_sync(c, (unsigned long long)s, limit_ns, !(skip_arrival && s == 0 && blockIdx.x == 0))) break;
         if (prof) {
@@ -738,6 +991,18 @@ __global__ void __launch_bounds__(kThreads, 4) k_persist(const Dev d, int T, uns
             ns[1] += e - b;
         }
         ++done;
+    }
+    if constexpr (MODE == kModeSmem) {
+        // after a timeout, give this block's last bulk copy a bounded wait
+        // before its shared memory is released
+        __syncthreads();
+        if (rs.nq > 0 && issued > 0 && (*(volatile unsigned int *)&c->status & kStTimeout))
+            mbar_wait(rs.bar, (uint32_t)((issued - 1) & 1), limit_ns);
+        // the resident state goes back to global memory
+        for (int lq = threadIdx.x; lq < rs.nq; lq += kThreads) {
+            reinterpret_cast<float4 *>(d.V)[rs.q0 + lq] = rs.V[lq];
+            reinterpret_cast<uint32_t *>(d.ref)[rs.q0 + lq] = rs.ref[lq];
+        }
     }
     if (lead) {
         if (t0 + done - 1 > closed) close_step(d, t0 + done - 1);

@@ -82,10 +82,13 @@ def _compare(sim, o, T, rec, t0=0):
     return c, r
 
 
-@pytest.fixture(params=["persistent", "graph"])
+@pytest.fixture(params=["persistent", "persistent-global", "graph"])
 def path(request, monkeypatch):
-    """Run a test on the persistent kernel and on the CUDA-graph path."""
-    monkeypatch.setenv("SNN_PERSIST", "1" if request.param == "persistent" else "0")
+    """Run a test on the persistent kernel (neuron state resident in shared
+    memory where it fits, or read from global memory every step) and on the
+    CUDA-graph path."""
+    monkeypatch.setenv("SNN_PERSIST", "0" if request.param == "graph" else "1")
+    monkeypatch.setenv("SNN_PERSIST_SMEM", "0" if request.param == "persistent-global" else "1")
     return request.param
 
 
@@ -94,7 +97,7 @@ def test_tiny_full_run(snn, path):
     cfg = synth.TINY
     g = synth.make_network(cfg)
     sim, o, rec, _ = _run_pair(snn, g, cfg, cfg.steps, cfg.P, cfg.n_vn, cur_every=50)
-    assert (sim.launches(10) == 1) == (path == "persistent")
+    assert (sim.launches(10) == 1) == path.startswith("persistent")
     sim.step(cfg.steps)
     c, _ = _compare(sim, o, cfg.steps, rec)
     assert sim.sync_status() == 0
