@@ -225,14 +225,14 @@ int snn_sim_create(const snn_network *net, const snn_routing *rt, const snn_sim_
  * spike compaction; (a4) level-1 bucketing by destination VN; (a5) level-2
  * relay expansion into per-partition inboxes; (a6) CSR fan-out of int16
  * weights into int32 ring accumulators.  Asynchronous on the sim's stream.
- * Every block of the step kernel runs a1-a6 on its share of the neurons
- * and delivers the spikes it found (a step's deliveries write only the
- * ring slots of later steps).  On a GPU with cooperative launch the T steps
- * run in one persistent kernel (every block resident, one grid barrier per
- * step, each barrier wait bounded by one second); otherwise, or with the
- * environment variable SNN_PERSIST=0 at snn_sim_create, as replays of
- * captured CUDA graphs of one kernel per step.  Both give the same results
- * bit for bit.
+ * A step runs in two halves: a1-a3 over the neurons into the step's spike
+ * list, then a4-a6 over equal shares of that list (a step's deliveries
+ * write only the ring slots of later steps).  On a GPU with cooperative
+ * launch the T steps run in one persistent kernel (every block resident, a
+ * grid barrier after each half, each barrier wait bounded by one second);
+ * otherwise, or with the environment variable SNN_PERSIST=0 at
+ * snn_sim_create, as replays of captured CUDA graphs of two kernels per
+ * step.  Both give the same results bit for bit.
  * Errors raised on the device are reported by snn_sync_status.
  * Errors: SNN_E_ARG, SNN_E_CUDA.
  */
@@ -281,19 +281,19 @@ int snn_load_state(snn_sim *sim, const void *host_buf, size_t bytes);
  * reupload != 0 the routing tables are copied to the device again. */
 int snn_sim_reset(snn_sim *sim, int32_t reupload);
 
-/* Kernels of one step: 1 (a1-a6 in one kernel). */
+/* Kernels of one step on the graph path: 2 (a1-a3, a4-a6). */
 int64_t snn_launches_per_step(const snn_sim *sim);
 /* Kernel launches one snn_step(sim, T) issues: 1 on the persistent path,
- * 1 per step plus one per replayed graph on the graph path. */
+ * 2 per step plus one per replayed graph on the graph path. */
 int64_t snn_launches(const snn_sim *sim, int32_t T);
 
 /*
  * Advance T steps like snn_step and return, in milliseconds summed over the
  * steps, phase_ms[0] = the steps' work (a1-a6) and phase_ms[1] = the wait
- * at the grid barrier after each step.  Persistent path: block 0 reads the
- * GPU's global timer at the start of a step, at its arrival at the barrier
- * and after the barrier.  Graph path: CUDA events recorded before and after
- * every step kernel (the event nodes add a little time to each step);
+ * at the grid barriers.  Persistent path: block 0 reads the GPU's global
+ * timer at the start of each half of a step, at its arrival at the barrier
+ * after it and when the barrier releases.  Graph path: CUDA events recorded before and after
+ * the two kernels of every step (the event nodes add a little time);
  * phase_ms[1] = 0.  Synchronises the stream.
  * Errors: SNN_E_ARG, SNN_E_CUDA.
  */

@@ -114,7 +114,7 @@ struct Layout {
     Region V, ref, ring, gid, src_part, syn_td, syn_w, l1_ptr, l1_vn, l1_l2, l2, row, l1_pair, l2_pair;
     Region bucket, bucket_slot, bucket_cnt, inbox, inbox_slot, inbox_cnt;
     Region tally;  // per-block tally rows
-    Region spk, raster_off, hash, cur_rec, counters, ctrl;
+    Region spk, spk_step, raster_off, hash, cur_rec, counters, ctrl;
     Region fwd, fo_cnt;  // snn_deliver_spikes: global -> internal map, scratch counters
     Region phase_ns;
     size_t total = 0;
@@ -202,6 +202,7 @@ static int make_layout(const snn_routing *rt, const snn_sim_params *p, Layout &L
     place(L, L.inbox_cnt, 2 * sizeof(uint32_t) * kPairStride * n_ip);  // by step parity
     place(L, L.tally, sizeof(unsigned long long) * C_N * (size_t)L.tally_rows);
     place(L, L.spk, sizeof(uint32_t) * (size_t)(p->raster_cap + M));
+    place(L, L.spk_step, sizeof(uint32_t) * (size_t)M);
     place(L, L.raster_off, sizeof(long long) * (size_t)(p->raster_steps + 1));
     place(L, L.hash, sizeof(unsigned long long) * 2 * (size_t)p->hash_steps);
     place(L, L.cur_rec, sizeof(int32_t) * (size_t)M * (size_t)p->cur_slots);
@@ -377,14 +378,14 @@ static int reset_state(snn_sim *s)
     return SNN_OK;
 }
 
-// Launch the step kernel for step ctrl->t + k.  With programmatic dependent
-// launch each kernel may be scheduled while the one before it drains; it
-// waits (griddepcontrol.wait) before reading.
-static cudaError_t launch_step(snn_sim *s, int k, cudaStream_t st)
+// Launch kernel `half` (0: k_update, 1: k_route) of step ctrl->t + k.  With
+// programmatic dependent launch each kernel may be scheduled while the one
+// before it drains; it waits (griddepcontrol.wait) before reading.
+static cudaError_t launch_half(snn_sim *s, int half, int k, cudaStream_t st)
 {
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
-    cfg.gridDim = dim3(s->grid_update);
+    cfg.gridDim = dim3(half == 0 ? s->grid_update : s->grid_route);
     cfg.blockDim = dim3(kThreads);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = st;
@@ -394,8 +395,15 @@ static cudaError_t launch_step(snn_sim *s, int k, cudaStream_t st)
         cfg.attrs = attr;
         cfg.numAttrs = 1;
     }
-    cudaLaunchKernelEx(&cfg, s->vec ? k_step<kModeVec> : k_step<kModeScalar>, s->dev, k);
+    if (half == 0) cudaLaunchKernelEx(&cfg, s->vec ? k_update<kModeVec> : k_update<kModeScalar>, s->dev, k);
+    else cudaLaunchKernelEx(&cfg, k_route, s->dev, k);
     return cudaGetLastError();
+}
+
+static cudaError_t launch_step(snn_sim *s, int k, cudaStream_t st)
+{
+    cudaError_t e = launch_half(s, 0, k, st);
+    return e == cudaSuccess ? launch_half(s, 1, k, st) : e;
 }
 
 static int capture(snn_sim *s, int steps, cudaGraphExec_t *out)
@@ -572,6 +580,7 @@ extern "C" int snn_sim_create(const snn_network *net, const snn_routing *rt, con
     d.inbox_cnt = (uint32_t *)(w + L.inbox_cnt.off);
     d.tally = (unsigned long long *)(w + L.tally.off);
     d.spk = (uint32_t *)(w + L.spk.off);
+    d.spk_step = (uint32_t *)(w + L.spk_step.off);
     d.raster_off = (long long *)(w + L.raster_off.off);
     d.hash = (unsigned long long *)(w + L.hash.off);
     d.cur_rec = (int32_t *)(w + L.cur_rec.off);
@@ -863,12 +872,12 @@ extern "C" int64_t snn_launches(const snn_sim *s, int32_t T)
     if (!s || T <= 0) return 0;
     if (s->persist) return 1;
     const int64_t graphs = (s->U > 1 ? T / s->U : 0) + (s->U > 1 ? T % s->U : T);
-    return (int64_t)T + graphs;  // step kernels + one k_advance per graph
+    return 2 * (int64_t)T + graphs;  // two step kernels + one k_advance per graph
 }
 
 extern "C" int64_t snn_launches_per_step(const snn_sim *s)
 {
-    return s ? 1 : 0;
+    return s ? 2 : 0;
 }
 
 static int read_ctrl(snn_sim *s, Ctrl *c)

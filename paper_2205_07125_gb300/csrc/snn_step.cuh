@@ -1,33 +1,36 @@
-// Step kernel of one simulation step t (sm_103a), included by snn_sim.cu.
+// Step kernels of one simulation step t (sm_103a), included by snn_sim.cu.
 //
 // The routing is the paper's two-level route (arXiv 2205.07125, Sec. IV.B);
 // the neuron model is LIF (Table I); the arithmetic follows the library's
-// documented readings (include/snn.h).  Every block runs the whole step on
-// its share of the neurons:
+// documented readings (include/snn.h).  A step has two halves, each block
+// taking an equal share of the work in both:
 //   a1 consume ring slot t mod D, Poisson drive (Philox4x32-10, inverse CDF);
 //   a2 FP32 LIF update + threshold (no FMA, fixed order);
-//   a3 warp-scan / block-scan compaction of the spikes into a block buffer
-//      and the step's spike list (4 neurons per thread, 16-byte loads);
-//   a4 level-1 bucketing, one warp per spike: the spike's entry is appended
-//      to the bucket of every destination VN in its level-1 row (one entry per
-//      VN: deduplicated);
+//   a3 warp-scan / block-scan compaction of the spikes into the step's spike
+//      list (one reservation per block);
+//   -- grid-wide synchronisation: the list is complete --
+//   a4 level-1 bucketing of an equal share of the list per block, the
+//      level-1 and level-2 entries of a round of spikes spread over the
+//      block's threads: each spike's entry is appended to the bucket of every
+//      destination VN in its level-1 row (one entry per VN: deduplicated);
 //   a5 level-2 relay expansion: every (spike, VN) entry becomes an inbox
 //      entry of each partition of that VN holding targets;
-//   a6 delivery of the block's spikes: the level-2 segments are staged in
-//      shared memory (long segments cut into 128-synapse pieces, one warp
-//      each; short ones walked by one lane) and every synapse adds its int16
-//      weight with a 32-bit reduction into ring[(t + d) mod D][target].
-// Delivery of step t writes only slots t+1 .. t+D-1 (D = max delay + 1), so
-// it may overlap the updates of step t; one grid-wide synchronisation per
-// step orders it before step t + 1 reads its slot.  Exchange fill counters
+//   a6 delivery of the round: the level-2 segments are staged in shared
+//      memory (long segments cut into 128-synapse pieces, one warp each;
+//      short ones walked by one lane) and every synapse adds its int16
+//      weight with a 32-bit reduction into ring[(t + d) mod D][target];
+//   -- grid-wide synchronisation: step t + 1 may read its ring slot --
+// Splitting the list evenly keeps a block that found many spikes from
+// holding up the step.  Delivery of step t writes only slots t+1 .. t+D-1
+// (D = max delay + 1), never the slot step t reads.  Exchange fill counters
 // are kept twice, by step parity: step t fills parity t & 1 and clears the
 // other one, which only step t - 1 used.  The spike counts and raster heads
 // of steps rotate through three slots (a step's slot is read during the
 // next step, cleared during the one after).
 //
-// Two ways to run: k_persist, one cooperative launch for T steps with a
-// bounded grid barrier after each step, and the CUDA-graph path, one k_step
-// launch per step with programmatic dependent launch.
+// Two ways to run: k_persist, one cooperative launch for T steps with
+// bounded grid barriers, and the CUDA-graph path, k_update and k_route per
+// step with programmatic dependent launch.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -39,7 +42,6 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kPTab = 32;
-constexpr int kSpkBuf = 1024;   // spikes a block buffers before routing them
 constexpr int kLongCap = 512;   // staged pieces of one routing round
 constexpr int kShortCap = 1024; // staged short segments of one routing round
 constexpr int kRound = 16;      // spikes routed per round (<= 32)
@@ -99,6 +101,7 @@ struct Dev {
     unsigned long long *inbox;               // segments offset << 24 | length, region (p, q)
     const ulonglong2 *inbox_slot;            // [n_ipair] region {first entry, capacity}
     uint32_t *inbox_cnt;                     // [2][n_ipair * kPairStride], by step parity
+    uint32_t *spk_step;  // [M] spikes of the running step (internal ids), in list order
     // records
     uint32_t *spk;
     long long *raster_off;
@@ -306,13 +309,11 @@ __device__ __forceinline__ long long next_head(const Dev &d, long long h, unsign
     return -1;
 }
 
-// Shared-memory state of one block's step (declared by run_step).
+// Shared-memory state of one routing round (from the block's StepShared).
 struct Stage {
-    uint32_t *spk;             // [kSpkBuf] buffered spikes (internal ids)
     unsigned long long *lng;   // [kLongCap] pieces: offset << 8 | length (<= kPiece)
     unsigned long long *sht;   // [kShortCap] short segments: offset << 8 | length (<= kShortSeg)
-    unsigned int *n, *gbase, *nl, *ns;
-    int *routed;
+    unsigned int *nl, *ns;
     unsigned int (*ty)[kTally];  // [kWarps][kTally] tallies: events, l1 local, l1 cross-VN, l2 by class
     uint32_t *e0, *f0;           // [kRound] first level-1 / level-2 entry of each spike of a round
     uint32_t *pre1, *pre2;       // [kRound + 1] prefix of the level-1 / level-2 entry counts
@@ -546,28 +547,17 @@ __device__ __forceinline__ void route_round(const Dev &d, int par, int tm, const
     __syncthreads();
 }
 
-// Route and deliver the block's buffered spikes in rounds of up to kRound
-// spikes, and append them to the step's spike list at raster head `head`
-// (all threads call).
-__device__ __forceinline__ void flush_spikes(const Dev &d, long long t, long long head, const Stage &sg)
+// a4-a6 for the spikes [lo, hi) of step t's spike list, in rounds of up to
+// kRound, and their copy into the raster at `head` (all threads call).
+__device__ __forceinline__ void route_range(const Dev &d, long long t, long long head, const Stage &sg,
+                                            unsigned int lo, unsigned int hi)
 {
-    __syncthreads();
-    const unsigned int n = *sg.n;
-    if (n == 0) return;
     const int par = (int)(t & 1);
     const int tm = (int)(t % d.D);
-    if (threadIdx.x == 0) {
-        *sg.gbase = atomicAdd(&d.ctrl->S_acc[slot3(t)], n);
-        *sg.routed = 1;
-    }
-    for (unsigned int b = 0; b < n; b += kRound) route_round(d, par, tm, sg.spk + b, min(n - b, (unsigned int)kRound), sg);
-    if (head >= 0) {
-        const unsigned int gb = *sg.gbase;
-        for (unsigned int k = threadIdx.x; k < n; k += kThreads) d.spk[head + gb + k] = sg.spk[k];
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) *sg.n = 0;
-    __syncthreads();
+    if (head >= 0)
+        for (unsigned int k = lo + threadIdx.x; k < hi; k += kThreads) d.spk[head + k] = d.spk_step[k];
+    for (unsigned int b = lo; b < hi; b += kRound)
+        route_round(d, par, tm, d.spk_step + b, min(hi - b, (unsigned int)kRound), sg);
 }
 
 // ---------------------------------------------------------------- a1-a6
@@ -653,14 +643,12 @@ __device__ __forceinline__ unsigned int update_quad(const Dev &d, const uint32_t
     return m;
 }
 
-// Shared-memory scratch of run_step.
+// Shared-memory scratch of a block's step.
 struct StepShared {
-    uint32_t spk[kSpkBuf];
     unsigned long long lng[kLongCap];
     unsigned long long sht[kShortCap];
     unsigned int wsum[kWarps];
-    unsigned int n, tot, gbase, nl, ns;
-    int routed;
+    unsigned int tot, gbase, nl, ns;
     long long head;
     long long t0;
     unsigned long long h[2][kWarps];
@@ -671,13 +659,12 @@ struct StepShared {
 };
 
 // a3: compaction of the spikes each thread collected in `bits` (bit b is
-// neuron id_of(b)) into the block buffer, then routing and delivery of the
-// buffer.  The block's spikes are numbered by a block-wide scan and go
-// through the buffer in windows of kSpkBuf (all threads call; without spikes
-// this costs one barrier).
+// neuron id_of(b)) into step t's spike list: a block-wide scan numbers them
+// and one reservation per block places them (all threads call; without
+// spikes this costs one barrier).
 template <class IdOf>
-__device__ __forceinline__ void compact_flush(const Dev &d, long long t, long long head, StepShared &sh,
-                                              const Stage &sg, uint32_t bits, IdOf id_of)
+__device__ __forceinline__ void compact_spikes(const Dev &d, long long t, StepShared &sh, uint32_t bits,
+                                               IdOf id_of)
 {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const unsigned int cnt = __popc(bits);
@@ -697,29 +684,22 @@ __device__ __forceinline__ void compact_flush(const Dev &d, long long t, long lo
             sh.wsum[w] = tot;
             tot += cw;
         }
-        sh.tot = tot;
+        sh.gbase = atomicAdd(&d.ctrl->S_acc[slot3(t)], tot);
     }
     __syncthreads();
-    const unsigned int first = sh.wsum[wid] + x - cnt, tot = sh.tot;
-    for (unsigned int w0 = 0; w0 < tot; w0 += kSpkBuf) {
-        unsigned int pos = first;
-        for (uint32_t bb = bits; bb; bb &= bb - 1u, ++pos)
-            if (pos >= w0 && pos < w0 + kSpkBuf) sh.spk[pos - w0] = id_of(__ffs(bb) - 1);
-        if (threadIdx.x == 0) sh.n = min((unsigned int)kSpkBuf, tot - w0);
-        flush_spikes(d, t, head, sg);
-    }
+    unsigned int pos = sh.gbase + sh.wsum[wid] + x - cnt;
+    for (uint32_t bb = bits; bb; bb &= bb - 1u) d.spk_step[pos++] = id_of(__ffs(bb) - 1);
 }
 
-// One step t on this block's share of the neurons (all threads call).  In
-// kModeSmem, rs is the block's resident state and `phase` the parity of the
-// bulk copy's mbarrier; a copy that does not complete within limit_ns
-// records kStTimeout.
+// First half of step t on this block's share of the neurons (all threads
+// call): a1-a3, the spikes into the step's list.  In kModeSmem, rs is the
+// block's resident state and `phase` the parity of the bulk copy's
+// mbarrier; a copy that does not complete within limit_ns records
+// kStTimeout.
 template <int MODE>
-__device__ __forceinline__ void run_step(const Dev &d, long long t, StepShared &sh, const Resident &rs,
-                                         uint32_t phase, unsigned long long limit_ns)
+__device__ __forceinline__ void update_step(const Dev &d, long long t, StepShared &sh, const Resident &rs,
+                                            uint32_t phase, unsigned long long limit_ns)
 {
-    const Stage sg{sh.spk, sh.lng, sh.sht, &sh.n, &sh.gbase, &sh.nl, &sh.ns, &sh.routed, sh.tally,
-                   sh.e0, sh.f0, sh.pre1, sh.pre2, sh.part};
     Ctrl *c = d.ctrl;
     const int par = (int)(t & 1);
     const int slot = (int)(t % d.D);
@@ -741,12 +721,6 @@ __device__ __forceinline__ void run_step(const Dev &d, long long t, StepShared &
             bulk_load(rs.ring, ring + rs.q0 * 4, (uint32_t)rs.nq * 16u, rs.bar);
         }
     }
-    // this step's raster head, from the previous step's head and spike count
-    // (one thread reads them: every warp loading the same words would queue
-    // thousands of requests on one L2 line)
-    if (threadIdx.x == 0)
-        sh.head = next_head(d, *(volatile long long *)&c->head[slot3(t - 1)],
-                            *(volatile unsigned int *)&c->S_acc[slot3(t - 1)], t - 1);
     {
         // clear the other parity (used by step t - 1 only; step t + 1 fills
         // it) and the spike count of step t + 1
@@ -759,13 +733,7 @@ __device__ __forceinline__ void run_step(const Dev &d, long long t, StepShared &
         if (blockIdx.x == 0 && threadIdx.x == 0) c->S_acc[slot3(t + 1)] = 0;
     }
     if (threadIdx.x < kPTab) sh.th[threadIdx.x] = d.th32[threadIdx.x];
-    if (threadIdx.x == 0) {
-        sh.n = 0;
-        sh.routed = 0;
-    }
-    if (threadIdx.x < kWarps * kTally) (&sh.tally[0][0])[threadIdx.x] = 0u;
     __syncthreads();
-    const long long head = sh.head;
 
     unsigned long long hc = 0, hv = 0;
     // a1 + a2 over this block's neurons; each thread collects its spikes as
@@ -795,7 +763,7 @@ __device__ __forceinline__ void run_step(const Dev &d, long long t, StepShared &
                     rs.ref[lq] = r4;
                 }
             }
-            compact_flush(d, t, head, sh, sg, bits,
+            compact_spikes(d, t, sh, bits,
                           [&](int b) { return (uint32_t)((qb + l0 + (b >> 2) * kThreads) * 4 + (b & 3)); });
         }
     } else if constexpr (MODE == kModeVec) {
@@ -822,7 +790,7 @@ __device__ __forceinline__ void run_step(const Dev &d, long long t, StepShared &
                 }
             }
             const long long base = b0 - (long long)blockIdx.x * kThreads;
-            compact_flush(d, t, head, sh, sg, bits,
+            compact_spikes(d, t, sh, bits,
                           [&](int b) { return (uint32_t)((qb + base + (b >> 2) * stride) * 4 + (b & 3)); });
         }
     } else {
@@ -853,7 +821,7 @@ __device__ __forceinline__ void run_step(const Dev &d, long long t, StepShared &
                 }
             }
             const long long base = b0 - (long long)blockIdx.x * kThreads;
-            compact_flush(d, t, head, sh, sg, bits, [&](int b) { return (uint32_t)(jb + base + b * stride); });
+            compact_spikes(d, t, sh, bits, [&](int b) { return (uint32_t)(jb + base + b * stride); });
         }
     }
     if (do_hash) {
@@ -874,15 +842,35 @@ __device__ __forceinline__ void run_step(const Dev &d, long long t, StepShared &
             atomicAdd(&d.hash[2 * t + 1], b);
         }
     }
+}
+
+// Second half of step t (all threads call): a4-a6 for this block's share of
+// the step's spikes, an equal share of the list for every block, and their
+// raster copy.
+__device__ __forceinline__ void route_step(const Dev &d, long long t, StepShared &sh)
+{
+    const Stage sg{sh.lng, sh.sht, &sh.nl, &sh.ns, sh.tally, sh.e0, sh.f0, sh.pre1, sh.pre2, sh.part};
+    Ctrl *c = d.ctrl;
+    if (threadIdx.x == 0) {
+        // one thread reads the step words: every warp loading them would
+        // queue thousands of requests on one L2 line
+        sh.tot = *(volatile unsigned int *)&c->S_acc[slot3(t)];
+        sh.head = *(volatile long long *)&c->head[slot3(t)];
+    }
+    if (threadIdx.x < kWarps * kTally) (&sh.tally[0][0])[threadIdx.x] = 0u;
     __syncthreads();
-    if (sh.routed) {
-        // tallies of the routed spikes into this block's row (no other block
-        // writes it, so plain adds)
-        if (threadIdx.x < kTally) {
-            unsigned long long a = 0;
-            for (int w = 0; w < kWarps; ++w) a += sh.tally[w][threadIdx.x];
-            d.tally[(size_t)blockIdx.x * C_N + C_EVENTS + threadIdx.x] += a;
-        }
+    const unsigned long long S = sh.tot;
+    const unsigned int lo = (unsigned int)(S * blockIdx.x / gridDim.x);
+    const unsigned int hi = (unsigned int)(S * (blockIdx.x + 1) / gridDim.x);
+    if (lo >= hi) return;
+    route_range(d, t, sh.head, sg, lo, hi);
+    // tallies of the routed spikes into this block's row (no other block
+    // writes it, so plain adds)
+    __syncthreads();
+    if (threadIdx.x < kTally) {
+        unsigned long long a = 0;
+        for (int w = 0; w < kWarps; ++w) a += sh.tally[w][threadIdx.x];
+        d.tally[(size_t)blockIdx.x * C_N + C_EVENTS + threadIdx.x] += a;
     }
 }
 
@@ -906,11 +894,12 @@ __device__ __forceinline__ void close_step(const Dev &d, long long t)
 }
 
 // ---------------------------------------------------------------- graph path
-// Step t = ctrl->t + k of a captured graph.  Block 0 closes step t - 1 (the
-// graph's first step was closed by the graph before); k_advance closes the
-// graph's last step and moves ctrl->t past its steps.
+// Step t = ctrl->t + k of a captured graph: k_update (a1-a3) then k_route
+// (a4-a6).  Block 0 of k_update closes step t - 1 (the graph's first step was
+// closed by the graph before); k_advance closes the graph's last step and
+// moves ctrl->t past its steps.
 template <int MODE>
-__global__ void __launch_bounds__(kThreads) k_step(const Dev d, int k)
+__global__ void __launch_bounds__(kThreads) k_update(const Dev d, int k)
 {
     __shared__ StepShared sh;
     pdl_enter();
@@ -918,7 +907,16 @@ __global__ void __launch_bounds__(kThreads) k_step(const Dev d, int k)
     __syncthreads();
     const long long t = sh.t0 + k;
     if (k > 0 && blockIdx.x == 0 && threadIdx.x == 0) close_step(d, t - 1);
-    run_step<MODE>(d, t, sh, Resident{}, 0u, 0ull);
+    update_step<MODE>(d, t, sh, Resident{}, 0u, 0ull);
+}
+
+__global__ void __launch_bounds__(kThreads) k_route(const Dev d, int k)
+{
+    __shared__ StepShared sh;
+    pdl_enter();
+    if (threadIdx.x == 0) sh.t0 = *(volatile long long *)&d.ctrl->t;
+    __syncthreads();
+    route_step(d, sh.t0 + k, sh);
 }
 
 __global__ void k_advance(const Dev d, int steps)
@@ -930,11 +928,12 @@ __global__ void k_advance(const Dev d, int steps)
 }
 
 // ---------------------------------------------------------------- persistent
-// T steps in one cooperative launch, a grid barrier after each.  Block 0
-// closes step t - 1 while step t runs and the last step after the final
-// barrier.  Every wait is bounded (limit_ns per barrier and per bulk copy); a
-// timeout ends the run with kStTimeout in the status word.  With phase_ns
-// set, block 0 sums its own work and its wait at the barrier.  skip_arrival
+// T steps in one cooperative launch: update_step, grid barrier, route_step,
+// grid barrier.  Block 0 closes step t - 1 while step t updates and the last
+// step after the final barrier.  Every wait is bounded (limit_ns per barrier
+// and per bulk copy); a timeout ends the run with kStTimeout in the status
+// word.  With phase_ns set, block 0 sums its own work of both halves and its
+// waits at the two barriers.  skip_arrival
 // (tests of the bounded wait only): block 0 waits at the first barrier
 // without arriving, so every block's wait runs out.  In kModeSmem block b
 // owns quads [b cq, (b + 1) cq) (cq = Dev::chunk_q) and keeps their V and
@@ -981,14 +980,18 @@ __global__ void __launch_bounds__(kThreads, 4) k_persist(const Dev d, int T, uns
             close_step(d, t - 1);
             closed = t - 1;
         }
-        run_step<MODE>(d, t, sh, rs, (uint32_t)(s & 1), limit_ns);
+        update_step<MODE>(d, t, sh, rs, (uint32_t)(s & 1), limit_ns);
         ++issued;
         const unsigned long long b = prof ? global_ns() : 0;
-        if (!grid_sync(c, (unsigned long long)s, limit_ns, !(skip_arrival && s == 0 && blockIdx.x == 0))) break;
+        if (!grid_sync(c, 2ull * s, limit_ns, !(skip_arrival && s == 0 && blockIdx.x == 0))) break;
+        const unsigned long long e = prof ? global_ns() : 0;
+        route_step(d, t, sh);
+        const unsigned long long f = prof ? global_ns() : 0;
+        if (!grid_sync(c, 2ull * s + 1ull, limit_ns)) break;
         if (prof) {
-            const unsigned long long e = global_ns();
-            ns[0] += b - a;
-            ns[1] += e - b;
+            const unsigned long long g = global_ns();
+            ns[0] += (b - a) + (f - e);
+            ns[1] += (e - b) + (g - f);
         }
         ++done;
     }
