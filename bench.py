@@ -226,7 +226,7 @@ def run_ours(args):
     persistent = sim.launches(2) == 1
     phases = {
         "work": {"what": "update, compaction, level-1 bucketing, level-2 expansion, delivery"
-                         + (" (block 0)" if persistent else " (k_step kernel)"),
+                         + (" (block 0)" if persistent else " (k_update + k_route kernels)"),
                  "ms_per_step": phase_ms[0] / NP},
         "sync": {"what": "block 0's wait at the grid barrier" if persistent else "none (kernel boundary)",
                  "ms_per_step": phase_ms[1] / NP},
@@ -243,16 +243,24 @@ def run_ours(args):
         achieved = step_bytes * K / (ms * 1e-3) / 1e9
         per_launch = step_bytes * K
     else:
-        kern = "k_step"
+        kern = "k_update+k_route"
         achieved = step_bytes / (phase_ms[0] / NP * 1e-3) / 1e9
         per_launch = step_bytes
-    traffic = load_traffic(kern)
+    traffic = load_traffic(kern, events_all / world / K)
     roof = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak,
             "peak_source": ("measured (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                             else "fallback 6.8 TB/s"),
             "algorithmic_bytes_per_launch": per_launch,
             "traffic": (traffic * (K if persistent else 1)) if traffic is not None else None}
+    # the deliveries are 32-bit reductions into the L2-resident delay ring:
+    # the whole step's event rate against the rate of the same reductions
+    # measured here on random targets
+    red_peak = red_rate(cfg.M * info["max_delay"], 1 << 22)
+    atom = {"what": "synaptic events (one 32-bit L2 reduction each) per second over the whole step, "
+                    "vs torch index_add_ of 4M random int32 reductions into a ring-sized buffer",
+            "achieved": events_all / world / (ms_max * 1e-3), "peak": red_peak, "unit": "reductions/s",
+            "frac": events_all / world / (ms_max * 1e-3) / red_peak}
 
     # end to end through the C ABI: upload of every table from pinned host
     # memory, K steps, read-back of the raster and the counters
@@ -294,6 +302,7 @@ def run_ours(args):
         "events_per_step": events_all / world / K,
         "rate_hz": spikes_all / world / K / cfg.M / (cfg.dyn.dt_ms * 1e-3),
         "roofline": roof,
+        "atomic_roofline": atom,
         "step_roofline": {"bytes_per_step": step_bytes,
                           "achieved_gbs": step_bytes / (ms_max / K * 1e-3) / 1e9,
                           "frac": step_bytes / (ms_max / K * 1e-3) / 1e9 / peak},
@@ -340,9 +349,12 @@ def kernel_source_sha() -> str:
     return hs.hexdigest()[:16]
 
 
-def load_traffic(kernel: str):
-    """dram bytes per launch of `kernel` from the committed ncu summary, if it
-    was taken on the current kernel source (else null)."""
+def load_traffic(kernel: str, events_per_step: float):
+    """DRAM bytes per step of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel source (else null).  The capture runs a
+    smaller network of the same recipe; the neuron state stays on chip, so
+    the traffic is the synapse and routing-table reads of the step's spikes:
+    it is scaled by the synaptic events per step."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -350,12 +362,30 @@ def load_traffic(kernel: str):
     except (OSError, ValueError):
         return None
     ent = t.get(kernel)
-    if not ent:
+    if not ent or ent.get("source_sha") != kernel_source_sha():
         return None
-    h = kernel_source_sha()
-    if ent.get("source_sha") != h:
-        return None
-    return ent.get("dram_bytes_per_launch")
+    return ent["dram_bytes_per_step"] * events_per_step / ent["events_per_step"]
+
+
+def red_rate(n_ring: int, n: int, reps: int = 20) -> float:
+    """32-bit atomic adds per second of torch index_add_ with n random targets
+    in an int32 buffer of n_ring entries (L2-resident like the delay ring)."""
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(7)
+    buf = torch.zeros(n_ring, dtype=torch.int32, device="cuda")
+    idx = torch.randint(0, n_ring, (n,), device="cuda", generator=g)
+    val = torch.ones(n, dtype=torch.int32, device="cuda")
+    for _ in range(3):
+        buf.index_add_(0, idx, val)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        buf.index_add_(0, idx, val)
+    e1.record()
+    torch.cuda.synchronize()
+    return n * reps / (e0.elapsed_time(e1) * 1e-3)
 
 
 # ------------------------------------------------------------------ CPU oracle

@@ -539,6 +539,7 @@ extern "C" int snn_routing_build(const snn_network *net, const int32_t *part_of,
         parallel_for(M, nt, [&](int64_t lo, int64_t hi, int) {
             std::vector<int32_t> cnt((size_t)P, 0), pos((size_t)P, 0);
             std::vector<int32_t> qs;
+            std::vector<uint64_t> key;
             for (int64_t kk = lo; kk < hi; ++kk) {
                 int64_t i = rt->perm_inv[kk];
                 int32_t ps = rt->ip_of_part[part_of[i]], hs = ps / s;
@@ -578,6 +579,21 @@ extern "C" int snn_routing_build(const snn_network *net, const int32_t *part_of,
                     int64_t o = base + pos[q]++;
                     rt->syn_td[o] = rt->perm_fwd[tg[e]] | ((uint32_t)(dd[e] - 1) << kTgtBits);
                     rt->syn_w[o] = net->syn_w[e];
+                }
+                // each segment by (delay, target): the delay-1 synapses first
+                for (int64_t x = l2p[kk]; x < f; ++x) {
+                    L2Entry &l = rt->l2[x];
+                    key.clear();
+                    for (uint32_t k = 0; k < l.len; ++k)
+                        key.push_back(((uint64_t)rt->syn_td[l.off + k] << 16) | (uint16_t)rt->syn_w[l.off + k]);
+                    std::sort(key.begin(), key.end());
+                    uint64_t n1 = 0;
+                    for (uint32_t k = 0; k < l.len; ++k) {
+                        rt->syn_td[l.off + k] = (uint32_t)(key[k] >> 16);
+                        rt->syn_w[l.off + k] = (int16_t)(uint16_t)(key[k] & 0xFFFFu);
+                        n1 += (key[k] >> (16 + kTgtBits)) == 0;
+                    }
+                    l.off |= n1 << kOffBits;
                 }
                 for (int32_t q : qs) cnt[q] = 0;
             }

@@ -33,9 +33,14 @@ enum : uint8_t {
     kClsRelayRemote = 3,  // destination VN != source VN, forwarded by the relay
 };
 
-// One (neuron, destination partition) entry of the level-2 table.
+// One (neuron, destination partition) entry of the level-2 table.  The
+// segment's synapses are ordered by delay, so the ones of delay 1 (the only
+// ones the next step reads) come first.
+constexpr int kOffBits = 40;  // E < 2^40
+constexpr uint64_t kOffMask = (1ull << kOffBits) - 1ull;
 struct L2Entry {
-    uint64_t off;   // first synapse of the segment in the internal CSR
+    uint64_t off;   // bits 0-39: first synapse of the segment in the internal CSR;
+                    // bits 40-63: synapses of delay 1 at the segment's start
     uint32_t len;   // synapses in the segment
     uint16_t q;     // internal destination partition
     uint8_t cls;    // kCls*

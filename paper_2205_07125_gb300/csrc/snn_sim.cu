@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(kThreads) k_fo_level2(const FoArgs a)
         for (uint32_t f = a.l1_l2[e]; f < a.l1_l2[e + 1]; ++f) {
             const DevL2 l = a.l2[f];
             const unsigned int pos = atomicAdd(&a.cnt[1], 1u);
-            if (pos < a.cap2) a.inbox[pos] = (l.off << kLenBits) | (unsigned long long)l.len;
+            if (pos < a.cap2) a.inbox[pos] = ((l.off & kOffMask) << kLenBits) | (unsigned long long)l.len;
             else st |= kFoStInbox;
         }
     }

@@ -506,17 +506,18 @@ __device__ __forceinline__ void route_round(const Dev &d, int par, int tm, const
             const uint32_t kq = d.l2_pair[f];
             pslot = d.inbox_slot[kq];
             ppos = atomicAdd(&icnt[(size_t)kq * kPairStride], 1u);
-            pval = (l.off << kLenBits) | (unsigned long long)l.len;
+            const unsigned long long off = l.off & kOffMask;  // (the high bits count delay-1 synapses)
+            pval = (off << kLenBits) | (unsigned long long)l.len;
             pk = 2;
             if (l.len <= kShortSeg) {
                 const unsigned int sb = atomicAdd(sg.ns, 1u);
-                if (sb < (unsigned int)kShortCap) sg.sht[sb] = (l.off << 8) | l.len;
-                else ev += deliver_run(d, tm, l.off, l.len);  // list full: this thread delivers it
+                if (sb < (unsigned int)kShortCap) sg.sht[sb] = (off << 8) | l.len;
+                else ev += deliver_run(d, tm, off, l.len);  // list full: this thread delivers it
             } else {
                 const unsigned int np = (l.len + kPiece - 1u) / kPiece;
                 unsigned int pb = atomicAdd(sg.nl, np);
                 for (unsigned int j = 0; j < np; ++j, ++pb) {
-                    const unsigned long long o = l.off + (unsigned long long)j * kPiece;
+                    const unsigned long long o = off + (unsigned long long)j * kPiece;
                     const unsigned int n = min(kPiece, l.len - j * kPiece);
                     if (pb < (unsigned int)kLongCap) sg.lng[pb] = (o << 8) | n;
                     else ev += deliver_run(d, tm, o, n);
@@ -865,12 +866,12 @@ __device__ __forceinline__ void route_step(const Dev &d, long long t, StepShared
     if (lo >= hi) return;
     route_range(d, t, sh.head, sg, lo, hi);
     // tallies of the routed spikes into this block's row (no other block
-    // writes it, so plain adds)
+    // touches it: the reductions never wait on another block)
     __syncthreads();
     if (threadIdx.x < kTally) {
         unsigned long long a = 0;
         for (int w = 0; w < kWarps; ++w) a += sh.tally[w][threadIdx.x];
-        d.tally[(size_t)blockIdx.x * C_N + C_EVENTS + threadIdx.x] += a;
+        if (a) atomicAdd(&d.tally[(size_t)blockIdx.x * C_N + C_EVENTS + threadIdx.x], a);
     }
 }
 
