@@ -132,12 +132,12 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ workload
-def workload(seed_offset: int = 0, neurons: int = 0):
+def workload(seed_offset: int = 0, neurons: int = 0, config: str = "scale"):
     import synth
-    cfg = synth.SCALE
+    cfg = {"scale": synth.SCALE, "paper": synth.PAPER_SHARE, "tiny": synth.TINY}[config]
     if neurons and neurons != cfg.M:
         # same per-neuron statistics on a smaller or larger network (profiling cases)
-        cfg = cfg.scaled(M=neurons, name="scale-%dn-%dp-%dvn-k%d" % (neurons, cfg.P, cfg.n_vn, cfg.K))
+        cfg = cfg.scaled(M=neurons, name="%s-%dn-%dp-%dvn-k%d" % (config, neurons, cfg.P, cfg.n_vn, cfg.K))
     dyn = cfg.dyn
     if seed_offset:
         import dataclasses
@@ -166,7 +166,7 @@ def run_ours(args):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    cfg = workload(rank, args.neurons)
+    cfg = workload(rank, args.neurons, args.config)
     K, W = args.steps, args.warmup
 
     t_setup = time.time()
@@ -291,11 +291,12 @@ def run_ours(args):
         "data": "synthetic (seeded generator; stands in for the paper's scanned brain model)",
         "config": {"workload": cfg.name, "neurons": cfg.M, "partitions": cfg.P,
                    "virtual_nodes": cfg.n_vn, "synapses": info["n_synapses"],
-                   "synapses_per_neuron": cfg.K, "locality": "700/200/100", "delays": "1-%d" % cfg.dmax,
+                   "synapses_per_neuron": cfg.K, "locality": ("uniform" if cfg.uniform_all else "%d/%d/%d" % (cfg.n_part, cfg.n_vn_t, cfg.n_remote)), "delays": "1-%d" % cfg.dmax,
                    "drive_lambda_per_step": cfg.dyn.drive_lambda, "w_ext": cfg.dyn.w_ext,
                    "parallelism": "replicas x%d" % world,
-                   "l2": "inputs larger than L2: 6.3 GB synapse CSR streamed per step; neuron state "
-                         "(V, ref, delay ring ~42 MB) stays L2-resident across steps",
+                   "l2": "inputs larger than L2: %.1f GB synapse CSR, the step's rows streamed from HBM; "
+                         "delay ring %.0f MB (L2-resident when it fits the 129 MB L2)"
+                         % (info["n_synapses"] * 6 / 1e9, cfg.M * (info["max_delay"] + 1) * 4 / 1e6),
                    "steps_per_graph": 32,
                    "execution": "persistent cooperative kernel" if persistent else "CUDA graphs"},
         "spikes_per_step": spikes_all / world / K,
@@ -421,7 +422,7 @@ def run_reference(args):
         return
     import synth
     import oracle
-    cfg = workload(0)
+    cfg = workload(0, args.neurons, args.config)
     g = synth.make_network(cfg)
     P = cfg.P
     o = oracle.Oracle(g, P, oracle.partition_planted(g.M, P), cfg.n_vn,
@@ -463,6 +464,10 @@ def main(argv=None):
                     help="network size with the scale workload's per-neuron statistics "
                          "(default: the 1,048,576-neuron workload)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--config", choices=("scale", "paper", "tiny"), default="scale",
+                    help="scale: 1,048,576 neurons / 64 partitions (the headline workload); "
+                         "paper: the paper-shaped per-GPU share, 5,000,000 neurons / 256 partitions; "
+                         "tiny: 4,096 neurons")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -68,3 +68,50 @@ def test_scale_workload_bit_exact():
     assert counts["events"] == S * cfg.K
     st = o.fp64_stats()
     assert st["max_rel_err"] <= 1e-5
+
+
+def test_paper_share_workload_bit_exact():
+    """The paper-shaped per-GPU share (5,000,000 neurons, 256 partitions over
+    64 VNs, 5e9 synapses) in the benchmark's launch configuration (persistent
+    kernel, neuron state in global memory at this size): 40 steps compared
+    with the oracle step by step, plus the closed forms of the message counts."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2205_07125_gb300 as snn
+    cfg = synth.PAPER_SHARE
+    T = 40
+    g = synth.make_network(cfg)
+    net = snn.Network.from_synth(g)
+    part, _ = snn.snn_partition(net, cfg.P, "planted")
+    rt = snn.Routing(net, part, cfg.P, cfg.n_vn, "contiguous")
+    prm = snn.sim_params(cfg.dyn, raster_cap=2_000_000, raster_steps=T, hash_steps=T, cur_every=13,
+                         cur_slots=4, steps_per_graph=32)
+    sim = snn.Sim(net, rt, prm, device="cuda:0")
+    sim.step(T)
+    assert sim.sync_status() == 0
+    ids, off = sim.read_raster(0, T)
+    ch, vh = sim.read_hashes(0, T)
+    cur = {s: sim.read_currents(s) for s in (13, 26, 39)}
+    V, ref, t = sim.read_state()
+    counts = sim.read_counts()
+    sim.close()
+    del sim, rt, net
+
+    o = oracle.Oracle(g, cfg.P, oracle.partition_planted(g.M, cfg.P), cfg.n_vn,
+                      oracle.group_contiguous(cfg.P, cfg.n_vn), cfg.dyn)
+    r = o.run(T, rec_steps=[13, 26, 39], raster_cap=2_000_000)
+    assert t == T
+    assert np.array_equal(off, r["raster_off"])
+    assert np.array_equal(ids, r["raster_ids"])
+    assert np.array_equal(ch, r["cur_hash"]) and np.array_equal(vh, r["v_hash"])
+    for s in (13, 26, 39):
+        assert np.array_equal(cur[s], r["currents"][s]), s
+    assert np.array_equal(V.view(np.uint32), o.V.view(np.uint32))
+    assert np.array_equal(ref, o.ref)
+    oc = o.count_dict()
+    for k, v in counts.items():
+        assert v == oc[k], (k, v, oc[k])
+    S = counts["spikes"]
+    assert S > 1000
+    assert counts["events"] == S * cfg.K
