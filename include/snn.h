@@ -220,6 +220,29 @@ int snn_sim_create(const snn_network *net, const snn_routing *rt, const snn_sim_
                    void *workspace, size_t workspace_bytes, void *stream, snn_sim **out);
 
 /*
+ * Batches (no counterpart in the paper, which simulates one network):
+ * n independent networks of any sizes stepped together by one sim, so one
+ * snn_step runs all of them in one persistent launch (or one graph).
+ * The caller concatenates the networks into `net`: network k owns ids
+ * [off[k], off[k+1]) (off[0] = 0, off[n] = M, every off[k] a multiple of 4,
+ * n <= 65535) and no synapse leaves its network; the partition vector gives
+ * each network its own partitions and the routing is built once on the
+ * concatenation, with every VN inside one network (contiguous grouping and a
+ * multiple of the VN size partitions per network).  params[k] gives network
+ * k its drive (drive_lambda, drive_seed: the Philox stream of network k counts
+ * its own ids from 0); all other fields come from params[0].  Routing,
+ * delivery and records are those of the concatenation: network k's spikes
+ * are the raster ids in [off[k], off[k+1]), the counts are sums over the
+ * networks.  `off` and `params` are copied.
+ * Errors: SNN_E_ARG (a check above fails, M % 4 != 0), plus those of
+ * snn_sim_create.
+ */
+int snn_batch_workspace_bytes(const snn_routing *rt, int32_t n, const snn_sim_params *params, size_t *bytes);
+int snn_batch_create(const snn_network *net, const snn_routing *rt, int32_t n, const int64_t *off,
+                     const snn_sim_params *params, void *workspace, size_t workspace_bytes, void *stream,
+                     snn_sim **out);
+
+/*
  * Advance T steps.  Each step: (a1) consume the delay-ring slot, add the
  * Poisson drive; (a2) LIF update and threshold; (a3) warp-ballot/prefix-sum
  * spike compaction; (a4) level-1 bucketing by destination VN; (a5) level-2

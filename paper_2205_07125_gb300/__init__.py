@@ -101,6 +101,9 @@ _sig("snn_sim_params_default", None, [_P(snn_sim_params)])
 _sig("snn_sim_workspace_bytes", ctypes.c_int, [_vp, _P(snn_sim_params), _P(ctypes.c_size_t)])
 _sig("snn_sim_create", ctypes.c_int, [_P(snn_network), _vp, _P(snn_sim_params), _vp, ctypes.c_size_t,
                                       _vp, _P(_vp)])
+_sig("snn_batch_workspace_bytes", ctypes.c_int, [_vp, _i32, _vp, _P(ctypes.c_size_t)])
+_sig("snn_batch_create", ctypes.c_int, [_P(snn_network), _vp, _i32, _vp, _vp, _vp, ctypes.c_size_t, _vp,
+                                        _P(_vp)])
 _sig("snn_step", ctypes.c_int, [_vp, _i32])
 _sig("snn_sync_status", ctypes.c_int, [_vp])
 _sig("snn_read_raster", ctypes.c_int, [_vp, _i64, _i64, _vp, _i64, _vp, _P(_i64)])
@@ -128,7 +131,7 @@ EXPORTS = ("snn_strerror", "snn_partition", "snn_routing_build", "snn_routing_in
            "snn_read_counts", "snn_read_state", "snn_read_inbox_pairs", "snn_state_bytes",
            "snn_save_state", "snn_load_state", "snn_sim_reset", "snn_launches_per_step", "snn_launches",
            "snn_profile_phases", "snn_deliver_spikes", "snn_deliver_spikes_static",
-           "snn_static_scratch_bytes", "snn_sim_destroy")
+           "snn_static_scratch_bytes", "snn_sim_destroy", "snn_batch_workspace_bytes", "snn_batch_create")
 
 
 class SnnError(RuntimeError):
@@ -242,26 +245,44 @@ def sim_params(dyn=None, **kw) -> snn_sim_params:
 
 
 class Sim:
-    """A simulation on one GPU; the workspace is a torch uint8 tensor."""
+    """A simulation on one GPU; the workspace is a torch uint8 tensor.
+
+    batch=(off, params_list): the network is a concatenation of len(params_list)
+    independent networks, network k owning ids off[k]..off[k+1]-1, each with
+    its own drive (drive_lambda, drive_seed of params_list[k]); see
+    snn_batch_create."""
 
     def __init__(self, net: Network, routing: Routing, params: snn_sim_params, device=None,
-                 stream=None):
+                 stream=None, batch=None):
         import torch
         self.net, self.routing, self.params = net, routing, params
         self.M = net.M
         dev = torch.device(device if device is not None else "cuda")
         self.device = dev
         nb = ctypes.c_size_t(0)
-        _ck(_lib.snn_sim_workspace_bytes(routing.h, ctypes.byref(params), ctypes.byref(nb)),
-            "snn_sim_workspace_bytes")
+        if batch is not None:
+            off, plist = batch
+            self._off = np.ascontiguousarray(off, np.int64)
+            self._plist = (snn_sim_params * len(plist))(*plist)
+            n = len(plist)
+            _ck(_lib.snn_batch_workspace_bytes(routing.h, n, self._plist, ctypes.byref(nb)),
+                "snn_batch_workspace_bytes")
+        else:
+            _ck(_lib.snn_sim_workspace_bytes(routing.h, ctypes.byref(params), ctypes.byref(nb)),
+                "snn_sim_workspace_bytes")
         self.workspace_bytes = nb.value
         with torch.cuda.device(dev):
             self.workspace = torch.empty(max(256, nb.value), dtype=torch.uint8, device=dev)
             self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
             h = _vp()
-            _ck(_lib.snn_sim_create(ctypes.byref(net.s), routing.h, ctypes.byref(params),
-                                    self.workspace.data_ptr(), nb.value, self.stream.cuda_stream,
-                                    ctypes.byref(h)), "snn_sim_create")
+            if batch is not None:
+                _ck(_lib.snn_batch_create(ctypes.byref(net.s), routing.h, n, self._off.ctypes.data, self._plist,
+                                          self.workspace.data_ptr(), nb.value, self.stream.cuda_stream,
+                                          ctypes.byref(h)), "snn_batch_create")
+            else:
+                _ck(_lib.snn_sim_create(ctypes.byref(net.s), routing.h, ctypes.byref(params),
+                                        self.workspace.data_ptr(), nb.value, self.stream.cuda_stream,
+                                        ctypes.byref(h)), "snn_sim_create")
         self.h = h.value
 
     def _dev(self):

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -114,6 +115,7 @@ struct Layout {
     Region V, ref, ring, gid, src_part, syn_td, syn_w, l1_ptr, l1_vn, l1_l2, l2, row, l1_pair, l2_pair;
     Region bucket, bucket_slot, bucket_cnt, inbox, inbox_slot, inbox_cnt;
     Region tally;  // per-block tally rows
+    Region net_of, net_drive;  // batches: network of each quad, drive of each network
     Region spk, spk_step, raster_off, hash, cur_rec, counters, ctrl;
     Region fwd, fo_cnt;  // snn_deliver_spikes: global -> internal map, scratch counters
     Region phase_ns;
@@ -121,6 +123,7 @@ struct Layout {
     std::vector<uint64_t> bucket_base_h, inbox_base_h;
     std::vector<uint32_t> bucket_cap_h, inbox_cap_h;
     int64_t tally_rows = 0;
+    int32_t n_net = 0;  // networks of a batch (0: a single network)
     int D = 2;
 };
 
@@ -143,10 +146,11 @@ static int64_t step_grid(int64_t M)
 // capped to the rows there are).
 constexpr int64_t kMinTallyRows = 2048;
 
-static int make_layout(const snn_routing *rt, const snn_sim_params *p, Layout &L)
+static int make_layout(const snn_routing *rt, const snn_sim_params *p, Layout &L, int32_t n_net = 0)
 {
     const int64_t M = rt->M, E = rt->E;
     L = Layout();
+    L.n_net = n_net;
     L.D = rt->max_delay + 1;
     auto cap = [](uint64_t exact, float frac) -> uint64_t {
         double c = std::ceil((double)exact * (double)frac);
@@ -201,6 +205,10 @@ static int make_layout(const snn_routing *rt, const snn_sim_params *p, Layout &L
     place(L, L.inbox_slot, sizeof(ulonglong2) * n_ip);
     place(L, L.inbox_cnt, 2 * sizeof(uint32_t) * kPairStride * n_ip);  // by step parity
     place(L, L.tally, sizeof(unsigned long long) * C_N * (size_t)L.tally_rows);
+    if (n_net > 0) {
+        place(L, L.net_of, sizeof(uint16_t) * (size_t)(M / 4));
+        place(L, L.net_drive, sizeof(NetDrive) * (size_t)n_net);
+    }
     place(L, L.spk, sizeof(uint32_t) * (size_t)(p->raster_cap + M));
     place(L, L.spk_step, sizeof(uint32_t) * (size_t)M);
     place(L, L.raster_off, sizeof(long long) * (size_t)(p->raster_steps + 1));
@@ -247,6 +255,17 @@ static int poisson_thresholds(double lambda, unsigned long long *th, int *len)
     return SNN_OK;
 }
 
+// The finite thresholds of the inverse-CDF table (every one but the closing
+// 2^32 fits in 32 bits) and their count.
+static void finite_thresholds(double lambda, uint32_t *th32, int *fin)
+{
+    unsigned long long th[kPTab];
+    int len = 0;
+    poisson_thresholds(lambda, th, &len);
+    *fin = len - 1;
+    for (int k = 0; k < kPTab; ++k) th32[k] = k < len - 1 ? (uint32_t)th[k] : 0xFFFFFFFFu;
+}
+
 }  // namespace
 
 struct snn_sim {
@@ -277,6 +296,9 @@ struct snn_sim {
     unsigned long long barrier_limit_ns = 1000000000ull;
     int test_skip_arrival = 0;  // tests of the bounded wait (SNN_TEST_SKIP_BARRIER)
     std::vector<void *> pinned;
+    // batches: the network of each quad and each network's drive (host copies)
+    std::vector<uint16_t> net_of_h;
+    std::vector<NetDrive> net_drive_h;
 };
 
 #define CK(x)                                     \
@@ -331,6 +353,10 @@ static int upload_tables(snn_sim *s)
     CK(up(L.l1_l2, rt->l1_l2.data()));
     CK(up(L.l2, rt->l2.data()));
     CK(up(L.src_part, rt->src_part.data()));
+    if (L.n_net > 0) {
+        CK(up(L.net_of, s->net_of_h.data()));
+        CK(up(L.net_drive, s->net_drive_h.data()));
+    }
     CK(up(L.l1_pair, rt->l1_pair.data()));
     {
         // first level-1 and level-2 entry of each neuron, read together
@@ -438,8 +464,82 @@ extern "C" void snn_sim_destroy(snn_sim *s)
     delete s;
 }
 
+// Checks of a batch (networks k = 0..n-1 own ids [off[k], off[k+1])): the
+// offsets are multiples of 4, no synapse leaves its network, and no
+// partition or VN mixes networks.
+static int batch_check(const snn_network *net, const snn_routing *rt, int32_t n, const int64_t *off,
+                       const snn_sim_params *params)
+{
+    const int64_t M = rt->M;
+    if (n < 1 || n > 65535 || !off || !params || off[0] != 0 || off[n] != M) return SNN_E_ARG;
+    for (int32_t k = 0; k < n; ++k) {
+        if (off[k + 1] <= off[k] || (off[k] & 3)) return SNN_E_ARG;
+        if (!(params[k].drive_lambda >= 0.0) || params[k].drive_lambda > 16.0) return SNN_E_ARG;
+    }
+    auto net_of = [&](int64_t i) { return (int32_t)(std::upper_bound(off, off + n + 1, i) - off - 1); };
+    std::atomic<int> bad{0};
+    parallel_for(M, resolve_threads(0), [&](int64_t lo, int64_t hi, int) {
+        int32_t k = net_of(lo);
+        for (int64_t i = lo; i < hi && !bad.load(std::memory_order_relaxed); ++i) {
+            while (i >= off[k + 1]) ++k;
+            for (int64_t e = net->syn_ptr[i]; e < net->syn_ptr[i + 1]; ++e)
+                if ((int64_t)net->syn_tgt[e] < off[k] || (int64_t)net->syn_tgt[e] >= off[k + 1]) {
+                    bad = 1;
+                    break;
+                }
+        }
+    });
+    if (bad) return SNN_E_ARG;
+    // every partition and every VN within one network
+    std::vector<int32_t> pnet((size_t)rt->P, -1);
+    for (int32_t ip = 0; ip < rt->P; ++ip)
+        for (int64_t k = rt->pbase[ip]; k < rt->pbase[ip + 1]; ++k) {
+            const int32_t x = net_of((int64_t)rt->perm_inv[k]);
+            if (pnet[ip] < 0) pnet[ip] = x;
+            else if (pnet[ip] != x) return SNN_E_ARG;
+        }
+    const int32_t vs = rt->P / rt->n_vn;
+    for (int32_t ip = 0; ip < rt->P; ++ip)
+        if (pnet[ip] != pnet[(ip / vs) * vs]) return SNN_E_ARG;
+    return SNN_OK;
+}
+
+static int sim_create(const snn_network *net, const snn_routing *rt, const snn_sim_params *p, int32_t n_net,
+                      const int64_t *off, const snn_sim_params *params, void *workspace, size_t ws_bytes,
+                      void *stream, snn_sim **out);
+
 extern "C" int snn_sim_create(const snn_network *net, const snn_routing *rt, const snn_sim_params *p,
                               void *workspace, size_t ws_bytes, void *stream, snn_sim **out)
+{
+    return sim_create(net, rt, p, 0, nullptr, nullptr, workspace, ws_bytes, stream, out);
+}
+
+extern "C" int snn_batch_workspace_bytes(const snn_routing *rt, int32_t n, const snn_sim_params *params,
+                                         size_t *bytes)
+{
+    if (!rt || !bytes || n < 1 || !params || !params_ok(&params[0]) || rt->M % 4) return SNN_E_ARG;
+    Layout L;
+    int rc = make_layout(rt, &params[0], L, n);
+    if (rc) return rc;
+    *bytes = L.total;
+    return SNN_OK;
+}
+
+extern "C" int snn_batch_create(const snn_network *net, const snn_routing *rt, int32_t n, const int64_t *off,
+                                const snn_sim_params *params, void *workspace, size_t ws_bytes, void *stream,
+                                snn_sim **out)
+{
+    if (!out) return SNN_E_ARG;
+    *out = nullptr;
+    if (!net || !rt || !params || !params_ok(&params[0]) || net->n_neurons != rt->M) return SNN_E_ARG;
+    int rc = batch_check(net, rt, n, off, params);
+    if (rc) return rc;
+    return sim_create(net, rt, &params[0], n, off, params, workspace, ws_bytes, stream, out);
+}
+
+static int sim_create(const snn_network *net, const snn_routing *rt, const snn_sim_params *p, int32_t n_net,
+                      const int64_t *off, const snn_sim_params *params, void *workspace, size_t ws_bytes,
+                      void *stream, snn_sim **out)
 {
     if (!out) return SNN_E_ARG;
     *out = nullptr;
@@ -452,7 +552,26 @@ extern "C" int snn_sim_create(const snn_network *net, const snn_routing *rt, con
     if (!s) return SNN_E_NOMEM;
     s->rt = rt;
     s->prm = *p;
-    int rc = make_layout(rt, p, s->L);
+    if (n_net > 0) {
+        // the network of each quad of ids, each network's drive
+        try {
+            s->net_of_h.resize((size_t)(rt->M / 4));
+            for (int32_t k = 0; k < n_net; ++k)
+                for (int64_t q = off[k] / 4; q < off[k + 1] / 4; ++q) s->net_of_h[q] = (uint16_t)k;
+            s->net_drive_h.assign((size_t)n_net, NetDrive{});
+            for (int32_t k = 0; k < n_net; ++k) {
+                NetDrive &nd = s->net_drive_h[k];
+                finite_thresholds(params[k].drive_lambda, nd.th, &nd.fin);
+                nd.key0 = (uint32_t)params[k].drive_seed;
+                nd.key1 = (uint32_t)(params[k].drive_seed >> 32);
+                nd.off = off[k];
+            }
+        } catch (const std::bad_alloc &) {
+            delete s;
+            return SNN_E_NOMEM;
+        }
+    }
+    int rc = make_layout(rt, p, s->L, n_net);
     if (rc) { delete s; return rc; }
     if (ws_bytes < s->L.total) { delete s; return SNN_E_NOMEM; }
     s->ws = (char *)workspace;
@@ -608,12 +727,10 @@ extern "C" int snn_sim_create(const snn_network *net, const snn_routing *rt, con
     d.hash_steps = p->hash_steps;
     d.cur_every = p->cur_every;
     d.cur_slots = p->cur_slots;
-    {
-        unsigned long long th[kPTab];
-        int len = 0;
-        poisson_thresholds(p->drive_lambda, th, &len);
-        d.th_fin = len - 1;  // every threshold but the closing 2^32 fits in 32 bits
-        for (int k = 0; k < kPTab; ++k) d.th32[k] = k < len - 1 ? (uint32_t)th[k] : 0xFFFFFFFFu;
+    finite_thresholds(p->drive_lambda, d.th32, &d.th_fin);
+    if (L.n_net > 0) {
+        d.net_of = (const uint16_t *)(w + L.net_of.off);
+        d.net_drive = (const NetDrive *)(w + L.net_drive.off);
     }
 
     rc = upload_tables(s);

@@ -69,6 +69,16 @@ struct Ctrl {
     alignas(128) unsigned long long bar;  // grid-barrier arrivals of the running k_persist launch
 };
 
+// Drive of one network of a batch (independent networks stepped together);
+// 16-byte aligned: the first four thresholds are read as one uint4.
+struct __align__(16) NetDrive {
+    uint32_t th[kPTab];  // finite Poisson thresholds, th[k] for k < fin
+    int fin;
+    uint32_t key0, key1;  // Philox key (the network's drive seed)
+    int pad;
+    long long off;        // first id of the network (a multiple of 4)
+};
+
 struct __align__(16) DevL2 {
     unsigned long long off;
     unsigned int len;
@@ -122,6 +132,10 @@ struct Dev {
     long long raster_cap, raster_steps, hash_steps;
     int cur_every, cur_slots;
     uint32_t th32[kPTab];   // finite Poisson thresholds (the closing 2^32 is implied)
+    // batches: the network of each quad of ids and every network's drive
+    // (nullptr for a single network, which takes th32 / th_fin / key0 / key1)
+    const uint16_t *net_of;
+    const NetDrive *net_drive;
 };
 
 // Counter arrays of step parity par.
@@ -265,21 +279,61 @@ __device__ __forceinline__ bool grid_sync(Ctrl *c, unsigned long long k, unsigne
     return s_ok != 0;
 }
 
-// a1 + a2 for one neuron: returns true on a spike.
-// th: the Poisson thresholds staged in shared memory (lanes index them
-// divergently, which the kernel-parameter bank would serialise).
-// u: the neuron's drive word.
-__device__ __forceinline__ bool lif_neuron(const Dev &d, const uint32_t *th, uint32_t u, int32_t irec, float &v,
+// Drive of a neuron: the Poisson thresholds (the first four as values, the
+// rest behind a pointer: shared memory for a single network, the batch table
+// otherwise) and the Philox key and id offset of its network.
+struct Drive {
+    uint32_t t0, t1, t2, t3;
+    int fin;
+    const uint32_t *th;
+    uint32_t key0, key1;
+    long long off;
+};
+
+// Drive of global id g; th_smem: the single network's thresholds staged in
+// shared memory (lanes index them divergently, which the kernel-parameter
+// bank would serialise).
+__device__ __forceinline__ Drive drive_of(const Dev &d, const uint32_t *th_smem, uint32_t g)
+{
+    Drive r;
+    if (!d.net_of) {
+        r.t0 = d.th32[0];
+        r.t1 = d.th32[1];
+        r.t2 = d.th32[2];
+        r.t3 = d.th32[3];
+        r.fin = d.th_fin;
+        r.th = th_smem;
+        r.key0 = d.key0;
+        r.key1 = d.key1;
+        r.off = 0;
+    } else {
+        const NetDrive *nd = d.net_drive + __ldg(d.net_of + (g >> 2));
+        const uint4 t = __ldg(reinterpret_cast<const uint4 *>(nd->th));
+        r.t0 = t.x;
+        r.t1 = t.y;
+        r.t2 = t.z;
+        r.t3 = t.w;
+        r.fin = __ldg(&nd->fin);
+        r.th = nd->th;
+        r.key0 = __ldg(&nd->key0);
+        r.key1 = __ldg(&nd->key1);
+        r.off = __ldg(&nd->off);
+    }
+    return r;
+}
+
+// a1 + a2 for one neuron: returns true on a spike.  u: the neuron's drive
+// word; dr: its network's drive.
+__device__ __forceinline__ bool lif_neuron(const Dev &d, const Drive &dr, uint32_t u, int32_t irec, float &v,
                                            uint32_t &r)
 {
     // k = number of finite thresholds <= u (they ascend): the first four
-    // compared at once against the kernel parameters, the rest (rare: k >= 4
-    // has probability ~1.4 % at 0.8 arrivals per step) from shared memory
-    int k = 0;
-#pragma unroll
-    for (int m = 0; m < 4; ++m) k += (m < d.th_fin && u >= d.th32[m]) ? 1 : 0;
+    // compared at once, the rest (rare: k >= 4 has probability ~1.4 % at 0.8
+    // arrivals per step) one by one
+    int k = (0 < dr.fin && u >= dr.t0) + (1 < dr.fin && u >= dr.t1) + (2 < dr.fin && u >= dr.t2) +
+            (3 < dr.fin && u >= dr.t3);
     if (k == 4)
-        while (k < d.th_fin && u >= th[k]) ++k;
+        while (k < dr.fin && u >= dr.th[k]) ++k;
     const int32_t I = (int32_t)((uint32_t)irec + (uint32_t)k * (uint32_t)d.w_ext + (uint32_t)d.i_bias);
     if (r > 0) {
         r -= 1;
@@ -621,19 +675,25 @@ __device__ __forceinline__ unsigned int update_quad(const Dev &d, const uint32_t
                                                     float (&vv)[4], const int32_t (&ii)[4], uint32_t &r4,
                                                     bool do_hash, unsigned long long &hc, unsigned long long &hv)
 {
-    // one Philox block serves the four neurons of a quad in the global
-    // order; a reordering map needs a block per neuron
+    // one Philox block serves the four neurons of a quad (networks of a batch
+    // start at multiples of 4); a reordering map needs a block per neuron
+    Drive dq = drive_of(d, th, d.gid ? d.gid[j0] : (uint32_t)j0);
     uint4 wq = make_uint4(0u, 0u, 0u, 0u);
-    if (!d.gid) wq = philox4(d.key0, d.key1, (uint32_t)(j0 >> 2), (uint32_t)t);
+    if (!d.gid) wq = philox4(dq.key0, dq.key1, (uint32_t)((j0 - dq.off) >> 2), (uint32_t)t);
     unsigned int m = 0;
     uint32_t r_out = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const uint32_t g = d.gid ? d.gid[j0 + k] : (uint32_t)(j0 + k);
-        const uint32_t u = d.gid ? uint4_word(philox4(d.key0, d.key1, g >> 2, (uint32_t)t), g & 3u)
-                                 : uint4_word(wq, (uint32_t)k);
+        uint32_t u;
+        if (d.gid) {
+            if (k > 0) dq = drive_of(d, th, g);
+            u = uint4_word(philox4(dq.key0, dq.key1, (uint32_t)((g - dq.off) >> 2), (uint32_t)t), g & 3u);
+        } else {
+            u = uint4_word(wq, (uint32_t)k);
+        }
         uint32_t r = (r4 >> (8 * k)) & 0xFFu;
-        if (lif_neuron(d, th, u, ii[k], vv[k], r)) m |= 1u << k;
+        if (lif_neuron(d, dq, u, ii[k], vv[k], r)) m |= 1u << k;
         r_out |= r << (8 * k);
         if (do_hash) {
             hc += mix64(((unsigned long long)g << 32) | (uint32_t)ii[k]);
@@ -808,8 +868,10 @@ __device__ __forceinline__ void update_step(const Dev &d, long long t, StepShare
                     ring[j] = 0;
                     if (cur) cur[j] = irec;
                     const uint32_t g = d.gid ? d.gid[j] : (uint32_t)j;
-                    const uint32_t u = uint4_word(philox4(d.key0, d.key1, g >> 2, (uint32_t)t), g & 3u);
-                    if (lif_neuron(d, sh.th, u, irec, v, r)) {
+                    const Drive dr = drive_of(d, sh.th, g);
+                    const uint32_t u =
+                        uint4_word(philox4(dr.key0, dr.key1, (uint32_t)((g - dr.off) >> 2), (uint32_t)t), g & 3u);
+                    if (lif_neuron(d, dr, u, irec, v, r)) {
                         bits |= 1u << k;
                         prefetch_rows(d, j, 1u);
                     }

@@ -199,3 +199,90 @@ def make_edges(M: int, edges, v0=None) -> Network:
                     dmax=int(d.max()) if len(d) else 1)
     return Network(cfg, syn_ptr, tgt, w, d, np.asarray(v0, np.float32),
                    np.ones(M, np.uint8))
+
+
+# ---------------------------------------------------------------- batches
+@dataclasses.dataclass
+class Batch:
+    """Independent networks concatenated into one: network k owns ids
+    off[k]..off[k+1]-1 and partitions poff[k]..poff[k+1]-1 (planted, VNs of
+    `vn_size` partitions inside each network); `net` is the concatenation."""
+    cfgs: list
+    nets: list
+    off: np.ndarray       # [n+1] first id of each network (multiples of 4)
+    poff: np.ndarray      # [n+1] first partition label of each network
+    net: Network          # the concatenation
+    part: np.ndarray      # [M] partition labels of the concatenation
+    vn_size: int
+
+    @property
+    def P(self) -> int:
+        return int(self.poff[-1])
+
+    @property
+    def n_vn(self) -> int:
+        return self.P // self.vn_size
+
+
+def batch_configs(n: int = 64, seed: int = 3000, m_lo: int = 10_000, m_hi: int = 500_000,
+                  k_lo: int = 100, k_hi: int = 1000, p_lo: int = 4, p_hi: int = 32, vn_size: int = 2,
+                  rate_lo: float = 5.0, rate_hi: float = 15.0, w_ext: int = 89) -> list:
+    """Configurations of a batch of independent networks: sizes log-uniform
+    in [m_lo, m_hi] (multiples of 4), out-degrees uniform in [k_lo, k_hi]
+    with the scale workload's locality mix (70 % same partition, 20 % same
+    VN, 10 % remote), partitions uniform in [p_lo, p_hi] (multiples of the VN
+    size, at least two VNs), delays 1..8, generator seed seed + k.  Network k
+    gets a rate r_k uniform in [rate_lo, rate_hi] Hz and drives its neurons
+    with r_k / 10 times the scale workload's Poisson drive (0.8 arrivals per
+    step): the drive is scaled, the resulting firing rates are measured."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        M = int(np.exp(rng.uniform(np.log(m_lo), np.log(m_hi)))) // 4 * 4
+        K = int(rng.integers(k_lo, k_hi + 1))
+        P = int(rng.integers(max(p_lo, 2 * vn_size) // vn_size, p_hi // vn_size + 1)) * vn_size
+        r = float(rng.uniform(rate_lo, rate_hi))
+        n_part = int(round(0.7 * K))
+        n_vn_t = int(round(0.2 * K))
+        dyn = Dynamics(drive_lambda=0.8 * r / 10.0, w_ext=w_ext, drive_seed=seed + 10_000 + k)
+        out.append(NetConfig(name="batch%d-%dn-%dp-k%d" % (k, M, P, K), M=M, P=P, n_vn=P // vn_size, K=K,
+                             uniform_all=False, n_part=n_part, n_vn_t=n_vn_t, n_remote=K - n_part - n_vn_t,
+                             dmax=8, seed=seed + k, steps=1000, dyn=dyn))
+    return out
+
+
+def make_batch(cfgs: list) -> Batch:
+    """Generate every network of `cfgs` and their concatenation."""
+    nets = [make_network(c) for c in cfgs]
+    vs = cfgs[0].vn_size
+    assert all(c.vn_size == vs and c.M % 4 == 0 for c in cfgs)
+    off = np.zeros(len(cfgs) + 1, np.int64)
+    poff = np.zeros(len(cfgs) + 1, np.int64)
+    for k, c in enumerate(cfgs):
+        off[k + 1] = off[k] + c.M
+        poff[k + 1] = poff[k] + c.P
+    M = int(off[-1])
+    E = sum(g.E for g in nets)
+    syn_ptr = np.empty(M + 1, np.int64)
+    tgt = np.empty(E, np.uint32)
+    w = np.empty(E, np.int16)
+    d = np.empty(E, np.uint8)
+    v0 = np.empty(M, np.float32)
+    is_exc = np.empty(M, np.uint8)
+    part = np.empty(M, np.int32)
+    e0 = 0
+    for k, (c, g) in enumerate(zip(cfgs, nets)):
+        a, b = int(off[k]), int(off[k + 1])
+        syn_ptr[a:b] = g.syn_ptr[:-1] + e0
+        tgt[e0:e0 + g.E] = g.tgt + np.uint32(a)
+        w[e0:e0 + g.E] = g.w
+        d[e0:e0 + g.E] = g.d
+        v0[a:b] = g.v0
+        is_exc[a:b] = g.is_exc
+        for p in range(c.P):
+            part[a + c.M * p // c.P:a + c.M * (p + 1) // c.P] = poff[k] + p
+        e0 += g.E
+    syn_ptr[M] = e0
+    ucfg = NetConfig(name="batch-%dnets-%dn" % (len(cfgs), M), M=M, P=int(poff[-1]),
+                     n_vn=int(poff[-1]) // vs, K=0, uniform_all=False, dmax=max(c.dmax for c in cfgs))
+    return Batch(cfgs, nets, off, poff, Network(ucfg, syn_ptr, tgt, w, d, v0, is_exc), part, vs)

@@ -192,3 +192,65 @@ def test_workspace_size_and_no_device(snn):
         rc = snn._lib.snn_sim_create(ctypes.byref(net.s), rt.h, ctypes.byref(p),
                                      ctypes.c_void_p(1 << 20), nb.value, None, ctypes.byref(h))
         assert rc == -7 and not h.value
+
+
+def _small_batch():
+    cfgs = synth.batch_configs(n=5, seed=77, m_lo=600, m_hi=4000, k_lo=12, k_hi=40, p_lo=4, p_hi=8)
+    return synth.make_batch(cfgs)
+
+
+def test_batch_concatenation_is_independent_networks():
+    b = _small_batch()
+    g = b.net
+    assert (b.off % 4 == 0).all() and b.off[-1] == g.M
+    src = np.repeat(np.arange(g.M), np.diff(g.syn_ptr))
+    k_src = np.searchsorted(b.off, src, side="right") - 1
+    k_tgt = np.searchsorted(b.off, g.tgt.astype(np.int64), side="right") - 1
+    assert np.array_equal(k_src, k_tgt)
+    for k, (c, n) in enumerate(zip(b.cfgs, b.nets)):
+        a, e = b.off[k], b.off[k + 1]
+        assert np.array_equal(b.part[a:e], oracle.partition_planted(c.M, c.P) + b.poff[k])
+        e0 = g.syn_ptr[a]
+        assert np.array_equal(g.tgt[e0:e0 + n.E], n.tgt + a) and np.array_equal(g.w[e0:e0 + n.E], n.w)
+
+
+def test_batch_create_checks(snn):
+    import torch
+    b = _small_batch()
+    net = snn.Network.from_synth(b.net)
+    rt = snn.Routing(net, b.part, b.P, b.n_vn, "contiguous")
+    plist = [snn.sim_params(c.dyn) for c in b.cfgs]
+    n = len(plist)
+    arr = (snn.snn_sim_params * n)(*plist)
+    nb = ctypes.c_size_t(0)
+    assert snn._lib.snn_batch_workspace_bytes(rt.h, n, arr, ctypes.byref(nb)) == 0
+    plain = ctypes.c_size_t(0)
+    assert snn._lib.snn_sim_workspace_bytes(rt.h, ctypes.byref(plist[0]), ctypes.byref(plain)) == 0
+    assert nb.value > plain.value
+
+    def create(off):
+        off = np.ascontiguousarray(off, np.int64)
+        h = ctypes.c_void_p()
+        return snn._lib.snn_batch_create(ctypes.byref(net.s), rt.h, n, off.ctypes.data, arr,
+                                         ctypes.c_void_p(1 << 20), nb.value, None, ctypes.byref(h))
+
+    bad = b.off.copy()
+    bad[2] += 2                       # not a multiple of 4
+    assert create(bad) == -1
+    bad = b.off.copy()
+    bad[2] += 4                       # synapses now leave their network
+    assert create(bad) == -1
+    bad = b.off.copy()
+    bad[-1] -= 4                      # does not end at M
+    assert create(bad) == -1
+    if not torch.cuda.is_available():
+        assert create(b.off) == -7     # checks pass, no device here
+    # partitions of a VN in two networks: group the concatenation's VNs across the seam
+    part2 = b.part.copy()
+    a = int(b.off[1])
+    part2[a:a + 4] = part2[a - 1]     # a few ids of network 1 join network 0's last partition
+    rt2 = snn.Routing(net, part2, b.P, b.n_vn, "contiguous")
+    h = ctypes.c_void_p()
+    off = np.ascontiguousarray(b.off, np.int64)
+    assert snn._lib.snn_batch_create(ctypes.byref(net.s), rt2.h, n, off.ctypes.data, arr,
+                                     ctypes.c_void_p(1 << 20), nb.value, None, ctypes.byref(h)) == -1
