@@ -304,6 +304,23 @@ int snn_load_state(snn_sim *sim, const void *host_buf, size_t bytes);
  * reupload != 0 the routing tables are copied to the device again. */
 int snn_sim_reset(snn_sim *sim, int32_t reupload);
 
+/*
+ * Launch-shape autotuner (no counterpart in the paper): time `steps` steps
+ * (after steps/4 warm-up steps) of every shape this GPU can run -- the
+ * persistent kernel with 4, 3, 2 or 1 blocks per SM and the neuron state in
+ * shared memory, in global memory with 16-byte accesses or one neuron per
+ * thread, and the CUDA-graph path -- each from the initial state, and keep
+ * the fastest.  Every shape gives the same results bit for bit.  The
+ * exchange capacities need no tuning: they are the exact worst case of the
+ * routing tables.  Leaves the sim in its initial state (as snn_sim_reset
+ * without re-upload); call it before stepping.  choice (may be NULL): 0 =
+ * graph path, else 100 * mode + blocks per SM (mode 2 shared-memory state,
+ * 1 global 16-byte, 0 global one neuron per thread); best_ms (may be NULL):
+ * the chosen shape's time per step.  Synchronises the stream.
+ * Errors: SNN_E_ARG, SNN_E_CUDA.
+ */
+int snn_autotune(snn_sim *sim, int32_t steps, int32_t *choice, double *best_ms);
+
 /* Kernels of one step on the graph path: 2 (a1-a3, a4-a6). */
 int64_t snn_launches_per_step(const snn_sim *sim);
 /* Kernel launches one snn_step(sim, T) issues: 1 on the persistent path,

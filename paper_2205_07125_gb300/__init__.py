@@ -105,6 +105,7 @@ _sig("snn_batch_workspace_bytes", ctypes.c_int, [_vp, _i32, _vp, _P(ctypes.c_siz
 _sig("snn_batch_create", ctypes.c_int, [_P(snn_network), _vp, _i32, _vp, _vp, _vp, ctypes.c_size_t, _vp,
                                         _P(_vp)])
 _sig("snn_step", ctypes.c_int, [_vp, _i32])
+_sig("snn_autotune", ctypes.c_int, [_vp, _i32, _P(_i32), _P(ctypes.c_double)])
 _sig("snn_sync_status", ctypes.c_int, [_vp])
 _sig("snn_read_raster", ctypes.c_int, [_vp, _i64, _i64, _vp, _i64, _vp, _P(_i64)])
 _sig("snn_read_currents", ctypes.c_int, [_vp, _i64, _vp])
@@ -131,7 +132,8 @@ EXPORTS = ("snn_strerror", "snn_partition", "snn_routing_build", "snn_routing_in
            "snn_read_counts", "snn_read_state", "snn_read_inbox_pairs", "snn_state_bytes",
            "snn_save_state", "snn_load_state", "snn_sim_reset", "snn_launches_per_step", "snn_launches",
            "snn_profile_phases", "snn_deliver_spikes", "snn_deliver_spikes_static",
-           "snn_static_scratch_bytes", "snn_sim_destroy", "snn_batch_workspace_bytes", "snn_batch_create")
+           "snn_static_scratch_bytes", "snn_sim_destroy", "snn_batch_workspace_bytes", "snn_batch_create",
+           "snn_autotune")
 
 
 class SnnError(RuntimeError):
@@ -362,6 +364,14 @@ class Sim:
     def reset(self, reupload: bool = False):
         with self._dev():
             _ck(_lib.snn_sim_reset(self.h, int(bool(reupload))), "snn_sim_reset")
+
+    def autotune(self, steps: int = 200):
+        """Pick the fastest launch shape (see snn_autotune); returns (choice, ms per step)."""
+        c = _i32(0)
+        ms = ctypes.c_double(0.0)
+        with self._dev():
+            _ck(_lib.snn_autotune(self.h, int(steps), ctypes.byref(c), ctypes.byref(ms)), "snn_autotune")
+        return int(c.value), float(ms.value)
 
     def profile_phases(self, T: int) -> np.ndarray:
         """Advance T steps and return the summed ms of [0] the steps' work

@@ -288,6 +288,9 @@ struct snn_sim {
     int pmode = kModeScalar;  // neuron-state access of k_persist
     size_t persist_smem = 0;  // dynamic shared memory of k_persist (kModeSmem)
     int64_t chunk_q = 0;      // quads per block of k_persist (kModeSmem)
+    int sms = 0;              // SMs of the device
+    bool coop = false;        // cooperative launch available
+    int persist_bps = 0;      // blocks per SM of k_persist
     bool pdl = true;       // programmatic dependent launch between step kernels
     bool persist = false;  // one cooperative launch per snn_step (k_persist)
     unsigned grid_persist = 1;
@@ -537,6 +540,45 @@ extern "C" int snn_batch_create(const snn_network *net, const snn_routing *rt, i
     return sim_create(net, rt, &params[0], n, off, params, workspace, ws_bytes, stream, out);
 }
 
+// Select the persistent kernel in neuron-state mode `mode` with b blocks per
+// SM if that many stay resident (kModeSmem: and the block's quads fit in its
+// shared memory).  Returns whether it was selected.
+static bool shape_persist(snn_sim *s, int mode, int b)
+{
+    const snn_routing *rt = s->rt;
+    const int64_t grid = std::min<int64_t>((int64_t)s->sms * b, s->L.tally_rows);
+    size_t dyn = 0;
+    int64_t cq = 0;
+    const void *fn = mode == kModeSmem ? (const void *)k_persist<kModeSmem>
+                     : mode == kModeVec ? (const void *)k_persist<kModeVec>
+                                        : (const void *)k_persist<kModeScalar>;
+    if (mode != kModeScalar && !s->vec) return false;
+    if (mode == kModeSmem) {
+        int smax = 0;
+        cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device);
+        cq = (rt->M / 4 + grid - 1) / grid;
+        dyn = (size_t)cq * 36;
+        if (dyn > (size_t)smax ||
+            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+    }
+    int op = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&op, fn, kThreads, dyn) != cudaSuccess || op < b) {
+        cudaGetLastError();
+        return false;
+    }
+    s->persist = true;
+    s->pmode = mode;
+    s->persist_bps = b;
+    s->grid_persist = (unsigned)grid;
+    s->persist_smem = dyn;
+    s->chunk_q = cq;
+    s->dev.chunk_q = cq;
+    return true;
+}
+
 static int sim_create(const snn_network *net, const snn_routing *rt, const snn_sim_params *p, int32_t n_net,
                       const int64_t *off, const snn_sim_params *params, void *workspace, size_t ws_bytes,
                       void *stream, snn_sim **out)
@@ -602,52 +644,18 @@ static int sim_create(const snn_network *net, const snn_routing *rt, const snn_s
         // (SNN_PERSIST=0 selects the CUDA-graph path).  With M % 4 == 0 each
         // block keeps its quads' state in shared memory when that fits at
         // the most blocks per SM that do (SNN_PERSIST_SMEM=0: global state).
+        s->sms = sms;
         int coop = 0;
         const char *e = std::getenv("SNN_PERSIST");
         const char *esm = std::getenv("SNN_PERSIST_SMEM");
         // SNN_PERSIST_BLOCKS_PER_SM lowers the resident blocks per SM (tuning)
         const char *bps = std::getenv("SNN_PERSIST_BLOCKS_PER_SM");
-        const int bmax = (bps && std::atoi(bps) > 0) ? std::atoi(bps) : 1 << 30;
-        if (!(e && e[0] == '0') &&
-            cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, s->device) == cudaSuccess && coop) {
-            if (s->vec && !(esm && esm[0] == '0')) {
-                int smax = 0;
-                cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device);
-                const int64_t nq = rt->M / 4;
-                for (int b = std::min(4, bmax); b >= 1 && s->pmode != kModeSmem; --b) {
-                    const int64_t grid = std::min<int64_t>((int64_t)sms * b, s->L.tally_rows);
-                    const int64_t cq = (nq + grid - 1) / grid;
-                    const size_t dyn = (size_t)cq * 36;
-                    if (dyn > (size_t)smax) continue;
-                    if (cudaFuncSetAttribute(k_persist<kModeSmem>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)dyn) != cudaSuccess)
-                        continue;
-                    int op = 0;
-                    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&op, k_persist<kModeSmem>, kThreads, dyn) !=
-                            cudaSuccess ||
-                        op < b)
-                        continue;
-                    s->persist = true;
-                    s->pmode = kModeSmem;
-                    s->grid_persist = (unsigned)grid;
-                    s->persist_smem = dyn;
-                    s->chunk_q = cq;
-                }
-                cudaGetLastError();
-            }
-            if (!s->persist) {
-                int op = 0;
-                const int mode = s->vec ? kModeVec : kModeScalar;
-                const cudaError_t oe =
-                    s->vec ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&op, k_persist<kModeVec>, kThreads, 0)
-                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&op, k_persist<kModeScalar>, kThreads, 0);
-                op = std::min(op, bmax);
-                if (oe == cudaSuccess && op > 0) {
-                    s->persist = true;
-                    s->pmode = mode;
-                    s->grid_persist = (unsigned)std::min<int64_t>((int64_t)sms * op, s->L.tally_rows);
-                }
-            }
+        const int bmax = (bps && std::atoi(bps) > 0) ? std::min(4, std::atoi(bps)) : 4;
+        s->coop = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, s->device) == cudaSuccess && coop;
+        if (!(e && e[0] == '0') && s->coop) {
+            if (!(esm && esm[0] == '0'))
+                for (int b = bmax; b >= 1 && !s->persist; --b) shape_persist(s, kModeSmem, b);
+            for (int b = bmax; b >= 1 && !s->persist; --b) shape_persist(s, s->vec ? kModeVec : kModeScalar, b);
         }
         cudaGetLastError();
         // tests of the bounded barrier wait: a shorter bound, and block 0
@@ -845,6 +853,64 @@ extern "C" int snn_profile_phases(snn_sim *s, int32_t T, double *phase_ms)
         }
     }
     return SNN_OK;
+}
+
+// ---------------------------------------------------------------- launch-shape autotuner
+static int read_ctrl(snn_sim *s, Ctrl *c);
+
+extern "C" int snn_autotune(snn_sim *s, int32_t steps, int32_t *choice, double *best_ms)
+{
+    if (!s || steps < 1) return SNN_E_ARG;
+    struct Shape {
+        bool persist;
+        int mode, b;
+    };
+    std::vector<Shape> cand;
+    if (s->coop)
+        for (int mode : {kModeSmem, kModeVec, kModeScalar})
+            for (int b = 4; b >= 1; --b) cand.push_back({true, mode, b});
+    cand.push_back({false, 0, 0});
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    double best = 1e300;
+    Shape pick = {s->persist, s->pmode, s->persist_bps};
+    int rc = SNN_OK;
+    for (const Shape &c : cand) {
+        if (c.persist) {
+            s->persist = false;
+            if (!shape_persist(s, c.mode, c.b)) continue;
+        } else {
+            s->persist = false;
+        }
+        // from the initial state: a quarter of the steps to warm up, then the timed steps
+        if ((rc = reset_state(s)) != SNN_OK) break;
+        if ((rc = snn_step(s, std::max(1, steps / 4))) != SNN_OK) break;
+        if (cudaEventRecord(e0, s->stream) != cudaSuccess) { rc = SNN_E_CUDA; break; }
+        if ((rc = snn_step(s, steps)) != SNN_OK) break;
+        if (cudaEventRecord(e1, s->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = SNN_E_CUDA;
+            break;
+        }
+        Ctrl ctl;
+        if ((rc = read_ctrl(s, &ctl)) != SNN_OK) break;
+        if (ctl.status & kStTimeout) continue;  // a shape that cannot run here
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            pick = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    s->persist = false;
+    if (pick.persist) shape_persist(s, pick.mode, pick.b);
+    const int rr = reset_state(s);
+    if (rc == SNN_OK) rc = rr;
+    if (choice) *choice = pick.persist ? 100 * pick.mode + pick.b : 0;
+    if (best_ms) *best_ms = best < 1e300 ? best / steps : -1.0;
+    return rc;
 }
 
 // Fill the table pointers of a fan-out from the sim's device view.

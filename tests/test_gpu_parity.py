@@ -247,3 +247,17 @@ def test_barrier_wait_is_bounded(snn, monkeypatch):
     assert sim.sync_status() == 0
     _, _, t = sim.read_state()
     assert t == 20
+
+
+def test_autotune_keeps_results(snn):
+    """The autotuner tries every launch shape from the initial state, keeps the
+    fastest and leaves the sim in its initial state: the run after it is the
+    oracle's run."""
+    cfg = synth.SCALE.scaled(M=16384, P=16, n_vn=4, K=200, n_part=140, n_vn_t=40, n_remote=20, steps=200)
+    g = synth.make_network(cfg)
+    sim, o, rec, _ = _run_pair(snn, g, cfg, 200, cfg.P, cfg.n_vn)
+    choice, ms = sim.autotune(40)
+    assert ms > 0 and (choice == 0 or choice % 100 in (1, 2, 3, 4))
+    sim.step(200)
+    _compare(sim, o, 200, rec)
+    assert sim.sync_status() == 0
