@@ -179,9 +179,10 @@ def run_ours(args):
     prm = snn.sim_params(cfg.dyn, raster_cap=raster_cap, raster_steps=K + W, steps_per_graph=32,
                          pin_host_tables=1)
     sim = snn.Sim(net, rt, prm, device=dev)
+    choice, tuned_ms = sim.autotune(200)
     setup_s = time.time() - t_setup
-    print("[bench] setup %.1f s (generate + partition + routing + upload)" % setup_s,
-          file=sys.stderr, flush=True)
+    print("[bench] setup %.1f s (generate + partition + routing + upload + autotune: shape %d, %.4f ms/step)"
+          % (setup_s, choice, tuned_ms), file=sys.stderr, flush=True)
     stream = sim.stream
 
     # warm-up, then EXACTLY K timed steps from graph replays
@@ -298,7 +299,10 @@ def run_ours(args):
                          "delay ring %.0f MB (L2-resident when it fits the 129 MB L2)"
                          % (info["n_synapses"] * 6 / 1e9, cfg.M * (info["max_delay"] + 1) * 4 / 1e6),
                    "steps_per_graph": 32,
-                   "execution": "persistent cooperative kernel" if persistent else "CUDA graphs"},
+                   "execution": "persistent cooperative kernel" if persistent else "CUDA graphs",
+                   "autotune": {"choice": choice, "ms_per_step": tuned_ms,
+                                "meaning": "0 graph path, else 100*mode + blocks per SM (mode 2 "
+                                           "shared-memory state, 1 global 16-byte, 0 global scalar)"}},
         "spikes_per_step": spikes_all / world / K,
         "events_per_step": events_all / world / K,
         "rate_hz": spikes_all / world / K / cfg.M / (cfg.dyn.dt_ms * 1e-3),
@@ -422,7 +426,7 @@ def run_reference(args):
         return
     import synth
     import oracle
-    cfg = workload(0, args.neurons, args.config)
+    cfg = workload(0, args.neurons, "scale" if args.config == "batch" else args.config)
     g = synth.make_network(cfg)
     P = cfg.P
     o = oracle.Oracle(g, P, oracle.partition_planted(g.M, P), cfg.n_vn,
@@ -451,6 +455,127 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_batch(args):
+    """The batched form: 64 independent networks of uneven sizes (10k-500k
+    neurons, 4-32 partitions, out-degree 100-1000, scaled drives) stepped by
+    one sim, against the same networks stepped one after another by one plain
+    sim each (the same work, one launch per network instead of one in all)."""
+    import torch
+    import synth
+    import paper_2205_07125_gb300 as snn
+
+    dist, rank, world = dist_init()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    K, W = args.steps, args.warmup
+    t_setup = time.time()
+    cfgs = synth.batch_configs(n=args.batch_nets, seed=3000 + 100 * rank)
+    b = synth.make_batch(cfgs)
+    net = snn.Network.from_synth(b.net)
+    rt = snn.Routing(net, b.part, b.P, b.n_vn, "contiguous")
+    info = rt.info()
+    plist = [snn.sim_params(c.dyn, steps_per_graph=32) for c in cfgs]
+    sim = snn.Sim(net, rt, plist[0], device=dev, batch=(b.off, plist))
+    choice, tuned_ms = sim.autotune(200)
+    setup_s = time.time() - t_setup
+    print("[bench] batch of %d networks, %d neurons, %d synapses; setup %.1f s; autotune choice %d (%.4f ms/step)"
+          % (len(cfgs), b.net.M, b.net.E, setup_s, choice, tuned_ms), file=sys.stderr, flush=True)
+    stream = sim.stream
+    sim.step(W)
+    if sim.sync_status() != 0:
+        raise RuntimeError("device status after warm-up: %d" % sim.sync_status())
+    c0 = sim.read_counts()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier(dist)
+    torch.cuda.synchronize()
+    wall0 = time.time()
+    e0.record(stream)
+    sim.step(K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    wall1 = time.time()
+    barrier(dist)
+    time.sleep(0.1)
+    clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if sim.sync_status() != 0:
+        raise RuntimeError("device status after the timed steps: %d" % sim.sync_status())
+    c1 = sim.read_counts()
+    dc = {k: c1[k] - c0[k] for k in c1}
+    assert dc["steps"] == K
+    # per-network firing rates of the timed steps (from a short recorded run)
+    events_all, ms_max, spikes_all = reduce_over_ranks(dist, float(dc["events"]), ms, float(dc["spikes"]))
+    pb4 = phase_bytes(b.net.M, K, dc, not info["identity_order"])
+    step_bytes = sum(pb4) / K
+    peak, peak_kind = _peaks()
+    launches = sim.launches(K)
+    sim.close()
+    del sim
+
+    # the same networks, one plain sim each, stepped one after another
+    KS = min(K, args.separate_steps)
+    sep_ms, sep_ev = 0.0, 0.0
+    for c, g, p in zip(cfgs, b.nets, plist):
+        n1 = snn.Network.from_synth(g)
+        part, _ = snn.snn_partition(n1, c.P, "planted")
+        r1 = snn.Routing(n1, part, c.P, c.n_vn, "contiguous")
+        s1 = snn.Sim(n1, r1, p, device=dev)
+        s1.step(W)
+        a0 = s1.read_counts()
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(s1.stream)
+        s1.step(KS)
+        f1.record(s1.stream)
+        torch.cuda.synchronize()
+        sep_ms += f0.elapsed_time(f1)
+        sep_ev += s1.read_counts()["events"] - a0["events"]
+        s1.close()
+        del s1, r1, n1
+    sep_rate = sep_ev / (sep_ms * 1e-3)
+    value = events_all / (ms_max * 1e-3)
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": ms_max / K, "steps_per_s": K / (ms_max * 1e-3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+i32",
+        "data": "synthetic (seeded generator; 64 independent networks stand in for a batch of models)",
+        "config": {"workload": "batch-%dnets-%dn" % (len(cfgs), b.net.M), "networks": len(cfgs),
+                   "neurons": b.net.M, "synapses": b.net.E, "partitions": b.P, "virtual_nodes": b.n_vn,
+                   "sizes": "log-uniform 10k-500k", "synapses_per_neuron": "uniform 100-1000",
+                   "partitions_per_network": "4-32 (VNs of 2)", "drive": "scale drive x r/10, r ~ U[5, 15] Hz",
+                   "parallelism": "replicas x%d" % world, "execution": "autotuned shape %d" % choice,
+                   "l2": "inputs larger than L2: %.1f GB synapse CSR" % (b.net.E * 6 / 1e9)},
+        "spikes_per_step": spikes_all / world / K, "events_per_step": events_all / world / K,
+        "rate_hz": spikes_all / world / K / b.net.M / 1e-4,
+        "roofline": {"bound": "hbm", "kernel": "k_persist" if launches == 1 else "k_update+k_route",
+                     "achieved": step_bytes * K / (ms_max * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": step_bytes * K / (ms_max * 1e-3) / 1e9 / peak,
+                     "peak_source": ("measured (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                                     else "fallback 6.8 TB/s"),
+                     "algorithmic_bytes_per_launch": step_bytes * (K if launches == 1 else 1), "traffic": None},
+        "vs_plain": {"what": "the same %d networks, one plain sim each, stepped one after another "
+                             "(%d steps each)" % (len(cfgs), KS),
+                     "value": sep_rate, "unit": UNIT, "batched_over_plain": value / sep_rate},
+        "autotune": {"choice": choice, "ms_per_step": tuned_ms,
+                     "meaning": "0 graph path, else 100*mode + blocks per SM (mode 2 shared-memory state, "
+                                "1 global 16-byte, 0 global scalar)"},
+        "gpu_launches": launches,
+        "clocks": clocks.summary(wall0, wall1),
+        "e2e": None,
+        "setup_s": setup_s,
+    }
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -464,15 +589,20 @@ def main(argv=None):
                     help="network size with the scale workload's per-neuron statistics "
                          "(default: the 1,048,576-neuron workload)")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--config", choices=("scale", "paper", "tiny"), default="scale",
+    ap.add_argument("--config", choices=("scale", "paper", "tiny", "batch"), default="scale",
                     help="scale: 1,048,576 neurons / 64 partitions (the headline workload); "
                          "paper: the paper-shaped per-GPU share, 5,000,000 neurons / 256 partitions; "
-                         "tiny: 4,096 neurons")
+                         "tiny: 4,096 neurons; batch: 64 independent networks of uneven sizes")
+    ap.add_argument("--batch-nets", type=int, default=64)
+    ap.add_argument("--separate-steps", type=int, default=1000,
+                    help="steps per network of the one-sim-per-network comparison (--config batch)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.config == "batch":
+        run_batch(args)
     else:
         run_ours(args)
 

@@ -310,7 +310,8 @@ int snn_sim_reset(snn_sim *sim, int32_t reupload);
  * persistent kernel with 4, 3, 2 or 1 blocks per SM and the neuron state in
  * shared memory, in global memory with 16-byte accesses or one neuron per
  * thread, and the CUDA-graph path -- each from the initial state, and keep
- * the fastest.  Every shape gives the same results bit for bit.  The
+ * the fastest (shapes excluded by SNN_PERSIST=0 / SNN_PERSIST_SMEM=0 at
+ * creation are not tried).  Every shape gives the same results bit for bit.  The
  * exchange capacities need no tuning: they are the exact worst case of the
  * routing tables.  Leaves the sim in its initial state (as snn_sim_reset
  * without re-upload); call it before stepping.  choice (may be NULL): 0 =

@@ -291,6 +291,7 @@ struct snn_sim {
     int sms = 0;              // SMs of the device
     bool coop = false;        // cooperative launch available
     int persist_bps = 0;      // blocks per SM of k_persist
+    bool allow_persist = true, allow_smem = true;  // SNN_PERSIST / SNN_PERSIST_SMEM
     bool pdl = true;       // programmatic dependent launch between step kernels
     bool persist = false;  // one cooperative launch per snn_step (k_persist)
     unsigned grid_persist = 1;
@@ -652,8 +653,10 @@ static int sim_create(const snn_network *net, const snn_routing *rt, const snn_s
         const char *bps = std::getenv("SNN_PERSIST_BLOCKS_PER_SM");
         const int bmax = (bps && std::atoi(bps) > 0) ? std::min(4, std::atoi(bps)) : 4;
         s->coop = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, s->device) == cudaSuccess && coop;
-        if (!(e && e[0] == '0') && s->coop) {
-            if (!(esm && esm[0] == '0'))
+        s->allow_persist = !(e && e[0] == '0') && s->coop;
+        s->allow_smem = !(esm && esm[0] == '0');
+        if (s->allow_persist) {
+            if (s->allow_smem)
                 for (int b = bmax; b >= 1 && !s->persist; --b) shape_persist(s, kModeSmem, b);
             for (int b = bmax; b >= 1 && !s->persist; --b) shape_persist(s, s->vec ? kModeVec : kModeScalar, b);
         }
@@ -866,9 +869,10 @@ extern "C" int snn_autotune(snn_sim *s, int32_t steps, int32_t *choice, double *
         int mode, b;
     };
     std::vector<Shape> cand;
-    if (s->coop)
+    if (s->allow_persist)
         for (int mode : {kModeSmem, kModeVec, kModeScalar})
-            for (int b = 4; b >= 1; --b) cand.push_back({true, mode, b});
+            for (int b = 4; b >= 1; --b)
+                if (mode != kModeSmem || s->allow_smem) cand.push_back({true, mode, b});
     cand.push_back({false, 0, 0});
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
