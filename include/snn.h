@@ -322,6 +322,60 @@ int snn_sim_reset(snn_sim *sim, int32_t reupload);
  */
 int snn_autotune(snn_sim *sim, int32_t steps, int32_t *choice, double *best_ms);
 
+/* ---------------------------------------------------------------- adjoint */
+/*
+ * Surrogate-gradient adjoint (no counterpart in the paper, which simulates
+ * but does not train).  The differentiable step keeps the routing and the
+ * integer delivery and adds parameters: population-pair gains G[a][b]
+ * (n_pop x n_pop, row = target population) and drive rates lam[a] (arrivals
+ * per step), populations pop(j) = 2 vn(j) + (1 if j is inhibitory), n_pop =
+ * 2 n_vn <= 8.  Forward step (fp32, fixed order, no FMA):
+ *   A_jb = int32 sum of the weights from population b arriving at j;
+ *   I_j  = (((G[a][0] A_j0 + G[a][1] A_j1) + ...) + w_ext (lam_a + sigma xi_j(t)),
+ *   xi_j(t) = (sum of the 12 bytes of words 0..2 of Philox4x32-10(counter
+ *   (global id j, t, 0xAD, 0), key = drive_seed) - 1530) / 256;
+ *   V_pre = (E_L + alpha (V - E_L)) + I 2^-10, spike V_pre >= V_th, reset and
+ *   refractory as the plain step.
+ * Rates r_a = (spikes of population a) / (T N_a).  Backward: surrogate
+ * dS/dV_pre = 1 / (1 + beta |V_pre - V_th|)^2, reset detached; each neuron
+ * gathers its targets' adjoints along its own level-2 entries (the
+ * transpose of the routed delivery); gradients in float64.
+ */
+typedef struct {
+    int32_t T;            /* forward steps per run (>= 1) */
+    int32_t ckpt_every;   /* membrane checkpoint interval K: state saved every K steps */
+    float sigma;          /* noise scale (0.9) */
+    float beta;           /* surrogate slope, 1/mV (5) */
+    int64_t reserved[2];
+} snn_adjoint_params;
+
+typedef struct snn_adjoint snn_adjoint;
+
+void snn_adjoint_params_default(snn_adjoint_params *ap);
+/* Device workspace: state, tables, one recorded segment of K steps and
+ * ceil(T/K) checkpoints of (V, ref, delay ring).  Errors: SNN_E_ARG,
+ * SNN_E_RANGE (n_pop > 8). */
+int snn_adjoint_workspace_bytes(const snn_routing *rt, const snn_sim_params *p, const snn_adjoint_params *ap,
+                                size_t *bytes);
+/* is_exc: [M] global order (1 excitatory).  p gives the LIF constants,
+ * w_ext, drive_seed and raster_cap (spike record of the forward).
+ * Workspace and stream as snn_sim_create.  Errors: SNN_E_ARG, SNN_E_NOMEM,
+ * SNN_E_CUDA, SNN_E_NODEV. */
+int snn_adjoint_create(const snn_network *net, const uint8_t *is_exc, const snn_routing *rt,
+                       const snn_sim_params *p, const snn_adjoint_params *ap, void *workspace,
+                       size_t workspace_bytes, void *stream, snn_adjoint **out);
+/* T steps from the initial state with parameters G [n_pop*n_pop], lam
+ * [n_pop] (host); rates [n_pop] (may be NULL), *spikes = total (may be
+ * NULL).  Synchronises the stream. */
+int snn_adjoint_forward(snn_adjoint *adj, const float *G, const float *lam, float *rates, int64_t *spikes);
+/* Gradients of a loss with dL/dr = grates [n_pop] through the last
+ * forward: dG [n_pop*n_pop], dlam [n_pop] (host, float64).  Recomputes each
+ * K-step segment from its checkpoint.  Errors: SNN_E_STATE (no forward). */
+int snn_adjoint_backward(snn_adjoint *adj, const double *grates, double *dG, double *dlam);
+/* Spikes of the last forward as (t << 32 | global id), unordered; *n = total. */
+int snn_adjoint_read_spikes(snn_adjoint *adj, uint64_t *out, int64_t cap, int64_t *n);
+void snn_adjoint_destroy(snn_adjoint *adj);
+
 /* Kernels of one step on the graph path: 2 (a1-a3, a4-a6). */
 int64_t snn_launches_per_step(const snn_sim *sim);
 /* Kernel launches one snn_step(sim, T) issues: 1 on the persistent path,

@@ -154,7 +154,7 @@ def forward_fp32(net: AdjointNet, G: np.ndarray, lam: np.ndarray, T: int) -> Tra
         ring[t % D] = 0
         Af = A.astype(f32)
         Gr = G[a]  # [M, npop]
-        irec = f32(0) + Gr[:, 0] * Af[:, 0]
+        irec = (Gr[:, 0] * Af[:, 0]).astype(f32)
         for b in range(1, npop):
             irec = (irec + Gr[:, b] * Af[:, b]).astype(f32)
         x1 = (SIGMA * noise(net.seed, M, t)).astype(f32)

@@ -76,6 +76,10 @@ COUNT_FIELDS = ("steps", "spikes", "events", "direct", "direct_xvn", "l1_local",
                 "l2_local", "l2_peer", "l2_relay_local", "l2_relay_remote")
 
 
+class snn_adjoint_params(ctypes.Structure):
+    _fields_ = [("T", _i32), ("ckpt_every", _i32), ("sigma", _f32), ("beta", _f32), ("reserved", _i64 * 2)]
+
+
 class snn_counts(ctypes.Structure):
     _fields_ = [(n, _u64) for n in COUNT_FIELDS]
 
@@ -124,6 +128,15 @@ _sig("snn_deliver_spikes", ctypes.c_int, [_vp, _vp, _i64, _vp, _vp])
 _sig("snn_deliver_spikes_static", ctypes.c_int, [_vp, _vp, _i64, _vp, _vp])
 _sig("snn_static_scratch_bytes", ctypes.c_size_t, [])
 _sig("snn_sim_destroy", None, [_vp])
+_sig("snn_adjoint_params_default", None, [_P(snn_adjoint_params)])
+_sig("snn_adjoint_workspace_bytes", ctypes.c_int, [_vp, _P(snn_sim_params), _P(snn_adjoint_params),
+                                                   _P(ctypes.c_size_t)])
+_sig("snn_adjoint_create", ctypes.c_int, [_P(snn_network), _vp, _vp, _P(snn_sim_params), _P(snn_adjoint_params),
+                                          _vp, ctypes.c_size_t, _vp, _P(_vp)])
+_sig("snn_adjoint_forward", ctypes.c_int, [_vp, _vp, _vp, _vp, _P(_i64)])
+_sig("snn_adjoint_backward", ctypes.c_int, [_vp, _vp, _vp, _vp])
+_sig("snn_adjoint_read_spikes", ctypes.c_int, [_vp, _vp, _i64, _P(_i64)])
+_sig("snn_adjoint_destroy", None, [_vp])
 
 EXPORTS = ("snn_strerror", "snn_partition", "snn_routing_build", "snn_routing_info_get",
            "snn_routing_groups", "snn_routing_connections", "snn_routing_destroy",
@@ -133,7 +146,8 @@ EXPORTS = ("snn_strerror", "snn_partition", "snn_routing_build", "snn_routing_in
            "snn_save_state", "snn_load_state", "snn_sim_reset", "snn_launches_per_step", "snn_launches",
            "snn_profile_phases", "snn_deliver_spikes", "snn_deliver_spikes_static",
            "snn_static_scratch_bytes", "snn_sim_destroy", "snn_batch_workspace_bytes", "snn_batch_create",
-           "snn_autotune")
+           "snn_autotune", "snn_adjoint_params_default", "snn_adjoint_workspace_bytes", "snn_adjoint_create",
+           "snn_adjoint_forward", "snn_adjoint_backward", "snn_adjoint_read_spikes", "snn_adjoint_destroy")
 
 
 class SnnError(RuntimeError):
@@ -410,3 +424,107 @@ class Sim:
 
     def __del__(self):
         self.close()
+
+
+# ---------------------------------------------------------------- adjoint
+def adjoint_params(**kw) -> snn_adjoint_params:
+    ap = snn_adjoint_params()
+    _lib.snn_adjoint_params_default(ctypes.byref(ap))
+    for k, v in kw.items():
+        if not hasattr(ap, k):
+            raise KeyError(k)
+        setattr(ap, k, v)
+    return ap
+
+
+class Adjoint:
+    """The surrogate-gradient adjoint of the step (see snn_adjoint_create):
+    forward(G, lam) -> population rates, backward(dL/drates) -> (dG, dlam)."""
+
+    def __init__(self, net: Network, is_exc, routing: Routing, params: snn_sim_params,
+                 aparams: snn_adjoint_params, device=None, stream=None):
+        import torch
+        self.net, self.routing, self.params, self.aparams = net, routing, params, aparams
+        self.is_exc = np.ascontiguousarray(is_exc, np.uint8)
+        self.n_pop = 2 * routing.info()["n_vn"]
+        dev = torch.device(device if device is not None else "cuda")
+        self.device = dev
+        nb = ctypes.c_size_t(0)
+        _ck(_lib.snn_adjoint_workspace_bytes(routing.h, ctypes.byref(params), ctypes.byref(aparams),
+                                             ctypes.byref(nb)), "snn_adjoint_workspace_bytes")
+        with torch.cuda.device(dev):
+            self.workspace = torch.empty(max(256, nb.value), dtype=torch.uint8, device=dev)
+            self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+            h = _vp()
+            _ck(_lib.snn_adjoint_create(ctypes.byref(net.s), self.is_exc.ctypes.data, routing.h,
+                                        ctypes.byref(params), ctypes.byref(aparams), self.workspace.data_ptr(),
+                                        nb.value, self.stream.cuda_stream, ctypes.byref(h)), "snn_adjoint_create")
+        self.h = h.value
+
+    def forward(self, G, lam):
+        G = np.ascontiguousarray(G, np.float32).reshape(self.n_pop, self.n_pop)
+        lam = np.ascontiguousarray(lam, np.float32)
+        rates = np.zeros(self.n_pop, np.float32)
+        n = _i64(0)
+        with torch_device(self.device):
+            _ck(_lib.snn_adjoint_forward(self.h, G.ctypes.data, lam.ctypes.data, rates.ctypes.data,
+                                         ctypes.byref(n)), "snn_adjoint_forward")
+        self.spikes = int(n.value)
+        return rates
+
+    def backward(self, grates):
+        g = np.ascontiguousarray(grates, np.float64)
+        dG = np.zeros((self.n_pop, self.n_pop), np.float64)
+        dlam = np.zeros(self.n_pop, np.float64)
+        with torch_device(self.device):
+            _ck(_lib.snn_adjoint_backward(self.h, g.ctypes.data, dG.ctypes.data, dlam.ctypes.data),
+                "snn_adjoint_backward")
+        return dG, dlam
+
+    def spikes_of_last_forward(self):
+        """(step, global id) of every spike of the last forward, sorted."""
+        n = _i64(0)
+        _ck(_lib.snn_adjoint_read_spikes(self.h, None, 0, ctypes.byref(n)), "snn_adjoint_read_spikes")
+        out = np.zeros(max(1, n.value), np.uint64)
+        _ck(_lib.snn_adjoint_read_spikes(self.h, out.ctypes.data, n.value, ctypes.byref(n)),
+            "snn_adjoint_read_spikes")
+        out = np.sort(out[:n.value])
+        return (out >> np.uint64(32)).astype(np.int64), (out & np.uint64(0xFFFFFFFF)).astype(np.int64)
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.snn_adjoint_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def torch_device(dev):
+    import torch
+    return torch.cuda.device(dev)
+
+
+def make_adjoint_function():
+    """torch.autograd.Function over an Adjoint: rates = f(G, lam); the
+    backward calls the adjoint kernels.  G, lam: CPU or CUDA float tensors."""
+    import torch
+
+    class AdjointFunction(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, G, lam, adj):
+            ctx.adj = adj
+            ctx.devs = (G.device, lam.device)
+            rates = adj.forward(G.detach().cpu().numpy(), lam.detach().cpu().numpy())
+            return torch.from_numpy(rates.astype(np.float64)).to(G.device)
+
+        @staticmethod
+        def backward(ctx, grates):
+            dG, dlam = ctx.adj.backward(grates.detach().cpu().numpy().astype(np.float64))
+            return (torch.from_numpy(dG).to(ctx.devs[0], dtype=torch.float32),
+                    torch.from_numpy(dlam).to(ctx.devs[1], dtype=torch.float32), None)
+
+    return AdjointFunction

@@ -1,4 +1,4 @@
-"""Compile libsnn.so in-tree with nvcc for sm_103a (two translation units in parallel)."""
+"""Compile libsnn.so in-tree with nvcc for sm_103a (the translation units in parallel)."""
 from __future__ import annotations
 
 import os
@@ -16,6 +16,7 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler",
 SOURCES = {
     "snn_host.o": ["snn_host.cpp"],
     "snn_sim.o": ["snn_sim.cu"],
+    "snn_adjoint.o": ["snn_adjoint.cu"],
 }
 
 
