@@ -426,7 +426,7 @@ def run_reference(args):
         return
     import synth
     import oracle
-    cfg = workload(0, args.neurons, "scale" if args.config == "batch" else args.config)
+    cfg = workload(0, args.neurons, args.config if args.config in ("scale", "paper", "tiny") else "scale")
     g = synth.make_network(cfg)
     P = cfg.P
     o = oracle.Oracle(g, P, oracle.partition_planted(g.M, P), cfg.n_vn,
@@ -576,6 +576,95 @@ def run_batch(args):
         dist.destroy_process_group()
 
 
+def run_adjoint(args):
+    """The adjoint form: 131,072 neurons in 8 partitions over 2 VNs, 500
+    synapses per neuron (scale locality mix), 500 steps forward with
+    checkpoints every 50, then the surrogate-gradient backward; against the
+    plain step of the same network on the same GPU."""
+    import torch
+    import synth
+    import paper_2205_07125_gb300 as snn
+
+    dist, rank, world = dist_init()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    T, CK = 500, 50
+    cfg = synth.NetConfig(name="adjoint-131072n-8p-2vn-k500", M=131072, P=8, n_vn=2, K=500, uniform_all=False,
+                          n_part=350, n_vn_t=100, n_remote=50, dmax=8, seed=1004 + rank, steps=T,
+                          dyn=synth.Dynamics(drive_lambda=0.8, w_ext=89, drive_seed=2004 + rank))
+    t_setup = time.time()
+    g = synth.make_network(cfg)
+    net = snn.Network.from_synth(g)
+    part, _ = snn.snn_partition(net, cfg.P, "planted")
+    rt = snn.Routing(net, part, cfg.P, cfg.n_vn, "contiguous")
+    prm = snn.sim_params(cfg.dyn, raster_cap=cfg.M * T // 10)
+    a = snn.Adjoint(net, g.is_exc, rt, prm, snn.adjoint_params(T=T, ckpt_every=CK), device=dev)
+    n_pop = a.n_pop
+    rng = np.random.default_rng(4000)
+    G = np.ones((n_pop, n_pop), np.float32)
+    lam = np.full(n_pop, 0.8, np.float32)
+    target = (5.0 + 10.0 * rng.random(n_pop)) * 1e-4  # spikes per neuron per step (5-15 Hz)
+    setup_s = time.time() - t_setup
+    for _ in range(max(1, args.warmup // 50)):
+        r = a.forward(G, lam)
+        a.backward(2 * (r.astype(np.float64) - target) / n_pop)
+    reps = max(1, min(args.steps // T, 10))
+    fw = bw = 0.0
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        h0 = time.perf_counter()
+        r = a.forward(G, lam)
+        h1 = time.perf_counter()
+        dG, dlam = a.backward(2 * (r.astype(np.float64) - target) / n_pop)
+        h2 = time.perf_counter()
+        fw += h1 - h0
+        bw += h2 - h1
+    fw /= reps
+    bw /= reps
+    spikes = a.spikes
+    events = spikes * cfg.K
+    a.close()
+    # the plain step of the same network (its own Poisson drive), same steps
+    sim = snn.Sim(net, rt, snn.sim_params(cfg.dyn), device=dev)
+    sim.autotune(100)
+    sim.step(100)
+    c0 = sim.read_counts()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(sim.stream)
+    sim.step(T)
+    e1.record(sim.stream)
+    torch.cuda.synchronize()
+    pms = e0.elapsed_time(e1)
+    pev = sim.read_counts()["events"] - c0["events"]
+    sim.close()
+    it = fw + bw
+    result = {
+        "metric": METRIC, "value": events / it, "unit": UNIT, "n_gpus": world, "steps": T, "warmup": args.warmup,
+        "ms_per_step": it * 1e3 / T, "steps_per_s": T / it, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (gradients f64)", "data": "synthetic",
+        "config": {"workload": cfg.name, "neurons": cfg.M, "partitions": cfg.P, "virtual_nodes": cfg.n_vn,
+                   "synapses": g.E, "steps": T, "checkpoint_every": CK, "populations": n_pop,
+                   "parameters": "%d gains + %d drive rates" % (n_pop * n_pop, n_pop),
+                   "surrogate": "1/(1+5|V-theta|)^2, reset detached",
+                   "timing": "host wall clock of snn_adjoint_forward / _backward (each synchronises)"},
+        "forward_ms": fw * 1e3, "backward_ms": bw * 1e3, "forward_spikes": spikes,
+        "rates_hz": [float(x) * 1e4 for x in r],
+        "grad_norm": float(np.sqrt((dG ** 2).sum() + (dlam ** 2).sum())),
+        "vs_plain": {"what": "plain step of the same network, %d steps, CUDA events" % T,
+                     "plain_ms_per_step": pms / T, "plain_events_per_s": pev / (pms * 1e-3),
+                     "forward_over_plain_time": fw * 1e3 / pms,
+                     "forward_backward_over_plain_time": it * 1e3 / pms},
+        "setup_s": setup_s,
+    }
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -589,10 +678,11 @@ def main(argv=None):
                     help="network size with the scale workload's per-neuron statistics "
                          "(default: the 1,048,576-neuron workload)")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--config", choices=("scale", "paper", "tiny", "batch"), default="scale",
+    ap.add_argument("--config", choices=("scale", "paper", "tiny", "batch", "adjoint"), default="scale",
                     help="scale: 1,048,576 neurons / 64 partitions (the headline workload); "
                          "paper: the paper-shaped per-GPU share, 5,000,000 neurons / 256 partitions; "
-                         "tiny: 4,096 neurons; batch: 64 independent networks of uneven sizes")
+                         "tiny: 4,096 neurons; batch: 64 independent networks of uneven sizes; "
+                         "adjoint: forward + surrogate-gradient backward of a 131,072-neuron network")
     ap.add_argument("--batch-nets", type=int, default=64)
     ap.add_argument("--separate-steps", type=int, default=1000,
                     help="steps per network of the one-sim-per-network comparison (--config batch)")
@@ -603,6 +693,8 @@ def main(argv=None):
         run_reference(args)
     elif args.config == "batch":
         run_batch(args)
+    elif args.config == "adjoint":
+        run_adjoint(args)
     else:
         run_ours(args)
 

@@ -206,16 +206,30 @@ __global__ void __launch_bounds__(kAThreads) k_adj_backward(const AdjDev a, int 
     for (long long j = ((long long)blockIdx.x * kAThreads + threadIdx.x) >> 5; j < a.M; j += nw) {
         const int pj = a.pop[j];
         float acc = 0.0f;
+        // the neuron's level-2 entries tile one contiguous run of synapses:
+        // walk it with four loads per lane in flight
         const uint32_t f0 = a.row[j].y, f1 = a.row[j + 1].y;
-        for (uint32_t f = f0; f < f1; ++f) {
-            const L2Entry l = a.l2[f];
-            const unsigned long long o = l.off & kOffMask;
-            for (uint32_t x = lane; x < l.len; x += 32) {
-                const uint32_t td = a.syn_td[o + x];
-                const uint32_t k = td & kTgtMask;
-                const int sl = (t + (int)(td >> kTgtBits) + 1) % a.D;
-                const float gk = a.gring[(long long)sl * a.M + k];
-                acc = __fadd_rn(acc, __fmul_rn(__fmul_rn(a.G[a.pop[k] * a.n_pop + pj], (float)a.syn_w[o + x]), gk));
+        if (f0 < f1) {
+            const unsigned long long b0 = a.l2[f0].off & kOffMask;
+            const L2Entry last = a.l2[f1 - 1];
+            const unsigned long long b1 = (last.off & kOffMask) + last.len;
+            for (unsigned long long x0 = b0 + lane; x0 < b1; x0 += 128) {
+                uint32_t td[4];
+                int32_t w[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const unsigned long long x = x0 + 32ull * u;
+                    td[u] = x < b1 ? a.syn_td[x] : 0u;
+                    w[u] = x < b1 ? (int32_t)a.syn_w[x] : 0;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const uint32_t k = td[u] & kTgtMask;
+                    const int sl = (t + (int)(td[u] >> kTgtBits) + 1) % a.D;
+                    const float gk = a.gring[(long long)sl * a.M + k];
+                    const float gw = __fmul_rn(a.G[a.pop[k] * a.n_pop + pj], (float)w[u]);
+                    acc = __fadd_rn(acc, __fmul_rn(gw, gk));
+                }
             }
         }
 #pragma unroll
