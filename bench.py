@@ -665,6 +665,157 @@ def run_adjoint(args):
         dist.destroy_process_group()
 
 
+def _permuted(g, seed):
+    """The network g with neuron ids relabelled by a seeded permutation (new id
+    = perm[old]), so that a partitioner cannot read the planted structure
+    off contiguous id ranges."""
+    import synth
+    rng = np.random.default_rng(seed)
+    perm = rng.permutation(g.M).astype(np.int64)
+    inv = np.argsort(perm)
+    deg = np.diff(g.syn_ptr)[inv]
+    syn_ptr = np.zeros(g.M + 1, np.int64)
+    syn_ptr[1:] = np.cumsum(deg)
+    order = np.concatenate([np.arange(g.syn_ptr[i], g.syn_ptr[i + 1]) for i in inv])
+    return synth.Network(g.cfg, syn_ptr, perm[g.tgt[order].astype(np.int64)].astype(np.uint32), g.w[order],
+                         g.d[order], g.v0[inv], g.is_exc[inv]), perm
+
+
+def _route_traffic(g, part, vn_of_part, relay_of, spikes):
+    """Messages per partition of the direct route and of the two-level route
+    for spike counts `spikes` [M] (messages = one (spike, destination) pair):
+    direct: partition p(i) sends one per destination partition q != p(i);
+    two-level: p(i) sends one per destination VN g != vn(p(i)) (level 1) and
+    one per peer partition of its own VN; relay_of[g, p(i)] forwards one per
+    partition of g holding targets other than itself (level 2)."""
+    P = int(part.max()) + 1
+    src = np.repeat(np.arange(g.M, dtype=np.int64), np.diff(g.syn_ptr))
+    q = part[g.tgt.astype(np.int64)].astype(np.int64)
+    pairs = np.unique(src * P + q)                       # (neuron, destination partition) with targets
+    i, qq = pairs // P, pairs % P
+    ps = part[i].astype(np.int64)
+    w = spikes[i].astype(np.float64)
+    direct = np.bincount(ps[qq != ps], weights=w[qq != ps], minlength=P)
+    vq, vp = vn_of_part[qq], vn_of_part[ps]
+    peer = (vq == vp) & (qq != ps)
+    l1_intra = np.bincount(ps[peer], weights=w[peer], minlength=P)
+    n_vn = int(vn_of_part.max()) + 1
+    rem = vq != vp
+    iv = np.unique(i[rem] * n_vn + vq[rem])              # (neuron, destination VN) level-1 messages
+    l1_x = np.bincount(part[iv // n_vn], weights=spikes[iv // n_vn].astype(np.float64), minlength=P)
+    r = relay_of[vq[rem], ps[rem]]                        # relay partition of each remote pair
+    fwd = qq[rem] != r
+    l2 = np.bincount(r[fwd], weights=w[rem][fwd], minlength=P)
+    return direct, l1_intra + l1_x + l2, l2
+
+
+def _relay_policies(vn_of_part, relay_vn, load):
+    """Relay maps relay_of[g, p] (destination VN g, source partition p):
+    per source VN (the library's: member h mod s of g, h = vn(p)); per source
+    partition (member p mod s); load-balanced per source partition (the
+    (g, p) pairs in decreasing forwarding load go to the least-loaded member
+    of g, longest-processing-time greedy).  load[g, p] = messages."""
+    n_vn, P = load.shape
+    members = [np.nonzero(vn_of_part == gg)[0] for gg in range(n_vn)]
+    by_vn = np.array([[relay_vn[gg, vn_of_part[p_]] for p_ in range(P)] for gg in range(n_vn)])
+    by_part = np.array([[members[gg][p_ % len(members[gg])] for p_ in range(P)] for gg in range(n_vn)])
+    bal = np.zeros((n_vn, P), np.int64)
+    for gg in range(n_vn):
+        acc = np.zeros(len(members[gg]))
+        for p_ in np.argsort(-load[gg], kind="stable"):
+            k = int(np.argmin(acc))
+            bal[gg, p_] = members[gg][k]
+            acc[k] += load[gg, p_]
+    return {"per_source_vn (library)": by_vn, "per_source_partition": by_part, "load_balanced": bal}
+
+
+def run_partition_study(args):
+    """Partition quality (random vs Algorithm 1 vs planted) and relay policy
+    (per source VN vs per source partition vs load-balanced) on seeded
+    networks with relabelled ids: cut, per-partition traffic of the direct
+    and two-level routes per step and the peak (max over partitions) over
+    mean ratio, from a GPU run's spikes; for VNs of 4 and of 8 partitions."""
+    import synth
+    import paper_2205_07125_gb300 as snn
+
+    M, P, K = args.study_neurons, 16, 200
+    T = 1000
+    out = {"ids": "relabelled by a seeded permutation", "steps": T, "studies": {}}
+    for n_vn in (4, 2):
+        cfg = synth.NetConfig(name="study-%dn-%dp-%dvn-k%d" % (M, P, n_vn, K), M=M, P=P, n_vn=n_vn, K=K,
+                              uniform_all=False, n_part=140, n_vn_t=40, n_remote=20, dmax=8, seed=1005,
+                              dyn=synth.Dynamics(drive_lambda=0.8, w_ext=96, drive_seed=2005))
+        g0 = synth.make_network(cfg)
+        g, perm = _permuted(g0, 77)
+        net = snn.Network.from_synth(g)
+        src = np.repeat(np.arange(M, dtype=np.int64), np.diff(g.syn_ptr))
+        tgt = g.tgt.astype(np.int64)
+        study = {}
+        for mode in ("random", "greedy", "planted"):
+            t0 = time.time()
+            if mode == "planted":
+                part = oracle_free_planted(M, P)[np.argsort(perm)]  # the generator's partitions, new ids
+                stats = {"objective": None}
+            else:
+                part, stats = snn.snn_partition(net, P, mode, iters=4, seed=11)
+            t_part = time.time() - t0
+            part = part.astype(np.int64)
+            rt = snn.Routing(net, part, P, n_vn, "greedy", iters=4, seed=11)
+            vn, relay = rt.groups()
+            vn = vn.astype(np.int64)
+            cd, ct = rt.connections()
+            sim = snn.Sim(net, rt, snn.sim_params(cfg.dyn, raster_cap=M * T // 20, raster_steps=T),
+                          device="cuda:0")
+            sim.step(T)
+            assert sim.sync_status() == 0
+            ids, off = sim.read_raster(0, T)
+            counts = sim.read_counts()
+            sim.close()
+            spikes = np.bincount(ids.astype(np.int64), minlength=M)
+            lib = _relay_policies(vn, relay.astype(np.int64), np.zeros((n_vn, P)))["per_source_vn (library)"]
+            direct, two, _ = _route_traffic(g, part, vn, lib, spikes)
+            # forwarding load of each (destination VN, source partition)
+            pq = np.unique(src * P + part[tgt])
+            i, qq = pq // P, pq % P
+            gv, hv = vn[qq], vn[part[i]]
+            rem = gv != hv
+            load = np.zeros((n_vn, P))
+            np.add.at(load, (gv[rem], part[i][rem]), spikes[i[rem]])
+            policies = {}
+            for name, rmap in _relay_policies(vn, relay.astype(np.int64), load).items():
+                _, two_r, l2_r = _route_traffic(g, part, vn, rmap, spikes)
+                policies[name] = {"l2_forward_peak_per_step": float(l2_r.max() / T),
+                                  "l2_forward_peak_over_mean": float(l2_r.max() / max(1e-9, l2_r.mean())),
+                                  "two_level_peak_per_step": float(two_r.max() / T)}
+            study[mode] = {
+                "partition_s": t_part, "objective": stats.get("objective"),
+                "cut_fraction": float((part[src] != part[tgt]).mean()),
+                "spikes_per_step": float(spikes.sum() / T),
+                "direct_msgs_per_step": {"total": float(direct.sum() / T), "peak": float(direct.max() / T),
+                                         "peak_over_mean": float(direct.max() / max(1e-9, direct.mean()))},
+                "two_level_msgs_per_step": {"total": float(two.sum() / T), "peak": float(two.max() / T),
+                                            "peak_over_mean": float(two.max() / max(1e-9, two.mean()))},
+                "library_direct_count_matches": bool(counts["direct"] == int(round(direct.sum()))),
+                "static_connections": {"direct_mean": float(cd.mean()), "direct_max": int(cd.max()),
+                                       "two_level_mean": float(ct.mean()), "two_level_max": int(ct.max())},
+                "relay_policy": policies,
+            }
+            print("[study] n_vn %d %s: cut %.3f, direct peak/step %.1f, two-level peak/step %.1f"
+                  % (n_vn, mode, study[mode]["cut_fraction"], direct.max() / T, two.max() / T),
+                  file=sys.stderr, flush=True)
+            rt.close()
+        out["studies"][cfg.name] = study
+    print(json.dumps(out), flush=True)
+
+
+def oracle_free_planted(M, P):
+    """The generator's planted partitions: p owns ids floor(pM/P) .. floor((p+1)M/P)-1."""
+    part = np.empty(M, np.int32)
+    for p_ in range(P):
+        part[M * p_ // P:M * (p_ + 1) // P] = p_
+    return part
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -678,11 +829,14 @@ def main(argv=None):
                     help="network size with the scale workload's per-neuron statistics "
                          "(default: the 1,048,576-neuron workload)")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--config", choices=("scale", "paper", "tiny", "batch", "adjoint"), default="scale",
+    ap.add_argument("--config", choices=("scale", "paper", "tiny", "batch", "adjoint", "partition"),
+                    default="scale",
                     help="scale: 1,048,576 neurons / 64 partitions (the headline workload); "
                          "paper: the paper-shaped per-GPU share, 5,000,000 neurons / 256 partitions; "
                          "tiny: 4,096 neurons; batch: 64 independent networks of uneven sizes; "
-                         "adjoint: forward + surrogate-gradient backward of a 131,072-neuron network")
+                         "adjoint: forward + surrogate-gradient backward of a 131,072-neuron network; "
+                         "partition: partition-quality and relay-policy study (JSON report)")
+    ap.add_argument("--study-neurons", type=int, default=65536)
     ap.add_argument("--batch-nets", type=int, default=64)
     ap.add_argument("--separate-steps", type=int, default=1000,
                     help="steps per network of the one-sim-per-network comparison (--config batch)")
@@ -695,6 +849,8 @@ def main(argv=None):
         run_batch(args)
     elif args.config == "adjoint":
         run_adjoint(args)
+    elif args.config == "partition":
+        run_partition_study(args)
     else:
         run_ours(args)
 
