@@ -378,7 +378,7 @@ struct Stage {
 // warp calls).
 __device__ __forceinline__ void tally_add(const Stage &sg, int k, unsigned int v)
 {
-    v = warp_sum(v);
+    v = __reduce_add_sync(0xFFFFFFFFu, v);  // one warp reduction instruction
     if ((threadIdx.x & 31) == 0) sg.ty[threadIdx.x >> 5][k] += v;
 }
 
