@@ -198,9 +198,13 @@ def run_ours(args):
     barrier(dist)
     torch.cuda.synchronize()
     wall0 = time.time()
+    # the NVTX range lets a profiler select the timed launches alone
+    # (ncu --nvtx --nvtx-include "timed/")
+    torch.cuda.nvtx.range_push("timed")
     e0.record(stream)
     sim.step(K)
     e1.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     wall1 = time.time()
     barrier(dist)
