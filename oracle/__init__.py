@@ -69,6 +69,8 @@ def _load():
     L.or_cut.restype = i64
     L.or_partition_greedy.argtypes = [i64, vp, vp, i32, i32, u64, vp, vp]
     L.or_partition_greedy.restype = ctypes.c_int
+    L.or_partition_greedy_batched.argtypes = [i64, vp, vp, i32, i32, u64, i32, i32, vp, vp]
+    L.or_partition_greedy_batched.restype = ctypes.c_int
     L.or_group_greedy.argtypes = [i64, vp, vp, vp, i32, i32, i32, u64, vp, vp]
     L.or_group_greedy.restype = ctypes.c_int
     L.or_create.argtypes = [i64, vp, vp, vp, vp, i32, vp, i32, vp, ctypes.POINTER(OrDyn)]
@@ -156,6 +158,20 @@ def partition_greedy(net, P: int, iters: int = 4, seed: int = 7):
                                      seed, out.ctypes.data, ctypes.byref(best))
     if rc != 0:
         raise ValueError("or_partition_greedy failed: %d" % rc)
+    return out, int(best.value)
+
+
+def partition_greedy_batched(net, P: int, batch: int, grow: int = 0, iters: int = 4, seed: int = 7):
+    """Algorithm 1 with batched growth: rounds of min(batch, max(1, n_k //
+    grow)) best-gain neurons (grow = 0: batch), ranked by the round's gains,
+    n_k the part's size so far.  batch = 1 is partition_greedy.
+    Returns (part_of, objective)."""
+    out = np.empty(net.M, np.int32)
+    best = ctypes.c_int64(0)
+    rc = _load().or_partition_greedy_batched(net.M, net.syn_ptr.ctypes.data, net.tgt.ctypes.data, P,
+                                             iters, seed, batch, grow, out.ctypes.data, ctypes.byref(best))
+    if rc != 0:
+        raise ValueError("or_partition_greedy_batched failed: %d" % rc)
     return out, int(best.value)
 
 

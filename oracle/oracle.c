@@ -31,9 +31,10 @@
  *   5. an FP64 shadow membrane driven by the same integer inputs, for the
  *      FP32-vs-FP64 membrane error.
  *
- * It also holds the partitioning (Algorithm 1) and grouping (Algorithm 2)
- * readings as plain greedy loops, for the partition tests and for the
- * message counts of a greedy mapping.
+ * It also holds the partitioning (Algorithm 1, sequential and batched
+ * growth) and grouping (Algorithm 2) readings as plain greedy loops, for the
+ * partition tests, the device partitioner's parity and the message counts
+ * of a greedy mapping.
  *
  * Readings of points the paper leaves open (all are listed with the design
  * notes):
@@ -261,6 +262,118 @@ int or_partition_greedy(int64_t M, const int64_t *syn_ptr, const uint32_t *tgt, 
     }
     *best_cut = best;
     free(in_ptr); free(in_src); free(gain); free(cur);
+    return 0;
+}
+
+/*
+ * Algorithm 1 (Sec. IV.A) with batched growth, the parallel form of the
+ * greedy the paper proposes as future work (Sec. VII, parallelization of
+ * algorithms).  Seeds, stopping rule, last part, iterations and objective
+ * are those of or_partition_greedy.  The difference is in how a part grows:
+ * in each round the `need` unassigned neurons with the largest gains (ties:
+ * lowest id) are taken, ranked by the gains of that round (no update inside
+ * the round); they join the part one at a time in rank order, the stopping
+ * rule checked after each; the gains of the ones that joined are added
+ * before the next round.  need = min(B, unassigned, max(1, n_k / g)) with
+ * n_k the neurons already in the part: with g > 0 a round grows with the
+ * part (a part's first rounds, whose gains rest on few members, stay small);
+ * g = 0 drops that term.  With B = 1 this is or_partition_greedy step for
+ * step.
+ * Naive: the batch is taken by `need` argmax scans, O(M * need) per round.
+ */
+int or_partition_greedy_batched(int64_t M, const int64_t *syn_ptr, const uint32_t *tgt, int32_t P,
+                                int32_t iters, uint64_t seed, int32_t B, int32_t g, int32_t *part_of,
+                                int64_t *best_cut)
+{
+    if (M <= 0 || P <= 0 || P > M || iters < 1 || B < 1 || g < 0) return -1;
+    int64_t E = syn_ptr[M];
+    int64_t *in_ptr = calloc((size_t)M + 1, sizeof(int64_t));
+    uint32_t *in_src = malloc((size_t)(E > 0 ? E : 1) * sizeof(uint32_t));
+    int64_t *gain = malloc((size_t)M * sizeof(int64_t));
+    int32_t *cur = malloc((size_t)M * sizeof(int32_t));
+    char *picked = calloc((size_t)M, 1);
+    int64_t *batch = malloc((size_t)B * sizeof(int64_t));
+    if (!in_ptr || !in_src || !gain || !cur || !picked || !batch) return -2;
+    for (int64_t e = 0; e < E; ++e) in_ptr[tgt[e] + 1]++;
+    for (int64_t i = 0; i < M; ++i) in_ptr[i + 1] += in_ptr[i];
+    {
+        int64_t *fill = malloc((size_t)M * sizeof(int64_t));
+        memcpy(fill, in_ptr, (size_t)M * sizeof(int64_t));
+        for (int64_t i = 0; i < M; ++i)
+            for (int64_t e = syn_ptr[i]; e < syn_ptr[i + 1]; ++e) in_src[fill[tgt[e]]++] = (uint32_t)i;
+        free(fill);
+    }
+    int64_t Wtot = E;
+    int64_t best = -1;
+    for (int32_t t = 1; t <= iters; ++t) {
+        for (int64_t i = 0; i < M; ++i) cur[i] = -1;
+        int64_t n_un = M;
+        for (int32_t k = 0; k < P; ++k) {
+            if (k == P - 1) {
+                for (int64_t i = 0; i < M; ++i) if (cur[i] < 0) cur[i] = k;
+                break;
+            }
+            if (n_un == 0) break;
+            int64_t s = -1;
+            if (t == 1) {
+                for (int64_t i = 0; i < M; ++i) if (cur[i] < 0) { s = i; break; }
+            } else {
+                int64_t r = (int64_t)(philox_word(seed, (uint32_t)t, (uint32_t)k, 0xA1u) % (uint64_t)n_un);
+                for (int64_t i = 0; i < M; ++i) if (cur[i] < 0) { if (r == 0) { s = i; break; } --r; }
+            }
+            for (int64_t i = 0; i < M; ++i) gain[i] = 0;
+            /* the seed is a round of one */
+            int64_t n_b = 1;
+            batch[0] = s;
+            int64_t wk = 0, n_k = 0;
+            int stop = 0;
+            while (!stop) {
+                /* members join in rank order until the part is full */
+                int64_t joined = 0;
+                for (int64_t r = 0; r < n_b; ++r) {
+                    int64_t a = batch[r];
+                    cur[a] = k;
+                    --n_un;
+                    wk += syn_ptr[a + 1] - syn_ptr[a];
+                    ++joined;
+                    ++n_k;
+                    if (!(wk * (int64_t)P < Wtot) || n_un == 0) { stop = 1; break; }
+                }
+                if (stop) break;
+                /* gains of the members that joined: (c_aj + c_ja) W_a W_j */
+                for (int64_t r = 0; r < joined; ++r) {
+                    int64_t a = batch[r];
+                    int64_t wa = syn_ptr[a + 1] - syn_ptr[a];
+                    for (int64_t e = syn_ptr[a]; e < syn_ptr[a + 1]; ++e) {
+                        int64_t j = tgt[e];
+                        gain[j] += wa * (syn_ptr[j + 1] - syn_ptr[j]);
+                    }
+                    for (int64_t e = in_ptr[a]; e < in_ptr[a + 1]; ++e) {
+                        int64_t j = in_src[e];
+                        gain[j] += wa * (syn_ptr[j + 1] - syn_ptr[j]);
+                    }
+                }
+                /* next round: the need best unassigned neurons, in rank order */
+                int64_t need = n_un < (int64_t)B ? n_un : (int64_t)B;
+                if (g > 0 && n_k / g < need) need = n_k / g > 1 ? n_k / g : 1;
+                for (n_b = 0; n_b < need; ++n_b) {
+                    int64_t add = -1, bg = -1;
+                    for (int64_t j = 0; j < M; ++j)
+                        if (cur[j] < 0 && !picked[j] && gain[j] > bg) { bg = gain[j]; add = j; }
+                    picked[add] = 1;
+                    batch[n_b] = add;
+                }
+                for (int64_t r = 0; r < n_b; ++r) picked[batch[r]] = 0;
+            }
+        }
+        int64_t c = or_cut(M, syn_ptr, tgt, cur);
+        if (best < 0 || c < best) {
+            best = c;
+            memcpy(part_of, cur, (size_t)M * sizeof(int32_t));
+        }
+    }
+    *best_cut = best;
+    free(in_ptr); free(in_src); free(gain); free(cur); free(picked); free(batch);
     return 0;
 }
 

@@ -381,6 +381,80 @@ def test_greedy_partition_recovers_planted_structure():
     assert oracle.cut(net, rnd) > 3 * obj
 
 
+# ---------------------------------------------------- Algorithm 1, batched growth
+# Eight neurons of out-degree 2 (W = 2 each, sum 16, a part is full at weight
+# 8 = four neurons).  From seed 0, neurons 1 and 2 gain 4 each; 1 leads to 3
+# by two synapses, 3 to 4 by two.  Sequential growth (ranking after every
+# join): 0, 1, then 3 (gain 8 > 4), then 4 (8 > 4).  A round of 3 ranked on
+# the seed's gains alone: 1, 2 (gain 4 each), then 3 (gain 0, lowest id).
+_HAND_EDGES = [(0, 1), (0, 2), (1, 3), (1, 3), (2, 5), (2, 6), (3, 4), (3, 4),
+               (4, 5), (4, 6), (5, 6), (5, 7), (6, 7), (6, 5), (7, 2), (7, 5)]
+
+
+@pytest.mark.parametrize("batch,grow,part0", [
+    (1, 0, {0, 1, 3, 4}),   # the sequential greedy
+    (3, 0, {0, 1, 2, 3}),   # one round ranked on the seed's gains
+    (2, 0, {0, 1, 2, 3}),   # rounds {1, 2}, then {3, 5}: 3 fills the part
+    (3, 2, {0, 1, 3, 4}),   # rounds of max(1, n_k // 2) = 1 while the part is small
+])
+def test_batched_greedy_hand_worked(batch, grow, part0):
+    net = synth.make_edges(8, [(a, b, 1, 1) for a, b in _HAND_EDGES])
+    part, obj = oracle.partition_greedy_batched(net, 2, batch, grow, iters=1, seed=1)
+    assert set(np.flatnonzero(part == 0).tolist()) == part0
+    assert obj == oracle.cut(net, part)
+
+
+@pytest.mark.parametrize("seed", [2, 11, 12])
+def test_batched_greedy_with_rounds_of_one_is_the_greedy(seed):
+    """Rounds of one neuron are the sequential greedy, step for step (every
+    seed of the t > 1 iterations included)."""
+    cfg = synth.NetConfig(name="t", M=600, P=6, n_vn=2, K=12, uniform_all=(seed == 2), n_part=8,
+                          n_vn_t=2, n_remote=2, seed=seed)
+    net = synth.make_network(cfg)
+    ref, obj = oracle.partition_greedy(net, 5, iters=3, seed=seed)
+    for grow in (0, 3):
+        part, o = oracle.partition_greedy_batched(net, 5, 1, grow, iters=3, seed=seed)
+        assert np.array_equal(part, ref) and o == obj
+
+
+@pytest.mark.parametrize("batch,grow", [(2, 0), (5, 0), (100, 0), (100, 2)])
+def test_batched_greedy_balance_and_planted_cliques(batch, grow):
+    """Two 6-cliques joined by one synapse: every round size finds them."""
+    edges = []
+    for blk in (0, 6):
+        for i in range(6):
+            for j in range(6):
+                if i != j:
+                    edges.append((blk + i, blk + j, 1, 1))
+    edges.append((2, 9, 1, 1))
+    net = synth.make_edges(12, edges)
+    part, obj = oracle.partition_greedy_batched(net, 2, batch, grow, iters=3, seed=1)
+    assert np.bincount(part).tolist() == [6, 6]
+    assert obj == _exhaustive_best(net, 2, [6, 6])
+
+
+@pytest.mark.parametrize("batch,grow", [(7, 0), (64, 4), (1000, 0)])
+def test_batched_greedy_balance_invariant(batch, grow):
+    """Every part but the last stops at the first join that brings its weight
+    to sum(W)/P: sum(W)/P <= W(part) < sum(W)/P + max W."""
+    cfg = synth.NetConfig(name="t", M=1500, P=6, n_vn=2, K=10, uniform_all=False, n_part=6,
+                          n_vn_t=2, n_remote=2, seed=5)
+    g = synth.make_network(cfg)
+    # unequal weights: drop a seeded share of each neuron's synapses
+    rng = np.random.default_rng(1)
+    keep = rng.random(len(g.tgt)) < 0.6
+    src = np.repeat(np.arange(g.M), np.diff(g.syn_ptr))
+    net = synth.make_edges(g.M, list(zip(src[keep].tolist(), g.tgt[keep].tolist(),
+                                         [1] * int(keep.sum()), [1] * int(keep.sum()))))
+    W = np.diff(net.syn_ptr)
+    part, obj = oracle.partition_greedy_batched(net, 6, batch, grow, iters=2, seed=4)
+    wsum = np.bincount(part, weights=W, minlength=6)
+    tot = W.sum()
+    for k in range(5):
+        assert wsum[k] * 6 >= tot and (wsum[k] - W.max()) * 6 < tot
+    assert obj == oracle.cut(net, part)
+
+
 # ------------------------------------------------------------------ Algorithm 2
 def _group_cost(PG, WG, grp):
     P = len(WG)
