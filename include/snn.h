@@ -98,6 +98,50 @@ typedef struct {
 int snn_partition(const snn_network *net, int32_t n_parts, const snn_partition_params *params,
                   int32_t *part_of, snn_partition_stats *stats);
 
+/*
+ * Algorithm 1 on the GPU with batched growth (the parallel form of the
+ * greedy that the paper names as future work, Sec. VII).  Seeds, stopping
+ * rule, last part, iterations and objective are those of snn_partition's
+ * greedy; a part grows in rounds: the `need` unassigned neurons with the
+ * largest gains (ties: lowest id) are ranked on the gains at the start of
+ * the round and join the part one at a time in that order until its weight
+ * reaches sum(W)/P; the gains of the round's members are added before the
+ * next round.  need = min(batch, unassigned, max(1, n_k / grow)) with n_k the
+ * part's size so far (grow = 0 drops the last term).  batch = 1 gives the
+ * sequential greedy of snn_partition bit for bit; every batch gives the same
+ * mapping on every run (integer gains, order-free sums).
+ */
+typedef struct {
+    int32_t iters;     /* Algorithm 1 iterations T (>= 1) */
+    int32_t batch;     /* largest round, 1 .. 2048 */
+    int32_t grow;      /* round <= max(1, n_k / grow) while the part is small; 0: off */
+    int32_t reserved;
+    uint64_t seed;     /* seed of the t > 1 starting neurons (as snn_partition) */
+} snn_partition_device_params;
+
+/* Defaults: iters 4, batch 1024, grow 4, seed 7. */
+void snn_partition_device_params_default(snn_partition_device_params *p);
+/* Device workspace for a network of M neurons and E synapses: 8E + ~44M
+ * bytes (out- and in-synapse lists, per-neuron state of the growth). */
+int snn_partition_device_workspace_bytes(const snn_network *net, int32_t n_parts, size_t *bytes);
+/*
+ * workspace: caller-owned device memory of at least the bytes above,
+ * 256-byte aligned; stream: the caller's cudaStream_t (the call copies the
+ * synapse lists in, runs on the stream and synchronises it before
+ * returning).  part_of: caller-owned host [M], receives the labels of the
+ * iteration with the smallest objective (the first one on ties).  stats may
+ * be NULL.  Errors: SNN_E_ARG (bad sizes or parameters, a target id >= M),
+ * SNN_E_NOMEM (workspace too small or misaligned), SNN_E_RANGE (M >= 2^28,
+ * or the largest possible gain and the id need more than 64 key bits),
+ * SNN_E_NODEV (no cooperative launch), SNN_E_CUDA, SNN_E_TIMEOUT (a bounded
+ * grid-barrier wait ran out; part_of is not written), SNN_E_STATE (a
+ * device-side consistency check failed: a round of the wrong size or no
+ * seed; the kernel skips the access and ends; part_of is not written).
+ */
+int snn_partition_device(const snn_network *net, int32_t n_parts, const snn_partition_device_params *params,
+                         void *workspace, size_t workspace_bytes, void *stream, int32_t *part_of,
+                         snn_partition_stats *stats);
+
 /* ---------------------------------------------------------------- routing */
 #define SNN_GROUP_CONTIGUOUS 0  /* VN g = partitions g*s .. g*s+s-1, s = P/n_vn */
 #define SNN_GROUP_GREEDY     1  /* Algorithm 2 grouping (best of `iters`) */

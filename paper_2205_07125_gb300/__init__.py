@@ -7,6 +7,7 @@ PyTorch is used for device memory (the caller-owned workspace) and streams.
 
 The names follow the C ABI in include/snn.h:
     snn_partition(net, P, mode)              -> part_of        (Algorithm 1)
+    snn_partition_device(net, P, batch, grow) -> part_of       (Algorithm 1, batched growth, GPU)
     Routing(net, part_of, P, n_vn, grouping)                   (Algorithm 2 + tables)
     Sim(net, routing, params).step(T)                          (the hot path)
     Sim.read_raster / read_currents / read_counts / read_hashes / read_state
@@ -48,6 +49,10 @@ class snn_partition_params(ctypes.Structure):
 
 class snn_partition_stats(ctypes.Structure):
     _fields_ = [("objective", _i64), ("min_weight", _i64), ("max_weight", _i64)]
+
+
+class snn_partition_device_params(ctypes.Structure):
+    _fields_ = [("iters", _i32), ("batch", _i32), ("grow", _i32), ("reserved", _i32), ("seed", _u64)]
 
 
 class snn_routing_params(ctypes.Structure):
@@ -95,6 +100,10 @@ _P = ctypes.POINTER
 _lib_strerror = _sig("snn_strerror", ctypes.c_char_p, [ctypes.c_int])
 _sig("snn_partition", ctypes.c_int, [_P(snn_network), _i32, _P(snn_partition_params), _vp,
                                      _P(snn_partition_stats)])
+_sig("snn_partition_device_params_default", None, [_P(snn_partition_device_params)])
+_sig("snn_partition_device_workspace_bytes", ctypes.c_int, [_P(snn_network), _i32, _P(ctypes.c_size_t)])
+_sig("snn_partition_device", ctypes.c_int, [_P(snn_network), _i32, _P(snn_partition_device_params), _vp,
+                                            ctypes.c_size_t, _vp, _vp, _P(snn_partition_stats)])
 _sig("snn_routing_build", ctypes.c_int, [_P(snn_network), _vp, _i32, _i32, _P(snn_routing_params),
                                          _P(_vp)])
 _sig("snn_routing_info_get", ctypes.c_int, [_vp, _P(snn_routing_info)])
@@ -138,7 +147,8 @@ _sig("snn_adjoint_backward", ctypes.c_int, [_vp, _vp, _vp, _vp])
 _sig("snn_adjoint_read_spikes", ctypes.c_int, [_vp, _vp, _i64, _P(_i64)])
 _sig("snn_adjoint_destroy", None, [_vp])
 
-EXPORTS = ("snn_strerror", "snn_partition", "snn_routing_build", "snn_routing_info_get",
+EXPORTS = ("snn_strerror", "snn_partition", "snn_partition_device_params_default",
+           "snn_partition_device_workspace_bytes", "snn_partition_device", "snn_routing_build", "snn_routing_info_get",
            "snn_routing_groups", "snn_routing_connections", "snn_routing_destroy",
            "snn_sim_params_default", "snn_sim_workspace_bytes", "snn_sim_create", "snn_step",
            "snn_sync_status", "snn_read_raster", "snn_read_currents", "snn_read_hashes",
@@ -195,6 +205,33 @@ def snn_partition(net: Network, n_parts: int, mode: str = "planted", iters: int 
     st = snn_partition_stats()
     _ck(_lib.snn_partition(ctypes.byref(net.s), n_parts, ctypes.byref(prm), out.ctypes.data,
                            ctypes.byref(st)), "snn_partition")
+    return out, {"objective": st.objective, "min_weight": st.min_weight,
+                 "max_weight": st.max_weight}
+
+
+def snn_partition_device(net: Network, n_parts: int, batch: int = 1024, grow: int = 4, iters: int = 4,
+                         seed: int = 7, device=None, stream=None):
+    """Algorithm 1 with batched growth on the GPU (batch = 1: the sequential
+    greedy of snn_partition).  The workspace is a torch tensor on `device`;
+    the call returns when the labels are on the host.
+    Returns (part_of int32[M], stats dict)."""
+    import torch
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    prm = snn_partition_device_params()
+    _lib.snn_partition_device_params_default(ctypes.byref(prm))
+    prm.iters, prm.batch, prm.grow, prm.seed = iters, batch, grow, seed
+    nb = ctypes.c_size_t(0)
+    _ck(_lib.snn_partition_device_workspace_bytes(ctypes.byref(net.s), n_parts, ctypes.byref(nb)),
+        "snn_partition_device_workspace_bytes")
+    out = np.empty(net.M, np.int32)
+    st = snn_partition_stats()
+    with torch.cuda.device(dev):
+        ws = torch.empty(max(256, nb.value), dtype=torch.uint8, device=dev)
+        strm = stream if stream is not None else torch.cuda.current_stream(dev)
+        _ck(_lib.snn_partition_device(ctypes.byref(net.s), n_parts, ctypes.byref(prm), ws.data_ptr(), nb.value,
+                                      strm.cuda_stream, out.ctypes.data, ctypes.byref(st)),
+            "snn_partition_device")
+        del ws
     return out, {"objective": st.objective, "min_weight": st.min_weight,
                  "max_weight": st.max_weight}
 

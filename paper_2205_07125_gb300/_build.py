@@ -17,6 +17,7 @@ SOURCES = {
     "snn_host.o": ["snn_host.cpp"],
     "snn_sim.o": ["snn_sim.cu"],
     "snn_adjoint.o": ["snn_adjoint.cu"],
+    "snn_part.o": ["snn_part.cu"],
 }
 
 

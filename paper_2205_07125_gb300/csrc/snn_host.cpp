@@ -59,6 +59,12 @@ static uint32_t philox_w0(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2)
     return x0;
 }
 
+// The same word for the device partitioner's seeds (snn_part.cu).
+uint32_t philox_word0(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2)
+{
+    return philox_w0(seed, c0, c1, c2);
+}
+
 static int check_network(const snn_network *net)
 {
     if (!net || net->n_neurons <= 0 || !net->syn_ptr || !net->v0) return SNN_E_ARG;
