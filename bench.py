@@ -812,6 +812,101 @@ def run_partition_study(args):
     print(json.dumps(out), flush=True)
 
 
+def _objective(g, part, chunk=1 << 24):
+    """Algorithm 1's objective: sum over synapses i -> j with part(i) !=
+    part(j) of W_i W_j, W = out-degree (numpy, in chunks of synapses)."""
+    W = np.diff(g.syn_ptr).astype(np.int64)
+    part = np.asarray(part, np.int64)
+    tot = 0
+    for i0 in range(0, g.M, max(1, chunk // max(1, int(W.max(initial=1))))):
+        i1 = min(g.M, i0 + max(1, chunk // max(1, int(W.max(initial=1)))))
+        src = np.repeat(np.arange(i0, i1, dtype=np.int64), W[i0:i1])
+        tgt = g.tgt[g.syn_ptr[i0]:g.syn_ptr[i1]].astype(np.int64)
+        cut = part[src] != part[tgt]
+        tot += int((W[src[cut]] * W[tgt[cut]]).sum())
+    return tot
+
+
+def run_partition_device(args):
+    """Algorithm 1 on the GPU (batched growth, one cooperative launch per
+    iteration) against the library's host greedy: wall time of the call
+    (synapse lists to the device, in-lists, 4 iterations, labels back),
+    objective and balance.  Rounds of one reproduce the host mapping bit for
+    bit; the batched rounds are compared by objective with the planted
+    partitions the generator used."""
+    import torch
+    import synth
+    import paper_2205_07125_gb300 as snn
+
+    torch.cuda.set_device(0)
+    out = {"what": "Algorithm 1 partition time, s (lower is better); objective = sum over cut synapses of "
+                   "W_i W_j", "networks": {}}
+    # context and module load outside the timings
+    tiny = synth.make_edges(64, [(i, (i + 1) % 64, 1, 1) for i in range(64)])
+    snn.snn_partition_device(snn.Network.from_synth(tiny), 2, device="cuda:0")
+
+    def device_run(net, P, batch, grow, iters):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        part, st = snn.snn_partition_device(net, P, batch=batch, grow=grow, iters=iters, seed=11,
+                                            device="cuda:0")
+        return part, st, time.perf_counter() - t0
+
+    # the study network (65,536 neurons, 16 planted partitions, ids relabelled)
+    M, P, K = args.study_neurons, 16, 200
+    cfg = synth.NetConfig(name="study-%dn-%dp-k%d" % (M, P, K), M=M, P=P, n_vn=4, K=K, uniform_all=False,
+                          n_part=140, n_vn_t=40, n_remote=20, dmax=8, seed=1005)
+    g, perm = _permuted(synth.make_network(cfg), 77)
+    net = snn.Network.from_synth(g)
+    planted = oracle_free_planted(M, P)[np.argsort(perm)]
+    res = {"neurons": M, "partitions": P, "synapses": int(g.syn_ptr[-1]), "ids": "relabelled",
+           "planted_objective": _objective(g, planted)}
+    t0 = time.perf_counter()
+    part_h, st_h = snn.snn_partition(net, P, "greedy", iters=4, seed=11)
+    res["host_greedy"] = {"s": time.perf_counter() - t0, "objective": st_h["objective"], "iters": 4,
+                          "threads": 1}
+    for batch, grow in ((1, 0), (64, 4), (1024, 4), (2048, 2)):
+        part, st, sec = device_run(net, P, batch, grow, 4)
+        r = {"s": sec, "objective": st["objective"], "max_over_min_weight": st["max_weight"] / max(1, st["min_weight"]),
+             "speedup_vs_host": res["host_greedy"]["s"] / sec}
+        if batch == 1:
+            r["equals_host_mapping"] = bool(np.array_equal(part, part_h))
+        res["device_batch%d_grow%d" % (batch, grow)] = r
+        print("[partition] %s batch %d grow %d: %.3f s, objective %d (host %.3f s, %d; planted %d)"
+              % (cfg.name, batch, grow, sec, st["objective"], res["host_greedy"]["s"], st_h["objective"],
+                 res["planted_objective"]), file=sys.stderr, flush=True)
+    out["networks"][cfg.name] = res
+
+    if args.no_scale:
+        print(json.dumps(out), flush=True)
+        return
+    # the scale workload (1,048,576 neurons, 64 planted partitions, 1.05e9 synapses)
+    cfg = workload(0, 0, "scale")
+    g = synth.make_network(cfg)
+    net = snn.Network.from_synth(g)
+    res = {"neurons": cfg.M, "partitions": cfg.P, "synapses": int(g.syn_ptr[-1]), "ids": "generator order",
+           "planted_objective": _objective(g, oracle_free_planted(cfg.M, cfg.P))}
+    for batch, grow, iters in ((2048, 2, 1), (2048, 2, 4), (1024, 4, 4)):
+        part, st, sec = device_run(net, cfg.P, batch, grow, iters)
+        res["device_batch%d_grow%d_iters%d" % (batch, grow, iters)] = {
+            "s": sec, "objective": st["objective"],
+            "objective_over_planted": st["objective"] / max(1, res["planted_objective"]),
+            "max_over_min_weight": st["max_weight"] / max(1, st["min_weight"])}
+        print("[partition] %s batch %d grow %d iters %d: %.3f s, objective / planted %.4f"
+              % (cfg.name, batch, grow, iters, sec, st["objective"] / max(1, res["planted_objective"])),
+              file=sys.stderr, flush=True)
+    if args.host_scale_iters > 0:
+        t0 = time.perf_counter()
+        _, st_h = snn.snn_partition(net, cfg.P, "greedy", iters=args.host_scale_iters, seed=11)
+        res["host_greedy_iters%d" % args.host_scale_iters] = {
+            "s": time.perf_counter() - t0, "objective": st_h["objective"], "threads": 1}
+        print("[partition] %s host greedy iters %d: %.1f s" % (cfg.name, args.host_scale_iters,
+                                                               time.perf_counter() - t0),
+              file=sys.stderr, flush=True)
+    out["networks"][cfg.name] = res
+    print(json.dumps(out), flush=True)
+
+
 def oracle_free_planted(M, P):
     """The generator's planted partitions: p owns ids floor(pM/P) .. floor((p+1)M/P)-1."""
     part = np.empty(M, np.int32)
@@ -833,14 +928,20 @@ def main(argv=None):
                     help="network size with the scale workload's per-neuron statistics "
                          "(default: the 1,048,576-neuron workload)")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--config", choices=("scale", "paper", "tiny", "batch", "adjoint", "partition"),
+    ap.add_argument("--config", choices=("scale", "paper", "tiny", "batch", "adjoint", "partition",
+                                         "partition-device"),
                     default="scale",
                     help="scale: 1,048,576 neurons / 64 partitions (the headline workload); "
                          "paper: the paper-shaped per-GPU share, 5,000,000 neurons / 256 partitions; "
                          "tiny: 4,096 neurons; batch: 64 independent networks of uneven sizes; "
                          "adjoint: forward + surrogate-gradient backward of a 131,072-neuron network; "
-                         "partition: partition-quality and relay-policy study (JSON report)")
+                         "partition: partition-quality and relay-policy study (JSON report); "
+                         "partition-device: Algorithm 1 on the GPU vs the host greedy (JSON report)")
     ap.add_argument("--study-neurons", type=int, default=65536)
+    ap.add_argument("--no-scale", action="store_true",
+                    help="--config partition-device: the study network only")
+    ap.add_argument("--host-scale-iters", type=int, default=1,
+                    help="host greedy iterations on the scale workload (--config partition-device; 0: skip)")
     ap.add_argument("--batch-nets", type=int, default=64)
     ap.add_argument("--separate-steps", type=int, default=1000,
                     help="steps per network of the one-sim-per-network comparison (--config batch)")
@@ -855,6 +956,8 @@ def main(argv=None):
         run_adjoint(args)
     elif args.config == "partition":
         run_partition_study(args)
+    elif args.config == "partition-device":
+        run_partition_device(args)
     else:
         run_ours(args)
 

@@ -119,7 +119,7 @@ typedef struct {
     uint64_t seed;     /* seed of the t > 1 starting neurons (as snn_partition) */
 } snn_partition_device_params;
 
-/* Defaults: iters 4, batch 1024, grow 4, seed 7. */
+/* Defaults: iters 4, batch 2048, grow 2, seed 7. */
 void snn_partition_device_params_default(snn_partition_device_params *p);
 /* Device workspace for a network of M neurons and E synapses: 8E + ~44M
  * bytes (out- and in-synapse lists, per-neuron state of the growth). */

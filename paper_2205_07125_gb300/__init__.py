@@ -209,7 +209,7 @@ def snn_partition(net: Network, n_parts: int, mode: str = "planted", iters: int 
                  "max_weight": st.max_weight}
 
 
-def snn_partition_device(net: Network, n_parts: int, batch: int = 1024, grow: int = 4, iters: int = 4,
+def snn_partition_device(net: Network, n_parts: int, batch: int = 2048, grow: int = 2, iters: int = 4,
                          seed: int = 7, device=None, stream=None):
     """Algorithm 1 with batched growth on the GPU (batch = 1: the sequential
     greedy of snn_partition).  The workspace is a torch tensor on `device`;

@@ -627,8 +627,8 @@ extern "C" void snn_partition_device_params_default(snn_partition_device_params 
     if (!p) return;
     std::memset(p, 0, sizeof(*p));
     p->iters = 4;
-    p->batch = 1024;
-    p->grow = 4;
+    p->batch = 2048;
+    p->grow = 2;
     p->seed = 7;
 }
 
@@ -662,7 +662,9 @@ extern "C" int snn_partition_device(const snn_network *net, int32_t P, const snn
     if (!coop) return SNN_E_NODEV;
     PCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_part_grow, kPT, 0));
     if (occ < 1) return SNN_E_NODEV;
-    const int grid = std::min(kMaxGrid, sms * std::min(occ, 4));
+    // two blocks per SM: the rounds' barriers cost more with more blocks,
+    // the scatter of a large round wants more than one per SM
+    const int grid = std::min(kMaxGrid, sms * std::min(occ, 2));
 
     PDev d;
     std::memset(&d, 0, sizeof(d));
