@@ -199,6 +199,40 @@ int snn_routing_info_get(const snn_routing *rt, snn_routing_info *out);
 int snn_routing_groups(const snn_routing *rt, int32_t *vn_of_part, int32_t *relay);
 /* Per-partition static connection counts (caller-owned [n_parts] each). */
 int snn_routing_connections(const snn_routing *rt, int32_t *direct, int32_t *two_level);
+/*
+ * Copy one of the routing's tables (host memory, internal order) into the
+ * caller's buffer `out` of `cap` bytes; *bytes receives the table's size.
+ * With out == NULL only the size is returned.  Names and element types:
+ * "syn_td" u32 [E] (internal target | (delay-1) << 28), "syn_w" i16 [E],
+ * "csr" i64 [M+1], "l1_ptr" u32 [M+1], "l1_vn" u16 [n_l1], "l1_l2" u32
+ * [n_l1+1], "l2" 16-byte entries [n_l2] {u64 offset | delay-1 count << 40,
+ * u32 length, u16 partition, u8 class, u8 0}, "l1_pair" u32 [n_l1],
+ * "l2_pair" u32 [n_l2], "bpair_ptr" / "ipair_ptr" u32 [P+1], "bpair_dst" /
+ * "ipair_dst" u16, "bpair_cap" / "ipair_cap" u32, "bucket_cap" u64 [n_vn],
+ * "inbox_cap" u64 [P], "perm_inv" / "perm_fwd" u32 [M], "src_part" u16 [M],
+ * "pbase" i64 [P+1], "v0" f32 [M], "vn_of_part" / "relay" i32.
+ * Errors: SNN_E_ARG (unknown name), SNN_E_NOMEM (cap too small).
+ */
+int snn_routing_export(const snn_routing *rt, const char *name, void *out, size_t cap, size_t *bytes);
+
+/*
+ * The same routing built on the GPU (the table building of the parallel
+ * design the paper names as future work, Sec. VII): the synapse scans
+ * (inter-partition counts, per-neuron segment and VN counts, exchange-pair
+ * worst cases) and the per-neuron sort of the synapses by (destination
+ * partition, delay, target, weight) with the level-1 / level-2 entries run
+ * on the device; grouping (Algorithm 2), orders and pair numbering on the
+ * host.  The tables equal snn_routing_build's byte for byte.  The result is
+ * an ordinary routing (host tables, copied back chunk by chunk).
+ * workspace: caller-owned device memory of snn_routing_build_device_
+ * workspace_bytes, 256-byte aligned; stream: the caller's cudaStream_t (the
+ * call synchronises it).  Limits beyond snn_routing_build's: out-degree <=
+ * 16384.  Errors: as snn_routing_build, plus SNN_E_NOMEM (workspace), SNN_E_CUDA.
+ */
+int snn_routing_build_device_workspace_bytes(const snn_network *net, int32_t n_parts, int32_t n_vn, size_t *bytes);
+int snn_routing_build_device(const snn_network *net, const int32_t *part_of, int32_t n_parts, int32_t n_vn,
+                             const snn_routing_params *params, void *workspace, size_t workspace_bytes,
+                             void *stream, snn_routing **out);
 void snn_routing_destroy(snn_routing *rt);
 
 /* ------------------------------------------------------------- simulation */

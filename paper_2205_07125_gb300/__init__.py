@@ -9,6 +9,7 @@ The names follow the C ABI in include/snn.h:
     snn_partition(net, P, mode)              -> part_of        (Algorithm 1)
     snn_partition_device(net, P, batch, grow) -> part_of       (Algorithm 1, batched growth, GPU)
     Routing(net, part_of, P, n_vn, grouping)                   (Algorithm 2 + tables)
+    Routing(..., build="device")                               (the same tables built on the GPU)
     Sim(net, routing, params).step(T)                          (the hot path)
     Sim.read_raster / read_currents / read_counts / read_hashes / read_state
 This module raises ImportError when libsnn.so has not been built; there is
@@ -107,6 +108,10 @@ _sig("snn_partition_device", ctypes.c_int, [_P(snn_network), _i32, _P(snn_partit
 _sig("snn_routing_build", ctypes.c_int, [_P(snn_network), _vp, _i32, _i32, _P(snn_routing_params),
                                          _P(_vp)])
 _sig("snn_routing_info_get", ctypes.c_int, [_vp, _P(snn_routing_info)])
+_sig("snn_routing_export", ctypes.c_int, [_vp, ctypes.c_char_p, _vp, ctypes.c_size_t, _P(ctypes.c_size_t)])
+_sig("snn_routing_build_device_workspace_bytes", ctypes.c_int, [_P(snn_network), _i32, _i32, _P(ctypes.c_size_t)])
+_sig("snn_routing_build_device", ctypes.c_int, [_P(snn_network), _vp, _i32, _i32, _P(snn_routing_params), _vp,
+                                                ctypes.c_size_t, _vp, _P(_vp)])
 _sig("snn_routing_groups", ctypes.c_int, [_vp, _vp, _vp])
 _sig("snn_routing_connections", ctypes.c_int, [_vp, _vp, _vp])
 _sig("snn_routing_destroy", None, [_vp])
@@ -148,7 +153,8 @@ _sig("snn_adjoint_read_spikes", ctypes.c_int, [_vp, _vp, _i64, _P(_i64)])
 _sig("snn_adjoint_destroy", None, [_vp])
 
 EXPORTS = ("snn_strerror", "snn_partition", "snn_partition_device_params_default",
-           "snn_partition_device_workspace_bytes", "snn_partition_device", "snn_routing_build", "snn_routing_info_get",
+           "snn_partition_device_workspace_bytes", "snn_partition_device", "snn_routing_build",
+           "snn_routing_export", "snn_routing_build_device_workspace_bytes", "snn_routing_build_device", "snn_routing_info_get",
            "snn_routing_groups", "snn_routing_connections", "snn_routing_destroy",
            "snn_sim_params_default", "snn_sim_workspace_bytes", "snn_sim_create", "snn_step",
            "snn_sync_status", "snn_read_raster", "snn_read_currents", "snn_read_hashes",
@@ -236,20 +242,55 @@ def snn_partition_device(net: Network, n_parts: int, batch: int = 2048, grow: in
                  "max_weight": st.max_weight}
 
 
+_TABLE_TYPES = {"syn_td": np.uint32, "syn_w": np.int16, "csr": np.int64, "l1_ptr": np.uint32, "l1_vn": np.uint16,
+                "l1_l2": np.uint32, "l2": np.uint8, "l1_pair": np.uint32, "l2_pair": np.uint32,
+                "bpair_ptr": np.uint32, "bpair_dst": np.uint16, "bpair_cap": np.uint32, "ipair_ptr": np.uint32,
+                "ipair_dst": np.uint16, "ipair_cap": np.uint32, "bucket_cap": np.uint64, "inbox_cap": np.uint64,
+                "perm_inv": np.uint32, "perm_fwd": np.uint32, "src_part": np.uint16, "pbase": np.int64,
+                "v0": np.float32, "vn_of_part": np.int32, "relay": np.int32}
+
+
 class Routing:
-    """Algorithm 2 grouping and the two-level routing tables (host memory)."""
+    """Algorithm 2 grouping and the two-level routing tables (host memory).
+    build="device" builds the same tables on the GPU (snn_routing_build_device;
+    the workspace is a torch tensor on `device`)."""
 
     def __init__(self, net: Network, part_of, n_parts: int, n_vn: int, grouping: str = "contiguous",
-                 iters: int = 4, seed: int = 7, n_threads: int = 0):
+                 iters: int = 4, seed: int = 7, n_threads: int = 0, build: str = "host", device=None):
         self.net = net
         self.part_of = np.ascontiguousarray(part_of, np.int32)
         g = {"contiguous": SNN_GROUP_CONTIGUOUS, "greedy": SNN_GROUP_GREEDY}[grouping]
         prm = snn_routing_params(g, iters, seed, n_threads, 0)
         h = _vp()
-        _ck(_lib.snn_routing_build(ctypes.byref(net.s), self.part_of.ctypes.data, n_parts, n_vn,
-                                   ctypes.byref(prm), ctypes.byref(h)), "snn_routing_build")
+        if build == "host":
+            _ck(_lib.snn_routing_build(ctypes.byref(net.s), self.part_of.ctypes.data, n_parts, n_vn,
+                                       ctypes.byref(prm), ctypes.byref(h)), "snn_routing_build")
+        elif build == "device":
+            import torch
+            dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+            nb = ctypes.c_size_t(0)
+            _ck(_lib.snn_routing_build_device_workspace_bytes(ctypes.byref(net.s), n_parts, n_vn, ctypes.byref(nb)),
+                "snn_routing_build_device_workspace_bytes")
+            with torch.cuda.device(dev):
+                ws = torch.empty(max(256, nb.value), dtype=torch.uint8, device=dev)
+                strm = torch.cuda.current_stream(dev)
+                _ck(_lib.snn_routing_build_device(ctypes.byref(net.s), self.part_of.ctypes.data, n_parts, n_vn,
+                                                  ctypes.byref(prm), ws.data_ptr(), nb.value, strm.cuda_stream,
+                                                  ctypes.byref(h)), "snn_routing_build_device")
+                del ws
+        else:
+            raise ValueError("build must be 'host' or 'device'")
         self.h = h.value
         self.P, self.n_vn = n_parts, n_vn
+
+    def export(self, name: str) -> np.ndarray:
+        """A copy of one routing table (snn_routing_export), as a numpy array."""
+        nb = ctypes.c_size_t(0)
+        _ck(_lib.snn_routing_export(self.h, name.encode(), None, 0, ctypes.byref(nb)), "snn_routing_export")
+        out = np.empty(nb.value, np.uint8)
+        _ck(_lib.snn_routing_export(self.h, name.encode(), out.ctypes.data, nb.value, ctypes.byref(nb)),
+            "snn_routing_export")
+        return out.view(_TABLE_TYPES[name])
 
     def info(self) -> dict:
         i = snn_routing_info()

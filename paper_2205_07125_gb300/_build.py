@@ -18,6 +18,7 @@ SOURCES = {
     "snn_sim.o": ["snn_sim.cu"],
     "snn_adjoint.o": ["snn_adjoint.cu"],
     "snn_part.o": ["snn_part.cu"],
+    "snn_route_dev.o": ["snn_route_dev.cu"],
 }
 
 

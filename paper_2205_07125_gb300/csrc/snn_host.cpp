@@ -9,6 +9,7 @@
 #include <mutex>
 #include <new>
 #include <queue>
+#include <string>
 
 #include "snn_internal.h"
 
@@ -336,6 +337,115 @@ static void group_greedy(int32_t P, int32_t n_vn, int32_t iters, uint64_t seed,
 
 }  // namespace
 
+namespace snn {
+
+void route_groups(snn_routing *rt, const snn_routing_params *prm, const std::vector<int64_t> &PG,
+                  const std::vector<int64_t> &WG)
+{
+    const int32_t P = rt->P, n_vn = rt->n_vn, s = rt->vn_size;
+    rt->vn_of_part.assign((size_t)P, 0);
+    if (prm->grouping == SNN_GROUP_CONTIGUOUS) {
+        for (int32_t p = 0; p < P; ++p) rt->vn_of_part[p] = p / s;
+        u128 c = 0;
+        for (int32_t p = 0; p < P; ++p)
+            for (int32_t q = 0; q < P; ++q)
+                if (p / s != q / s) c += (u128)PG[(size_t)p * P + q] * (u128)WG[p] * (u128)WG[q];
+        rt->group_cost = c;
+    } else {
+        group_greedy(P, n_vn, prm->iters, prm->seed, PG, WG, rt->vn_of_part, rt->group_cost);
+    }
+}
+
+void route_order(snn_routing *rt, const snn_network *net, const int32_t *part_of, const std::vector<int64_t> &sizes)
+{
+    const int32_t P = rt->P, n_vn = rt->n_vn, s = rt->vn_size;
+    const int64_t M = rt->M;
+    // internal partition order: by (VN, label)
+    rt->part_of_ip.resize((size_t)P);
+    rt->ip_of_part.resize((size_t)P);
+    {
+        std::vector<int32_t> fill((size_t)n_vn, 0);
+        for (int32_t p = 0; p < P; ++p) {
+            int32_t g = rt->vn_of_part[p];
+            int32_t ip = g * s + fill[g]++;
+            rt->ip_of_part[p] = ip;
+            rt->part_of_ip[ip] = p;
+        }
+    }
+    // relay of VN g for source VN h: (h mod s)-th member of g in label order,
+    // which is internal partition g*s + h % s
+    rt->relay.resize((size_t)n_vn * n_vn);
+    for (int32_t g = 0; g < n_vn; ++g)
+        for (int32_t h = 0; h < n_vn; ++h) rt->relay[(size_t)g * n_vn + h] = rt->part_of_ip[g * s + h % s];
+    // internal neuron order: partition-major, ascending global id
+    rt->pbase.assign((size_t)P + 1, 0);
+    for (int32_t p = 0; p < P; ++p) rt->pbase[rt->ip_of_part[p] + 1] = sizes[p];
+    for (int32_t ip = 0; ip < P; ++ip) rt->pbase[ip + 1] += rt->pbase[ip];
+    rt->perm_inv.resize((size_t)M);
+    rt->perm_fwd.resize((size_t)M);
+    {
+        std::vector<int64_t> fill(rt->pbase.begin(), rt->pbase.end() - 1);
+        for (int64_t i = 0; i < M; ++i) {
+            int64_t k = fill[rt->ip_of_part[part_of[i]]]++;
+            rt->perm_inv[k] = (uint32_t)i;
+            rt->perm_fwd[i] = (uint32_t)k;
+        }
+    }
+    rt->identity = true;
+    for (int64_t i = 0; i < M; ++i)
+        if (rt->perm_fwd[i] != (uint32_t)i) { rt->identity = false; break; }
+    rt->v0.resize((size_t)M);
+    for (int64_t k = 0; k < M; ++k) rt->v0[k] = net->v0[rt->perm_inv[k]];
+    rt->src_part.resize((size_t)M);
+    for (int32_t ip = 0; ip < P; ++ip)
+        for (int64_t k = rt->pbase[ip]; k < rt->pbase[ip + 1]; ++k) rt->src_part[k] = (uint16_t)ip;
+}
+
+void route_connections(snn_routing *rt, const std::vector<uint8_t> &conn)
+{
+    const int32_t P = rt->P, n_vn = rt->n_vn, s = rt->vn_size;
+    // static connections per partition (label order)
+    rt->conn_direct.assign((size_t)P, 0);
+    rt->conn_two.assign((size_t)P, 0);
+    for (int32_t p = 0; p < P; ++p) {
+        int32_t ip = rt->ip_of_part[p], h = ip / s;
+        std::vector<uint8_t> gr((size_t)n_vn, 0);
+        for (int32_t q = 0; q < P; ++q) {
+            if (q == ip || !conn[(size_t)ip * P + q]) continue;
+            rt->conn_direct[p]++;
+            if (q / s == h) rt->conn_two[p]++;
+            else gr[q / s] = 1;
+        }
+        for (int32_t g = 0; g < n_vn; ++g) rt->conn_two[p] += gr[g];
+    }
+}
+
+void route_number_pairs(snn_routing *rt, std::vector<uint32_t> &bc, std::vector<uint32_t> &ic)
+{
+    const int32_t P = rt->P;
+    // number the pairs; the dense tables then hold each pair's id
+    auto number = [P](std::vector<uint32_t> &dense, int32_t n_dst, std::vector<uint32_t> &ptr,
+                      std::vector<uint16_t> &dst, std::vector<uint32_t> &cap) {
+        ptr.assign((size_t)P + 1, 0);
+        dst.clear();
+        cap.clear();
+        for (int32_t ip = 0; ip < P; ++ip) {
+            for (int32_t x = 0; x < n_dst; ++x) {
+                uint32_t &v = dense[(size_t)ip * n_dst + x];
+                if (!v) continue;
+                dst.push_back((uint16_t)x);
+                cap.push_back(v);
+                v = (uint32_t)(cap.size() - 1);
+            }
+            ptr[ip + 1] = (uint32_t)cap.size();
+        }
+    };
+    number(bc, rt->n_vn, rt->bpair_ptr, rt->bpair_dst, rt->bpair_cap);
+    number(ic, P, rt->ipair_ptr, rt->ipair_dst, rt->ipair_cap);
+}
+
+}  // namespace snn
+
 extern "C" int snn_routing_build(const snn_network *net, const int32_t *part_of, int32_t P,
                                  int32_t n_vn, const snn_routing_params *prm, snn_routing **out)
 {
@@ -402,55 +512,9 @@ extern "C" int snn_routing_build(const snn_network *net, const int32_t *part_of,
         pg_t.clear();
         for (int64_t i = 0; i < M; ++i) WG[part_of[i]] += sp[i + 1] - sp[i];
 
-        // ---- Algorithm 2: groups
-        rt->vn_of_part.assign((size_t)P, 0);
-        if (prm->grouping == SNN_GROUP_CONTIGUOUS) {
-            for (int32_t p = 0; p < P; ++p) rt->vn_of_part[p] = p / s;
-            u128 c = 0;
-            for (int32_t p = 0; p < P; ++p)
-                for (int32_t q = 0; q < P; ++q)
-                    if (p / s != q / s) c += (u128)PG[(size_t)p * P + q] * (u128)WG[p] * (u128)WG[q];
-            rt->group_cost = c;
-        } else {
-            group_greedy(P, n_vn, prm->iters, prm->seed, PG, WG, rt->vn_of_part, rt->group_cost);
-        }
-        // internal partition order: by (VN, label)
-        rt->part_of_ip.resize((size_t)P);
-        rt->ip_of_part.resize((size_t)P);
-        {
-            std::vector<int32_t> fill((size_t)n_vn, 0);
-            for (int32_t p = 0; p < P; ++p) {
-                int32_t g = rt->vn_of_part[p];
-                int32_t ip = g * s + fill[g]++;
-                rt->ip_of_part[p] = ip;
-                rt->part_of_ip[ip] = p;
-            }
-        }
-        // relay of VN g for source VN h: (h mod s)-th member of g in label order,
-        // which is internal partition g*s + h % s
-        rt->relay.resize((size_t)n_vn * n_vn);
-        for (int32_t g = 0; g < n_vn; ++g)
-            for (int32_t h = 0; h < n_vn; ++h) rt->relay[(size_t)g * n_vn + h] = rt->part_of_ip[g * s + h % s];
-
-        // ---- internal neuron order: partition-major, ascending global id
-        rt->pbase.assign((size_t)P + 1, 0);
-        for (int32_t p = 0; p < P; ++p) rt->pbase[rt->ip_of_part[p] + 1] = sizes[p];
-        for (int32_t ip = 0; ip < P; ++ip) rt->pbase[ip + 1] += rt->pbase[ip];
-        rt->perm_inv.resize((size_t)M);
-        rt->perm_fwd.resize((size_t)M);
-        {
-            std::vector<int64_t> fill(rt->pbase.begin(), rt->pbase.end() - 1);
-            for (int64_t i = 0; i < M; ++i) {
-                int64_t k = fill[rt->ip_of_part[part_of[i]]]++;
-                rt->perm_inv[k] = (uint32_t)i;
-                rt->perm_fwd[i] = (uint32_t)k;
-            }
-        }
-        rt->identity = true;
-        for (int64_t i = 0; i < M; ++i)
-            if (rt->perm_fwd[i] != (uint32_t)i) { rt->identity = false; break; }
-        rt->v0.resize((size_t)M);
-        for (int64_t k = 0; k < M; ++k) rt->v0[k] = net->v0[rt->perm_inv[k]];
+        // ---- Algorithm 2: groups; internal order
+        route_groups(rt, prm, PG, WG);
+        route_order(rt, net, part_of, sizes);
 
         // ---- pass 1: per internal neuron, segment and VN counts
         std::vector<int64_t> csr((size_t)M + 1, 0), l2p((size_t)M + 1, 0);
@@ -503,9 +567,6 @@ extern "C" int snn_routing_build(const snn_network *net, const int32_t *part_of,
         if (n_l2 >= ((int64_t)1 << 32)) { delete rt; return SNN_E_RANGE; }
         rt->n_l1 = n_l1;
         rt->n_l2 = n_l2;
-        rt->src_part.resize((size_t)M);
-        for (int32_t ip = 0; ip < P; ++ip)
-            for (int64_t k = rt->pbase[ip]; k < rt->pbase[ip + 1]; ++k) rt->src_part[k] = (uint16_t)ip;
         rt->bucket_cap.assign((size_t)n_vn, 0);
         rt->inbox_cap.assign((size_t)P, 0);
         std::vector<uint8_t> conn((size_t)P * P, 0);
@@ -519,20 +580,7 @@ extern "C" int snn_routing_build(const snn_network *net, const int32_t *part_of,
         icap_t.clear();
         conn_t.clear();
 
-        // ---- static connections per partition (label order)
-        rt->conn_direct.assign((size_t)P, 0);
-        rt->conn_two.assign((size_t)P, 0);
-        for (int32_t p = 0; p < P; ++p) {
-            int32_t ip = rt->ip_of_part[p], h = ip / s;
-            std::vector<uint8_t> gr((size_t)n_vn, 0);
-            for (int32_t q = 0; q < P; ++q) {
-                if (q == ip || !conn[(size_t)ip * P + q]) continue;
-                rt->conn_direct[p]++;
-                if (q / s == h) rt->conn_two[p]++;
-                else gr[q / s] = 1;
-            }
-            for (int32_t g = 0; g < n_vn; ++g) rt->conn_two[p] += gr[g];
-        }
+        route_connections(rt, conn);
 
         // ---- pass 2: fill the CSR and the level-1 / level-2 tables
         rt->syn_td.alloc(E);
@@ -619,23 +667,7 @@ extern "C" int snn_routing_build(const snn_network *net, const int32_t *part_of,
                 }
             }
         });
-        // number the pairs; the dense tables then hold each pair's id
-        auto number = [P](std::vector<uint32_t> &dense, int32_t n_dst, std::vector<uint32_t> &ptr,
-                          std::vector<uint16_t> &dst, std::vector<uint32_t> &cap) {
-            ptr.assign((size_t)P + 1, 0);
-            for (int32_t ip = 0; ip < P; ++ip) {
-                for (int32_t x = 0; x < n_dst; ++x) {
-                    uint32_t &v = dense[(size_t)ip * n_dst + x];
-                    if (!v) continue;
-                    dst.push_back((uint16_t)x);
-                    cap.push_back(v);
-                    v = (uint32_t)(cap.size() - 1);
-                }
-                ptr[ip + 1] = (uint32_t)cap.size();
-            }
-        };
-        number(bc, n_vn, rt->bpair_ptr, rt->bpair_dst, rt->bpair_cap);
-        number(ic, P, rt->ipair_ptr, rt->ipair_dst, rt->ipair_cap);
+        route_number_pairs(rt, bc, ic);
         rt->l1_pair.alloc(n_l1);
         rt->l2_pair.alloc(n_l2);
         parallel_for(P, nt, [&](int64_t plo, int64_t phi, int) {
@@ -692,6 +724,48 @@ extern "C" int snn_routing_connections(const snn_routing *rt, int32_t *direct, i
     if (!rt) return SNN_E_ARG;
     if (direct) std::memcpy(direct, rt->conn_direct.data(), sizeof(int32_t) * (size_t)rt->P);
     if (two_level) std::memcpy(two_level, rt->conn_two.data(), sizeof(int32_t) * (size_t)rt->P);
+    return SNN_OK;
+}
+
+extern "C" int snn_routing_export(const snn_routing *rt, const char *name, void *out, size_t cap, size_t *bytes)
+{
+    if (!rt || !name) return SNN_E_ARG;
+    const void *src = nullptr;
+    size_t n = 0;
+    auto take = [&](const void *p, size_t b) {
+        src = p;
+        n = b;
+    };
+    const std::string k(name);
+    if (k == "syn_td") take(rt->syn_td.data(), 4 * (size_t)rt->E);
+    else if (k == "syn_w") take(rt->syn_w.data(), 2 * (size_t)rt->E);
+    else if (k == "csr") take(rt->csr.data(), 8 * rt->csr.size());
+    else if (k == "l1_ptr") take(rt->l1_ptr.data(), 4 * (size_t)(rt->M + 1));
+    else if (k == "l1_vn") take(rt->l1_vn.data(), 2 * (size_t)rt->n_l1);
+    else if (k == "l1_l2") take(rt->l1_l2.data(), 4 * (size_t)(rt->n_l1 + 1));
+    else if (k == "l2") take(rt->l2.data(), sizeof(L2Entry) * (size_t)rt->n_l2);
+    else if (k == "l1_pair") take(rt->l1_pair.data(), 4 * (size_t)rt->n_l1);
+    else if (k == "l2_pair") take(rt->l2_pair.data(), 4 * (size_t)rt->n_l2);
+    else if (k == "bpair_ptr") take(rt->bpair_ptr.data(), 4 * rt->bpair_ptr.size());
+    else if (k == "bpair_dst") take(rt->bpair_dst.data(), 2 * rt->bpair_dst.size());
+    else if (k == "bpair_cap") take(rt->bpair_cap.data(), 4 * rt->bpair_cap.size());
+    else if (k == "ipair_ptr") take(rt->ipair_ptr.data(), 4 * rt->ipair_ptr.size());
+    else if (k == "ipair_dst") take(rt->ipair_dst.data(), 2 * rt->ipair_dst.size());
+    else if (k == "ipair_cap") take(rt->ipair_cap.data(), 4 * rt->ipair_cap.size());
+    else if (k == "bucket_cap") take(rt->bucket_cap.data(), 8 * rt->bucket_cap.size());
+    else if (k == "inbox_cap") take(rt->inbox_cap.data(), 8 * rt->inbox_cap.size());
+    else if (k == "perm_inv") take(rt->perm_inv.data(), 4 * rt->perm_inv.size());
+    else if (k == "perm_fwd") take(rt->perm_fwd.data(), 4 * rt->perm_fwd.size());
+    else if (k == "src_part") take(rt->src_part.data(), 2 * rt->src_part.size());
+    else if (k == "pbase") take(rt->pbase.data(), 8 * rt->pbase.size());
+    else if (k == "v0") take(rt->v0.data(), 4 * rt->v0.size());
+    else if (k == "vn_of_part") take(rt->vn_of_part.data(), 4 * rt->vn_of_part.size());
+    else if (k == "relay") take(rt->relay.data(), 4 * rt->relay.size());
+    else return SNN_E_ARG;
+    if (bytes) *bytes = n;
+    if (!out) return SNN_OK;
+    if (cap < n) return SNN_E_NOMEM;
+    if (n) std::memcpy(out, src, n);
     return SNN_OK;
 }
 

@@ -110,4 +110,18 @@ namespace snn {
 // Run f(lo, hi) over [0, n) split into contiguous chunks on up to nthreads threads.
 void parallel_for(int64_t n, int nthreads, const std::function<void(int64_t, int64_t, int)> &f);
 int resolve_threads(int requested);
+
+// Steps of the routing build shared by the host and device builders
+// (snn_host.cpp): Algorithm 2 grouping from the inter-partition synapse
+// counts PG[p*P+q] (label order) and partition weights WG; the internal
+// partition and neuron order, relay map, initial state and source
+// partitions; the static connections from the connection matrix
+// conn[ip*P+q] (internal order); the exchange-pair numbering from the dense
+// worst cases bc[ip*n_vn+g] and ic[ip*P+q], which become pair ids.
+void route_groups(snn_routing *rt, const snn_routing_params *prm, const std::vector<int64_t> &PG,
+                  const std::vector<int64_t> &WG);
+void route_order(snn_routing *rt, const snn_network *net, const int32_t *part_of, const std::vector<int64_t> &sizes);
+void route_connections(snn_routing *rt, const std::vector<uint8_t> &conn);
+void route_number_pairs(snn_routing *rt, std::vector<uint32_t> &bc, std::vector<uint32_t> &ic);
+uint32_t philox_word0(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2);
 }  // namespace snn

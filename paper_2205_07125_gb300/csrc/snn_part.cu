@@ -25,10 +25,6 @@
 
 #include "snn_internal.h"
 
-namespace snn {
-uint32_t philox_word0(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2);
-}
-
 namespace {
 
 constexpr int kPT = 256;                 // threads per block
