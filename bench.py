@@ -833,7 +833,8 @@ def run_partition_device(args):
     (synapse lists to the device, in-lists, 4 iterations, labels back),
     objective and balance.  Rounds of one reproduce the host mapping bit for
     bit; the batched rounds are compared by objective with the planted
-    partitions the generator used."""
+    partitions the generator used.  On the scale workload also the routing
+    tables built by the host (all cores) and by the GPU, checked equal."""
     import torch
     import synth
     import paper_2205_07125_gb300 as snn
@@ -895,6 +896,25 @@ def run_partition_device(args):
         print("[partition] %s batch %d grow %d iters %d: %.3f s, objective / planted %.4f"
               % (cfg.name, batch, grow, iters, sec, st["objective"] / max(1, res["planted_objective"])),
               file=sys.stderr, flush=True)
+    # routing tables (Algorithm 2 contiguous grouping + level-1/level-2 tables) on the host
+    # (all cores) and on the GPU, for the device mapping
+    part = part.astype(np.int32)
+    t0 = time.perf_counter()
+    rt_h = snn.Routing(net, part, cfg.P, cfg.n_vn, "contiguous")
+    t_h = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rt_d = snn.Routing(net, part, cfg.P, cfg.n_vn, "contiguous", build="device", device="cuda:0")
+    t_d = time.perf_counter() - t0
+    same = all(np.array_equal(rt_h.export(t).view(np.uint8), rt_d.export(t).view(np.uint8))
+               for t in ("syn_td", "syn_w", "l2", "l1_vn", "l1_l2", "l1_ptr", "l1_pair", "l2_pair", "csr"))
+    res["routing_build"] = {"host_s": t_h, "host_threads": os.cpu_count(), "device_s": t_d,
+                            "speedup": t_h / t_d, "tables_equal": bool(same),
+                            "n_l1": rt_d.info()["n_l1"], "n_l2": rt_d.info()["n_l2"]}
+    print("[partition] %s routing build: host %.2f s (%d threads), device %.2f s, tables equal %s"
+          % (cfg.name, t_h, os.cpu_count(), t_d, same), file=sys.stderr, flush=True)
+    rt_h.close()
+    rt_d.close()
     if args.host_scale_iters > 0:
         t0 = time.perf_counter()
         _, st_h = snn.snn_partition(net, cfg.P, "greedy", iters=args.host_scale_iters, seed=11)
