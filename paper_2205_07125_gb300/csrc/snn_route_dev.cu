@@ -19,6 +19,8 @@
 
 #include <algorithm>
 #include <cstring>
+#include <system_error>
+#include <thread>
 #include <vector>
 
 #include "snn_internal.h"
@@ -361,6 +363,47 @@ RLayout r_layout(long long M, long long E, int P, int n_vn, long long maxdeg)
     return L;
 }
 
+// First touch of fresh pageable host memory on all cores: the tables'
+// pages are faulted in by CPU threads instead of one by one under the
+// device-to-host copies.
+void touch_pages(void *p, size_t bytes)
+{
+    constexpr size_t kPage = 4096;
+    const int64_t n = (int64_t)((bytes + kPage - 1) / kPage);
+    parallel_for(n, 0, [p](int64_t lo, int64_t hi, int) {
+        volatile char *c = (volatile char *)p;
+        for (int64_t x = lo; x < hi; ++x) c[(size_t)x * kPage] = 0;
+    });
+}
+
+// The two largest tables, allocated and faulted in on a host thread while
+// the first passes run on the device (joined before any return: the thread
+// touches only its own arrays).
+struct Prefault {
+    HostArray<uint32_t> td;
+    HostArray<int16_t> w;
+    std::thread th;
+    bool bad = false;
+    void start(int64_t E)
+    {
+        th = std::thread([this, E] {
+            try {
+                td.alloc(E);
+                w.alloc(E);
+                touch_pages(td.data(), 4 * (size_t)E);
+                touch_pages(w.data(), 2 * (size_t)E);
+            } catch (...) {
+                bad = true;
+            }
+        });
+    }
+    void join()
+    {
+        if (th.joinable()) th.join();
+    }
+    ~Prefault() { join(); }
+};
+
 #define RCK(x)                                          \
     do {                                                \
         if ((x) != cudaSuccess) {                       \
@@ -434,6 +477,13 @@ extern "C" int snn_routing_build_device(const snn_network *net, const int32_t *p
     rt->vn_size = P / n_vn;
     const int s = rt->vn_size;
 
+    Prefault pf;
+    try {
+        pf.start(E);
+    } catch (const std::system_error &) {
+        delete rt;
+        return SNN_E_NOMEM;
+    }
     RDev d;
     std::memset(&d, 0, sizeof(d));
     d.sp = (const long long *)(ws + L.sp);
@@ -550,14 +600,21 @@ extern "C" int snn_routing_build_device(const snn_network *net, const int32_t *p
         RCK(cudaMemcpyAsync((void *)d.l1p, rt->l1_ptr.data(), 4 * (size_t)(M + 1), cudaMemcpyHostToDevice, st));
 
         // ---- pass C in chunks of internal neurons, each copied back
-        rt->syn_td.alloc(E);
-        rt->syn_w.alloc(E);
         rt->l1_vn.alloc(n_l1);
         rt->l1_l2.alloc(n_l1 + 1);
         rt->l2.alloc(n_l2);
         rt->l1_pair.alloc(n_l1);
         rt->l2_pair.alloc(n_l2);
+        touch_pages(rt->l1_vn.data(), 2 * (size_t)n_l1);
+        touch_pages(rt->l1_l2.data(), 4 * (size_t)(n_l1 + 1));
+        touch_pages(rt->l2.data(), sizeof(L2Entry) * (size_t)n_l2);
+        touch_pages(rt->l1_pair.data(), 4 * (size_t)n_l1);
+        touch_pages(rt->l2_pair.data(), 4 * (size_t)n_l2);
         rt->l1_l2[n_l1] = (uint32_t)n_l2;
+        pf.join();
+        if (pf.bad) { delete rt; return SNN_E_NOMEM; }
+        rt->syn_td = std::move(pf.td);
+        rt->syn_w = std::move(pf.w);
         if (cudaFuncSetAttribute(k_route_emit_big, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBigSmem) !=
             cudaSuccess) {
             delete rt;
