@@ -558,7 +558,7 @@ static bool shape_persist(snn_sim *s, int mode, int b)
         int smax = 0;
         cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, s->device);
         cq = (rt->M / 4 + grid - 1) / grid;
-        dyn = (size_t)cq * 36;
+        dyn = (size_t)cq * 52;  // V, ring slot, drive (16 B per quad each), refractory counters (4)
         if (dyn > (size_t)smax ||
             cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) != cudaSuccess) {
             cudaGetLastError();

@@ -248,15 +248,21 @@ __device__ __forceinline__ void pdl_enter()
 // visible to every block after it.  The wait is bounded: past limit_ns the
 // block records kStTimeout and gives up, and a block that sees another one's
 // timeout gives up too.  Returns false when the block gave up.
-__device__ __forceinline__ bool grid_sync(Ctrl *c, unsigned long long k, unsigned long long limit_ns,
-                                          bool arrive = true)
+// The barrier in two halves: grid_arrive (block-wide barrier, then the
+// release add) and grid_wait (the bounded acquire wait, then a block-wide
+// barrier); work between them must not depend on other blocks.
+__device__ __forceinline__ void grid_arrive(Ctrl *c, bool arrive = true)
+{
+    __syncthreads();
+    if (threadIdx.x == 0 && arrive) red_release(&c->bar, 1ull);
+}
+
+__device__ __forceinline__ bool grid_wait(Ctrl *c, unsigned long long k, unsigned long long limit_ns)
 {
     __shared__ int s_ok;
-    __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
         const unsigned long long target = (k + 1ull) * gridDim.x;
-        if (arrive) red_release(&c->bar, 1ull);
         const unsigned long long deadline = global_ns() + limit_ns;
         unsigned int spins = 0;
         while (ld_acquire(&c->bar) < target) {
@@ -277,6 +283,13 @@ __device__ __forceinline__ bool grid_sync(Ctrl *c, unsigned long long k, unsigne
     }
     __syncthreads();
     return s_ok != 0;
+}
+
+__device__ __forceinline__ bool grid_sync(Ctrl *c, unsigned long long k, unsigned long long limit_ns,
+                                          bool arrive = true)
+{
+    grid_arrive(c, arrive);
+    return grid_wait(c, k, limit_ns);
 }
 
 // Drive of a neuron: the Poisson thresholds (the first four as values, the
@@ -322,27 +335,39 @@ __device__ __forceinline__ Drive drive_of(const Dev &d, const uint32_t *th_smem,
     return r;
 }
 
-// a1 + a2 for one neuron: returns true on a spike.  u: the neuron's drive
-// word; dr: its network's drive.
-__device__ __forceinline__ bool lif_neuron(const Dev &d, const Drive &dr, uint32_t u, int32_t irec, float &v,
-                                           uint32_t &r)
+// Drive of one neuron in weight units: k * w_ext + i_bias (uint32
+// arithmetic), k = number of finite thresholds <= u (they ascend): the first
+// four compared at once, the rest (rare: k >= 4 has probability ~1.4 % at
+// 0.8 arrivals per step) one by one.  u: the neuron's drive word; dr: its
+// network's drive.
+__device__ __forceinline__ uint32_t drive_units(const Dev &d, const Drive &dr, uint32_t u)
 {
-    // k = number of finite thresholds <= u (they ascend): the first four
-    // compared at once, the rest (rare: k >= 4 has probability ~1.4 % at 0.8
-    // arrivals per step) one by one
     int k = (0 < dr.fin && u >= dr.t0) + (1 < dr.fin && u >= dr.t1) + (2 < dr.fin && u >= dr.t2) +
             (3 < dr.fin && u >= dr.t3);
     if (k == 4)
         while (k < dr.fin && u >= dr.th[k]) ++k;
-    const int32_t I = (int32_t)((uint32_t)irec + (uint32_t)k * (uint32_t)d.w_ext + (uint32_t)d.i_bias);
+    return (uint32_t)k * (uint32_t)d.w_ext + (uint32_t)d.i_bias;
+}
+
+// The leak of a non-refractory neuron: e_l + alpha * (V - e_l).
+__device__ __forceinline__ float lif_leak(const Dev &d, float v)
+{
+    const float uu = __fsub_rn(v, d.e_l);
+    const float au = __fmul_rn(d.alpha, uu);
+    return __fadd_rn(d.e_l, au);
+}
+
+// The rest of a2 once the recurrent input is known: I = irec + ext (the
+// same uint32 sum as irec + k * w_ext + i_bias); v holds the leaked
+// potential on entry and the new one on return.  Returns true on a spike.
+__device__ __forceinline__ bool lif_finish(const Dev &d, uint32_t ext, int32_t irec, float &v, uint32_t &r)
+{
+    const int32_t I = (int32_t)((uint32_t)irec + ext);
     if (r > 0) {
         r -= 1;
         v = d.v_reset;
         return false;
     }
-    const float uu = __fsub_rn(v, d.e_l);
-    const float au = __fmul_rn(d.alpha, uu);
-    v = __fadd_rn(d.e_l, au);
     const float x = __fmul_rn(__int2float_rn(I), 0.0009765625f);
     v = __fadd_rn(v, x);
     if (v >= d.v_th) {
@@ -351,6 +376,16 @@ __device__ __forceinline__ bool lif_neuron(const Dev &d, const Drive &dr, uint32
         return true;
     }
     return false;
+}
+
+// a1 + a2 for one neuron: returns true on a spike.  u: the neuron's drive
+// word; dr: its network's drive.
+__device__ __forceinline__ bool lif_neuron(const Dev &d, const Drive &dr, uint32_t u, int32_t irec, float &v,
+                                           uint32_t &r)
+{
+    const uint32_t ext = drive_units(d, dr, u);
+    v = lif_leak(d, v);
+    return lif_finish(d, ext, irec, v, r);
 }
 
 // Raster write head of step t + 1 from step t's head h and spike count S:
@@ -629,6 +664,7 @@ enum { kModeScalar = 0, kModeVec = 1, kModeSmem = 2 };
 struct Resident {
     float4 *V;                 // [cq] membrane potentials of the block's quads
     int4 *ring;                // [cq] this step's ring slot, staged by the bulk copy
+    int4 *ext;                 // [cq] this step's drive in weight units (pre_update)
     uint32_t *ref;             // [cq] refractory counters, one byte per neuron
     unsigned long long *bar;   // mbarrier of the bulk copy
     long long q0;              // first quad of the block
@@ -702,6 +738,41 @@ __device__ __forceinline__ unsigned int update_quad(const Dev &d, const uint32_t
     }
     r4 = r_out;
     return m;
+}
+
+// The input-free half of a1 + a2 of step t for the block's resident quads
+// (kModeSmem), run while the block waits at the grid barrier that ends step
+// t - 1: the drive of each neuron in weight units into rs.ext and the leak
+// e_l + alpha * (V - e_l) in place of V.  update_step<kModeSmem> adds the
+// recurrent input in the order lif_neuron uses.  th: the thresholds staged in
+// shared memory.
+__device__ __forceinline__ void pre_update(const Dev &d, long long t, const uint32_t *th, const Resident &rs)
+{
+    for (int lq = threadIdx.x; lq < rs.nq; lq += kThreads) {
+        const long long j0 = (rs.q0 + lq) * 4;
+        Drive dq = drive_of(d, th, d.gid ? d.gid[j0] : (uint32_t)j0);
+        uint4 wq = make_uint4(0u, 0u, 0u, 0u);
+        if (!d.gid) wq = philox4(dq.key0, dq.key1, (uint32_t)((j0 - dq.off) >> 2), (uint32_t)t);
+        const float4 v4 = rs.V[lq];
+        const float vv[4] = {v4.x, v4.y, v4.z, v4.w};
+        uint32_t ex[4];
+        float lv[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            uint32_t u;
+            if (d.gid) {
+                const uint32_t g = d.gid[j0 + k];
+                if (k > 0) dq = drive_of(d, th, g);
+                u = uint4_word(philox4(dq.key0, dq.key1, (uint32_t)((g - dq.off) >> 2), (uint32_t)t), g & 3u);
+            } else {
+                u = uint4_word(wq, (uint32_t)k);
+            }
+            ex[k] = drive_units(d, dq, u);
+            lv[k] = lif_leak(d, vv[k]);
+        }
+        rs.V[lq] = make_float4(lv[0], lv[1], lv[2], lv[3]);
+        rs.ext[lq] = make_int4((int)ex[0], (int)ex[1], (int)ex[2], (int)ex[3]);
+    }
 }
 
 // Shared-memory scratch of a block's step.
@@ -815,13 +886,29 @@ __device__ __forceinline__ void update_step(const Dev &d, long long t, StepShare
                     uint32_t r4 = rs.ref[lq];
                     *reinterpret_cast<int4 *>(ring + j0) = make_int4(0, 0, 0, 0);
                     if (cur) *reinterpret_cast<int4 *>(cur + j0) = i4;
+                    // rs.V holds the leaked potentials and rs.ext the drive
+                    // (pre_update, during the last grid barrier)
+                    const int4 e4 = rs.ext[lq];
                     float vv[4] = {v4.x, v4.y, v4.z, v4.w};
                     const int32_t ii[4] = {i4.x, i4.y, i4.z, i4.w};
-                    const unsigned int m = update_quad(d, sh.th, t, j0, vv, ii, r4, do_hash, hc, hv);
+                    const uint32_t ex[4] = {(uint32_t)e4.x, (uint32_t)e4.y, (uint32_t)e4.z, (uint32_t)e4.w};
+                    unsigned int m = 0;
+                    uint32_t r_out = 0;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        uint32_t r = (r4 >> (8 * q)) & 0xFFu;
+                        if (lif_finish(d, ex[q], ii[q], vv[q], r)) m |= 1u << q;
+                        r_out |= r << (8 * q);
+                        if (do_hash) {
+                            const uint32_t g = d.gid ? d.gid[j0 + q] : (uint32_t)(j0 + q);
+                            hc += mix64(((unsigned long long)g << 32) | (uint32_t)ii[q]);
+                            hv += mix64(((unsigned long long)g << 32) | __float_as_uint(vv[q]));
+                        }
+                    }
                     prefetch_rows(d, j0, m);
                     bits |= m << (4 * k);
                     rs.V[lq] = make_float4(vv[0], vv[1], vv[2], vv[3]);
-                    rs.ref[lq] = r4;
+                    rs.ref[lq] = r_out;
                 }
             }
             compact_spikes(d, t, sh, bits,
@@ -1000,7 +1087,10 @@ __global__ void k_advance(const Dev d, int steps)
 // (tests of the bounded wait only): block 0 waits at the first barrier
 // without arriving, so every block's wait runs out.  In kModeSmem block b
 // owns quads [b cq, (b + 1) cq) (cq = Dev::chunk_q) and keeps their V and
-// ref in dynamic shared memory from the launch's start to its end.
+// ref in dynamic shared memory from the launch's start to its end, and the
+// second barrier of a step is split: between its arrival and its wait the
+// block computes the next step's drive and leak (pre_update), which need no
+// other block's data.
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, 4) k_persist(const Dev d, int T, unsigned long long limit_ns,
                                                          int skip_arrival)
@@ -1014,7 +1104,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_persist(const Dev d, int T, uns
         const long long cq = d.chunk_q;
         rs.V = reinterpret_cast<float4 *>(s_dyn);
         rs.ring = reinterpret_cast<int4 *>(s_dyn + cq * 16);
-        rs.ref = reinterpret_cast<uint32_t *>(s_dyn + cq * 32);
+        rs.ext = reinterpret_cast<int4 *>(s_dyn + cq * 32);
+        rs.ref = reinterpret_cast<uint32_t *>(s_dyn + cq * 48);
         rs.bar = &s_bar;
         rs.q0 = (long long)blockIdx.x * cq;
         rs.nq = (int)max(0ll, min(cq, d.M / 4 - rs.q0));
@@ -1029,8 +1120,12 @@ __global__ void __launch_bounds__(kThreads, 4) k_persist(const Dev d, int T, uns
         __syncthreads();
     }
     if (threadIdx.x == 0) sh.t0 = *(volatile long long *)&c->t;
+    if (threadIdx.x < kPTab) sh.th[threadIdx.x] = d.th32[threadIdx.x];
     __syncthreads();
     const long long t0 = sh.t0;
+    if constexpr (MODE == kModeSmem) {
+        if (T > 0) pre_update(d, t0, sh.th, rs);
+    }
     const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
     const bool prof = d.phase_ns != nullptr && lead;
     int done = 0, issued = 0;
@@ -1049,8 +1144,13 @@ __global__ void __launch_bounds__(kThreads, 4) k_persist(const Dev d, int T, uns
         if (!grid_sync(c, 2ull * s, limit_ns, !(skip_arrival && s == 0 && blockIdx.x == 0))) break;
         const unsigned long long e = prof ? global_ns() : 0;
         route_step(d, t, sh);
+        // the next step's input-free update runs while the barrier completes
+        grid_arrive(c);
+        if constexpr (MODE == kModeSmem) {
+            if (s + 1 < T) pre_update(d, t + 1, sh.th, rs);
+        }
         const unsigned long long f = prof ? global_ns() : 0;
-        if (!grid_sync(c, 2ull * s + 1ull, limit_ns)) break;
+        if (!grid_wait(c, 2ull * s + 1ull, limit_ns)) break;
         if (prof) {
             const unsigned long long g = global_ns();
             ns[0] += (b - a) + (f - e);
