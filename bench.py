@@ -281,8 +281,11 @@ def run_ours(args):
         h1 = time.perf_counter()
         e2e_ms = (h1 - h0) * 1e3
         e2e_events, e2e_ms_max, _ = reduce_over_ranks(dist, float(ce["events"]), e2e_ms)
-        h2d = (info["n_synapses"] * 6 + info["n_l2"] * 16 + info["n_l1"] * 6 + (cfg.M + 1) * 4
-               + cfg.M * 6)
+        # the tables snn_sim_reset(reupload) copies: synapses (6 B), level-2 entries and pair
+        # ids (20 B), level-1 entries and pair ids (10 B), per-neuron rows (l1_ptr, row, csr:
+        # 20 B), source partitions (2 B), initial potentials (4 B), order maps when not identity
+        h2d = (info["n_synapses"] * 6 + info["n_l2"] * 20 + info["n_l1"] * 10 + (cfg.M + 1) * 20
+               + cfg.M * 6 + (0 if info["identity_order"] else cfg.M * 8))
         d2h = ids.nbytes + off.nbytes + 88
         e2e = {"value": e2e_events / (e2e_ms_max * 1e-3), "unit": UNIT,
                "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K,
@@ -827,6 +830,30 @@ def _objective(g, part, chunk=1 << 24):
     return tot
 
 
+def routing_compare(snn, net, part, P, n_vn, grouping, name):
+    """Routing tables (Algorithm 2 grouping + level-1/level-2 tables) built on
+    the host (all cores) and on the GPU for the same mapping: times and a
+    byte comparison of the tables."""
+    import torch
+    part = np.ascontiguousarray(part, np.int32)
+    t0 = time.perf_counter()
+    rt_h = snn.Routing(net, part, P, n_vn, grouping)
+    t_h = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rt_d = snn.Routing(net, part, P, n_vn, grouping, build="device", device="cuda:0")
+    t_d = time.perf_counter() - t0
+    same = all(np.array_equal(rt_h.export(t).view(np.uint8), rt_d.export(t).view(np.uint8))
+               for t in ("syn_td", "syn_w", "l2", "l1_vn", "l1_l2", "l1_ptr", "l1_pair", "l2_pair", "csr"))
+    r = {"host_s": t_h, "host_threads": os.cpu_count(), "device_s": t_d, "speedup": t_h / t_d,
+         "tables_equal": bool(same), "grouping": grouping, "n_l1": rt_d.info()["n_l1"], "n_l2": rt_d.info()["n_l2"]}
+    print("[partition] %s routing build: host %.2f s (%d threads), device %.2f s, tables equal %s"
+          % (name, t_h, os.cpu_count(), t_d, same), file=sys.stderr, flush=True)
+    rt_h.close()
+    rt_d.close()
+    return r
+
+
 def run_partition_device(args):
     """Algorithm 1 on the GPU (batched growth, one cooperative launch per
     iteration) against the library's host greedy: wall time of the call
@@ -876,6 +903,7 @@ def run_partition_device(args):
         print("[partition] %s batch %d grow %d: %.3f s, objective %d (host %.3f s, %d; planted %d)"
               % (cfg.name, batch, grow, sec, st["objective"], res["host_greedy"]["s"], st_h["objective"],
                  res["planted_objective"]), file=sys.stderr, flush=True)
+    res["routing_build"] = routing_compare(snn, net, part, P, 4, "greedy", cfg.name)
     out["networks"][cfg.name] = res
 
     if args.no_scale:
@@ -896,25 +924,7 @@ def run_partition_device(args):
         print("[partition] %s batch %d grow %d iters %d: %.3f s, objective / planted %.4f"
               % (cfg.name, batch, grow, iters, sec, st["objective"] / max(1, res["planted_objective"])),
               file=sys.stderr, flush=True)
-    # routing tables (Algorithm 2 contiguous grouping + level-1/level-2 tables) on the host
-    # (all cores) and on the GPU, for the device mapping
-    part = part.astype(np.int32)
-    t0 = time.perf_counter()
-    rt_h = snn.Routing(net, part, cfg.P, cfg.n_vn, "contiguous")
-    t_h = time.perf_counter() - t0
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    rt_d = snn.Routing(net, part, cfg.P, cfg.n_vn, "contiguous", build="device", device="cuda:0")
-    t_d = time.perf_counter() - t0
-    same = all(np.array_equal(rt_h.export(t).view(np.uint8), rt_d.export(t).view(np.uint8))
-               for t in ("syn_td", "syn_w", "l2", "l1_vn", "l1_l2", "l1_ptr", "l1_pair", "l2_pair", "csr"))
-    res["routing_build"] = {"host_s": t_h, "host_threads": os.cpu_count(), "device_s": t_d,
-                            "speedup": t_h / t_d, "tables_equal": bool(same),
-                            "n_l1": rt_d.info()["n_l1"], "n_l2": rt_d.info()["n_l2"]}
-    print("[partition] %s routing build: host %.2f s (%d threads), device %.2f s, tables equal %s"
-          % (cfg.name, t_h, os.cpu_count(), t_d, same), file=sys.stderr, flush=True)
-    rt_h.close()
-    rt_d.close()
+    res["routing_build"] = routing_compare(snn, net, part, cfg.P, cfg.n_vn, "contiguous", cfg.name)
     if args.host_scale_iters > 0:
         t0 = time.perf_counter()
         _, st_h = snn.snn_partition(net, cfg.P, "greedy", iters=args.host_scale_iters, seed=11)

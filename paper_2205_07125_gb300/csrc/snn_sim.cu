@@ -112,7 +112,7 @@ struct Region {
 };
 
 struct Layout {
-    Region V, ref, ring, gid, src_part, syn_td, syn_w, l1_ptr, l1_vn, l1_l2, l2, row, l1_pair, l2_pair;
+    Region V, ref, ring, gid, src_part, syn_td, syn_w, l1_ptr, l1_vn, l1_l2, l2, row, csr, l1_pair, l2_pair;
     Region bucket, bucket_slot, bucket_cnt, inbox, inbox_slot, inbox_cnt;
     Region tally;  // per-block tally rows
     Region net_of, net_drive;  // batches: network of each quad, drive of each network
@@ -196,6 +196,7 @@ static int make_layout(const snn_routing *rt, const snn_sim_params *p, Layout &L
     place(L, L.l1_l2, sizeof(uint32_t) * (size_t)(rt->n_l1 + 1));
     place(L, L.l2, sizeof(L2Entry) * (size_t)rt->n_l2);
     place(L, L.row, sizeof(uint2) * (size_t)(M + 1));
+    place(L, L.csr, sizeof(unsigned long long) * (size_t)(M + 1));
     place(L, L.l1_pair, sizeof(uint32_t) * (size_t)rt->n_l1);
     place(L, L.l2_pair, sizeof(uint32_t) * (size_t)rt->n_l2);
     place(L, L.bucket, sizeof(uint32_t) * (size_t)nb);
@@ -369,6 +370,7 @@ static int upload_tables(snn_sim *s)
         CK(cudaMemcpy(w + L.row.off, row.data(), L.row.bytes, cudaMemcpyHostToDevice));
     }
     CK(up(L.l2_pair, rt->l2_pair.data()));
+    CK(up(L.csr, rt->csr.data()));
     if (!rt->identity) CK(up(L.gid, rt->perm_inv.data()));
     if (!rt->identity) CK(up(L.fwd, rt->perm_fwd.data()));
     {
@@ -694,6 +696,7 @@ static int sim_create(const snn_network *net, const snn_routing *rt, const snn_s
     d.gid = rt->identity ? nullptr : (const uint32_t *)(w + L.gid.off);
     d.src_part = (const uint16_t *)(w + L.src_part.off);
     d.row = (const uint2 *)(w + L.row.off);
+    d.csr = (const unsigned long long *)(w + L.csr.off);
     d.l1_pair = (const uint32_t *)(w + L.l1_pair.off);
     d.l2_pair = (const uint32_t *)(w + L.l2_pair.off);
     d.syn_td = (const uint32_t *)(w + L.syn_td.off);

@@ -45,6 +45,7 @@ constexpr int kPTab = 32;
 constexpr int kLongCap = 512;   // staged pieces of one routing round
 constexpr int kShortCap = 1024; // staged short segments of one routing round
 constexpr int kRound = 16;      // spikes routed per round (<= 32)
+constexpr int kOwn = 64;        // own spikes of a step whose tables a block prefetches
 // Exchange fill counters are keyed by (source partition, destination) pair,
 // so each sees only the spikes of one source partition, and each owns a
 // 128-byte line: the counters of one partition then spread over many L2
@@ -102,6 +103,7 @@ struct Dev {
     const uint32_t *l1_l2;
     const DevL2 *l2;
     const uint2 *row;         // [M+1] first level-1 and level-2 entry of each internal neuron
+    const unsigned long long *csr;  // [M+1] first synapse of each internal neuron
     const uint32_t *l1_pair;  // exchange pair (source partition, VN) of each level-1 entry
     const uint32_t *l2_pair;  // exchange pair (source partition, partition) of each level-2 entry
     // exchange buffers, one region per pair (source partition p, destination)
@@ -216,7 +218,17 @@ __device__ __forceinline__ void prefetch_rows(const Dev &d, long long j0, unsign
         const long long i = j0 + __ffs(m) - 1;
         prefetch_l2(d.row + i);
         prefetch_l2(d.row + i + 1);
+        prefetch_l2(d.csr + i);
+        prefetch_l2(d.csr + i + 1);
     }
+}
+
+// Every 128-byte line of [a, b), one line per lane in turn (whole warp).
+__device__ __forceinline__ void prefetch_span(const void *a, const void *b, int lane)
+{
+    const uintptr_t e = (uintptr_t)b;
+    for (uintptr_t x = ((uintptr_t)a & ~(uintptr_t)127) + (uintptr_t)lane * 128u; x < e; x += 32u * 128u)
+        prefetch_l2((const void *)x);
 }
 
 __device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long *p)
@@ -788,6 +800,8 @@ struct StepShared {
     uint32_t th[kPTab];
     uint32_t e0[kRound], f0[kRound], pre1[kRound + 1], pre2[kRound + 1];
     int part[kRound];
+    uint32_t own[kOwn];       // the block's own spikes of the step (the first kOwn)
+    unsigned int n_own, obase;
 };
 
 // a3: compaction of the spikes each thread collected in `bits` (bit b is
@@ -817,10 +831,39 @@ __device__ __forceinline__ void compact_spikes(const Dev &d, long long t, StepSh
             tot += cw;
         }
         sh.gbase = atomicAdd(&d.ctrl->S_acc[slot3(t)], tot);
+        sh.obase = sh.n_own;
+        sh.n_own += tot;
     }
     __syncthreads();
     unsigned int pos = sh.gbase + sh.wsum[wid] + x - cnt;
-    for (uint32_t bb = bits; bb; bb &= bb - 1u) d.spk_step[pos++] = id_of(__ffs(bb) - 1);
+    unsigned int lp = sh.obase + sh.wsum[wid] + x - cnt;
+    for (uint32_t bb = bits; bb; bb &= bb - 1u, ++lp) {
+        const uint32_t id = id_of(__ffs(bb) - 1);
+        d.spk_step[pos++] = id;
+        if (lp < (unsigned int)kOwn) sh.own[lp] = id;
+    }
+}
+
+// While the block waits at the grid barrier after a3: pull the routing
+// tables and synapses of its own spikes (whichever block routes them) from
+// HBM into L2 — level-1 and level-2 entries, their pair ids and the synapse
+// run — one spike per warp.
+__device__ __forceinline__ void prefetch_own(const Dev &d, const StepShared &sh)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned int n = min(sh.n_own, (unsigned int)kOwn);
+    for (unsigned int x = wid; x < n; x += kWarps) {
+        const uint32_t i = sh.own[x];
+        const uint2 r0 = d.row[i], r1 = d.row[i + 1];
+        const unsigned long long s0 = d.csr[i], s1 = d.csr[i + 1];
+        prefetch_span(d.l1_vn + r0.x, d.l1_vn + r1.x, lane);
+        prefetch_span(d.l1_l2 + r0.x, d.l1_l2 + r1.x, lane);
+        prefetch_span(d.l1_pair + r0.x, d.l1_pair + r1.x, lane);
+        prefetch_span(d.l2 + r0.y, d.l2 + r1.y, lane);
+        prefetch_span(d.l2_pair + r0.y, d.l2_pair + r1.y, lane);
+        prefetch_span(d.syn_td + s0, d.syn_td + s1, lane);
+        prefetch_span(d.syn_w + s0, d.syn_w + s1, lane);
+    }
 }
 
 // First half of step t on this block's share of the neurons (all threads
@@ -865,6 +908,7 @@ __device__ __forceinline__ void update_step(const Dev &d, long long t, StepShare
         if (blockIdx.x == 0 && threadIdx.x == 0) c->S_acc[slot3(t + 1)] = 0;
     }
     if (threadIdx.x < kPTab) sh.th[threadIdx.x] = d.th32[threadIdx.x];
+    if (threadIdx.x == 0) sh.n_own = 0u;
     __syncthreads();
 
     unsigned long long hc = 0, hv = 0;
@@ -1141,7 +1185,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_persist(const Dev d, int T, uns
         update_step<MODE>(d, t, sh, rs, (uint32_t)(s & 1), limit_ns);
         ++issued;
         const unsigned long long b = prof ? global_ns() : 0;
-        if (!grid_sync(c, 2ull * s, limit_ns, !(skip_arrival && s == 0 && blockIdx.x == 0))) break;
+        grid_arrive(c, !(skip_arrival && s == 0 && blockIdx.x == 0));
+        prefetch_own(d, sh);
+        if (!grid_wait(c, 2ull * s, limit_ns)) break;
         const unsigned long long e = prof ? global_ns() : 0;
         route_step(d, t, sh);
         // the next step's input-free update runs while the barrier completes
