@@ -759,18 +759,24 @@ static int sim_create(const snn_network *net, const snn_routing *rt, const snn_s
 
 static int launch_persist(snn_sim *s, int32_t T, const Dev &d)
 {
-    if (T <= 0) return SNN_OK;
-    int tt = T;
     unsigned long long lim = s->barrier_limit_ns;
-    int skip = s->test_skip_arrival;
-    s->test_skip_arrival = 0;  // once: the test checks the first launch's status
-    void *args[] = {(void *)&d, (void *)&tt, (void *)&lim, (void *)&skip};
     const void *fn = s->pmode == kModeSmem  ? (const void *)k_persist<kModeSmem>
                      : s->pmode == kModeVec ? (const void *)k_persist<kModeVec>
                                             : (const void *)k_persist<kModeScalar>;
-    // the grid barrier counts arrivals from zero in every launch
-    CK(cudaMemsetAsync(s->ws + s->L.ctrl.off + offsetof(Ctrl, bar), 0, sizeof(unsigned long long), s->stream));
-    CK(cudaLaunchCooperativeKernel(fn, dim3(s->grid_persist), dim3(kThreads), args, s->persist_smem, s->stream));
+    // a launch's barrier arrivals (2 per step per block) stay below 2^32
+    const int32_t cap = (int32_t)std::min<unsigned long long>(
+        0x7FFFFFFFull, (0xFFFFFFFFull / (2ull * s->grid_persist)) - 1ull);
+    while (T > 0) {
+        int tt = std::min(T, cap);
+        int skip = s->test_skip_arrival;
+        s->test_skip_arrival = 0;  // once: the test checks the first launch's status
+        void *args[] = {(void *)&d, (void *)&tt, (void *)&lim, (void *)&skip};
+        // the grid barrier counts arrivals from zero in every launch
+        CK(cudaMemsetAsync(s->ws + s->L.ctrl.off + offsetof(Ctrl, bar), 0, sizeof(unsigned long long), s->stream));
+        CK(cudaLaunchCooperativeKernel(fn, dim3(s->grid_persist), dim3(kThreads), args, s->persist_smem,
+                                       s->stream));
+        T -= tt;
+    }
     return SNN_OK;
 }
 

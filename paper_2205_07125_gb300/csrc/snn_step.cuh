@@ -253,9 +253,11 @@ __device__ __forceinline__ void pdl_enter()
 }
 
 // Grid-wide barrier number k of a k_persist launch (all blocks co-resident:
-// cooperative launch).  Each block adds one arrival to Ctrl::bar, which the
-// host zeroes before the launch; barrier k is complete when the count reaches
-// (k + 1) * gridDim.x.  A block-wide barrier, then a release add and acquire
+// cooperative launch).  Each block adds one arrival to the low 32 bits of
+// Ctrl::bar, which the host zeroes before the launch (and keeps the
+// arrivals of a launch below 2^32); barrier k is complete when they reach
+// (k + 1) * gridDim.x.  The high 32 bits carry what the arrivals add there:
+// each block's spike count of the step at the step's first barrier.  A block-wide barrier, then a release add and acquire
 // loads at GPU scope make every write of every block before the barrier
 // visible to every block after it.  The wait is bounded: past limit_ns the
 // block records kStTimeout and gives up, and a block that sees another one's
@@ -263,13 +265,14 @@ __device__ __forceinline__ void pdl_enter()
 // The barrier in two halves: grid_arrive (block-wide barrier, then the
 // release add) and grid_wait (the bounded acquire wait, then a block-wide
 // barrier); work between them must not depend on other blocks.
-__device__ __forceinline__ void grid_arrive(Ctrl *c, bool arrive = true)
+__device__ __forceinline__ void grid_arrive(Ctrl *c, bool arrive = true, unsigned long long add = 1ull)
 {
     __syncthreads();
-    if (threadIdx.x == 0 && arrive) red_release(&c->bar, 1ull);
+    if (threadIdx.x == 0 && arrive) red_release(&c->bar, add);
 }
 
-__device__ __forceinline__ bool grid_wait(Ctrl *c, unsigned long long k, unsigned long long limit_ns)
+__device__ __forceinline__ bool grid_wait(Ctrl *c, unsigned long long k, unsigned long long limit_ns,
+                                          unsigned long long *word = nullptr)
 {
     __shared__ int s_ok;
     if (threadIdx.x == 0) {
@@ -277,7 +280,8 @@ __device__ __forceinline__ bool grid_wait(Ctrl *c, unsigned long long k, unsigne
         const unsigned long long target = (k + 1ull) * gridDim.x;
         const unsigned long long deadline = global_ns() + limit_ns;
         unsigned int spins = 0;
-        while (ld_acquire(&c->bar) < target) {
+        unsigned long long v;
+        while (((v = ld_acquire(&c->bar)) & 0xFFFFFFFFull) < target) {
             if ((++spins & 15u) == 0u) {
                 if (*(volatile unsigned int *)&c->status & kStTimeout) {
                     ok = 0;
@@ -291,6 +295,7 @@ __device__ __forceinline__ bool grid_wait(Ctrl *c, unsigned long long k, unsigne
             }
             __nanosleep(64);
         }
+        if (word) *word = v;  // (shared memory: read after the barrier below)
         s_ok = ok;
     }
     __syncthreads();
@@ -802,6 +807,11 @@ struct StepShared {
     int part[kRound];
     uint32_t own[kOwn];       // the block's own spikes of the step (the first kOwn)
     unsigned int n_own, obase;
+    // k_persist: the first barrier's word, the spike sum it carried at the
+    // last step, and the raster head of the next step
+    unsigned long long word;
+    uint32_t prevS;
+    long long headv;
 };
 
 // a3: compaction of the spikes each thread collected in `bits` (bit b is
@@ -1041,15 +1051,26 @@ __device__ __forceinline__ void update_step(const Dev &d, long long t, StepShare
 // Second half of step t (all threads call): a4-a6 for this block's share of
 // the step's spikes, an equal share of the list for every block, and their
 // raster copy.
-__device__ __forceinline__ void route_step(const Dev &d, long long t, StepShared &sh)
+__device__ __forceinline__ void route_step(const Dev &d, long long t, StepShared &sh, bool carried = false)
 {
     const Stage sg{sh.lng, sh.sht, &sh.nl, &sh.ns, sh.tally, sh.e0, sh.f0, sh.pre1, sh.pre2, sh.part};
     Ctrl *c = d.ctrl;
     if (threadIdx.x == 0) {
-        // one thread reads the step words: every warp loading them would
-        // queue thousands of requests on one L2 line
-        sh.tot = *(volatile unsigned int *)&c->S_acc[slot3(t)];
-        sh.head = *(volatile long long *)&c->head[slot3(t)];
+        if (carried) {
+            // k_persist: the step's spike count from the barrier word (the sum
+            // of the blocks' counts less the last one) and the raster head
+            // this block carries from step to step as close_step does
+            const uint32_t hiw = (uint32_t)(sh.word >> 32);
+            sh.tot = hiw - sh.prevS;
+            sh.prevS = hiw;
+            sh.head = sh.headv;
+            sh.headv = next_head(d, sh.headv, sh.tot, t);
+        } else {
+            // one thread reads the step words: every warp loading them would
+            // queue thousands of requests on one L2 line
+            sh.tot = *(volatile unsigned int *)&c->S_acc[slot3(t)];
+            sh.head = *(volatile long long *)&c->head[slot3(t)];
+        }
     }
     if (threadIdx.x < kWarps * kTally) (&sh.tally[0][0])[threadIdx.x] = 0u;
     __syncthreads();
@@ -1163,7 +1184,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_persist(const Dev d, int T, uns
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) sh.t0 = *(volatile long long *)&c->t;
+    if (threadIdx.x == 0) {
+        sh.t0 = *(volatile long long *)&c->t;
+        sh.headv = *(volatile long long *)&c->head[slot3(sh.t0)];
+        sh.prevS = 0u;
+    }
     if (threadIdx.x < kPTab) sh.th[threadIdx.x] = d.th32[threadIdx.x];
     __syncthreads();
     const long long t0 = sh.t0;
@@ -1185,11 +1210,12 @@ __global__ void __launch_bounds__(kThreads, 4) k_persist(const Dev d, int T, uns
         update_step<MODE>(d, t, sh, rs, (uint32_t)(s & 1), limit_ns);
         ++issued;
         const unsigned long long b = prof ? global_ns() : 0;
-        grid_arrive(c, !(skip_arrival && s == 0 && blockIdx.x == 0));
+        // the first barrier carries the block's spike count in the word's high half
+        grid_arrive(c, !(skip_arrival && s == 0 && blockIdx.x == 0), 1ull + ((unsigned long long)sh.n_own << 32));
         prefetch_own(d, sh);
-        if (!grid_wait(c, 2ull * s, limit_ns)) break;
+        if (!grid_wait(c, 2ull * s, limit_ns, &sh.word)) break;
         const unsigned long long e = prof ? global_ns() : 0;
-        route_step(d, t, sh);
+        route_step(d, t, sh, true);
         // the next step's input-free update runs while the barrier completes
         grid_arrive(c);
         if constexpr (MODE == kModeSmem) {
