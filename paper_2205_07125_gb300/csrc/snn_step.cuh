@@ -1157,7 +1157,7 @@ __global__ void k_advance(const Dev d, int steps)
 // block computes the next step's drive and leak (pre_update), which need no
 // other block's data.
 template <int MODE>
-__global__ void __launch_bounds__(kThreads, 4) k_persist(const Dev d, int T, unsigned long long limit_ns,
+__global__ void __launch_bounds__(kThreads, 3) k_persist(const Dev d, int T, unsigned long long limit_ns,
                                                          int skip_arrival)
 {
     __shared__ StepShared sh;
