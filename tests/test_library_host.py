@@ -346,3 +346,58 @@ def test_exported_tables_follow_the_network(snn):
     assert np.array_equal(rt.export("bucket_cap"), bcnt.sum(0))
     with pytest.raises(RuntimeError):
         rt.export("no_such_table")
+
+
+def test_device_builders_check_arguments_before_the_device(snn):
+    """snn_partition_device and snn_routing_build_device reject bad arguments
+    and short or misaligned workspaces before any CUDA call (no GPU here)."""
+    g = synth.make_network(synth.NetConfig(name="t", M=256, P=4, n_vn=2, K=6, uniform_all=True, dmax=3))
+    net = snn.Network.from_synth(g)
+    lib = snn._lib
+    out = np.empty(g.M, np.int32)
+    nb = ctypes.c_size_t(0)
+    assert lib.snn_partition_device_workspace_bytes(ctypes.byref(net.s), 4, ctypes.byref(nb)) == 0
+    assert nb.value >= 8 * g.E
+    prm = snn.snn_partition_device_params()
+    lib.snn_partition_device_params_default(ctypes.byref(prm))
+    assert (prm.iters, prm.batch, prm.grow, prm.seed) == (4, 2048, 2, 7)
+    fake = 1 << 20  # never dereferenced: every check below fails first
+
+    def part(P, **kw):
+        p = snn.snn_partition_device_params()
+        lib.snn_partition_device_params_default(ctypes.byref(p))
+        for k, v in kw.items():
+            setattr(p, k, v)
+        ws = kw.pop("ws", fake)
+        return lib.snn_partition_device(ctypes.byref(net.s), P, ctypes.byref(p), ws, nb.value, None,
+                                        out.ctypes.data, None)
+    E_ARG, E_NOMEM = -1, -2
+    assert part(4, batch=0) == E_ARG
+    assert part(4, batch=4096) == E_ARG
+    assert part(4, grow=-1) == E_ARG
+    assert part(4, iters=0) == E_ARG
+    assert part(0) == E_ARG and part(g.M + 1) == E_ARG
+    assert lib.snn_partition_device(ctypes.byref(net.s), 4, ctypes.byref(prm), fake, nb.value - 256, None,
+                                    out.ctypes.data, None) == E_NOMEM
+    assert lib.snn_partition_device(ctypes.byref(net.s), 4, ctypes.byref(prm), fake + 8, nb.value, None,
+                                    out.ctypes.data, None) == E_NOMEM
+    # routing
+    assert lib.snn_routing_build_device_workspace_bytes(ctypes.byref(net.s), 4, 2, ctypes.byref(nb)) == 0
+    rp = snn.snn_routing_params(0, 1, 1, 0, 0)
+    h = ctypes.c_void_p()
+    po = oracle.partition_planted(g.M, 4)
+
+    def route(P, n_vn, p_of=po, size=nb.value, ws=fake):
+        return lib.snn_routing_build_device(ctypes.byref(net.s), p_of.ctypes.data, P, n_vn, ctypes.byref(rp), ws,
+                                            size, None, ctypes.byref(h))
+    assert route(4, 3) == E_ARG                      # P not a multiple of n_vn
+    bad = po.copy()
+    bad[7] = 4
+    assert route(4, 2, bad) == E_ARG                 # a label out of range
+    assert route(5, 1, po) == E_ARG                  # partition 4 has no neuron
+    assert route(4, 2, size=nb.value - 256) == E_NOMEM
+    assert route(4, 2, ws=fake + 16) == E_NOMEM
+    big = synth.make_edges(4, [(0, j % 4, 1, 1) for j in range(16385)])
+    bnet = snn.Network.from_synth(big)
+    assert lib.snn_routing_build_device(ctypes.byref(bnet.s), np.zeros(4, np.int32).ctypes.data, 1, 1,
+                                        ctypes.byref(rp), fake, 1 << 30, None, ctypes.byref(h)) == -5
