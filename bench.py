@@ -177,7 +177,7 @@ def run_ours(args):
     info = rt.info()
     raster_cap = int(cfg.M * (K + W) * 0.002) + 100000
     prm = snn.sim_params(cfg.dyn, raster_cap=raster_cap, raster_steps=K + W, steps_per_graph=32,
-                         pin_host_tables=1)
+                         pin_host_tables=1, defer_delayed=1 if args.defer else 0)
     sim = snn.Sim(net, rt, prm, device=dev)
     choice, tuned_ms = sim.autotune(200)
     setup_s = time.time() - t_setup
@@ -306,7 +306,8 @@ def run_ours(args):
                          "delay ring %.0f MB (L2-resident when it fits the 129 MB L2)"
                          % (info["n_synapses"] * 6 / 1e9, cfg.M * (info["max_delay"] + 1) * 4 / 1e6),
                    "steps_per_graph": 32,
-                   "execution": "persistent cooperative kernel" if persistent else "CUDA graphs",
+                   "execution": ("persistent cooperative kernel" if persistent else "CUDA graphs")
+                                + (", minimum-delay batching" if args.defer else ""),
                    "autotune": {"choice": choice, "ms_per_step": tuned_ms,
                                 "meaning": "0 graph path, else 100*mode + blocks per SM (mode 2 "
                                            "shared-memory state, 1 global 16-byte, 0 global scalar)"}},
@@ -958,6 +959,9 @@ def main(argv=None):
                     help="network size with the scale workload's per-neuron statistics "
                          "(default: the 1,048,576-neuron workload)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--defer", action="store_true",
+                    help="minimum-delay batching: delay >= 2 synapses delivered during the next step's "
+                         "table walk (persistent shared-memory shape)")
     ap.add_argument("--config", choices=("scale", "paper", "tiny", "batch", "adjoint", "partition",
                                          "partition-device"),
                     default="scale",

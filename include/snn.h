@@ -262,6 +262,10 @@ typedef struct {
     float bucket_frac, inbox_frac;
     int32_t steps_per_graph;     /* steps unrolled per CUDA graph (1..256) */
     int32_t pin_host_tables;     /* page-lock the routing tables for uploads */
+    int32_t defer_delayed;       /* 0/1: minimum-delay batching on the persistent shared-memory shape:
+                                  * each step's delay >= 2 synapses are delivered during the next
+                                  * step's table walk (exact; slower on GB300 for the scale
+                                  * workload, off by default) */
 } snn_sim_params;
 
 /* Fill p with the defaults (no records, exact capacities, 32 steps/graph). */

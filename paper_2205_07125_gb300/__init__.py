@@ -75,7 +75,7 @@ class snn_sim_params(ctypes.Structure):
                 ("drive_seed", _u64), ("raster_cap", _i64), ("raster_steps", _i64),
                 ("hash_steps", _i64), ("cur_every", _i32), ("cur_slots", _i32),
                 ("bucket_frac", _f32), ("inbox_frac", _f32), ("steps_per_graph", _i32),
-                ("pin_host_tables", _i32)]
+                ("pin_host_tables", _i32), ("defer_delayed", _i32)]
 
 
 COUNT_FIELDS = ("steps", "spikes", "events", "direct", "direct_xvn", "l1_local", "l1_xvn",

@@ -231,6 +231,7 @@ static bool params_ok(const snn_sim_params *p)
     if (p->cur_every < 0 || p->cur_slots < 0) return false;
     if (!(p->bucket_frac >= 0.0f) || !(p->inbox_frac >= 0.0f)) return false;
     if (p->steps_per_graph < 1 || p->steps_per_graph > 256) return false;
+    if (p->defer_delayed != 0 && p->defer_delayed != 1) return false;
     return true;
 }
 
@@ -295,6 +296,7 @@ struct snn_sim {
     bool allow_persist = true, allow_smem = true;  // SNN_PERSIST / SNN_PERSIST_SMEM
     bool pdl = true;       // programmatic dependent launch between step kernels
     bool persist = false;  // one cooperative launch per snn_step (k_persist)
+    bool defer = false;    // k_persist with minimum-delay batching (shared-memory state only)
     unsigned grid_persist = 1;
     // bound on one grid-barrier wait of k_persist: a healthy barrier takes
     // microseconds; past this the kernel records a timeout and returns
@@ -543,6 +545,14 @@ extern "C" int snn_batch_create(const snn_network *net, const snn_routing *rt, i
     return sim_create(net, rt, &params[0], n, off, params, workspace, ws_bytes, stream, out);
 }
 
+// The k_persist instance of a state-access mode; the minimum-delay
+// batching one exists for the shared-memory mode.
+static const void *persist_fn(int mode, bool defer)
+{
+    if (mode == kModeSmem) return defer ? (const void *)k_persist<kModeSmem, true> : (const void *)k_persist<kModeSmem, false>;
+    return mode == kModeVec ? (const void *)k_persist<kModeVec, false> : (const void *)k_persist<kModeScalar, false>;
+}
+
 // Select the persistent kernel in neuron-state mode `mode` with b blocks per
 // SM if that many stay resident (kModeSmem: and the block's quads fit in its
 // shared memory).  Returns whether it was selected.
@@ -552,9 +562,7 @@ static bool shape_persist(snn_sim *s, int mode, int b)
     const int64_t grid = std::min<int64_t>((int64_t)s->sms * b, s->L.tally_rows);
     size_t dyn = 0;
     int64_t cq = 0;
-    const void *fn = mode == kModeSmem ? (const void *)k_persist<kModeSmem>
-                     : mode == kModeVec ? (const void *)k_persist<kModeVec>
-                                        : (const void *)k_persist<kModeScalar>;
+    const void *fn = persist_fn(mode, s->defer);
     if (mode != kModeScalar && !s->vec) return false;
     if (mode == kModeSmem) {
         int smax = 0;
@@ -655,6 +663,10 @@ static int sim_create(const snn_network *net, const snn_routing *rt, const snn_s
         const char *bps = std::getenv("SNN_PERSIST_BLOCKS_PER_SM");
         const int bmax = (bps && std::atoi(bps) > 0) ? std::min(4, std::atoi(bps)) : 4;
         s->coop = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, s->device) == cudaSuccess && coop;
+        // minimum-delay batching on the shared-memory persistent shape
+        // (SNN_PERSIST_DEFER=1 turns it on as the parameter does: tests)
+        const char *edf = std::getenv("SNN_PERSIST_DEFER");
+        s->defer = p->defer_delayed != 0 || (edf && edf[0] == '1');
         s->allow_persist = !(e && e[0] == '0') && s->coop;
         s->allow_smem = !(esm && esm[0] == '0');
         if (s->allow_persist) {
@@ -760,9 +772,7 @@ static int sim_create(const snn_network *net, const snn_routing *rt, const snn_s
 static int launch_persist(snn_sim *s, int32_t T, const Dev &d)
 {
     unsigned long long lim = s->barrier_limit_ns;
-    const void *fn = s->pmode == kModeSmem  ? (const void *)k_persist<kModeSmem>
-                     : s->pmode == kModeVec ? (const void *)k_persist<kModeVec>
-                                            : (const void *)k_persist<kModeScalar>;
+    const void *fn = persist_fn(s->pmode, s->defer);
     // a launch's barrier arrivals (2 per step per block) stay below 2^32
     const int32_t cap = (int32_t)std::min<unsigned long long>(
         0x7FFFFFFFull, (0xFFFFFFFFull / (2ull * s->grid_persist)) - 1ull);

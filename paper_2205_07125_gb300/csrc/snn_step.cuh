@@ -460,18 +460,21 @@ __device__ __forceinline__ unsigned int deliver_run(const Dev &d, int tm, unsign
     return n;
 }
 
-// a6 for the staged work of one routing round, all warps of the block: a
-// piece per warp (4 synapses per lane, every load in flight before the
-// reductions), then short segments a lane each.
-__device__ __forceinline__ void deliver_staged(const Dev &d, int tm, const Stage &sg, unsigned int nl,
-                                               unsigned int ns)
+// a6 for staged lists (pieces lng[0, nl), short segments sht[0, ns)) by
+// the warps [w0, w0 + nwarp) of the block: a piece per warp (4 synapses per
+// lane, every load in flight before the reductions), then short segments a
+// lane each.  Delays count from slot tm (the spikes' step).  Returns the
+// synapses this thread delivered.
+__device__ __forceinline__ unsigned int deliver_lists(const Dev &d, int tm, const unsigned long long *lng,
+                                                      unsigned int nl, const unsigned long long *sht,
+                                                      unsigned int ns, int w0, int nwarp)
 {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, wid = (int)(threadIdx.x >> 5) - w0;
     unsigned int ev = 0;
     const unsigned int units = nl + (ns + 31u) / 32u;
-    for (unsigned int u = (unsigned int)wid; u < units; u += kWarps) {
+    for (unsigned int u = (unsigned int)wid; u < units; u += (unsigned int)nwarp) {
         if (u < nl) {
-            const unsigned long long e = sg.lng[u];
+            const unsigned long long e = lng[u];
             const unsigned long long o = e >> 8;
             const unsigned int n = (unsigned int)(e & 0xFFu);
             uint32_t td[kPiece / 32];
@@ -497,7 +500,7 @@ __device__ __forceinline__ void deliver_staged(const Dev &d, int tm, const Stage
         } else {
             const unsigned int x = (u - nl) * 32u + (unsigned int)lane;
             if (x < ns) {
-                const unsigned long long e = sg.sht[x];
+                const unsigned long long e = sht[x];
                 const unsigned long long o = e >> 8;
                 const unsigned int n = (unsigned int)(e & 0xFFu);
                 // 4 loads in flight, then their reductions
@@ -522,22 +525,98 @@ __device__ __forceinline__ void deliver_staged(const Dev &d, int tm, const Stage
             }
         }
     }
-    tally_add(sg, 0, ev);
+    return ev;
 }
 
-// a4 + a5 + a6 for the nr <= kRound spikes spk[0 .. nr) by the whole block:
-// the level-1 and level-2 entries of all of them are numbered through and
-// taken a thread each, so one spike's entries go out together.  Each
-// level-2 entry's delivery is staged in shared memory as soon as the entry is
-// read; the fill-counter reservation of a thread's last entry is left in
-// flight during the delivery and its exchange write done after it.  Counters
-// of step parity par.
-__device__ __forceinline__ void route_round(const Dev &d, int par, int tm, const uint32_t *spk, unsigned int nr,
-                                            const Stage &sg)
+// a6 for the staged work of one routing round, all warps of the block.
+__device__ __forceinline__ void deliver_staged(const Dev &d, int tm, const Stage &sg, unsigned int nl,
+                                               unsigned int ns)
+{
+    tally_add(sg, 0, deliver_lists(d, tm, sg.lng, nl, sg.sht, ns, 0, kWarps));
+}
+
+// Minimum-delay batching (k_persist): the synapses of delay >= 2 of a
+// step's segments are not needed before step t + 2, so a block keeps their
+// staged lists from one step's routing to the next and delivers them while
+// its other warps walk the next step's routing tables (a latency chain that
+// leaves the reduction units idle).  Lists by step parity.
+constexpr int kDefLong = 256, kDefShort = 512;
+constexpr int kTravWarps = 4;  // warps that walk the tables while the others deliver
+struct Deferred {
+    unsigned long long lng[2][kDefLong];
+    unsigned long long sht[2][kDefShort];
+    unsigned int nl[2], ns[2];
+};
+
+// The lists in a deferring k_persist, nothing in the others.
+template <bool ON>
+struct DeferSlot {
+    Deferred df;
+    __device__ Deferred *get() { return &df; }
+};
+template <>
+struct DeferSlot<false> {
+    __device__ Deferred *get() { return nullptr; }
+};
+
+// Stage the run of n synapses at o: a short run on the short list, a long
+// one cut into pieces.  What does not fit is delivered by this thread at
+// once (slot base tm: delivering early is exact, the run's slots are read
+// later).  Returns the synapses delivered here.
+__device__ __forceinline__ unsigned int stage_run(const Dev &d, int tm, unsigned long long o, unsigned int n,
+                                                  unsigned long long *lng, unsigned int *nl, unsigned int capl,
+                                                  unsigned long long *sht, unsigned int *ns, unsigned int caps)
+{
+    unsigned int ev = 0;
+    if (n <= kShortSeg) {
+        const unsigned int sb = atomicAdd(ns, 1u);
+        if (sb < caps) sht[sb] = (o << 8) | n;
+        else ev += deliver_run(d, tm, o, n);
+    } else {
+        const unsigned int np = (n + kPiece - 1u) / kPiece;
+        unsigned int pb = atomicAdd(nl, np);
+        for (unsigned int j = 0; j < np; ++j, ++pb) {
+            const unsigned long long oo = o + (unsigned long long)j * kPiece;
+            const unsigned int m = min(kPiece, n - j * kPiece);
+            if (pb < capl) lng[pb] = (oo << 8) | m;
+            else ev += deliver_run(d, tm, oo, m);
+        }
+    }
+    return ev;
+}
+
+// What a thread owes after walking its entries: the exchange write of its
+// last entry (kind 1 bucket, 2 inbox; the fill-counter reservation stays in
+// flight meanwhile), synapses it delivered itself, overflow bits.
+struct Pending {
+    int pk;
+    unsigned int ppos;
+    ulonglong2 pslot;
+    unsigned long long pval;
+    unsigned int ev, ovf;
+};
+
+// Barrier of the block, or of its threads [0, nthr) (named barrier 1).
+__device__ __forceinline__ void sync_part(int nthr)
+{
+    if (nthr == kThreads) __syncthreads();
+    else asm volatile("bar.sync 1, %0;" ::"r"(nthr) : "memory");
+}
+
+// a4 + a5 for the nr <= kRound spikes at positions b0 .. b0+nr of the step's
+// list, by the threads [0, nthr) (whole warps): the level-1 and level-2
+// entries of all of them are numbered through and taken a thread each, so
+// one spike's entries go out together.  Each level-2 entry's delivery is
+// staged in shared memory as soon as the entry is read: all of the segment
+// on the round's lists, or with df its delay-1 head (the synapses the next
+// step reads; segments are sorted by delay) there and the rest on df's lists
+// of parity cur.  Counters of step parity par.
+__device__ __forceinline__ Pending route_traverse(const Dev &d, int par, int tm, unsigned int b0, unsigned int nr,
+                                                  const Stage &sg, int nthr, Deferred *df, int cur)
 {
     const int lane = threadIdx.x & 31;
     if (threadIdx.x < nr) {
-        const uint32_t i = spk[threadIdx.x];
+        const uint32_t i = d.spk_step[b0 + threadIdx.x];
         const uint2 a = d.row[i], b = d.row[i + 1];
         sg.e0[threadIdx.x] = a.x;
         sg.f0[threadIdx.x] = a.y;
@@ -549,7 +628,7 @@ __device__ __forceinline__ void route_round(const Dev &d, int par, int tm, const
         *sg.nl = 0;
         *sg.ns = 0;
     }
-    __syncthreads();
+    sync_part(nthr);
     if (threadIdx.x < 32) {
         // inclusive scans of the counts (kRound <= 32: one warp)
         uint32_t v1 = (unsigned int)lane < nr ? sg.pre1[lane + 1] : 0u;
@@ -571,24 +650,20 @@ __device__ __forceinline__ void route_round(const Dev &d, int par, int tm, const
             sg.pre2[0] = 0;
         }
     }
-    __syncthreads();
+    sync_part(nthr);
     uint32_t *bcnt = bucket_cnt_of(d, par);
     uint32_t *icnt = inbox_cnt_of(d, par);
     const uint32_t N1 = sg.pre1[nr], N = N1 + sg.pre2[nr];
-    unsigned int ev = 0, l1_loc = 0, l1_xvn = 0, ovf = 0;
+    unsigned int l1_loc = 0, l1_xvn = 0;
     unsigned int cls[4] = {0, 0, 0, 0};
-    // the exchange write still to do: kind 1 bucket, 2 inbox
-    int pk = 0;
-    unsigned int ppos = 0;
-    ulonglong2 pslot = make_ulonglong2(0ull, 0ull);
-    unsigned long long pval = 0;
-    for (uint32_t x = threadIdx.x; x < N; x += kThreads) {
-        if (pk == 1) {
-            if (ppos < pslot.y) d.bucket[pslot.x + ppos] = (uint32_t)pval;
-            else ovf |= kStBucket;
-        } else if (pk == 2) {
-            if (ppos < pslot.y) d.inbox[pslot.x + ppos] = pval;
-            else ovf |= kStInbox;
+    Pending pn{0, 0u, make_ulonglong2(0ull, 0ull), 0ull, 0u, 0u};
+    for (uint32_t x = threadIdx.x; x < N; x += (uint32_t)nthr) {
+        if (pn.pk == 1) {
+            if (pn.ppos < pn.pslot.y) d.bucket[pn.pslot.x + pn.ppos] = (uint32_t)pn.pval;
+            else pn.ovf |= kStBucket;
+        } else if (pn.pk == 2) {
+            if (pn.ppos < pn.pslot.y) d.inbox[pn.pslot.x + pn.ppos] = pn.pval;
+            else pn.ovf |= kStInbox;
         }
         if (x < N1) {
             // a4: one level-1 entry per destination VN, appended to bucket (p, g)
@@ -596,10 +671,10 @@ __device__ __forceinline__ void route_round(const Dev &d, int par, int tm, const
             const uint32_t e = sg.e0[k] + (x - sg.pre1[k]);
             const int g = d.l1_vn[e];
             const uint32_t kp = d.l1_pair[e];
-            pslot = d.bucket_slot[kp];
-            ppos = atomicAdd(&bcnt[(size_t)kp * kPairStride], 1u);
-            pval = e;
-            pk = 1;
+            pn.pslot = d.bucket_slot[kp];
+            pn.ppos = atomicAdd(&bcnt[(size_t)kp * kPairStride], 1u);
+            pn.pval = e;
+            pn.pk = 1;
             if (g == sg.part[k] / d.vn_size) ++l1_loc;
             else ++l1_xvn;
         } else {
@@ -610,24 +685,19 @@ __device__ __forceinline__ void route_round(const Dev &d, int par, int tm, const
             const uint32_t f = sg.f0[k] + (y - sg.pre2[k]);
             const DevL2 l = d.l2[f];
             const uint32_t kq = d.l2_pair[f];
-            pslot = d.inbox_slot[kq];
-            ppos = atomicAdd(&icnt[(size_t)kq * kPairStride], 1u);
-            const unsigned long long off = l.off & kOffMask;  // (the high bits count delay-1 synapses)
-            pval = (off << kLenBits) | (unsigned long long)l.len;
-            pk = 2;
-            if (l.len <= kShortSeg) {
-                const unsigned int sb = atomicAdd(sg.ns, 1u);
-                if (sb < (unsigned int)kShortCap) sg.sht[sb] = (off << 8) | l.len;
-                else ev += deliver_run(d, tm, off, l.len);  // list full: this thread delivers it
+            pn.pslot = d.inbox_slot[kq];
+            pn.ppos = atomicAdd(&icnt[(size_t)kq * kPairStride], 1u);
+            const unsigned long long off = l.off & kOffMask;
+            pn.pval = (off << kLenBits) | (unsigned long long)l.len;
+            pn.pk = 2;
+            if (!df) {
+                pn.ev += stage_run(d, tm, off, l.len, sg.lng, sg.nl, kLongCap, sg.sht, sg.ns, kShortCap);
             } else {
-                const unsigned int np = (l.len + kPiece - 1u) / kPiece;
-                unsigned int pb = atomicAdd(sg.nl, np);
-                for (unsigned int j = 0; j < np; ++j, ++pb) {
-                    const unsigned long long o = off + (unsigned long long)j * kPiece;
-                    const unsigned int n = min(kPiece, l.len - j * kPiece);
-                    if (pb < (unsigned int)kLongCap) sg.lng[pb] = (o << 8) | n;
-                    else ev += deliver_run(d, tm, o, n);
-                }
+                const unsigned int n1 = (unsigned int)(l.off >> kOffBits);  // delay-1 head of the segment
+                if (n1) pn.ev += stage_run(d, tm, off, n1, sg.lng, sg.nl, kLongCap, sg.sht, sg.ns, kShortCap);
+                if (l.len > n1)
+                    pn.ev += stage_run(d, tm, off + n1, l.len - n1, df->lng[cur], &df->nl[cur], kDefLong,
+                                       df->sht[cur], &df->ns[cur], kDefShort);
             }
             // per-class tallies without a dynamically indexed (local-memory) array
             cls[0] += l.cls == 0;
@@ -636,36 +706,30 @@ __device__ __forceinline__ void route_round(const Dev &d, int par, int tm, const
             cls[3] += l.cls == 3;
         }
     }
-    __syncthreads();
-    deliver_staged(d, tm, sg, min(*sg.nl, (unsigned int)kLongCap), min(*sg.ns, (unsigned int)kShortCap));
-    if (pk == 1) {
-        if (ppos < pslot.y) d.bucket[pslot.x + ppos] = (uint32_t)pval;
-        else ovf |= kStBucket;
-    } else if (pk == 2) {
-        if (ppos < pslot.y) d.inbox[pslot.x + ppos] = pval;
-        else ovf |= kStInbox;
-    }
-    if (ovf) atomicOr(&d.ctrl->status, ovf);
-    tally_add(sg, 0, ev);
     tally_add(sg, 1, l1_loc);
     tally_add(sg, 2, l1_xvn);
 #pragma unroll
     for (int k = 0; k < 4; ++k) tally_add(sg, 3 + k, cls[k]);
-    __syncthreads();
+    return pn;
 }
 
-// a4-a6 for the spikes [lo, hi) of step t's spike list, in rounds of up to
-// kRound, and their copy into the raster at `head` (all threads call).
-__device__ __forceinline__ void route_range(const Dev &d, long long t, long long head, const Stage &sg,
-                                            unsigned int lo, unsigned int hi)
+// a6 of a round (whole block, after a block barrier) and the exchange write
+// each thread still owes (pn from route_traverse; zero for the threads that
+// did not walk).
+__device__ __forceinline__ void route_finish(const Dev &d, int tm, const Stage &sg, Pending pn)
 {
-    const int par = (int)(t & 1);
-    const int tm = (int)(t % d.D);
-    if (head >= 0)
-        for (unsigned int k = lo + threadIdx.x; k < hi; k += kThreads) d.spk[head + k] = d.spk_step[k];
-    for (unsigned int b = lo; b < hi; b += kRound)
-        route_round(d, par, tm, d.spk_step + b, min(hi - b, (unsigned int)kRound), sg);
+    deliver_staged(d, tm, sg, min(*sg.nl, (unsigned int)kLongCap), min(*sg.ns, (unsigned int)kShortCap));
+    if (pn.pk == 1) {
+        if (pn.ppos < pn.pslot.y) d.bucket[pn.pslot.x + pn.ppos] = (uint32_t)pn.pval;
+        else pn.ovf |= kStBucket;
+    } else if (pn.pk == 2) {
+        if (pn.ppos < pn.pslot.y) d.inbox[pn.pslot.x + pn.ppos] = pn.pval;
+        else pn.ovf |= kStInbox;
+    }
+    if (pn.ovf) atomicOr(&d.ctrl->status, pn.ovf);
+    tally_add(sg, 0, pn.ev);
 }
+
 
 // ---------------------------------------------------------------- a1-a6
 // How a step reaches its neurons' state:
@@ -1051,7 +1115,8 @@ __device__ __forceinline__ void update_step(const Dev &d, long long t, StepShare
 // Second half of step t (all threads call): a4-a6 for this block's share of
 // the step's spikes, an equal share of the list for every block, and their
 // raster copy.
-__device__ __forceinline__ void route_step(const Dev &d, long long t, StepShared &sh, bool carried = false)
+__device__ __forceinline__ void route_step(const Dev &d, long long t, StepShared &sh, bool carried = false,
+                                           Deferred *df = nullptr, int cur = 0)
 {
     const Stage sg{sh.lng, sh.sht, &sh.nl, &sh.ns, sh.tally, sh.e0, sh.f0, sh.pre1, sh.pre2, sh.part};
     Ctrl *c = d.ctrl;
@@ -1073,12 +1138,38 @@ __device__ __forceinline__ void route_step(const Dev &d, long long t, StepShared
         }
     }
     if (threadIdx.x < kWarps * kTally) (&sh.tally[0][0])[threadIdx.x] = 0u;
+    if (df && threadIdx.x == 0) {
+        df->nl[cur] = 0u;
+        df->ns[cur] = 0u;
+    }
     __syncthreads();
     const unsigned long long S = sh.tot;
     const unsigned int lo = (unsigned int)(S * blockIdx.x / gridDim.x);
     const unsigned int hi = (unsigned int)(S * (blockIdx.x + 1) / gridDim.x);
-    if (lo >= hi) return;
-    route_range(d, t, sh.head, sg, lo, hi);
+    const int par = (int)(t & 1);
+    const int tm = (int)(t % d.D);
+    // with df: the delay >= 2 lists of step t - 1 (slot base of that step),
+    // delivered by some warps while the others walk the first round's tables
+    const int prev = cur ^ 1;
+    const int tmp = (int)((t - 1 + d.D) % d.D);
+    const unsigned int pl = df ? min(df->nl[prev], (unsigned int)kDefLong) : 0u;
+    const unsigned int ps = df ? min(df->ns[prev], (unsigned int)kDefShort) : 0u;
+    if (df && lo >= hi) tally_add(sg, 0, deliver_lists(d, tmp, df->lng[prev], pl, df->sht[prev], ps, 0, kWarps));
+    for (unsigned int b = lo; b < hi; b += kRound) {
+        const unsigned int nr = min(hi - b, (unsigned int)kRound);
+        const bool split = df && b == lo;
+        Pending pn{0, 0u, make_ulonglong2(0ull, 0ull), 0ull, 0u, 0u};
+        if (!split || threadIdx.x < kTravWarps * 32)
+            pn = route_traverse(d, par, tm, b, nr, sg, split ? kTravWarps * 32 : kThreads, df, cur);
+        else
+            tally_add(sg, 0,
+                      deliver_lists(d, tmp, df->lng[prev], pl, df->sht[prev], ps, kTravWarps, kWarps - kTravWarps));
+        __syncthreads();
+        route_finish(d, tm, sg, pn);
+        __syncthreads();
+    }
+    if (sh.head >= 0)
+        for (unsigned int k = lo + threadIdx.x; k < hi; k += kThreads) d.spk[sh.head + k] = d.spk_step[k];
     // tallies of the routed spikes into this block's row (no other block
     // touches it: the reductions never wait on another block)
     __syncthreads();
@@ -1155,12 +1246,15 @@ __global__ void k_advance(const Dev d, int steps)
 // ref in dynamic shared memory from the launch's start to its end, and the
 // second barrier of a step is split: between its arrival and its wait the
 // block computes the next step's drive and leak (pre_update), which need no
-// other block's data.
-template <int MODE>
+// other block's data.  DEFER: minimum-delay batching (Deferred); the last
+// step's delay >= 2 lists are delivered before the launch ends.
+template <int MODE, bool DEFER>
 __global__ void __launch_bounds__(kThreads, 3) k_persist(const Dev d, int T, unsigned long long limit_ns,
                                                          int skip_arrival)
 {
     __shared__ StepShared sh;
+    __shared__ DeferSlot<DEFER> dslot;
+    Deferred *df = dslot.get();
     __shared__ __align__(8) unsigned long long s_bar;
     extern __shared__ __align__(128) unsigned char s_dyn[];
     Ctrl *c = d.ctrl;
@@ -1188,6 +1282,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_persist(const Dev d, int T, uns
         sh.t0 = *(volatile long long *)&c->t;
         sh.headv = *(volatile long long *)&c->head[slot3(sh.t0)];
         sh.prevS = 0u;
+        if constexpr (DEFER) {
+            df->nl[0] = df->nl[1] = 0u;
+            df->ns[0] = df->ns[1] = 0u;
+        }
     }
     if (threadIdx.x < kPTab) sh.th[threadIdx.x] = d.th32[threadIdx.x];
     __syncthreads();
@@ -1215,7 +1313,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_persist(const Dev d, int T, uns
         prefetch_own(d, sh);
         if (!grid_wait(c, 2ull * s, limit_ns, &sh.word)) break;
         const unsigned long long e = prof ? global_ns() : 0;
-        route_step(d, t, sh, true);
+        route_step(d, t, sh, true, df, s & 1);
         // the next step's input-free update runs while the barrier completes
         grid_arrive(c);
         if constexpr (MODE == kModeSmem) {
@@ -1229,6 +1327,26 @@ __global__ void __launch_bounds__(kThreads, 3) k_persist(const Dev d, int T, uns
             ns[1] += (e - b) + (g - f);
         }
         ++done;
+    }
+    if constexpr (DEFER) {
+        if (T > 0 && done == T) {
+            // the last step's delay >= 2 lists: their slots are read by the
+            // next launch's steps, after this one ends
+            const Stage sg{sh.lng, sh.sht, &sh.nl, &sh.ns, sh.tally, sh.e0, sh.f0, sh.pre1, sh.pre2, sh.part};
+            const int last = (T - 1) & 1;
+            if (threadIdx.x < kWarps * kTally) (&sh.tally[0][0])[threadIdx.x] = 0u;
+            __syncthreads();
+            tally_add(sg, 0,
+                      deliver_lists(d, (int)((t0 + T - 1) % d.D), df->lng[last],
+                                    min(df->nl[last], (unsigned int)kDefLong), df->sht[last],
+                                    min(df->ns[last], (unsigned int)kDefShort), 0, kWarps));
+            __syncthreads();
+            if (threadIdx.x < kTally) {
+                unsigned long long a = 0;
+                for (int w = 0; w < kWarps; ++w) a += sh.tally[w][threadIdx.x];
+                if (a) atomicAdd(&d.tally[(size_t)blockIdx.x * C_N + C_EVENTS + threadIdx.x], a);
+            }
+        }
     }
     if constexpr (MODE == kModeSmem) {
         // after a timeout, give this block's last bulk copy a bounded wait

@@ -21,10 +21,11 @@ def snn():
     return m
 
 
-@pytest.fixture(params=["persistent", "persistent-global", "graph"])
+@pytest.fixture(params=["persistent", "persistent-global", "graph", "persistent-deferred"])
 def path(request, monkeypatch):
     monkeypatch.setenv("SNN_PERSIST", "0" if request.param == "graph" else "1")
     monkeypatch.setenv("SNN_PERSIST_SMEM", "0" if request.param == "persistent-global" else "1")
+    monkeypatch.setenv("SNN_PERSIST_DEFER", "1" if request.param == "persistent-deferred" else "0")
     return request.param
 
 

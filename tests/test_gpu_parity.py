@@ -82,13 +82,15 @@ def _compare(sim, o, T, rec, t0=0):
     return c, r
 
 
-@pytest.fixture(params=["persistent", "persistent-global", "graph"])
+@pytest.fixture(params=["persistent", "persistent-global", "graph", "persistent-deferred"])
 def path(request, monkeypatch):
     """Run a test on the persistent kernel (neuron state resident in shared
-    memory where it fits, or read from global memory every step) and on the
-    CUDA-graph path."""
+    memory where it fits, or read from global memory every step; with
+    minimum-delay batching of the delay >= 2 synapses) and on the CUDA-graph
+    path."""
     monkeypatch.setenv("SNN_PERSIST", "0" if request.param == "graph" else "1")
     monkeypatch.setenv("SNN_PERSIST_SMEM", "0" if request.param == "persistent-global" else "1")
+    monkeypatch.setenv("SNN_PERSIST_DEFER", "1" if request.param == "persistent-deferred" else "0")
     return request.param
 
 

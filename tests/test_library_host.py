@@ -401,3 +401,14 @@ def test_device_builders_check_arguments_before_the_device(snn):
     bnet = snn.Network.from_synth(big)
     assert lib.snn_routing_build_device(ctypes.byref(bnet.s), np.zeros(4, np.int32).ctypes.data, 1, 1,
                                         ctypes.byref(rp), fake, 1 << 30, None, ctypes.byref(h)) == -5
+
+
+def test_defer_parameter_is_checked(snn):
+    """defer_delayed is 0 or 1 (minimum-delay batching switch); anything else
+    is rejected before any device work."""
+    g = synth.make_network(synth.NetConfig(name="t", M=64, P=4, n_vn=2, K=4, uniform_all=True, dmax=2))
+    rt = snn.Routing(snn.Network.from_synth(g), oracle.partition_planted(64, 4), 4, 2)
+    nb = ctypes.c_size_t(0)
+    for v, rc in ((0, 0), (1, 0), (2, -1), (-1, -1)):
+        p = snn.sim_params(defer_delayed=v)
+        assert snn._lib.snn_sim_workspace_bytes(rt.h, ctypes.byref(p), ctypes.byref(nb)) == rc
