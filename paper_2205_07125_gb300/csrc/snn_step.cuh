@@ -29,8 +29,11 @@
 // next step, cleared during the one after).
 //
 // Two ways to run: k_persist, one cooperative launch for T steps with
-// bounded grid barriers, and the CUDA-graph path, k_update and k_route per
-// step with programmatic dependent launch.
+// bounded grid barriers (each split into arrival and wait, with work that
+// needs no other block in between), and the CUDA-graph path, k_update and
+// k_route per step with programmatic dependent launch.  k_persist<kModeSmem,
+// true> adds minimum-delay batching: the delay >= 2 synapses of a step are
+// delivered during the next step's table walk.
 #pragma once
 
 #include <cuda_runtime.h>
