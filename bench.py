@@ -352,13 +352,23 @@ def routing_report(dc, info, rt):
     }
 
 
+def _code_only(text: str) -> str:
+    """C++ source without comments and blank lines (string literals in these
+    files hold no comment markers)."""
+    import re
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(l.rstrip() for l in text.splitlines() if l.strip())
+
+
 def kernel_source_sha() -> str:
-    """Hash of the step-kernel sources (a capture taken on other sources is stale)."""
+    """Hash of the step-kernel code, comments left out (a capture taken on
+    other code is stale)."""
     import hashlib
     hs = hashlib.sha256()
     for f in ("snn_step.cuh", "snn_sim.cu"):
-        with open(os.path.join(ROOT, "paper_2205_07125_gb300", "csrc", f), "rb") as fh:
-            hs.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2205_07125_gb300", "csrc", f), encoding="utf-8") as fh:
+            hs.update(_code_only(fh.read()).encode())
     return hs.hexdigest()[:16]
 
 
