@@ -74,3 +74,28 @@ def test_bench_rejects_short_warmup(argv):
     import bench
     with pytest.raises(SystemExit):
         bench.main(argv)
+
+
+def test_study_helpers_against_the_oracle():
+    """bench.py's partition-study helpers: the numpy objective equals the
+    oracle's cut, the id relabelling keeps every synapse (and the planted
+    mapping follows the ids), the planted mapping is the generator's."""
+    import numpy as np
+    import bench
+    import oracle
+    import synth
+    cfg = synth.NetConfig(name="t", M=2000, P=8, n_vn=2, K=12, uniform_all=False, n_part=8, n_vn_t=2,
+                          n_remote=2, seed=6)
+    g = synth.make_network(cfg)
+    part = np.random.default_rng(2).integers(0, 8, g.M).astype(np.int32)
+    assert bench._objective(g, part) == oracle.cut(g, part)
+    assert bench._objective(g, part, chunk=37) == oracle.cut(g, part)
+    assert np.array_equal(bench.oracle_free_planted(g.M, 8), oracle.partition_planted(g.M, 8))
+    h, perm = bench._permuted(g, 5)
+    src_g = np.repeat(np.arange(g.M), np.diff(g.syn_ptr))
+    src_h = np.repeat(np.arange(h.M), np.diff(h.syn_ptr))
+    a = sorted(zip(perm[src_g].tolist(), perm[g.tgt.astype(np.int64)].tolist(), g.w.tolist(), g.d.tolist()))
+    b = sorted(zip(src_h.tolist(), h.tgt.tolist(), h.w.tolist(), h.d.tolist()))
+    assert a == b
+    planted = oracle.partition_planted(g.M, 8)
+    assert oracle.cut(h, planted[np.argsort(perm)]) == oracle.cut(g, planted)
