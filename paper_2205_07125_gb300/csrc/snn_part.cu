@@ -41,7 +41,8 @@ struct PCtl {
     alignas(128) unsigned long long bar;  // grid-barrier arrivals of the running launch
     alignas(128) unsigned int nsel;       // members found by the selection
     alignas(128) unsigned int status;
-    unsigned int seed_id;                 // t == 1: lowest unassigned id (atomicMin)
+    unsigned int seed_id;                 // seed of part k: lowest unassigned id (t == 1, atomicMin) or the
+                                          // drawn one (t > 1); all ones between parts
     int stop;                             // part k is full
     int na;                               // members that joined in the last round
     long long wk, nk, n_un;               // weight and size of part k, unassigned neurons
