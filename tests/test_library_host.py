@@ -412,3 +412,42 @@ def test_defer_parameter_is_checked(snn):
     for v, rc in ((0, 0), (1, 0), (2, -1), (-1, -1)):
         p = snn.sim_params(defer_delayed=v)
         assert snn._lib.snn_sim_workspace_bytes(rt.h, ctypes.byref(p), ctypes.byref(nb)) == rc
+
+
+def test_min_delay_schedule_is_exact():
+    """The minimum-delay batching schedule on a delay ring of D = max delay + 1
+    slots, modelled with the kernels' slot arithmetic (slot of a synapse of
+    delay d from a spike of step s: (s mod D + d) mod D): delivering a step's
+    delay-1 synapses in the step and its delay >= 2 synapses one step later
+    (from the same base s) leaves every slot with the same sum when its step
+    reads and clears it, for random spike trains and delays 1..8."""
+    rng = np.random.default_rng(0)
+    dmax = 8
+    D = dmax + 1
+    M, T = 50, 400
+    for trial in range(5):
+        syn = [(rng.integers(0, M, 20), rng.integers(1, dmax + 1, 20), rng.integers(-50, 50, 20))
+               for _ in range(M)]
+        spikes = [np.flatnonzero(rng.random(M) < 0.05) for _ in range(T)]
+        ring_a = np.zeros((D, M), np.int64)
+        ring_b = np.zeros((D, M), np.int64)
+        deferred = []
+        for t in range(T):
+            # step t reads and clears its slot
+            ra, rb = ring_a[t % D].copy(), ring_b[t % D].copy()
+            assert np.array_equal(ra, rb), (trial, t)
+            ring_a[t % D] = 0
+            ring_b[t % D] = 0
+            # schedule A: everything in step t
+            for i in spikes[t]:
+                tg, dl, w = syn[i]
+                np.add.at(ring_a, ((t % D + dl) % D, tg), w)
+            # schedule B: the previous step's delay >= 2 lists, then this step's delay-1 heads
+            for (s, tg, dl, w) in deferred:
+                np.add.at(ring_b, ((s % D + dl) % D, tg), w)
+            deferred = []
+            for i in spikes[t]:
+                tg, dl, w = syn[i]
+                one = dl == 1
+                np.add.at(ring_b, ((t % D + dl[one]) % D, tg[one]), w[one])
+                deferred.append((t, tg[~one], dl[~one], w[~one]))
