@@ -179,10 +179,21 @@ def forward_fp32(net: AdjointNet, G: np.ndarray, lam: np.ndarray, T: int) -> Tra
     return tr
 
 
-def _gather(net: AdjointNet, G: np.ndarray, gring: np.ndarray, t: int, D: int) -> np.ndarray:
-    """sum_{j->k, d} G[pop k][pop j] w gVpre_k(t+d) for every j (float64)."""
+def _gather_tables(net: AdjointNet, G: np.ndarray):
+    """Loop invariants of the gather: the synapses' sources, the products
+    G[pop k][pop j] w (float64) and the position of each synapse's (delay,
+    target) in a [D, M] table of adjoints indexed by delay."""
     src = net.src
-    val = G[net.pop[net.tgt], net.pop[src]] * net.w * gring[(t + net.d) % D, net.tgt]
+    gw = G[net.pop[net.tgt], net.pop[src]] * net.w
+    pos = net.d * net.M + net.tgt
+    return src, gw, pos
+
+
+def _gather(net: AdjointNet, tabs, ahead: np.ndarray) -> np.ndarray:
+    """sum_{j->k, d} G[pop k][pop j] w gVpre_k(t+d) for every j (float64);
+    ahead[d] holds gVpre(t+d) for d = 0..D-1 (tabs from _gather_tables)."""
+    src, gw, pos = tabs
+    val = gw * ahead.reshape(-1)[pos]
     return np.bincount(src, weights=val, minlength=net.M)
 
 
@@ -197,14 +208,18 @@ def backward(net: AdjointNet, G: np.ndarray, lam: np.ndarray, tr: Trajectory, gr
     c = 2.0 ** -10
     a = net.pop
     direct = np.asarray(grates, np.float64)[a] / (T * net.pop_sizes()[a])
-    gring = np.zeros((D, M))
+    # ahead[d] = gVpre(t + d) for the step t being processed (d = 0..D-1)
+    ahead = np.zeros((D, M))
+    tabs = _gather_tables(net, G)
     gV = np.zeros(M)
     dG = np.zeros_like(G)
     dlam = np.zeros(net.n_pop)
     theta = float(net.v_th)
     gap = float(net.v_th) - float(net.v_reset)
     for t in range(T - 1, -1, -1):
-        gS = direct + c * _gather(net, G, gring, t, D)
+        ahead = np.roll(ahead, 1, axis=0)
+        ahead[0] = 0.0
+        gS = direct + c * _gather(net, tabs, ahead)
         x = tr.vpre[t].astype(np.float64) - theta
         if smooth:
             s = 1.0 / (1.0 + np.exp(-beta * x))
@@ -214,7 +229,7 @@ def backward(net: AdjointNet, G: np.ndarray, lam: np.ndarray, tr: Trajectory, gr
             sg = 1.0 / (1.0 + beta * np.abs(x)) ** 2
             gvp = gV * (1.0 - tr.spk[t]) + gS * sg
             gvp = np.where(tr.refr[t], 0.0, gvp)
-        gring[t % D] = gvp
+        ahead[0] = gvp
         gV = float(net.alpha) * gvp
         dG += c * np.stack([np.bincount(a, weights=gvp * tr.A[t][:, b], minlength=net.n_pop)
                             for b in range(net.n_pop)], axis=1)
