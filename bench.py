@@ -31,6 +31,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "synaptic events/s & sim steps/s vs HBM roofline; batched/adjoint vs plain"
+DELIVERY = {"ring": 0, "arrival": 1, "auto": 2}
 UNIT = "synaptic events/s"
 
 
@@ -177,7 +178,8 @@ def run_ours(args):
     info = rt.info()
     raster_cap = int(cfg.M * (K + W) * 0.002) + 100000
     prm = snn.sim_params(cfg.dyn, raster_cap=raster_cap, raster_steps=K + W, steps_per_graph=32,
-                         pin_host_tables=1, defer_delayed=1 if args.defer else 0)
+                         pin_host_tables=1, defer_delayed=1 if args.defer else 0,
+                         delivery=0 if args.defer else DELIVERY[args.delivery])
     sim = snn.Sim(net, rt, prm, device=dev)
     choice, tuned_ms = sim.autotune(200)
     setup_s = time.time() - t_setup
@@ -981,6 +983,10 @@ def main(argv=None):
                          "adjoint: forward + surrogate-gradient backward of a 131,072-neuron network; "
                          "partition: partition-quality and relay-policy study (JSON report); "
                          "partition-device: Algorithm 1 on the GPU vs the host greedy (JSON report)")
+    ap.add_argument("--delivery", choices=tuple(DELIVERY), default="auto",
+                    help="ring: every delay at the spike step into the delay ring; arrival: each step "
+                         "writes only the next step's input slot (delayed runs queued by arrival step); "
+                         "auto: the autotuner picks")
     ap.add_argument("--study-neurons", type=int, default=65536)
     ap.add_argument("--no-scale", action="store_true",
                     help="--config partition-device: the study network only")

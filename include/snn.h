@@ -67,6 +67,78 @@ typedef struct {
     const float *v0;          /* [M] */
 } snn_network;
 
+/* ------------------------------------------------------------------ model */
+/*
+ * The first setup stage of the paper's statement of the problem (Sec. I:
+ * a simulation model is generated, then dispersed over the GPUs; the
+ * partitioning and routing of Sec. IV take it as input).  The paper's model
+ * is a scanned human brain, which is not available; snn_model_build makes a
+ * seeded synthetic LIF network in its place:
+ *   - M neurons in n_parts planted partitions of contiguous ids (partition p
+ *     holds ids floor(pM/P) .. floor((p+1)M/P)-1), planted VNs = runs of
+ *     vn_size partitions; the first round(frac_exc * size) ids of each
+ *     planted partition are excitatory;
+ *   - exactly syn_per_neuron out-synapses per neuron, drawn with replacement,
+ *     no autapses: uniform over all other neurons (uniform = 1), or
+ *     n_same_part in the own partition, n_same_vn in the other partitions of
+ *     the own VN and n_remote outside it;
+ *   - int16 weights in units of 2^-10 mV: excitatory lround(mu_e + sd_e z)
+ *     clamped to [1, 32767], inhibitory -lround(mu_i + sd_i z) clamped to
+ *     [-32768, -1], z = (sum of 12 uniforms) - 6 computed exactly in double;
+ *   - delays uniform in 1..max_delay steps; V0 = v_reset + u (v_th - v_reset);
+ *   - randomness: splitmix64 seeded per neuron from `seed`, so the network
+ *     has the same bits for any thread count and on any host.
+ * The model owns its arrays; snn_model_network gives a borrowed
+ * snn_network view of them (valid until snn_model_destroy) for
+ * snn_partition, snn_routing_build and snn_sim_create.
+ */
+typedef struct {
+    int64_t n_neurons;
+    int32_t n_parts, vn_size;
+    int32_t syn_per_neuron;
+    int32_t uniform;                             /* 1: targets uniform over all other neurons */
+    int32_t n_same_part, n_same_vn, n_remote;    /* locality mix (sum = syn_per_neuron) */
+    int32_t max_delay;                           /* 1..16 */
+    uint64_t seed;
+    double v_reset, v_th;                        /* range of the initial potentials (mV) */
+    double frac_exc, mu_e, sd_e, mu_i, sd_i;
+} snn_model_params;
+
+typedef struct snn_model snn_model;
+
+/* Workloads: 4,096 neurons / 4 partitions / 100 uniform synapses, delay 1;
+ * 1,048,576 / 64 partitions in VNs of 4 / 1,000 synapses (70/20/10 locality,
+ * delays 1-8); the per-GPU share of the paper's 10-billion-neuron run on
+ * 2,000 GPUs (Sec. V): 5,000,000 / 256 partitions in VNs of 4 / 1,000
+ * synapses; the adjoint network: 131,072 / 8 partitions in VNs of 4 / 500
+ * synapses (the same mix). */
+#define SNN_WORKLOAD_TINY        0
+#define SNN_WORKLOAD_SCALE       1
+#define SNN_WORKLOAD_PAPER_SHARE 2
+#define SNN_WORKLOAD_ADJOINT     4
+/* Fill p with a workload's recipe.  Errors: SNN_E_ARG (unknown workload). */
+int snn_model_params_preset(int32_t workload, snn_model_params *p);
+/* Generate the network (host, all cores).  Errors: SNN_E_ARG (invalid
+ * parameters: M < 2 or >= 2^28, a mix that does not sum to syn_per_neuron,
+ * n_parts not a multiple of vn_size, E >= 2^40), SNN_E_NOMEM. */
+int snn_model_build(const snn_model_params *params, snn_model **out);
+/* Borrowed view of the model's arrays; is_exc (may be NULL) receives the
+ * [M] excitatory flags (snn_adjoint_create takes them).  Errors: SNN_E_ARG. */
+int snn_model_network(const snn_model *model, snn_network *net, const uint8_t **is_exc);
+/*
+ * Write the model as an edge-list file: 8 magic bytes "SNNMODL1", then
+ * little-endian u64 M, u64 E, u32 max_delay, u32 0, then syn_ptr i64[M+1],
+ * syn_tgt u32[E], syn_w i16[E], syn_d u8[E], v0 f32[M], is_exc u8[M]
+ * (source-major: neuron i's synapses are syn_ptr[i] .. syn_ptr[i+1]-1).
+ * Errors: SNN_E_ARG (NULL arguments, the file cannot be written).
+ */
+int snn_model_save(const snn_model *model, const char *path);
+/* Read a file written by snn_model_save, checking that the synapse list is
+ * well formed (offsets, target ids < M, delays within 1..max_delay).
+ * Errors: SNN_E_ARG (unreadable or malformed file), SNN_E_NOMEM. */
+int snn_model_load(const char *path, snn_model **out);
+void snn_model_destroy(snn_model *model);
+
 /* -------------------------------------------------------------- partition */
 #define SNN_PART_PLANTED 0   /* contiguous id ranges: part(i) = p, floor(pM/P) <= i < floor((p+1)M/P) */
 #define SNN_PART_GREEDY  1   /* Algorithm 1 (greedy growth, best of `iters`) */
@@ -266,7 +338,28 @@ typedef struct {
                                   * each step's delay >= 2 synapses are delivered during the next
                                   * step's table walk (exact; slower on GB300 for the scale
                                   * workload, off by default) */
+    /* SNN_DELIVER_*: when a spike's synapses reach their targets' input.
+     *   RING (default): every delay at the spike's step, into a delay ring
+     *     of max_delay + 1 slots of M int32 (the slots a step writes span
+     *     the whole ring);
+     *   ARRIVAL: each step writes only the next step's input slot: the
+     *     delay-1 run of each routed segment at once, the run of delay d >= 2
+     *     queued on the list of step t + d - 1 and delivered by that step
+     *     (segments are sorted by delay).  Two input slots of M int32 stay
+     *     hot in L2 however large the ring would be.  Needs max_delay <= 8
+     *     and segments of at most 65535 synapses (else SNN_E_RANGE);
+     *   AUTO: the workspace holds both; snn_autotune picks the faster (until
+     *     then ARRIVAL when it is available, else RING).
+     * Sums are integers, so every mode gives the same results bit for bit. */
+    int32_t delivery;
+    /* capacity of each arrival list as a fraction of its exact worst case
+     * (1.0, the default, never overflows; overflow sets SNN_E_CAPACITY) */
+    float arrival_frac;
 } snn_sim_params;
+
+#define SNN_DELIVER_RING    0
+#define SNN_DELIVER_ARRIVAL 1
+#define SNN_DELIVER_AUTO    2
 
 /* Fill p with the defaults (no records, exact capacities, 32 steps/graph). */
 void snn_sim_params_default(snn_sim_params *p);
@@ -490,7 +583,8 @@ int snn_profile_phases(snn_sim *sim, int32_t T, double *phase_ms);
  *   level-1 entries, level-2 entries and synaptic events of this call.
  * Scratch: the level-1 bucket and level-2 inbox regions of the sim's
  * workspace, so the call must not overlap snn_step on the same sim.
- * Runs on the sim's stream and synchronises it before returning.
+ * Runs on the sim's stream, with the sim's device current (the caller's
+ * current device is restored), and synchronises the stream before returning.
  * Errors: SNN_E_ARG (n < 0, NULL pointers with n > 0, an id >= M),
  * SNN_E_CAPACITY (the spikes need more bucket/inbox room than the
  * workspace holds), SNN_E_CUDA.
@@ -511,7 +605,10 @@ int snn_deliver_spikes(snn_sim *sim, const uint32_t *ids, int64_t n, int32_t *ou
  * no cudaFree.
  *   - The first call on a device looks up the array's device address once
  *     (cudaGetSymbolAddress, with that device current); make that first
- *     call before any stream capture.
+ *     call before any stream capture.  The address stays cached for the
+ *     life of the process: after cudaDeviceReset (or a reset of the
+ *     device's primary context) the library's module is unloaded and this
+ *     call must not be used again in that process.
  *   - Size limit: n * (4 B * longest level-1 row + 8 B * most level-2
  *     entries of any neuron) + 512 B must fit in the array; larger calls
  *     return SNN_E_RANGE and do nothing.

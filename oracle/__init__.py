@@ -192,6 +192,42 @@ def group_greedy(net, part_of, P: int, n_vn: int, iters: int = 4, seed: int = 7)
     return out, int(cost[0]) + (int(cost[1]) << 64)
 
 
+# ---------------------------------------------------------------- model file
+class ModelFile:
+    """A network read from an edge-list file (the library's snn_model_save
+    format), with this package's own reader: 8 magic bytes "SNNMODL1", then
+    little-endian u64 M, u64 E, u32 max_delay, u32 0, then syn_ptr i64[M+1],
+    tgt u32[E], w i16[E], d u8[E], v0 f32[M], is_exc u8[M]."""
+
+    MAGIC = b"SNNMODL1"
+
+    def __init__(self, path: str):
+        with open(path, "rb") as f:
+            head = f.read(32)
+            if len(head) != 32 or head[:8] != self.MAGIC:
+                raise ValueError("not a model file: %s" % path)
+            M, E = (int(x) for x in np.frombuffer(head[8:24], "<u8"))
+            self.max_delay = int(np.frombuffer(head[24:28], "<u4")[0])
+
+            def take(dtype, n):
+                a = np.fromfile(f, dtype=dtype, count=n)
+                if a.shape[0] != n:
+                    raise ValueError("truncated model file: %s" % path)
+                return a
+
+            self.syn_ptr = take("<i8", M + 1)
+            self.tgt = take("<u4", E)
+            self.w = take("<i2", E)
+            self.d = take("u1", E)
+            self.v0 = take("<f4", M)
+            self.is_exc = take("u1", M)
+        self.M, self.E = M, E
+
+
+def load_model(path: str) -> ModelFile:
+    return ModelFile(path)
+
+
 # ---------------------------------------------------------------- simulator
 class Oracle:
     """Sequential simulator over a network (borrowed arrays) and a mapping.

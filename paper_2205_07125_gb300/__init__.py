@@ -32,6 +32,7 @@ _lib = ctypes.CDLL(_SO)
 
 SNN_PART_PLANTED, SNN_PART_GREEDY, SNN_PART_RANDOM = 0, 1, 2
 SNN_GROUP_CONTIGUOUS, SNN_GROUP_GREEDY = 0, 1
+SNN_DELIVER_RING, SNN_DELIVER_ARRIVAL, SNN_DELIVER_AUTO = 0, 1, 2
 SNN_E_CAPACITY = -3
 
 _i32, _i64, _u64, _u32, _f32, _f64, _vp = (ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64,
@@ -42,6 +43,13 @@ _i32, _i64, _u64, _u32, _f32, _f64, _vp = (ctypes.c_int32, ctypes.c_int64, ctype
 class snn_network(ctypes.Structure):
     _fields_ = [("n_neurons", _i64), ("syn_ptr", _vp), ("syn_tgt", _vp), ("syn_w", _vp),
                 ("syn_d", _vp), ("v0", _vp)]
+
+
+class snn_model_params(ctypes.Structure):
+    _fields_ = [("n_neurons", _i64), ("n_parts", _i32), ("vn_size", _i32), ("syn_per_neuron", _i32),
+                ("uniform", _i32), ("n_same_part", _i32), ("n_same_vn", _i32), ("n_remote", _i32),
+                ("max_delay", _i32), ("seed", _u64), ("v_reset", _f64), ("v_th", _f64), ("frac_exc", _f64),
+                ("mu_e", _f64), ("sd_e", _f64), ("mu_i", _f64), ("sd_i", _f64)]
 
 
 class snn_partition_params(ctypes.Structure):
@@ -75,7 +83,8 @@ class snn_sim_params(ctypes.Structure):
                 ("drive_seed", _u64), ("raster_cap", _i64), ("raster_steps", _i64),
                 ("hash_steps", _i64), ("cur_every", _i32), ("cur_slots", _i32),
                 ("bucket_frac", _f32), ("inbox_frac", _f32), ("steps_per_graph", _i32),
-                ("pin_host_tables", _i32), ("defer_delayed", _i32)]
+                ("pin_host_tables", _i32), ("defer_delayed", _i32), ("delivery", _i32),
+                ("arrival_frac", _f32)]
 
 
 COUNT_FIELDS = ("steps", "spikes", "events", "direct", "direct_xvn", "l1_local", "l1_xvn",
@@ -99,6 +108,12 @@ def _sig(name, res, args):
 
 _P = ctypes.POINTER
 _lib_strerror = _sig("snn_strerror", ctypes.c_char_p, [ctypes.c_int])
+_sig("snn_model_params_preset", ctypes.c_int, [_i32, _P(snn_model_params)])
+_sig("snn_model_build", ctypes.c_int, [_P(snn_model_params), _P(_vp)])
+_sig("snn_model_network", ctypes.c_int, [_vp, _P(snn_network), _P(_vp)])
+_sig("snn_model_save", ctypes.c_int, [_vp, ctypes.c_char_p])
+_sig("snn_model_load", ctypes.c_int, [ctypes.c_char_p, _P(_vp)])
+_sig("snn_model_destroy", None, [_vp])
 _sig("snn_partition", ctypes.c_int, [_P(snn_network), _i32, _P(snn_partition_params), _vp,
                                      _P(snn_partition_stats)])
 _sig("snn_partition_device_params_default", None, [_P(snn_partition_device_params)])
@@ -152,7 +167,8 @@ _sig("snn_adjoint_backward", ctypes.c_int, [_vp, _vp, _vp, _vp])
 _sig("snn_adjoint_read_spikes", ctypes.c_int, [_vp, _vp, _i64, _P(_i64)])
 _sig("snn_adjoint_destroy", None, [_vp])
 
-EXPORTS = ("snn_strerror", "snn_partition", "snn_partition_device_params_default",
+EXPORTS = ("snn_strerror", "snn_model_params_preset", "snn_model_build", "snn_model_network", "snn_model_save",
+           "snn_model_load", "snn_model_destroy", "snn_partition", "snn_partition_device_params_default",
            "snn_partition_device_workspace_bytes", "snn_partition_device", "snn_routing_build",
            "snn_routing_export", "snn_routing_build_device_workspace_bytes", "snn_routing_build_device", "snn_routing_info_get",
            "snn_routing_groups", "snn_routing_connections", "snn_routing_destroy",
@@ -199,6 +215,79 @@ class Network:
     @classmethod
     def from_synth(cls, net):
         return cls(net.syn_ptr, net.tgt, net.w, net.d, net.v0)
+
+
+SNN_WORKLOAD_TINY, SNN_WORKLOAD_SCALE, SNN_WORKLOAD_PAPER_SHARE, SNN_WORKLOAD_ADJOINT = 0, 1, 2, 4
+_WORKLOADS = {"tiny": SNN_WORKLOAD_TINY, "scale": SNN_WORKLOAD_SCALE, "paper": SNN_WORKLOAD_PAPER_SHARE,
+              "adjoint": SNN_WORKLOAD_ADJOINT}
+
+
+def model_params(workload=None, **kw) -> snn_model_params:
+    """snn_model_params of a workload preset ("tiny", "scale", "paper",
+    "adjoint" or an SNN_WORKLOAD_* code) with keyword overrides."""
+    p = snn_model_params()
+    code = _WORKLOADS.get(workload, workload) if workload is not None else SNN_WORKLOAD_TINY
+    _ck(_lib.snn_model_params_preset(int(code), ctypes.byref(p)), "snn_model_params_preset")
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+class Model:
+    """A network owned by the library (snn_model_build / snn_model_load); its
+    arrays are exposed as numpy views, valid while the model lives."""
+
+    def __init__(self, h):
+        self.h = h
+        net = snn_network()
+        exc = _vp()
+        _ck(_lib.snn_model_network(h, ctypes.byref(net), ctypes.byref(exc)), "snn_model_network")
+        M = int(net.n_neurons)
+        P = ctypes.POINTER
+
+        def view(ptr, ctype, n):
+            return np.ctypeslib.as_array(ctypes.cast(ptr, P(ctype)), shape=(n,)) if n else np.zeros(0)
+
+        self.M = M
+        self.syn_ptr = view(net.syn_ptr, ctypes.c_int64, M + 1)
+        self.E = int(self.syn_ptr[M])
+        self.tgt = view(net.syn_tgt, ctypes.c_uint32, self.E)
+        self.w = view(net.syn_w, ctypes.c_int16, self.E)
+        self.d = view(net.syn_d, ctypes.c_uint8, self.E)
+        self.v0 = view(net.v0, ctypes.c_float, M)
+        self.is_exc = view(exc, ctypes.c_uint8, M)
+
+    @classmethod
+    def build(cls, params: snn_model_params = None, **kw) -> "Model":
+        p = params if params is not None else model_params(**kw)
+        h = _vp()
+        _ck(_lib.snn_model_build(ctypes.byref(p), ctypes.byref(h)), "snn_model_build")
+        return cls(h.value)
+
+    @classmethod
+    def load(cls, path: str) -> "Model":
+        h = _vp()
+        _ck(_lib.snn_model_load(os.fsencode(path), ctypes.byref(h)), "snn_model_load")
+        return cls(h.value)
+
+    def save(self, path: str):
+        _ck(_lib.snn_model_save(self.h, os.fsencode(path)), "snn_model_save")
+
+    def network(self) -> "Network":
+        """Network view of the model's arrays (no copy; keeps the model alive)."""
+        net = Network(self.syn_ptr, self.tgt, self.w, self.d, self.v0)
+        net._model = self
+        return net
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.snn_model_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
 
 
 _PART_MODES = {"planted": SNN_PART_PLANTED, "greedy": SNN_PART_GREEDY, "random": SNN_PART_RANDOM}

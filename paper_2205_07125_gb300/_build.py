@@ -13,8 +13,11 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
           "-I", INCLUDE]
+SYNTH = os.path.join(os.path.dirname(HERE), "synth", "synth.c")
 SOURCES = {
     "snn_host.o": ["snn_host.cpp"],
+    "snn_model.o": ["snn_model.cpp"],
+    "synth.o": [SYNTH],
     "snn_sim.o": ["snn_sim.cu"],
     "snn_adjoint.o": ["snn_adjoint.cu"],
     "snn_part.o": ["snn_part.cu"],
@@ -33,7 +36,7 @@ def _stale() -> bool:
     if not os.path.exists(OUT):
         return True
     t = os.path.getmtime(OUT)
-    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "snn.h")]
+    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "snn.h"), SYNTH]
     return any(os.path.getmtime(p) > t for p in deps)
 
 
@@ -50,6 +53,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
         cmd = [nvcc] + COMMON + ARCH + ["-fmad=false", "-c", src, "-o", o]
         if src.endswith(".cpp"):
             cmd = [nvcc] + COMMON + ["-x", "c++", "-c", src, "-o", o]
+        elif src.endswith(".c"):
+            # the seeded network generator (C, OpenMP), behind snn_model_build
+            cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-fvisibility=hidden",
+                   "-c", src, "-o", o]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
@@ -61,7 +68,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if verbose and out:
             print(out.decode(errors="replace"))
     tmp = OUT + ".tmp%d" % os.getpid()
-    link = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread"]
+    link = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread", "-lgomp"]
     r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
     if r.returncode != 0:
         raise RuntimeError("link failed: %s\n%s" % (" ".join(link), r.stdout.decode(errors="replace")))

@@ -2,6 +2,7 @@
 // the device simulation (snn_sim.cu).  Not part of the public ABI.
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 #include <cstring>
 #include <functional>
@@ -104,6 +105,11 @@ struct snn_routing {
     std::vector<int64_t> csr;          // [M+1] first synapse of each internal neuron
     std::vector<uint16_t> src_part;    // [M] internal partition of each internal neuron
     int64_t n_l1 = 0, n_l2 = 0;
+    // Delivery by arrival step, from the level-2 entries (computed once, on
+    // first use): the longest segment; segments holding a synapse of delay
+    // >= 2; the sum over segments of min(max_delay - 1, synapses of delay >= 2)
+    // (-1: not computed yet).
+    mutable std::atomic<int64_t> seg_maxlen{-1}, seg_delayed{-1}, seg_runs{-1};
 };
 
 namespace snn {

@@ -106,6 +106,60 @@ __global__ void __launch_bounds__(kThreads) k_fo_deliver(const FoArgs a)
     if (lane == 0 && ev) atomicAdd(a.ev, ev);
 }
 
+// ---------------------------------------------------------------- delivery by arrival step
+// Delay counts of every level-2 segment (the segment's synapses are sorted by
+// delay): dcnt[f] holds c[k] = synapses of delay <= k + 1, k = 0..7, as 16-bit
+// fields (segments of at most 65535 synapses, delays up to 8).
+__global__ void __launch_bounds__(kThreads) k_delay_counts(const DevL2 *l2, const uint32_t *syn_td, long long n_l2,
+                                                           uint4 *dcnt)
+{
+    for (long long f = (long long)blockIdx.x * kThreads + threadIdx.x; f < n_l2;
+         f += (long long)gridDim.x * kThreads) {
+        const DevL2 l = l2[f];
+        const unsigned long long o = l.off & kOffMask;
+        uint32_t c[kMaxArr] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (uint32_t k = 0; k < l.len; ++k) {
+            const uint32_t dl = syn_td[o + k] >> kTgtBits;
+#pragma unroll
+            for (int x = 0; x < kMaxArr; ++x) c[x] += dl <= (uint32_t)x;
+        }
+        dcnt[f] = make_uint4(c[0] | (c[1] << 16), c[2] | (c[3] << 16), c[4] | (c[5] << 16), c[6] | (c[7] << 16));
+    }
+}
+
+// Checkpoint of a sim with delivery by arrival step, next step t: move the
+// state into the delay-ring form a checkpoint holds.  Step t's input slot
+// goes into ring slot t mod D; every run still queued (lists of steps t ..
+// t + n_arr - 2, arriving at step s + 1) is added into ring slot (s + 1) mod
+// D.  The caller then clears the lists and lets steps < t + D consume their
+// ring slots (Ctrl::inject_until), so the sim continues unchanged.
+__global__ void __launch_bounds__(kThreads) k_materialize(const Dev d, long long t)
+{
+    const long long stride = (long long)gridDim.x * kThreads;
+    const long long x0 = (long long)blockIdx.x * kThreads + threadIdx.x;
+    int32_t *in = d.acc + (size_t)(t & 1) * (size_t)d.M;
+    int32_t *slot = d.ring + (size_t)(t % d.D) * (size_t)d.M;
+    for (long long j = x0; j < d.M; j += stride) {
+        slot[j] = (int32_t)((uint32_t)slot[j] + (uint32_t)in[j]);
+        in[j] = 0;
+    }
+    for (int k = 0; k + 1 < d.n_arr; ++k) {
+        const long long s = t + k;
+        const int li = (int)(s % d.n_arr);
+        const unsigned long long n =
+            min((unsigned long long)d.arr_cnt[(size_t)li * kPairStride], d.arr_cap);
+        int32_t *dst = d.ring + (size_t)((s + 1) % d.D) * (size_t)d.M;
+        const unsigned long long *recs = d.arr + (size_t)li * d.arr_cap;
+        for (long long r = x0; r < (long long)n; r += stride) {
+            const unsigned long long rec = recs[r];
+            const unsigned long long o = rec >> kLenBits;
+            const unsigned int len = (unsigned int)(rec & kLenMask);
+            for (unsigned int y = 0; y < len; ++y)
+                atomicAdd(dst + (d.syn_td[o + y] & kTgtMask), (int32_t)d.syn_w[o + y]);
+        }
+    }
+}
+
 // ---------------------------------------------------------------- host helpers
 struct Region {
     size_t off = 0, bytes = 0;
@@ -119,7 +173,10 @@ struct Layout {
     Region spk, spk_step, raster_off, hash, cur_rec, counters, ctrl;
     Region fwd, fo_cnt;  // snn_deliver_spikes: global -> internal map, scratch counters
     Region phase_ns;
+    Region acc, arr, arr_cnt, dcnt;  // delivery by arrival step (absent with SNN_DELIVER_RING)
     size_t total = 0;
+    int n_arr = 0;                   // arrival lists (the largest delay); 0: no arrival regions
+    uint64_t arr_cap = 0;            // runs per arrival list
     std::vector<uint64_t> bucket_base_h, inbox_base_h;
     std::vector<uint32_t> bucket_cap_h, inbox_cap_h;
     int64_t tally_rows = 0;
@@ -145,6 +202,47 @@ static int64_t step_grid(int64_t M)
 // Tally rows: one per block of either launch shape (a persistent grid is
 // capped to the rows there are).
 constexpr int64_t kMinTallyRows = 2048;
+
+// Level-2 statistics of delivery by arrival step (cached in the routing):
+// the longest segment, the segments holding a synapse of delay >= 2 and the
+// sum over segments of min(max_delay - 1, synapses of delay >= 2).
+static void arrival_stats(const snn_routing *rt)
+{
+    if (rt->seg_runs.load() >= 0) return;
+    const int nt = resolve_threads(0);
+    std::vector<int64_t> mx((size_t)nt, 0), dl((size_t)nt, 0), rn((size_t)nt, 0);
+    const int64_t lim = std::max(0, rt->max_delay - 1);
+    parallel_for(rt->n_l2, nt, [&](int64_t lo, int64_t hi, int k) {
+        int64_t a = 0, b = 0, c = 0;
+        for (int64_t f = lo; f < hi; ++f) {
+            const L2Entry &e = rt->l2[f];
+            const int64_t n1 = (int64_t)(e.off >> kOffBits), late = (int64_t)e.len - n1;
+            a = std::max<int64_t>(a, e.len);
+            b += late > 0;
+            c += std::min(lim, late);
+        }
+        mx[k] = a;
+        dl[k] = b;
+        rn[k] = c;
+    });
+    int64_t a = 0, b = 0, c = 0;
+    for (int k = 0; k < nt; ++k) {
+        a = std::max(a, mx[k]);
+        b += dl[k];
+        c += rn[k];
+    }
+    rt->seg_maxlen.store(a);
+    rt->seg_delayed.store(b);
+    rt->seg_runs.store(c);
+}
+
+// Whether the routing allows delivery by arrival step: delays up to
+// kMaxArr and segments short enough for the 16-bit delay counts.
+static bool arrival_possible(const snn_routing *rt)
+{
+    arrival_stats(rt);
+    return rt->max_delay <= kMaxArr && rt->seg_maxlen.load() <= 0xFFFF;
+}
 
 static int make_layout(const snn_routing *rt, const snn_sim_params *p, Layout &L, int32_t n_net = 0)
 {
@@ -218,6 +316,30 @@ static int make_layout(const snn_routing *rt, const snn_sim_params *p, Layout &L
     place(L, L.fwd, rt->identity ? 0 : sizeof(uint32_t) * (size_t)M);
     place(L, L.fo_cnt, 64);
     place(L, L.phase_ns, 2 * sizeof(unsigned long long));
+    // SNN_DELIVERY=0|1|2 overrides the parameter (tests of every path)
+    int delivery = p->delivery;
+    if (const char *e = std::getenv("SNN_DELIVERY"))
+        if (e[0] >= '0' && e[0] <= '2' && e[1] == 0) delivery = e[0] - '0';
+    if (delivery != SNN_DELIVER_RING && !p->defer_delayed) {
+        if (!arrival_possible(rt)) {
+            if (delivery == SNN_DELIVER_ARRIVAL) return SNN_E_RANGE;
+        } else {
+            // each arrival list's exact worst case: with t_ref >= max_delay - 2 a
+            // neuron spikes at most once in the max_delay - 1 steps that feed a
+            // list (at most one run per segment), else one run per delay >= 2
+            // present in the segment
+            L.n_arr = rt->max_delay;
+            const int64_t worst = p->t_ref >= L.n_arr - 2 ? rt->seg_delayed.load() : rt->seg_runs.load();
+            double c = std::ceil((double)worst * (double)p->arrival_frac);
+            if (c > (double)worst) c = (double)worst;
+            if (c > 4294967295.0) return SNN_E_RANGE;  // 32-bit fill counters
+            L.arr_cap = (uint64_t)c;
+            place(L, L.acc, 2 * sizeof(int32_t) * (size_t)M);
+            place(L, L.arr, sizeof(unsigned long long) * (size_t)L.n_arr * (size_t)L.arr_cap);
+            place(L, L.arr_cnt, sizeof(uint32_t) * kPairStride * (size_t)L.n_arr);
+            place(L, L.dcnt, sizeof(uint4) * (size_t)rt->n_l2);
+        }
+    }
     return SNN_OK;
 }
 
@@ -232,6 +354,9 @@ static bool params_ok(const snn_sim_params *p)
     if (!(p->bucket_frac >= 0.0f) || !(p->inbox_frac >= 0.0f)) return false;
     if (p->steps_per_graph < 1 || p->steps_per_graph > 256) return false;
     if (p->defer_delayed != 0 && p->defer_delayed != 1) return false;
+    if (p->delivery < SNN_DELIVER_RING || p->delivery > SNN_DELIVER_AUTO) return false;
+    if (!(p->arrival_frac >= 0.0f)) return false;
+    if (p->defer_delayed && p->delivery == SNN_DELIVER_ARRIVAL) return false;
     return true;
 }
 
@@ -297,6 +422,7 @@ struct snn_sim {
     bool pdl = true;       // programmatic dependent launch between step kernels
     bool persist = false;  // one cooperative launch per snn_step (k_persist)
     bool defer = false;    // k_persist with minimum-delay batching (shared-memory state only)
+    bool arrival = false;  // delivery by arrival step active (the workspace holds its regions)
     unsigned grid_persist = 1;
     // bound on one grid-barrier wait of k_persist: a healthy barrier takes
     // microseconds; past this the kernel records a timeout and returns
@@ -331,6 +457,8 @@ extern "C" void snn_sim_params_default(snn_sim_params *p)
     p->bucket_frac = 1.0f;
     p->inbox_frac = 1.0f;
     p->steps_per_graph = 32;
+    p->delivery = SNN_DELIVER_RING;
+    p->arrival_frac = 1.0f;
 }
 
 extern "C" int snn_sim_workspace_bytes(const snn_routing *rt, const snn_sim_params *p, size_t *bytes)
@@ -373,6 +501,14 @@ static int upload_tables(snn_sim *s)
     }
     CK(up(L.l2_pair, rt->l2_pair.data()));
     CK(up(L.csr, rt->csr.data()));
+    if (L.dcnt.bytes && rt->n_l2 > 0) {
+        // delay counts of every segment, from the uploaded tables
+        const long long g = std::min<long long>((rt->n_l2 + kThreads - 1) / kThreads, (long long)s->sms * 8);
+        k_delay_counts<<<(unsigned)std::max(1ll, g), kThreads, 0, st>>>(
+            (const DevL2 *)(w + L.l2.off), (const uint32_t *)(w + L.syn_td.off), (long long)rt->n_l2,
+            (uint4 *)(w + L.dcnt.off));
+        CK(cudaGetLastError());
+    }
     if (!rt->identity) CK(up(L.gid, rt->perm_inv.data()));
     if (!rt->identity) CK(up(L.fwd, rt->perm_fwd.data()));
     {
@@ -403,6 +539,8 @@ static int reset_state(snn_sim *s)
     if (L.raster_off.bytes) CK(cudaMemsetAsync(w + L.raster_off.off, 0, L.raster_off.bytes, st));
     if (L.hash.bytes) CK(cudaMemsetAsync(w + L.hash.off, 0, L.hash.bytes, st));
     if (L.cur_rec.bytes) CK(cudaMemsetAsync(w + L.cur_rec.off, 0, L.cur_rec.bytes, st));
+    if (L.acc.bytes) CK(cudaMemsetAsync(w + L.acc.off, 0, L.acc.bytes, st));
+    if (L.arr_cnt.bytes) CK(cudaMemsetAsync(w + L.arr_cnt.off, 0, L.arr_cnt.bytes, st));
     Ctrl c;
     std::memset(&c, 0, sizeof(c));
     const bool rec = s->prm.raster_cap > 0 && s->prm.raster_steps > 0;
@@ -429,8 +567,15 @@ static cudaError_t launch_half(snn_sim *s, int half, int k, cudaStream_t st)
         cfg.attrs = attr;
         cfg.numAttrs = 1;
     }
-    if (half == 0) cudaLaunchKernelEx(&cfg, s->vec ? k_update<kModeVec> : k_update<kModeScalar>, s->dev, k);
-    else cudaLaunchKernelEx(&cfg, k_route, s->dev, k);
+    if (s->arrival) {
+        if (half == 0)
+            cudaLaunchKernelEx(&cfg, s->vec ? k_update<kModeVec, true> : k_update<kModeScalar, true>, s->dev, k);
+        else cudaLaunchKernelEx(&cfg, k_route<true>, s->dev, k);
+    } else {
+        if (half == 0)
+            cudaLaunchKernelEx(&cfg, s->vec ? k_update<kModeVec, false> : k_update<kModeScalar, false>, s->dev, k);
+        else cudaLaunchKernelEx(&cfg, k_route<false>, s->dev, k);
+    }
     return cudaGetLastError();
 }
 
@@ -547,10 +692,16 @@ extern "C" int snn_batch_create(const snn_network *net, const snn_routing *rt, i
 
 // The k_persist instance of a state-access mode; the minimum-delay
 // batching one exists for the shared-memory mode.
-static const void *persist_fn(int mode, bool defer)
+static const void *persist_fn(int mode, bool defer, bool arr)
 {
-    if (mode == kModeSmem) return defer ? (const void *)k_persist<kModeSmem, true> : (const void *)k_persist<kModeSmem, false>;
-    return mode == kModeVec ? (const void *)k_persist<kModeVec, false> : (const void *)k_persist<kModeScalar, false>;
+    if (arr) {
+        if (mode == kModeSmem) return (const void *)k_persist<kModeSmem, false, true>;
+        return mode == kModeVec ? (const void *)k_persist<kModeVec, false, true>
+                                : (const void *)k_persist<kModeScalar, false, true>;
+    }
+    if (mode == kModeSmem)
+        return defer ? (const void *)k_persist<kModeSmem, true, false> : (const void *)k_persist<kModeSmem, false, false>;
+    return mode == kModeVec ? (const void *)k_persist<kModeVec, false, false> : (const void *)k_persist<kModeScalar, false, false>;
 }
 
 // Select the persistent kernel in neuron-state mode `mode` with b blocks per
@@ -562,7 +713,7 @@ static bool shape_persist(snn_sim *s, int mode, int b)
     const int64_t grid = std::min<int64_t>((int64_t)s->sms * b, s->L.tally_rows);
     size_t dyn = 0;
     int64_t cq = 0;
-    const void *fn = persist_fn(mode, s->defer);
+    const void *fn = persist_fn(mode, s->defer, s->arrival);
     if (mode != kModeScalar && !s->vec) return false;
     if (mode == kModeSmem) {
         int smax = 0;
@@ -753,12 +904,42 @@ static int sim_create(const snn_network *net, const snn_routing *rt, const snn_s
     d.hash_steps = p->hash_steps;
     d.cur_every = p->cur_every;
     d.cur_slots = p->cur_slots;
+    if (L.n_arr > 0) {
+        d.acc = (int32_t *)(w + L.acc.off);
+        d.arr = (unsigned long long *)(w + L.arr.off);
+        d.arr_cnt = (uint32_t *)(w + L.arr_cnt.off);
+        d.dcnt = (const uint4 *)(w + L.dcnt.off);
+        d.arr_cap = L.arr_cap;
+        // SNN_DELIVER_AUTO starts with delivery by arrival step (snn_autotune
+        // may switch); minimum-delay batching (SNN_PERSIST_DEFER) keeps the ring
+        s->arrival = !s->defer;
+    }
+    d.n_arr = s->arrival ? L.n_arr : 0;
+    if (s->arrival && s->persist) {
+        // the persistent shape again, for its instance with delivery by arrival step
+        const int m = s->pmode, b = s->persist_bps;
+        s->persist = false;
+        for (int bb = b; bb >= 1 && !s->persist; --bb) shape_persist(s, m, bb);
+        cudaGetLastError();
+    }
     finite_thresholds(p->drive_lambda, d.th32, &d.th_fin);
     if (L.n_net > 0) {
         d.net_of = (const uint16_t *)(w + L.net_of.off);
         d.net_drive = (const NetDrive *)(w + L.net_drive.off);
     }
 
+    {
+        // the worst case per spike of snn_deliver_spikes_static: the longest
+        // level-1 row and the most level-2 entries of a neuron
+        int64_t m1 = 0, m2 = 0;
+        for (int64_t k = 0; k < rt->M; ++k) {
+            const uint32_t a = rt->l1_ptr[k], b = rt->l1_ptr[k + 1];
+            m1 = std::max<int64_t>(m1, (int64_t)(b - a));
+            m2 = std::max<int64_t>(m2, (int64_t)rt->l1_l2[b] - (int64_t)rt->l1_l2[a]);
+        }
+        s->static_row_l1 = m1;
+        s->static_row_l2 = m2;
+    }
     rc = upload_tables(s);
     if (!rc) rc = reset_state(s);
     if (rc) {
@@ -772,7 +953,7 @@ static int sim_create(const snn_network *net, const snn_routing *rt, const snn_s
 static int launch_persist(snn_sim *s, int32_t T, const Dev &d)
 {
     unsigned long long lim = s->barrier_limit_ns;
-    const void *fn = persist_fn(s->pmode, s->defer);
+    const void *fn = persist_fn(s->pmode, s->defer, s->arrival);
     // a launch's barrier arrivals (2 per step per block) stay below 2^32
     const int32_t cap = (int32_t)std::min<unsigned long long>(
         0x7FFFFFFFull, (0xFFFFFFFFull / (2ull * s->grid_persist)) - 1ull);
@@ -880,26 +1061,47 @@ extern "C" int snn_profile_phases(snn_sim *s, int32_t T, double *phase_ms)
 // ---------------------------------------------------------------- launch-shape autotuner
 static int read_ctrl(snn_sim *s, Ctrl *c);
 
+// Turn delivery by arrival step on or off (the workspace holds its regions);
+// captured graphs hold the old device view and are dropped.
+static void set_arrival(snn_sim *s, bool on)
+{
+    on = on && s->L.n_arr > 0 && !s->defer;
+    if (on == s->arrival) return;
+    s->arrival = on;
+    s->dev.n_arr = on ? s->L.n_arr : 0;
+    for (cudaGraphExec_t *g : {&s->g1, &s->gU, &s->gP})
+        if (*g) {
+            cudaGraphExecDestroy(*g);
+            *g = nullptr;
+        }
+}
+
 extern "C" int snn_autotune(snn_sim *s, int32_t steps, int32_t *choice, double *best_ms)
 {
     if (!s || steps < 1) return SNN_E_ARG;
     struct Shape {
         bool persist;
         int mode, b;
+        bool arrival;
     };
     std::vector<Shape> cand;
-    if (s->allow_persist)
-        for (int mode : {kModeSmem, kModeVec, kModeScalar})
-            for (int b = 4; b >= 1; --b)
-                if (mode != kModeSmem || s->allow_smem) cand.push_back({true, mode, b});
-    cand.push_back({false, 0, 0});
+    std::vector<bool> dels{false};
+    if (s->L.n_arr > 0 && !s->defer) dels = {true, false};
+    for (bool arr : dels) {
+        if (s->allow_persist)
+            for (int mode : {kModeSmem, kModeVec, kModeScalar})
+                for (int b = 4; b >= 1; --b)
+                    if (mode != kModeSmem || s->allow_smem) cand.push_back({true, mode, b, arr});
+        cand.push_back({false, 0, 0, arr});
+    }
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     double best = 1e300;
-    Shape pick = {s->persist, s->pmode, s->persist_bps};
+    Shape pick = {s->persist, s->pmode, s->persist_bps, s->arrival};
     int rc = SNN_OK;
     for (const Shape &c : cand) {
+        set_arrival(s, c.arrival);
         if (c.persist) {
             s->persist = false;
             if (!shape_persist(s, c.mode, c.b)) continue;
@@ -928,10 +1130,11 @@ extern "C" int snn_autotune(snn_sim *s, int32_t steps, int32_t *choice, double *
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     s->persist = false;
+    set_arrival(s, pick.arrival);
     if (pick.persist) shape_persist(s, pick.mode, pick.b);
     const int rr = reset_state(s);
     if (rc == SNN_OK) rc = rr;
-    if (choice) *choice = pick.persist ? 100 * pick.mode + pick.b : 0;
+    if (choice) *choice = (pick.persist ? 100 * pick.mode + pick.b : 0) + (pick.arrival ? 1000 : 0);
     if (best_ms) *best_ms = best < 1e300 ? best / steps : -1.0;
     return rc;
 }
@@ -985,6 +1188,18 @@ static int run_fanout(snn_sim *s, const FoArgs &a, uint64_t *counts)
     return SNN_OK;
 }
 
+// run_fanout with the sim's device current (the caller's current device is
+// restored afterwards).
+static int run_fanout_on_device(snn_sim *s, const FoArgs &a, uint64_t *counts)
+{
+    int prev = -1;
+    if (cudaGetDevice(&prev) != cudaSuccess) return SNN_E_CUDA;
+    if (prev != s->device && cudaSetDevice(s->device) != cudaSuccess) return SNN_E_CUDA;
+    const int rc = run_fanout(s, a, counts);
+    if (prev != s->device && cudaSetDevice(prev) != cudaSuccess) return SNN_E_CUDA;
+    return rc;
+}
+
 extern "C" int snn_deliver_spikes(snn_sim *s, const uint32_t *ids, int64_t n, int32_t *out,
                                   uint64_t *counts)
 {
@@ -996,7 +1211,7 @@ extern "C" int snn_deliver_spikes(snn_sim *s, const uint32_t *ids, int64_t n, in
     a.cap2 = s->L.inbox.bytes / sizeof(unsigned long long);
     a.cnt = (unsigned int *)(s->ws + s->L.fo_cnt.off);
     a.ev = (unsigned long long *)(s->ws + s->L.fo_cnt.off + 16);
-    return run_fanout(s, a, counts);
+    return run_fanout_on_device(s, a, counts);
 }
 
 // ---------------------------------------------------------------- fan-out without allocation
@@ -1042,18 +1257,8 @@ extern "C" int snn_deliver_spikes_static(snn_sim *s, const uint32_t *ids, int64_
                                          uint64_t *counts)
 {
     if (!s || n < 0 || (n > 0 && (!ids || !out))) return SNN_E_ARG;
-    // worst case per spike: its longest level-1 row and its most level-2 entries
-    if (s->static_row_l1 < 0) {
-        const snn_routing *rt = s->rt;
-        int64_t m1 = 0, m2 = 0;
-        for (int64_t k = 0; k < rt->M; ++k) {
-            const uint32_t a = rt->l1_ptr[k], b = rt->l1_ptr[k + 1];
-            m1 = std::max<int64_t>(m1, (int64_t)(b - a));
-            m2 = std::max<int64_t>(m2, (int64_t)rt->l1_l2[b] - (int64_t)rt->l1_l2[a]);
-        }
-        s->static_row_l1 = m1;
-        s->static_row_l2 = m2;
-    }
+    // worst case per spike (s->static_row_l1 / _l2, found when the sim was
+    // created): its longest level-1 row and its most level-2 entries
     if (n > (int64_t)kStaticScratchBytes) return SNN_E_RANGE;
     const size_t head = 256;
     const size_t need1 = (((size_t)n * (size_t)s->static_row_l1 * sizeof(uint32_t)) + 255) & ~(size_t)255;
@@ -1070,7 +1275,7 @@ extern "C" int snn_deliver_spikes_static(snn_sim *s, const uint32_t *ids, int64_
     a.cap1 = need1 / sizeof(uint32_t);
     a.inbox = (unsigned long long *)(b + head + need1);
     a.cap2 = need2 / sizeof(unsigned long long);
-    return run_fanout(s, a, counts);
+    return run_fanout_on_device(s, a, counts);
 }
 
 extern "C" int64_t snn_launches(const snn_sim *s, int32_t T)
@@ -1102,7 +1307,7 @@ extern "C" int snn_sync_status(snn_sim *s)
     int rc = read_ctrl(s, &c);
     if (rc) return rc;
     if (c.status & kStTimeout) return SNN_E_TIMEOUT;
-    if (c.status & (kStBucket | kStInbox)) return SNN_E_CAPACITY;
+    if (c.status & (kStBucket | kStInbox | kStArrival)) return SNN_E_CAPACITY;
     return SNN_OK;
 }
 
@@ -1295,6 +1500,18 @@ extern "C" int snn_save_state(snn_sim *s, void *buf, size_t capb)
     int rc = read_ctrl(s, &c);
     if (rc) return rc;
     const Layout &L = s->L;
+    if (s->arrival) {
+        // delivery by arrival step: the input slot and the queued runs move
+        // into the delay ring the checkpoint holds (the sim goes on unchanged)
+        const unsigned g = (unsigned)std::max(1, s->sms * 4);
+        k_materialize<<<g, kThreads, 0, s->stream>>>(s->dev, (long long)c.t);
+        CK(cudaGetLastError());
+        CK(cudaMemsetAsync(s->ws + L.arr_cnt.off, 0, L.arr_cnt.bytes, s->stream));
+        const long long until = c.t + L.D;
+        CK(cudaMemcpyAsync(s->ws + L.ctrl.off + offsetof(Ctrl, inject_until), &until, sizeof(until),
+                           cudaMemcpyHostToDevice, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+    }
     char *b = (char *)buf;
     CkptHeader h{kCkptMagic, s->rt->M, L.D, 0, c.t};
     std::memcpy(b, &h, sizeof(h));
@@ -1329,12 +1546,17 @@ extern "C" int snn_load_state(snn_sim *s, const void *buf, size_t bytes)
     Ctrl c;
     std::memset(&c, 0, sizeof(c));
     c.t = h.t;
+    // delivery by arrival step: the ring holds the restored partial sums of
+    // steps h.t .. h.t + D - 1, which those steps consume
+    c.inject_until = s->arrival ? h.t + L.D : 0;
     for (int k = 0; k < 3; ++k) c.head[k] = -1;  // records restart empty and stay off after a restore
     CK(cudaMemcpy(s->dev.ctrl, &c, sizeof(c), cudaMemcpyHostToDevice));
     if (h.t < s->prm.hash_steps)
         CK(cudaMemset(s->dev.hash + 2 * h.t, 0, sizeof(unsigned long long) * 2 * (size_t)(s->prm.hash_steps - h.t)));
     CK(cudaMemset(s->dev.bucket_cnt, 0, L.bucket_cnt.bytes));
     CK(cudaMemset(s->dev.inbox_cnt, 0, L.inbox_cnt.bytes));
+    if (L.acc.bytes) CK(cudaMemset(s->ws + L.acc.off, 0, L.acc.bytes));
+    if (L.arr_cnt.bytes) CK(cudaMemset(s->ws + L.arr_cnt.off, 0, L.arr_cnt.bytes));
     return SNN_OK;
 }
 

@@ -56,7 +56,15 @@ constexpr int kOwn = 64;        // own spikes of a step whose tables a block pre
 constexpr int kPairStride = 32;
 
 // status bits
-constexpr uint32_t kStBucket = 1u, kStInbox = 2u, kStRaster = 4u, kStTimeout = 8u;
+constexpr uint32_t kStBucket = 1u, kStInbox = 2u, kStRaster = 4u, kStTimeout = 8u, kStArrival = 16u;
+
+// Delivery by arrival step (Dev::n_arr > 0): a step delivers only into the
+// input slot of the next step.  The delay-1 runs of its segments go there at
+// once; the run of delay d >= 2 is queued on the list of step t + d - 1 and
+// delivered by that step.  Runs staged in shared memory per routing round
+// before one reservation per list and round: kArrPool runs, kMaxArr lists.
+constexpr int kArrPool = 1024;
+constexpr int kMaxArr = 8;
 
 // counter slots: steps and spikes in Dev::counters (closing thread), the
 // others in each block's tally row
@@ -67,6 +75,8 @@ struct Ctrl {
     long long t;              // next step to run
     long long head[3];        // raster write head of step t at slot t mod 3 (-1: recording stopped)
     long long rec_steps;      // steps whose raster offsets are valid
+    long long inject_until;   // delivery by arrival step: steps < inject_until also consume their
+                              // delay-ring slot (partial sums restored from a checkpoint)
     unsigned int status;
     int pad;
     alignas(128) unsigned int S_acc[3];   // spikes of step t at slot t mod 3
@@ -126,6 +136,14 @@ struct Dev {
     unsigned long long *tally;     // [tally_rows][C_N] per-block event and message tallies
     unsigned long long *phase_ns;  // [2] k_persist: block 0's work and barrier wait (profiling)
     Ctrl *ctrl;
+    // delivery by arrival step (n_arr > 0; 0: every delay at the spike step
+    // into the delay ring)
+    int32_t *acc;                  // [2][M] input of step t in slot t & 1
+    unsigned long long *arr;       // [n_arr][arr_cap] queued runs: offset << 24 | length
+    unsigned int *arr_cnt;         // [n_arr * kPairStride] fill of each list
+    const uint4 *dcnt;             // [n_l2] u16 x 8: synapses of delay <= k + 1 in the segment
+    unsigned long long arr_cap;
+    int n_arr;                     // lists: the largest delay (list of step s: s mod n_arr)
     // scalars
     long long M;
     int P, n_vn, vn_size, D;
@@ -427,6 +445,13 @@ struct Stage {
     uint32_t *e0, *f0;           // [kRound] first level-1 / level-2 entry of each spike of a round
     uint32_t *pre1, *pre2;       // [kRound + 1] prefix of the level-1 / level-2 entry counts
     int *part;                   // [kRound] source partition of each spike
+    // delivery by arrival step: the round's queued runs (pool) with their
+    // list and rank in it, the runs per list and each list's reservation
+    unsigned long long *arec;    // [kArrPool]
+    unsigned short *atag;        // [kArrPool] rank << 4 | list
+    unsigned int *an;            // runs in the pool
+    unsigned int *ak;            // [kMaxArr] runs per list
+    unsigned long long *abase;   // [kMaxArr] first slot reserved in each list
 };
 
 // Add a warp's per-lane tally v into slot k of its shared tally row (whole
@@ -449,16 +474,26 @@ __device__ __forceinline__ int prefix_find(const uint32_t *pre, int n, uint32_t 
     return lo;
 }
 
+// Accumulator of a synapse of packed target word td: with fix (delivery by
+// arrival step) fix[target], the next step's input slot, whatever the delay;
+// else the delay-ring slot of step tm + delay.
+__device__ __forceinline__ int32_t *syn_dst(const Dev &d, int tm, int32_t *fix, uint32_t td)
+{
+    if (fix) return fix + (td & kTgtMask);
+    int sl = tm + (int)(td >> kTgtBits) + 1;
+    if (sl >= d.D) sl -= d.D;
+    return d.ring + (long long)sl * d.M + (td & kTgtMask);
+}
+
 // a6 for n consecutive synapses from offset o by one thread (the rare
 // overflow of a staging list).
-__device__ __forceinline__ unsigned int deliver_run(const Dev &d, int tm, unsigned long long o, unsigned int n)
+__device__ __forceinline__ unsigned int deliver_run(const Dev &d, int tm, int32_t *fix, unsigned long long o,
+                                                    unsigned int n)
 {
     for (unsigned int k = 0; k < n; ++k) {
         const uint32_t td = __ldcs(d.syn_td + o + k);
         const int32_t w = __ldcs(d.syn_w + o + k);
-        int sl = tm + (int)(td >> kTgtBits) + 1;
-        if (sl >= d.D) sl -= d.D;
-        atomicAdd(&d.ring[(long long)sl * d.M + (td & kTgtMask)], w);
+        atomicAdd(syn_dst(d, tm, fix, td), w);
     }
     return n;
 }
@@ -466,9 +501,9 @@ __device__ __forceinline__ unsigned int deliver_run(const Dev &d, int tm, unsign
 // a6 for staged lists (pieces lng[0, nl), short segments sht[0, ns)) by
 // the warps [w0, w0 + nwarp) of the block: a piece per warp (4 synapses per
 // lane, every load in flight before the reductions), then short segments a
-// lane each.  Delays count from slot tm (the spikes' step).  Returns the
-// synapses this thread delivered.
-__device__ __forceinline__ unsigned int deliver_lists(const Dev &d, int tm, const unsigned long long *lng,
+// lane each.  Delays count from slot tm (the spikes' step), or every synapse
+// goes to fix (syn_dst).  Returns the synapses this thread delivered.
+__device__ __forceinline__ unsigned int deliver_lists(const Dev &d, int tm, int32_t *fix, const unsigned long long *lng,
                                                       unsigned int nl, const unsigned long long *sht,
                                                       unsigned int ns, int w0, int nwarp)
 {
@@ -493,11 +528,7 @@ __device__ __forceinline__ unsigned int deliver_lists(const Dev &d, int tm, cons
 #pragma unroll
             for (int k = 0; k < (int)(kPiece / 32); ++k) {
                 const unsigned int x = (unsigned int)k * 32u + (unsigned int)lane;
-                if (x < n) {
-                    int sl = tm + (int)(td[k] >> kTgtBits) + 1;
-                    if (sl >= d.D) sl -= d.D;
-                    atomicAdd(&d.ring[(long long)sl * d.M + (td[k] & kTgtMask)], w[k]);
-                }
+                if (x < n) atomicAdd(syn_dst(d, tm, fix, td[k]), w[k]);
             }
             if (lane == 0) ev += n;
         } else {
@@ -518,11 +549,7 @@ __device__ __forceinline__ unsigned int deliver_lists(const Dev &d, int tm, cons
                         }
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
-                        if (k0 + k < n) {
-                            int sl = tm + (int)(td[k] >> kTgtBits) + 1;
-                            if (sl >= d.D) sl -= d.D;
-                            atomicAdd(&d.ring[(long long)sl * d.M + (td[k] & kTgtMask)], w[k]);
-                        }
+                        if (k0 + k < n) atomicAdd(syn_dst(d, tm, fix, td[k]), w[k]);
                 }
                 ev += n;
             }
@@ -532,10 +559,12 @@ __device__ __forceinline__ unsigned int deliver_lists(const Dev &d, int tm, cons
 }
 
 // a6 for the staged work of one routing round, all warps of the block.
-__device__ __forceinline__ void deliver_staged(const Dev &d, int tm, const Stage &sg, unsigned int nl,
+// With delivery by arrival step the events were counted when routed.
+__device__ __forceinline__ void deliver_staged(const Dev &d, int tm, int32_t *fix, const Stage &sg, unsigned int nl,
                                                unsigned int ns)
 {
-    tally_add(sg, 0, deliver_lists(d, tm, sg.lng, nl, sg.sht, ns, 0, kWarps));
+    const unsigned int ev = deliver_lists(d, tm, fix, sg.lng, nl, sg.sht, ns, 0, kWarps);
+    tally_add(sg, 0, fix ? 0u : ev);
 }
 
 // Minimum-delay batching (k_persist): the synapses of delay >= 2 of a
@@ -566,7 +595,7 @@ struct DeferSlot<false> {
 // one cut into pieces.  What does not fit is delivered by this thread at
 // once (slot base tm: delivering early is exact, the run's slots are read
 // later).  Returns the synapses delivered here.
-__device__ __forceinline__ unsigned int stage_run(const Dev &d, int tm, unsigned long long o, unsigned int n,
+__device__ __forceinline__ unsigned int stage_run(const Dev &d, int tm, int32_t *fix, unsigned long long o, unsigned int n,
                                                   unsigned long long *lng, unsigned int *nl, unsigned int capl,
                                                   unsigned long long *sht, unsigned int *ns, unsigned int caps)
 {
@@ -574,7 +603,7 @@ __device__ __forceinline__ unsigned int stage_run(const Dev &d, int tm, unsigned
     if (n <= kShortSeg) {
         const unsigned int sb = atomicAdd(ns, 1u);
         if (sb < caps) sht[sb] = (o << 8) | n;
-        else ev += deliver_run(d, tm, o, n);
+        else ev += deliver_run(d, tm, fix, o, n);
     } else {
         const unsigned int np = (n + kPiece - 1u) / kPiece;
         unsigned int pb = atomicAdd(nl, np);
@@ -582,7 +611,7 @@ __device__ __forceinline__ unsigned int stage_run(const Dev &d, int tm, unsigned
             const unsigned long long oo = o + (unsigned long long)j * kPiece;
             const unsigned int m = min(kPiece, n - j * kPiece);
             if (pb < capl) lng[pb] = (oo << 8) | m;
-            else ev += deliver_run(d, tm, oo, m);
+            else ev += deliver_run(d, tm, fix, oo, m);
         }
     }
     return ev;
@@ -606,6 +635,25 @@ __device__ __forceinline__ void sync_part(int nthr)
     else asm volatile("bar.sync 1, %0;" ::"r"(nthr) : "memory");
 }
 
+// Queue the run of n synapses at o on arrival list `list` (delivery by
+// arrival step): in the round's pool, or straight on the list when the pool
+// is full.
+__device__ __forceinline__ void arrival_queue(const Dev &d, const Stage &sg, int list, unsigned long long o,
+                                              unsigned int n, unsigned int &ovf)
+{
+    const unsigned long long rec = (o << kLenBits) | (unsigned long long)n;
+    const unsigned int ps = atomicAdd(sg.an, 1u);
+    if (ps < (unsigned int)kArrPool) {
+        const unsigned int r = atomicAdd(&sg.ak[list], 1u);
+        sg.arec[ps] = rec;
+        sg.atag[ps] = (unsigned short)((r << 4) | (unsigned int)list);
+    } else {
+        const unsigned int pos = atomicAdd(&d.arr_cnt[(size_t)list * kPairStride], 1u);
+        if (pos < d.arr_cap) d.arr[(size_t)list * d.arr_cap + pos] = rec;
+        else ovf |= kStArrival;
+    }
+}
+
 // a4 + a5 for the nr <= kRound spikes at positions b0 .. b0+nr of the step's
 // list, by the threads [0, nthr) (whole warps): the level-1 and level-2
 // entries of all of them are numbered through and taken a thread each, so
@@ -613,9 +661,14 @@ __device__ __forceinline__ void sync_part(int nthr)
 // staged in shared memory as soon as the entry is read: all of the segment
 // on the round's lists, or with df its delay-1 head (the synapses the next
 // step reads; segments are sorted by delay) there and the rest on df's lists
-// of parity cur.  Counters of step parity par.
+// of parity cur.  With delivery by arrival step (fix: the next step's input
+// slot) the delay-1 head is staged for fix and the run of each delay
+// d >= 2 is queued for step t + d - 1 (t = the step, tmod = t mod n_arr).
+// Counters of step parity par.
+template <bool ARR>
 __device__ __forceinline__ Pending route_traverse(const Dev &d, int par, int tm, unsigned int b0, unsigned int nr,
-                                                  const Stage &sg, int nthr, Deferred *df, int cur)
+                                                  const Stage &sg, int nthr, Deferred *df, int cur,
+                                                  int32_t *fix = nullptr, int tmod = 0)
 {
     const int lane = threadIdx.x & 31;
     if (threadIdx.x < nr) {
@@ -630,7 +683,9 @@ __device__ __forceinline__ Pending route_traverse(const Dev &d, int par, int tm,
     if (threadIdx.x == 0) {
         *sg.nl = 0;
         *sg.ns = 0;
+        if (ARR) *sg.an = 0;
     }
+    if (ARR && threadIdx.x < kMaxArr) sg.ak[threadIdx.x] = 0;
     sync_part(nthr);
     if (threadIdx.x < 32) {
         // inclusive scans of the counts (kRound <= 32: one warp)
@@ -693,13 +748,28 @@ __device__ __forceinline__ Pending route_traverse(const Dev &d, int par, int tm,
             const unsigned long long off = l.off & kOffMask;
             pn.pval = (off << kLenBits) | (unsigned long long)l.len;
             pn.pk = 2;
-            if (!df) {
-                pn.ev += stage_run(d, tm, off, l.len, sg.lng, sg.nl, kLongCap, sg.sht, sg.ns, kShortCap);
+            if constexpr (ARR) {
+                // runs by delay: c[k] = synapses of delay <= k + 1
+                const uint4 dc = d.dcnt[f];
+                const uint32_t c[kMaxArr] = {dc.x & 0xFFFFu, dc.x >> 16, dc.y & 0xFFFFu, dc.y >> 16,
+                                             dc.z & 0xFFFFu, dc.z >> 16, dc.w & 0xFFFFu, dc.w >> 16};
+                if (c[0]) stage_run(d, tm, fix, off, c[0], sg.lng, sg.nl, kLongCap, sg.sht, sg.ns, kShortCap);
+#pragma unroll
+                for (int k = 1; k < kMaxArr; ++k) {
+                    if (k < d.n_arr && c[k] > c[k - 1]) {
+                        int li = tmod + k;
+                        if (li >= d.n_arr) li -= d.n_arr;
+                        arrival_queue(d, sg, li, off + c[k - 1], c[k] - c[k - 1], pn.ovf);
+                    }
+                }
+                pn.ev += l.len;  // events counted when routed
+            } else if (!df) {
+                pn.ev += stage_run(d, tm, nullptr, off, l.len, sg.lng, sg.nl, kLongCap, sg.sht, sg.ns, kShortCap);
             } else {
                 const unsigned int n1 = (unsigned int)(l.off >> kOffBits);  // delay-1 head of the segment
-                if (n1) pn.ev += stage_run(d, tm, off, n1, sg.lng, sg.nl, kLongCap, sg.sht, sg.ns, kShortCap);
+                if (n1) pn.ev += stage_run(d, tm, nullptr, off, n1, sg.lng, sg.nl, kLongCap, sg.sht, sg.ns, kShortCap);
                 if (l.len > n1)
-                    pn.ev += stage_run(d, tm, off + n1, l.len - n1, df->lng[cur], &df->nl[cur], kDefLong,
+                    pn.ev += stage_run(d, tm, nullptr, off + n1, l.len - n1, df->lng[cur], &df->nl[cur], kDefLong,
                                        df->sht[cur], &df->ns[cur], kDefShort);
             }
             // per-class tallies without a dynamically indexed (local-memory) array
@@ -718,10 +788,28 @@ __device__ __forceinline__ Pending route_traverse(const Dev &d, int par, int tm,
 
 // a6 of a round (whole block, after a block barrier) and the exchange write
 // each thread still owes (pn from route_traverse; zero for the threads that
-// did not walk).
-__device__ __forceinline__ void route_finish(const Dev &d, int tm, const Stage &sg, Pending pn)
+// did not walk).  With delivery by arrival step (fix) the round's queued
+// runs go to their lists: one reservation per list, issued before the
+// delivery, the copy after it.
+template <bool ARR>
+__device__ __forceinline__ void route_finish(const Dev &d, int tm, int32_t *fix, const Stage &sg, Pending pn)
 {
-    deliver_staged(d, tm, sg, min(*sg.nl, (unsigned int)kLongCap), min(*sg.ns, (unsigned int)kShortCap));
+    if (ARR && threadIdx.x < (unsigned int)d.n_arr) {
+        const unsigned int n = sg.ak[threadIdx.x];
+        if (n) sg.abase[threadIdx.x] = atomicAdd(&d.arr_cnt[(size_t)threadIdx.x * kPairStride], n);
+    }
+    deliver_staged(d, tm, fix, sg, min(*sg.nl, (unsigned int)kLongCap), min(*sg.ns, (unsigned int)kShortCap));
+    if constexpr (ARR) {
+        __syncthreads();
+        const unsigned int na = min(*sg.an, (unsigned int)kArrPool);
+        for (unsigned int x = threadIdx.x; x < na; x += kThreads) {
+            const unsigned int tag = sg.atag[x];
+            const unsigned int li = tag & 15u;
+            const unsigned long long pos = sg.abase[li] + (tag >> 4);
+            if (pos < d.arr_cap) d.arr[(size_t)li * d.arr_cap + pos] = sg.arec[x];
+            else pn.ovf |= kStArrival;
+        }
+    }
     if (pn.pk == 1) {
         if (pn.ppos < pn.pslot.y) d.bucket[pn.pslot.x + pn.ppos] = (uint32_t)pn.pval;
         else pn.ovf |= kStBucket;
@@ -733,6 +821,61 @@ __device__ __forceinline__ void route_finish(const Dev &d, int tm, const Stage &
     tally_add(sg, 0, pn.ev);
 }
 
+
+// a6 for runs queued on an arrival list (delivery by arrival step): records
+// recs[lo, hi) (offset << 24 | length) into fix by the block's warps, 32
+// records per warp at a time: runs of up to kShortSeg synapses a lane each
+// (4 loads in flight), longer ones by the whole warp (4 per lane in flight).
+__device__ __forceinline__ void deliver_records(const Dev &d, int32_t *fix, const unsigned long long *recs,
+                                                unsigned long long lo, unsigned long long hi)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (unsigned long long b = lo + (unsigned long long)wid * 32u; b < hi; b += (unsigned long long)kWarps * 32u) {
+        const unsigned long long x = b + (unsigned long long)lane;
+        const unsigned long long rec = x < hi ? __ldcs(recs + x) : 0ull;
+        const unsigned long long o = rec >> kLenBits;
+        const unsigned int n = (unsigned int)(rec & kLenMask);
+        if (n <= kShortSeg) {
+            for (unsigned int k0 = 0; k0 < n; k0 += 4u) {
+                uint32_t td[4];
+                int32_t w[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (k0 + k < n) {
+                        td[k] = __ldcs(d.syn_td + o + k0 + k);
+                        w[k] = __ldcs(d.syn_w + o + k0 + k);
+                    }
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (k0 + k < n) atomicAdd(fix + (td[k] & kTgtMask), w[k]);
+            }
+        }
+        unsigned int m = __ballot_sync(0xFFFFFFFFu, n > kShortSeg);
+        while (m) {
+            const int src = __ffs(m) - 1;
+            m &= m - 1u;
+            const unsigned long long oo = __shfl_sync(0xFFFFFFFFu, o, src);
+            const unsigned int nn = __shfl_sync(0xFFFFFFFFu, n, src);
+            for (unsigned int k0 = 0; k0 < nn; k0 += 128u) {
+                uint32_t td[4];
+                int32_t w[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const unsigned int y = k0 + (unsigned int)k * 32u + (unsigned int)lane;
+                    if (y < nn) {
+                        td[k] = __ldcs(d.syn_td + oo + y);
+                        w[k] = __ldcs(d.syn_w + oo + y);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const unsigned int y = k0 + (unsigned int)k * 32u + (unsigned int)lane;
+                    if (y < nn) atomicAdd(fix + (td[k] & kTgtMask), w[k]);
+                }
+            }
+        }
+    }
+}
 
 // ---------------------------------------------------------------- a1-a6
 // How a step reaches its neurons' state:
@@ -879,7 +1022,30 @@ struct StepShared {
     unsigned long long word;
     uint32_t prevS;
     long long headv;
+    // delivery by arrival step: the routing round's queued runs (Stage), the
+    // step's arrival list share of this block, restored ring slots
+    unsigned long long arec[kArrPool];
+    unsigned short atag[kArrPool];
+    unsigned int an, ak[kMaxArr];
+    unsigned long long abase[kMaxArr];
+    unsigned int arr_n;
+    long long inj_until;
 };
+
+// Delivery by arrival step: this block's equal share of the runs queued for
+// step t (list t mod n_arr, complete since the last step's routing) into
+// the next step's input slot (all threads call).
+__device__ __forceinline__ void arrival_share(const Dev &d, long long t, StepShared &sh)
+{
+    const int li = (int)(t % d.n_arr);
+    if (threadIdx.x == 0)
+        sh.arr_n = min(*(volatile unsigned int *)&d.arr_cnt[(size_t)li * kPairStride],
+                       (unsigned int)min(d.arr_cap, 0xFFFFFFFFull));
+    __syncthreads();
+    const unsigned long long n = sh.arr_n;
+    const unsigned long long lo = n * blockIdx.x / gridDim.x, hi = n * (blockIdx.x + 1) / gridDim.x;
+    deliver_records(d, d.acc + (size_t)((t + 1) & 1) * (size_t)d.M, d.arr + (size_t)li * d.arr_cap, lo, hi);
+}
 
 // a3: compaction of the spikes each thread collected in `bits` (bit b is
 // neuron id_of(b)) into step t's spike list: a block-wide scan numbers them
@@ -943,12 +1109,22 @@ __device__ __forceinline__ void prefetch_own(const Dev &d, const StepShared &sh)
     }
 }
 
+// Input of a quad plus the restored partial sums at p (delivery by arrival
+// step, first steps after a restore), which are consumed (zeroed).
+__device__ __forceinline__ int4 take_restored(int32_t *p, int4 i4)
+{
+    const int4 x = *reinterpret_cast<const int4 *>(p);
+    *reinterpret_cast<int4 *>(p) = make_int4(0, 0, 0, 0);
+    return make_int4((int)((uint32_t)i4.x + (uint32_t)x.x), (int)((uint32_t)i4.y + (uint32_t)x.y),
+                     (int)((uint32_t)i4.z + (uint32_t)x.z), (int)((uint32_t)i4.w + (uint32_t)x.w));
+}
+
 // First half of step t on this block's share of the neurons (all threads
 // call): a1-a3, the spikes into the step's list.  In kModeSmem, rs is the
 // block's resident state and `phase` the parity of the bulk copy's
 // mbarrier; a copy that does not complete within limit_ns records
 // kStTimeout.
-template <int MODE>
+template <int MODE, bool ARR>
 __device__ __forceinline__ void update_step(const Dev &d, long long t, StepShared &sh, const Resident &rs,
                                             uint32_t phase, unsigned long long limit_ns)
 {
@@ -958,7 +1134,11 @@ __device__ __forceinline__ void update_step(const Dev &d, long long t, StepShare
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const bool do_hash = t < d.hash_steps;
     const bool do_cur = d.cur_every > 0 && (t % d.cur_every) == 0 && (t / d.cur_every) < d.cur_slots;
-    int32_t *ring = d.ring + (long long)slot * d.M;
+    // the step's input: its delay-ring slot, or with delivery by arrival
+    // step its input slot t & 1 plus, for the first steps after a restore,
+    // the ring slot holding the restored partial sums (inj)
+    int32_t *ring = ARR ? d.acc + (size_t)(t & 1) * (size_t)d.M : d.ring + (long long)slot * d.M;
+    int32_t *inj = (ARR && t < sh.inj_until) ? d.ring + (long long)slot * d.M : nullptr;
     int32_t *cur = do_cur ? d.cur_rec + (t / d.cur_every) * d.M : nullptr;
     if constexpr (MODE == kModeSmem) {
         // a1: the block's part of ring slot t, in flight while the counters
@@ -982,7 +1162,11 @@ __device__ __forceinline__ void update_step(const Dev &d, long long t, StepShare
             if (x < nb) b1[(size_t)x * kPairStride] = 0;
             else i1[(size_t)(x - nb) * kPairStride] = 0;
         }
-        if (blockIdx.x == 0 && threadIdx.x == 0) c->S_acc[slot3(t + 1)] = 0;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            c->S_acc[slot3(t + 1)] = 0;
+            // the arrival list step t - 1 delivered (step t's routing refills it)
+            if (ARR) d.arr_cnt[(size_t)((t + d.n_arr - 1) % d.n_arr) * kPairStride] = 0;
+        }
     }
     if (threadIdx.x < kPTab) sh.th[threadIdx.x] = d.th32[threadIdx.x];
     if (threadIdx.x == 0) sh.n_own = 0u;
@@ -1003,9 +1187,10 @@ __device__ __forceinline__ void update_step(const Dev &d, long long t, StepShare
                 if (lq < rs.nq) {
                     const long long j0 = (rs.q0 + lq) * 4;
                     const float4 v4 = rs.V[lq];
-                    const int4 i4 = rs.ring[lq];
+                    int4 i4 = rs.ring[lq];
                     uint32_t r4 = rs.ref[lq];
                     *reinterpret_cast<int4 *>(ring + j0) = make_int4(0, 0, 0, 0);
+                    if (inj) i4 = take_restored(inj + j0, i4);
                     if (cur) *reinterpret_cast<int4 *>(cur + j0) = i4;
                     // rs.V holds the leaked potentials and rs.ext the drive
                     // (pre_update, during the last grid barrier)
@@ -1045,9 +1230,10 @@ __device__ __forceinline__ void update_step(const Dev &d, long long t, StepShare
                 if (q < nq) {
                     const long long j0 = q * 4;
                     const float4 v4 = *reinterpret_cast<const float4 *>(d.V + j0);
-                    const int4 i4 = *reinterpret_cast<const int4 *>(ring + j0);
+                    int4 i4 = *reinterpret_cast<const int4 *>(ring + j0);
                     uint32_t r4 = *reinterpret_cast<const uint32_t *>(d.ref + j0);
                     *reinterpret_cast<int4 *>(ring + j0) = make_int4(0, 0, 0, 0);
+                    if (inj) i4 = take_restored(inj + j0, i4);
                     if (cur) *reinterpret_cast<int4 *>(cur + j0) = i4;
                     float vv[4] = {v4.x, v4.y, v4.z, v4.w};
                     const int32_t ii[4] = {i4.x, i4.y, i4.z, i4.w};
@@ -1071,9 +1257,13 @@ __device__ __forceinline__ void update_step(const Dev &d, long long t, StepShare
                 const long long j = b0 + k * stride + threadIdx.x;
                 if (j < d.M) {
                     float v = d.V[j];
-                    const int32_t irec = ring[j];
+                    int32_t irec = ring[j];
                     uint32_t r = d.ref[j];
                     ring[j] = 0;
+                    if (inj) {
+                        irec = (int32_t)((uint32_t)irec + (uint32_t)inj[j]);
+                        inj[j] = 0;
+                    }
                     if (cur) cur[j] = irec;
                     const uint32_t g = d.gid ? d.gid[j] : (uint32_t)j;
                     const Drive dr = drive_of(d, sh.th, g);
@@ -1118,11 +1308,17 @@ __device__ __forceinline__ void update_step(const Dev &d, long long t, StepShare
 // Second half of step t (all threads call): a4-a6 for this block's share of
 // the step's spikes, an equal share of the list for every block, and their
 // raster copy.
+template <bool ARR>
 __device__ __forceinline__ void route_step(const Dev &d, long long t, StepShared &sh, bool carried = false,
                                            Deferred *df = nullptr, int cur = 0)
 {
-    const Stage sg{sh.lng, sh.sht, &sh.nl, &sh.ns, sh.tally, sh.e0, sh.f0, sh.pre1, sh.pre2, sh.part};
+    const Stage sg{sh.lng, sh.sht, &sh.nl, &sh.ns, sh.tally, sh.e0, sh.f0, sh.pre1, sh.pre2, sh.part,
+                   sh.arec, sh.atag, &sh.an, sh.ak, sh.abase};
     Ctrl *c = d.ctrl;
+    // delivery by arrival step: everything this step delivers goes to the
+    // next step's input slot
+    int32_t *fix = ARR ? d.acc + (size_t)((t + 1) & 1) * (size_t)d.M : nullptr;
+    const int tmod = ARR ? (int)(t % d.n_arr) : 0;
     if (threadIdx.x == 0) {
         if (carried) {
             // k_persist: the step's spike count from the barrier word (the sum
@@ -1157,18 +1353,20 @@ __device__ __forceinline__ void route_step(const Dev &d, long long t, StepShared
     const int tmp = (int)((t - 1 + d.D) % d.D);
     const unsigned int pl = df ? min(df->nl[prev], (unsigned int)kDefLong) : 0u;
     const unsigned int ps = df ? min(df->ns[prev], (unsigned int)kDefShort) : 0u;
-    if (df && lo >= hi) tally_add(sg, 0, deliver_lists(d, tmp, df->lng[prev], pl, df->sht[prev], ps, 0, kWarps));
+    if (df && lo >= hi)
+        tally_add(sg, 0, deliver_lists(d, tmp, nullptr, df->lng[prev], pl, df->sht[prev], ps, 0, kWarps));
     for (unsigned int b = lo; b < hi; b += kRound) {
         const unsigned int nr = min(hi - b, (unsigned int)kRound);
         const bool split = df && b == lo;
         Pending pn{0, 0u, make_ulonglong2(0ull, 0ull), 0ull, 0u, 0u};
         if (!split || threadIdx.x < kTravWarps * 32)
-            pn = route_traverse(d, par, tm, b, nr, sg, split ? kTravWarps * 32 : kThreads, df, cur);
+            pn = route_traverse<ARR>(d, par, tm, b, nr, sg, split ? kTravWarps * 32 : kThreads, df, cur, fix, tmod);
         else
             tally_add(sg, 0,
-                      deliver_lists(d, tmp, df->lng[prev], pl, df->sht[prev], ps, kTravWarps, kWarps - kTravWarps));
+                      deliver_lists(d, tmp, nullptr, df->lng[prev], pl, df->sht[prev], ps, kTravWarps,
+                                    kWarps - kTravWarps));
         __syncthreads();
-        route_finish(d, tm, sg, pn);
+        route_finish<ARR>(d, tm, fix, sg, pn);
         __syncthreads();
     }
     if (sh.head >= 0)
@@ -1207,25 +1405,32 @@ __device__ __forceinline__ void close_step(const Dev &d, long long t)
 // (a4-a6).  Block 0 of k_update closes step t - 1 (the graph's first step was
 // closed by the graph before); k_advance closes the graph's last step and
 // moves ctrl->t past its steps.
-template <int MODE>
+template <int MODE, bool ARR>
 __global__ void __launch_bounds__(kThreads) k_update(const Dev d, int k)
 {
     __shared__ StepShared sh;
     pdl_enter();
-    if (threadIdx.x == 0) sh.t0 = *(volatile long long *)&d.ctrl->t;
+    if (threadIdx.x == 0) {
+        sh.t0 = *(volatile long long *)&d.ctrl->t;
+        sh.inj_until = *(volatile long long *)&d.ctrl->inject_until;
+    }
     __syncthreads();
     const long long t = sh.t0 + k;
     if (k > 0 && blockIdx.x == 0 && threadIdx.x == 0) close_step(d, t - 1);
-    update_step<MODE>(d, t, sh, Resident{}, 0u, 0ull);
+    update_step<MODE, ARR>(d, t, sh, Resident{}, 0u, 0ull);
+    // delivery by arrival step: the runs queued for this step (they go to
+    // the next step's input slot, which no block reads in this kernel)
+    if constexpr (ARR) arrival_share(d, t, sh);
 }
 
+template <bool ARR>
 __global__ void __launch_bounds__(kThreads) k_route(const Dev d, int k)
 {
     __shared__ StepShared sh;
     pdl_enter();
     if (threadIdx.x == 0) sh.t0 = *(volatile long long *)&d.ctrl->t;
     __syncthreads();
-    route_step(d, sh.t0 + k, sh);
+    route_step<ARR>(d, sh.t0 + k, sh);
 }
 
 __global__ void k_advance(const Dev d, int steps)
@@ -1251,7 +1456,7 @@ __global__ void k_advance(const Dev d, int steps)
 // block computes the next step's drive and leak (pre_update), which need no
 // other block's data.  DEFER: minimum-delay batching (Deferred); the last
 // step's delay >= 2 lists are delivered before the launch ends.
-template <int MODE, bool DEFER>
+template <int MODE, bool DEFER, bool ARR>
 __global__ void __launch_bounds__(kThreads, 3) k_persist(const Dev d, int T, unsigned long long limit_ns,
                                                          int skip_arrival)
 {
@@ -1283,6 +1488,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_persist(const Dev d, int T, uns
     }
     if (threadIdx.x == 0) {
         sh.t0 = *(volatile long long *)&c->t;
+        sh.inj_until = *(volatile long long *)&c->inject_until;
         sh.headv = *(volatile long long *)&c->head[slot3(sh.t0)];
         sh.prevS = 0u;
         if constexpr (DEFER) {
@@ -1308,15 +1514,18 @@ __global__ void __launch_bounds__(kThreads, 3) k_persist(const Dev d, int T, uns
             close_step(d, t - 1);
             closed = t - 1;
         }
-        update_step<MODE>(d, t, sh, rs, (uint32_t)(s & 1), limit_ns);
+        update_step<MODE, ARR>(d, t, sh, rs, (uint32_t)(s & 1), limit_ns);
         ++issued;
         const unsigned long long b = prof ? global_ns() : 0;
         // the first barrier carries the block's spike count in the word's high half
         grid_arrive(c, !(skip_arrival && s == 0 && blockIdx.x == 0), 1ull + ((unsigned long long)sh.n_own << 32));
         prefetch_own(d, sh);
+        // delivery by arrival step: the runs queued for this step, while the
+        // barrier completes (they need no spike of this step)
+        if constexpr (ARR) arrival_share(d, t, sh);
         if (!grid_wait(c, 2ull * s, limit_ns, &sh.word)) break;
         const unsigned long long e = prof ? global_ns() : 0;
-        route_step(d, t, sh, true, df, s & 1);
+        route_step<ARR>(d, t, sh, true, df, s & 1);
         // the next step's input-free update runs while the barrier completes
         grid_arrive(c);
         if constexpr (MODE == kModeSmem) {
@@ -1335,12 +1544,13 @@ __global__ void __launch_bounds__(kThreads, 3) k_persist(const Dev d, int T, uns
         if (T > 0 && done == T) {
             // the last step's delay >= 2 lists: their slots are read by the
             // next launch's steps, after this one ends
-            const Stage sg{sh.lng, sh.sht, &sh.nl, &sh.ns, sh.tally, sh.e0, sh.f0, sh.pre1, sh.pre2, sh.part};
+            const Stage sg{sh.lng, sh.sht, &sh.nl, &sh.ns, sh.tally, sh.e0, sh.f0, sh.pre1, sh.pre2, sh.part,
+                           sh.arec, sh.atag, &sh.an, sh.ak, sh.abase};
             const int last = (T - 1) & 1;
             if (threadIdx.x < kWarps * kTally) (&sh.tally[0][0])[threadIdx.x] = 0u;
             __syncthreads();
             tally_add(sg, 0,
-                      deliver_lists(d, (int)((t0 + T - 1) % d.D), df->lng[last],
+                      deliver_lists(d, (int)((t0 + T - 1) % d.D), nullptr, df->lng[last],
                                     min(df->nl[last], (unsigned int)kDefLong), df->sht[last],
                                     min(df->ns[last], (unsigned int)kDefShort), 0, kWarps));
             __syncthreads();

@@ -21,12 +21,15 @@ def snn():
     return m
 
 
-@pytest.fixture(params=["persistent", "persistent-global", "graph", "persistent-deferred"])
+@pytest.fixture(params=["persistent", "persistent-global", "graph", "persistent-deferred",
+                        "persistent-arrival", "persistent-global-arrival", "graph-arrival"])
 def path(request, monkeypatch):
-    monkeypatch.setenv("SNN_PERSIST", "0" if request.param == "graph" else "1")
-    monkeypatch.setenv("SNN_PERSIST_SMEM", "0" if request.param == "persistent-global" else "1")
-    monkeypatch.setenv("SNN_PERSIST_DEFER", "1" if request.param == "persistent-deferred" else "0")
-    return request.param
+    p = request.param
+    monkeypatch.setenv("SNN_PERSIST", "0" if p.startswith("graph") else "1")
+    monkeypatch.setenv("SNN_PERSIST_SMEM", "0" if p.startswith("persistent-global") else "1")
+    monkeypatch.setenv("SNN_PERSIST_DEFER", "1" if p == "persistent-deferred" else "0")
+    monkeypatch.setenv("SNN_DELIVERY", "1" if p.endswith("arrival") else "0")
+    return p
 
 
 def _batch_run(snn, b, T, rec):
@@ -100,3 +103,28 @@ def test_batch_of_one_equals_plain_sim(snn):
     assert np.array_equal(a[0], b_[0]) and np.array_equal(a[1], b_[1])
     assert np.array_equal(s1.read_hashes(0, T)[1], s2.read_hashes(0, T)[1])
     assert s1.read_counts() == s2.read_counts()
+
+
+def test_batch_at_workload_sizes_autotuned(snn):
+    """Eight networks drawn from the batched workload's distribution at its
+    sizes (12k-441k neurons, 304-825 synapses per neuron, 4-30 partitions,
+    1.1M neurons and 6.2e8 synapses in all), stepped 100 steps in the launch
+    shape the autotuner picks; every network against its own oracle."""
+    cfgs = synth.batch_configs(n=8, seed=3000)
+    b = synth.make_batch(cfgs)
+    assert min(c.M for c in cfgs) < 20_000 and max(c.M for c in cfgs) > 400_000
+    T, rec = 100, [0, 33, 66, 99]
+    net = snn.Network.from_synth(b.net)
+    rt = snn.Routing(net, b.part, b.P, b.n_vn, "contiguous")
+    plist = [snn.sim_params(c.dyn, raster_cap=b.net.M * T // 5 + 4096, raster_steps=T, cur_every=33,
+                            cur_slots=len(rec), steps_per_graph=32) for c in b.cfgs]
+    sim = snn.Sim(net, rt, plist[0], device="cuda:0", batch=(b.off, plist))
+    choice, _ = sim.autotune(40)
+    sim.step(T)
+    assert sim.sync_status() == 0
+    out = {"raster": sim.read_raster(0, T), "cur": {s: sim.read_currents(s) for s in rec},
+           "state": sim.read_state(), "counts": sim.read_counts()}
+    sim.close()
+    print("autotuned shape %d" % choice)
+    tot = _check(b, out, T, rec)
+    assert tot["spikes"] > 10_000
