@@ -218,12 +218,34 @@ int snn_partition_device(const snn_network *net, int32_t n_parts, const snn_part
 #define SNN_GROUP_CONTIGUOUS 0  /* VN g = partitions g*s .. g*s+s-1, s = P/n_vn */
 #define SNN_GROUP_GREEDY     1  /* Algorithm 2 grouping (best of `iters`) */
 
+/*
+ * Relay ("bridge") of destination VN g for a source partition p in another
+ * VN (paper Sec. IV.B: traffic to another group goes through one bridge;
+ * which member of g relays whose traffic is the design choice behind the
+ * peak level-2 traffic of Sec. V, Fig. 3(b)).  Members of a VN are ranked
+ * by ascending partition label.
+ *   PER_VN (default): member (vn(p) mod s) of g, one relay per pair of VNs;
+ *   PER_PARTITION: member (rank of p in its own VN, mod s) of g, which
+ *     spreads the s partitions of a VN over the s members of g;
+ *   BALANCED: per g, the sources p in decreasing static load (ties: lower
+ *     label) each go to the member of g with the least load so far (ties:
+ *     lower rank) -- longest-processing-time first -- where the static
+ *     load of (g, p) is the number of (neuron of p, partition of g) pairs
+ *     with synapses, the level-2 entries p sends into g; sources of load 0
+ *     take the PER_PARTITION member.
+ * The relay decides only which level-2 entries the relay forwards (message
+ * accounting and connections); delivery and results are the same.
+ */
+#define SNN_RELAY_PER_VN        0
+#define SNN_RELAY_PER_PARTITION 1
+#define SNN_RELAY_BALANCED      2
+
 typedef struct {
     int32_t grouping;   /* SNN_GROUP_* */
     int32_t iters;      /* Algorithm 2 iterations T (>= 1) */
     uint64_t seed;      /* seed of the random choices */
     int32_t n_threads;  /* host threads for the build (0 = all) */
-    int32_t reserved;
+    int32_t relay;      /* SNN_RELAY_* */
 } snn_routing_params;
 
 typedef struct {
@@ -267,10 +289,33 @@ int snn_routing_build(const snn_network *net, const int32_t *part_of, int32_t n_
                       int32_t n_vn, const snn_routing_params *params, snn_routing **out);
 int snn_routing_info_get(const snn_routing *rt, snn_routing_info *out);
 /* vn_of_part: caller-owned [n_parts]; relay: caller-owned [n_vn*n_vn],
- * relay[g*n_vn + h] = partition label relaying VN h's traffic inside VN g. */
+ * relay[g*n_vn + h] = partition label relaying VN h's traffic inside VN g
+ * (SNN_RELAY_PER_VN; -1 under the other policies, see snn_routing_relays). */
 int snn_routing_groups(const snn_routing *rt, int32_t *vn_of_part, int32_t *relay);
+/* relay: caller-owned [n_vn*n_parts], relay[g*n_parts + p] = partition label
+ * relaying the traffic of source partition p (label) inside VN g, or -1 for
+ * p in g.  policy: SNN_RELAY_* to compute that policy's map for this
+ * routing, or -1 for the routing's own.  Errors: SNN_E_ARG. */
+int snn_routing_relays(const snn_routing *rt, int32_t policy, int32_t *relay);
 /* Per-partition static connection counts (caller-owned [n_parts] each). */
 int snn_routing_connections(const snn_routing *rt, int32_t *direct, int32_t *two_level);
+/*
+ * Messages per partition that a multiset of spikes causes, on the direct
+ * route and on the two-level route (the per-GPU traffic whose peak the
+ * paper compares, Sec. V, Fig. 3).  A message is one (spike, destination)
+ * pair.  Direct route: a spike of partition p sends one message to every
+ * partition q != p holding targets of it.  Two-level route: p sends one
+ * message to each own-VN peer holding targets and one to the relay of each
+ * other VN holding targets (level 1); the relay forwards one to every other
+ * partition of its VN holding targets (level 2), counted as the relay's
+ * traffic.  ids: host uint32 [n] global spike ids (repeats count again,
+ * e.g. a raster over many steps).  relay_policy: SNN_RELAY_* (the relays of
+ * that policy on this routing's groups), or -1 for the routing's own.  Outputs (caller-owned [n_parts], label
+ * order, each may be NULL): messages sent and received per partition on
+ * each route.  Errors: SNN_E_ARG (NULL arrays with n > 0, an id >= M).
+ */
+int snn_routing_traffic(const snn_routing *rt, const uint32_t *ids, int64_t n, int32_t relay_policy,
+                        int64_t *direct_out, int64_t *direct_in, int64_t *two_level_out, int64_t *two_level_in);
 /*
  * Copy one of the routing's tables (host memory, internal order) into the
  * caller's buffer `out` of `cap` bytes; *bytes receives the table's size.

@@ -75,6 +75,8 @@ def _load():
     L.or_group_greedy.restype = ctypes.c_int
     L.or_create.argtypes = [i64, vp, vp, vp, vp, i32, vp, i32, vp, ctypes.POINTER(OrDyn)]
     L.or_create.restype = vp
+    L.or_set_relay_policy.argtypes = [vp, i32, vp]
+    L.or_set_relay_policy.restype = ctypes.c_int
     L.or_destroy.argtypes = [vp]
     L.or_destroy.restype = None
     L.or_run.argtypes = [vp, i64, i32, i32, vp, vp, vp, vp, vp, i64, vp, vp, vp, i32, vp, vp,
@@ -236,7 +238,9 @@ class Oracle:
     D = max delay, FP64 shadow v64 (float64 [M]), and the global step t.
     """
 
-    def __init__(self, net, P, part_of, n_vn, vn_of_part, dyn):
+    RELAY = {"per_vn": 0, "per_partition": 1, "balanced": 2}
+
+    def __init__(self, net, P, part_of, n_vn, vn_of_part, dyn, relay: str = "per_vn"):
         self._L = _load()
         self.net = net
         self.M = net.M
@@ -252,6 +256,9 @@ class Oracle:
                                     self.vn_of_part.ctypes.data, ctypes.byref(self._dyn))
         if not self._h:
             raise ValueError("or_create rejected the network")
+        self.relay = np.zeros((self.n_vn, self.P), np.int32)
+        if self._L.or_set_relay_policy(self._h, self.RELAY[relay], self.relay.ctypes.data) != 0:
+            raise ValueError("unknown relay policy %r" % relay)
         self.V = net.v0.astype(np.float32).copy()
         self.ref = np.zeros(self.M, np.uint8)
         self.ring = np.zeros((self.D, self.M), np.int32)

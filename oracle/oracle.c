@@ -47,9 +47,19 @@
  *     (j mod 4) of the block with key = drive seed and counter =
  *     (j div 4, step, 0, 0), so one block serves four consecutive neurons;
  *     thresholds floor(2^32 * CDF(k)) in double.
- *   - relay of destination group g for source group h: the
- *     (h mod |g|)-th partition of g in ascending partition index; for the
- *     own group the source partition sends directly.
+ *   - relay of destination group g for a source partition p of another
+ *     group (the "bridge" of Sec. IV.B; which member relays whose traffic
+ *     is the design choice the paper's level-2 traffic result rests on,
+ *     Sec. V, Fig. 3(b)), members of a group ranked by ascending partition
+ *     index, by policy:
+ *       per group (default): the (h mod |g|)-th member of g, h = group of p;
+ *       per partition: the (rank of p in its own group mod |g|)-th member;
+ *       balanced: longest-processing-time first -- the sources of g in
+ *       decreasing static load (ties: lower index) each join the member of
+ *       g with the least load so far (ties: lower rank); the static load of
+ *       (g, p) is the number of (neuron of p, partition of g) pairs with
+ *       synapses; sources of load 0 take the per-partition member;
+ *     for the own group the source partition sends directly.
  *
  * Compile with -ffp-contract=off so that no multiply-add is fused.
  */
@@ -464,15 +474,29 @@ int or_group_greedy(int64_t M, const int64_t *syn_ptr, const uint32_t *tgt,
     return 0;
 }
 
-/* relay(g, h): the (h mod |g|)-th partition of group g, ascending index. */
-static int32_t relay_of(const int32_t *vn_of_part, int32_t P, int32_t g, int32_t h)
+/* The k-th partition of group g in ascending index (k taken mod |g|). */
+static int32_t member_of(const int32_t *vn_of_part, int32_t P, int32_t g, int32_t k)
 {
     int32_t sz = 0;
     for (int32_t p = 0; p < P; ++p) if (vn_of_part[p] == g) ++sz;
-    int32_t want = h % sz;
+    int32_t want = k % sz;
     for (int32_t p = 0; p < P; ++p)
         if (vn_of_part[p] == g) { if (want == 0) return p; --want; }
     return -1;
+}
+
+/* relay(g, h): the (h mod |g|)-th partition of group g, ascending index. */
+static int32_t relay_of(const int32_t *vn_of_part, int32_t P, int32_t g, int32_t h)
+{
+    return member_of(vn_of_part, P, g, h);
+}
+
+/* Rank of partition p among the partitions of its own group (ascending index). */
+static int32_t rank_in_group(const int32_t *vn_of_part, int32_t p)
+{
+    int32_t r = 0;
+    for (int32_t x = 0; x < p; ++x) r += vn_of_part[x] == vn_of_part[p];
+    return r;
 }
 
 /* ------------------------------------------------------------------ */
@@ -503,7 +527,7 @@ typedef struct {
     int32_t P, n_vn;
     int32_t *part_of;      /* copy */
     int32_t *vn_of_part;   /* copy */
-    int32_t *relay;        /* [n_vn * n_vn]: relay[g * n_vn + h] */
+    int32_t *relay;        /* [n_vn * P]: relay[g * P + p] of source partition p, -1 for p in g */
     or_dyn dyn;
     float alpha;
     double alpha64;
@@ -545,9 +569,10 @@ void *or_create(int64_t M, const int64_t *syn_ptr, const uint32_t *tgt, const in
         if (vn_of_part[p] < 0 || vn_of_part[p] >= n_vn) { or_destroy(h); return NULL; }
     for (int64_t i = 0; i < M; ++i)
         if (part_of[i] < 0 || part_of[i] >= P) { or_destroy(h); return NULL; }
-    h->relay = malloc(sizeof(int32_t) * (size_t)n_vn * (size_t)n_vn);
+    h->relay = malloc(sizeof(int32_t) * (size_t)n_vn * (size_t)P);
     for (int32_t g = 0; g < n_vn; ++g)
-        for (int32_t hh = 0; hh < n_vn; ++hh) h->relay[g * n_vn + hh] = relay_of(vn_of_part, P, g, hh);
+        for (int32_t p = 0; p < P; ++p)
+            h->relay[g * P + p] = vn_of_part[p] == g ? -1 : relay_of(vn_of_part, P, g, vn_of_part[p]);
     h->alpha = (float)exp(-dyn->dt_ms / dyn->tau_ms);
     h->alpha64 = exp(-dyn->dt_ms / dyn->tau_ms);
     if (or_poisson_table(dyn->drive_lambda, h->th, &h->th_len)) { or_destroy(h); return NULL; }
@@ -792,7 +817,7 @@ int or_run(void *hv, int64_t t0, int32_t T, int32_t D,
                         if (g == hv_) {
                             if (q == p) counts[OC_L2_LOCAL]++; else counts[OC_L2_PEER]++;
                         } else {
-                            if (q == h->relay[g * h->n_vn + hv_]) counts[OC_L2_RELAY_LOCAL]++;
+                            if (q == h->relay[g * P + p]) counts[OC_L2_RELAY_LOCAL]++;
                             else counts[OC_L2_RELAY_REMOTE]++;
                         }
                     }
@@ -815,6 +840,62 @@ int64_t or_num_segments(void *hv)
 {
     or_net *h = (or_net *)hv;
     return h ? h->seg_ptr[h->M] : -1;
+}
+
+/* Relays of a policy (0 per group, 1 per partition, 2 balanced; see the
+ * header) for the network's mapping; the two-level counts of later runs use
+ * them.  out (may be NULL) receives relay[g * P + p].  Returns 0, -1 on a
+ * bad policy. */
+int or_set_relay_policy(void *hv, int32_t policy, int32_t *out)
+{
+    or_net *h = (or_net *)hv;
+    if (!h || policy < 0 || policy > 2) return -1;
+    const int32_t P = h->P, n_vn = h->n_vn;
+    const int32_t *vp = h->vn_of_part;
+    for (int32_t g = 0; g < n_vn; ++g)
+        for (int32_t p = 0; p < P; ++p)
+            h->relay[g * P + p] = vp[p] == g ? -1
+                                  : policy == 0 ? relay_of(vp, P, g, vp[p])
+                                                : member_of(vp, P, g, rank_in_group(vp, p));
+    if (policy == 2) {
+        /* static loads: (neuron of p, partition of g) pairs with synapses */
+        int64_t *load = calloc((size_t)n_vn * (size_t)P, sizeof(int64_t));
+        for (int64_t i = 0; i < h->M; ++i) {
+            int32_t p = h->part_of[i];
+            for (int64_t sg = h->seg_ptr[i]; sg < h->seg_ptr[i + 1]; ++sg) {
+                int32_t g = vp[h->seg_q[sg]];
+                if (g != vp[p]) load[(int64_t)g * P + p]++;
+            }
+        }
+        int32_t *mem = malloc(sizeof(int32_t) * (size_t)P);
+        int64_t *acc = malloc(sizeof(int64_t) * (size_t)P);
+        char *done = malloc((size_t)P);
+        for (int32_t g = 0; g < n_vn; ++g) {
+            int32_t nm = 0;
+            for (int32_t p = 0; p < P; ++p)
+                if (vp[p] == g) { mem[nm] = p; acc[nm] = 0; ++nm; }
+            memset(done, 0, (size_t)P);
+            for (;;) {
+                /* the heaviest unassigned source (ties: lower index) */
+                int32_t best = -1;
+                for (int32_t p = 0; p < P; ++p) {
+                    int64_t l = load[(int64_t)g * P + p];
+                    if (vp[p] == g || done[p] || l == 0) continue;
+                    if (best < 0 || l > load[(int64_t)g * P + best]) best = p;
+                }
+                if (best < 0) break;
+                done[best] = 1;
+                int32_t k = 0;
+                for (int32_t m = 1; m < nm; ++m)
+                    if (acc[m] < acc[k]) k = m;
+                acc[k] += load[(int64_t)g * P + best];
+                h->relay[g * P + best] = mem[k];
+            }
+        }
+        free(load); free(mem); free(acc); free(done);
+    }
+    if (out) memcpy(out, h->relay, sizeof(int32_t) * (size_t)n_vn * (size_t)P);
+    return 0;
 }
 
 /* Single-precision alpha = fl32(exp(-dt/tau)) as the oracle uses it. */

@@ -33,6 +33,9 @@ _lib = ctypes.CDLL(_SO)
 SNN_PART_PLANTED, SNN_PART_GREEDY, SNN_PART_RANDOM = 0, 1, 2
 SNN_GROUP_CONTIGUOUS, SNN_GROUP_GREEDY = 0, 1
 SNN_DELIVER_RING, SNN_DELIVER_ARRIVAL, SNN_DELIVER_AUTO = 0, 1, 2
+SNN_RELAY_PER_VN, SNN_RELAY_PER_PARTITION, SNN_RELAY_BALANCED = 0, 1, 2
+RELAY_POLICIES = {"per_vn": SNN_RELAY_PER_VN, "per_partition": SNN_RELAY_PER_PARTITION,
+                  "balanced": SNN_RELAY_BALANCED}
 SNN_E_CAPACITY = -3
 
 _i32, _i64, _u64, _u32, _f32, _f64, _vp = (ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64,
@@ -66,7 +69,7 @@ class snn_partition_device_params(ctypes.Structure):
 
 class snn_routing_params(ctypes.Structure):
     _fields_ = [("grouping", _i32), ("iters", _i32), ("seed", _u64), ("n_threads", _i32),
-                ("reserved", _i32)]
+                ("relay", _i32)]
 
 
 class snn_routing_info(ctypes.Structure):
@@ -129,6 +132,8 @@ _sig("snn_routing_build_device", ctypes.c_int, [_P(snn_network), _vp, _i32, _i32
                                                 ctypes.c_size_t, _vp, _P(_vp)])
 _sig("snn_routing_groups", ctypes.c_int, [_vp, _vp, _vp])
 _sig("snn_routing_connections", ctypes.c_int, [_vp, _vp, _vp])
+_sig("snn_routing_traffic", ctypes.c_int, [_vp, _vp, _i64, _i32, _vp, _vp, _vp, _vp])
+_sig("snn_routing_relays", ctypes.c_int, [_vp, _i32, _vp])
 _sig("snn_routing_destroy", None, [_vp])
 _sig("snn_sim_params_default", None, [_P(snn_sim_params)])
 _sig("snn_sim_workspace_bytes", ctypes.c_int, [_vp, _P(snn_sim_params), _P(ctypes.c_size_t)])
@@ -171,7 +176,8 @@ EXPORTS = ("snn_strerror", "snn_model_params_preset", "snn_model_build", "snn_mo
            "snn_model_load", "snn_model_destroy", "snn_partition", "snn_partition_device_params_default",
            "snn_partition_device_workspace_bytes", "snn_partition_device", "snn_routing_build",
            "snn_routing_export", "snn_routing_build_device_workspace_bytes", "snn_routing_build_device", "snn_routing_info_get",
-           "snn_routing_groups", "snn_routing_connections", "snn_routing_destroy",
+           "snn_routing_groups", "snn_routing_connections", "snn_routing_traffic", "snn_routing_relays",
+           "snn_routing_destroy",
            "snn_sim_params_default", "snn_sim_workspace_bytes", "snn_sim_create", "snn_step",
            "snn_sync_status", "snn_read_raster", "snn_read_currents", "snn_read_hashes",
            "snn_read_counts", "snn_read_state", "snn_read_inbox_pairs", "snn_state_bytes",
@@ -345,11 +351,12 @@ class Routing:
     the workspace is a torch tensor on `device`)."""
 
     def __init__(self, net: Network, part_of, n_parts: int, n_vn: int, grouping: str = "contiguous",
-                 iters: int = 4, seed: int = 7, n_threads: int = 0, build: str = "host", device=None):
+                 iters: int = 4, seed: int = 7, n_threads: int = 0, build: str = "host", device=None,
+                 relay: str = "per_vn"):
         self.net = net
         self.part_of = np.ascontiguousarray(part_of, np.int32)
         g = {"contiguous": SNN_GROUP_CONTIGUOUS, "greedy": SNN_GROUP_GREEDY}[grouping]
-        prm = snn_routing_params(g, iters, seed, n_threads, 0)
+        prm = snn_routing_params(g, iters, seed, n_threads, RELAY_POLICIES[relay])
         h = _vp()
         if build == "host":
             _ck(_lib.snn_routing_build(ctypes.byref(net.s), self.part_of.ctypes.data, n_parts, n_vn,
@@ -400,6 +407,27 @@ class Routing:
         _ck(_lib.snn_routing_connections(self.h, a.ctypes.data, b.ctypes.data),
             "snn_routing_connections")
         return a, b
+
+    def relays(self, policy=None) -> np.ndarray:
+        """[n_vn, P] relay label of each (destination VN, source partition),
+        -1 inside the own VN; policy None: the routing's own (snn_routing_relays)."""
+        out = np.empty(self.n_vn * self.P, np.int32)
+        code = -1 if policy is None else RELAY_POLICIES.get(policy, policy)
+        _ck(_lib.snn_routing_relays(self.h, int(code), out.ctypes.data), "snn_routing_relays")
+        return out.reshape(self.n_vn, self.P)
+
+    def traffic(self, ids, policy=None) -> dict:
+        """Messages per partition (label order) that the spikes `ids` (global
+        ids, repeats count again) cause on the direct and the two-level route,
+        sent and received, with the relays of `policy` (None: the routing's
+        own; snn_routing_traffic)."""
+        ids = np.ascontiguousarray(ids, np.uint32)
+        code = -1 if policy is None else RELAY_POLICIES.get(policy, policy)
+        out = {k: np.zeros(self.P, np.int64) for k in ("direct_out", "direct_in", "two_level_out", "two_level_in")}
+        _ck(_lib.snn_routing_traffic(self.h, ids.ctypes.data, len(ids), int(code), out["direct_out"].ctypes.data,
+                                     out["direct_in"].ctypes.data, out["two_level_out"].ctypes.data,
+                                     out["two_level_in"].ctypes.data), "snn_routing_traffic")
+        return out
 
     def close(self):
         if getattr(self, "h", None):

@@ -377,6 +377,7 @@ void route_order(snn_routing *rt, const snn_network *net, const int32_t *part_of
     rt->relay.resize((size_t)n_vn * n_vn);
     for (int32_t g = 0; g < n_vn; ++g)
         for (int32_t h = 0; h < n_vn; ++h) rt->relay[(size_t)g * n_vn + h] = rt->part_of_ip[g * s + h % s];
+
     // internal neuron order: partition-major, ascending global id
     rt->pbase.assign((size_t)P + 1, 0);
     for (int32_t p = 0; p < P; ++p) rt->pbase[rt->ip_of_part[p] + 1] = sizes[p];
@@ -444,6 +445,71 @@ void route_number_pairs(snn_routing *rt, std::vector<uint32_t> &bc, std::vector<
     number(ic, P, rt->ipair_ptr, rt->ipair_dst, rt->ipair_cap);
 }
 
+void route_relay_map(const snn_routing *rt, int32_t policy, std::vector<int32_t> &relay_ip)
+{
+    const int32_t P = rt->P, n_vn = rt->n_vn, s = rt->vn_size;
+    relay_ip.assign((size_t)n_vn * P, -1);
+    for (int32_t g = 0; g < n_vn; ++g)
+        for (int32_t ip = 0; ip < P; ++ip) {
+            if (ip / s == g) continue;
+            // internal partitions are VN-major, by ascending label inside a VN:
+            // the rank of ip in its VN is ip mod s, member k of g is g*s + k
+            relay_ip[(size_t)g * P + ip] = policy == SNN_RELAY_PER_VN ? g * s + (ip / s) % s : g * s + ip % s;
+        }
+    if (policy != SNN_RELAY_BALANCED) return;
+    // static load of (g, source ip): its level-2 pairs into the partitions of g
+    std::vector<int64_t> load((size_t)n_vn * P, 0);
+    for (int32_t ip = 0; ip < P; ++ip)
+        for (uint32_t k = rt->ipair_ptr[ip]; k < rt->ipair_ptr[ip + 1]; ++k) {
+            const int32_t q = rt->ipair_dst[k];
+            if (q / s != ip / s) load[(size_t)(q / s) * P + ip] += rt->ipair_cap[k];
+        }
+    std::vector<int32_t> src;
+    std::vector<int64_t> acc((size_t)s);
+    for (int32_t g = 0; g < n_vn; ++g) {
+        src.clear();
+        for (int32_t ip = 0; ip < P; ++ip)
+            if (ip / s != g && load[(size_t)g * P + ip] > 0) src.push_back(ip);
+        const int64_t *lg = &load[(size_t)g * P];
+        std::sort(src.begin(), src.end(), [&](int32_t a, int32_t b) {
+            if (lg[a] != lg[b]) return lg[a] > lg[b];
+            return rt->part_of_ip[a] < rt->part_of_ip[b];
+        });
+        std::fill(acc.begin(), acc.end(), 0);
+        for (int32_t ip : src) {
+            int32_t k = 0;
+            for (int32_t m = 1; m < s; ++m)
+                if (acc[m] < acc[k]) k = m;
+            acc[k] += lg[ip];
+            relay_ip[(size_t)g * P + ip] = g * s + k;
+        }
+    }
+}
+
+void route_relays(snn_routing *rt, int32_t policy, int nthreads)
+{
+    const int32_t P = rt->P, n_vn = rt->n_vn, s = rt->vn_size;
+    rt->relay_policy = policy;
+    route_relay_map(rt, policy, rt->relay_ip);
+    if (policy != SNN_RELAY_PER_VN) std::fill(rt->relay.begin(), rt->relay.end(), -1);
+    if (policy == SNN_RELAY_PER_VN) return;  // the builders' classes already follow it
+    // the relay classes of the level-2 entries under the policy's relays
+    parallel_for(P, nthreads, [&](int64_t plo, int64_t phi, int) {
+        for (int64_t ip = plo; ip < phi; ++ip) {
+            const int32_t hs = (int32_t)ip / s;
+            for (int64_t k = rt->pbase[ip]; k < rt->pbase[ip + 1]; ++k)
+                for (uint32_t e = rt->l1_ptr[k]; e < rt->l1_ptr[k + 1]; ++e) {
+                    const int32_t g = rt->l1_vn[e];
+                    if (g == hs) continue;
+                    const int32_t r = rt->relay_ip[(size_t)g * P + ip];
+                    for (uint32_t f = rt->l1_l2[e]; f < rt->l1_l2[e + 1]; ++f)
+                        rt->l2[f].cls = rt->l2[f].q == r ? kClsRelayLocal : kClsRelayRemote;
+                }
+        }
+    });
+    (void)n_vn;
+}
+
 }  // namespace snn
 
 extern "C" int snn_routing_build(const snn_network *net, const int32_t *part_of, int32_t P,
@@ -457,6 +523,7 @@ extern "C" int snn_routing_build(const snn_network *net, const int32_t *part_of,
     if (P > 4096) return SNN_E_RANGE;
     if (prm->grouping != SNN_GROUP_CONTIGUOUS && prm->grouping != SNN_GROUP_GREEDY) return SNN_E_ARG;
     if (prm->grouping == SNN_GROUP_GREEDY && prm->iters < 1) return SNN_E_ARG;
+    if (prm->relay < SNN_RELAY_PER_VN || prm->relay > SNN_RELAY_BALANCED) return SNN_E_ARG;
     if (M >= (int64_t)1 << kTgtBits) return SNN_E_RANGE;
     if (E >= (int64_t)1 << 40) return SNN_E_RANGE;
     const int nt = resolve_threads(prm->n_threads);
@@ -679,6 +746,7 @@ extern "C" int snn_routing_build(const snn_network *net, const int32_t *part_of,
                             rt->l2_pair[f] = ic[(size_t)ip * P + rt->l2[f].q];
                     }
         });
+        route_relays(rt, prm->relay, nt);
     } catch (const std::bad_alloc &) {
         delete rt;
         return SNN_E_NOMEM;
@@ -716,6 +784,76 @@ extern "C" int snn_routing_groups(const snn_routing *rt, int32_t *vn_of_part, in
     if (!rt) return SNN_E_ARG;
     if (vn_of_part) std::memcpy(vn_of_part, rt->vn_of_part.data(), sizeof(int32_t) * (size_t)rt->P);
     if (relay) std::memcpy(relay, rt->relay.data(), sizeof(int32_t) * rt->relay.size());
+    return SNN_OK;
+}
+
+extern "C" int snn_routing_traffic(const snn_routing *rt, const uint32_t *ids, int64_t n, int32_t relay_policy,
+                                   int64_t *direct_out, int64_t *direct_in, int64_t *two_out, int64_t *two_in)
+{
+    if (!rt || n < 0 || (n > 0 && !ids)) return SNN_E_ARG;
+    if (relay_policy < -1 || relay_policy > SNN_RELAY_BALANCED) return SNN_E_ARG;
+    std::vector<int32_t> own;
+    if (relay_policy >= 0 && relay_policy != rt->relay_policy) route_relay_map(rt, relay_policy, own);
+    const std::vector<int32_t> &relay_ip = own.empty() ? rt->relay_ip : own;
+    for (int64_t x = 0; x < n; ++x)
+        if ((int64_t)ids[x] >= rt->M) return SNN_E_ARG;
+    const int32_t P = rt->P, s = rt->vn_size;
+    const int nt = resolve_threads(0);
+    // per thread: [4][P] in internal partition order
+    std::vector<std::vector<int64_t>> acc((size_t)nt);
+    parallel_for(n, nt, [&](int64_t lo, int64_t hi, int k) {
+        std::vector<int64_t> &a = acc[k];
+        a.assign((size_t)4 * P, 0);
+        int64_t *dout = a.data(), *din = dout + P, *tout = din + P, *tin = tout + P;
+        for (int64_t x = lo; x < hi; ++x) {
+            const int64_t i = rt->perm_fwd[ids[x]];
+            const int32_t ps = rt->src_part[i], hs = ps / s;
+            for (uint32_t e = rt->l1_ptr[i]; e < rt->l1_ptr[i + 1]; ++e) {
+                const int32_t g = rt->l1_vn[e];
+                const int32_t r = g == hs ? -1 : relay_ip[(size_t)g * P + ps];
+                if (g != hs) {  // level 1: one message to the relay of g
+                    ++tout[ps];
+                    ++tin[r];
+                }
+                for (uint32_t f = rt->l1_l2[e]; f < rt->l1_l2[e + 1]; ++f) {
+                    const int32_t q = rt->l2[f].q;
+                    if (q == ps) continue;
+                    ++dout[ps];
+                    ++din[q];
+                    if (g == hs) {  // peer of the own VN: direct
+                        ++tout[ps];
+                        ++tin[q];
+                    } else if (q != r) {  // level 2: the relay forwards
+                        ++tout[r];
+                        ++tin[q];
+                    }
+                }
+            }
+        }
+    });
+    int64_t *outs[4] = {direct_out, direct_in, two_out, two_in};
+    for (int c = 0; c < 4; ++c) {
+        if (!outs[c]) continue;
+        for (int32_t p = 0; p < P; ++p) outs[c][p] = 0;
+        for (int k = 0; k < nt; ++k)
+            if (!acc[k].empty())
+                for (int32_t ip = 0; ip < P; ++ip) outs[c][rt->part_of_ip[ip]] += acc[k][(size_t)c * P + ip];
+    }
+    return SNN_OK;
+}
+
+extern "C" int snn_routing_relays(const snn_routing *rt, int32_t policy, int32_t *relay)
+{
+    if (!rt || !relay || policy < -1 || policy > SNN_RELAY_BALANCED) return SNN_E_ARG;
+    std::vector<int32_t> own;
+    if (policy >= 0 && policy != rt->relay_policy) route_relay_map(rt, policy, own);
+    const std::vector<int32_t> &rip = own.empty() ? rt->relay_ip : own;
+    const int32_t P = rt->P;
+    for (int32_t g = 0; g < rt->n_vn; ++g)
+        for (int32_t p = 0; p < P; ++p) {
+            const int32_t r = rip[(size_t)g * P + rt->ip_of_part[p]];
+            relay[(size_t)g * P + p] = r < 0 ? -1 : rt->part_of_ip[r];
+        }
     return SNN_OK;
 }
 

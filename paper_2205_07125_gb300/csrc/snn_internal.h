@@ -74,7 +74,9 @@ struct snn_routing {
     std::vector<int32_t> vn_of_part;  // label -> VN
     std::vector<int32_t> ip_of_part;  // label -> internal partition
     std::vector<int32_t> part_of_ip;  // internal partition -> label
-    std::vector<int32_t> relay;       // [g*n_vn + h] -> label
+    std::vector<int32_t> relay;       // [g*n_vn + h] -> label (per-VN relay policy; -1 otherwise)
+    std::vector<int32_t> relay_ip;    // [g*P + ip] relay (internal partition) of VN g for source ip
+    int32_t relay_policy = 0;         // SNN_RELAY_*
     std::vector<int64_t> pbase;       // [P+1] first internal neuron of each internal partition
     std::vector<uint32_t> perm_inv;   // internal -> global
     std::vector<uint32_t> perm_fwd;   // global -> internal
@@ -129,5 +131,12 @@ void route_groups(snn_routing *rt, const snn_routing_params *prm, const std::vec
 void route_order(snn_routing *rt, const snn_network *net, const int32_t *part_of, const std::vector<int64_t> &sizes);
 void route_connections(snn_routing *rt, const std::vector<uint8_t> &conn);
 void route_number_pairs(snn_routing *rt, std::vector<uint32_t> &bc, std::vector<uint32_t> &ic);
+// Relays of a relay policy (SNN_RELAY_*): relay_ip[g*P + ip] = the internal
+// partition of VN g relaying source ip's traffic (-1 for ip in g); the
+// balanced policy weighs the level-2 pair worst cases (after
+// route_number_pairs).  route_relays sets the routing's own map and the
+// relay classes of its level-2 entries under it.
+void route_relay_map(const snn_routing *rt, int32_t policy, std::vector<int32_t> &relay_ip);
+void route_relays(snn_routing *rt, int32_t policy, int nthreads);
 uint32_t philox_word0(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2);
 }  // namespace snn

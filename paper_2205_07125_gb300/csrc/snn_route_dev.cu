@@ -437,6 +437,7 @@ extern "C" int snn_routing_build_device(const snn_network *net, const int32_t *p
     if (P < 1 || n_vn < 1 || P % n_vn || P > M) return SNN_E_ARG;
     if (P > 4096) return SNN_E_RANGE;
     if (prm->grouping != SNN_GROUP_CONTIGUOUS && prm->grouping != SNN_GROUP_GREEDY) return SNN_E_ARG;
+    if (prm->relay < SNN_RELAY_PER_VN || prm->relay > SNN_RELAY_BALANCED) return SNN_E_ARG;
     if (prm->grouping == SNN_GROUP_GREEDY && prm->iters < 1) return SNN_E_ARG;
     if (M >= (1ll << kTgtBits)) return SNN_E_RANGE;
     if (E >= (1ll << 40)) return SNN_E_RANGE;
@@ -663,6 +664,7 @@ extern "C" int snn_routing_build_device(const snn_network *net, const int32_t *p
         RCK(cudaMemcpyAsync(fl, d.flags, sizeof(fl), cudaMemcpyDeviceToHost, st));
         RCK(cudaStreamSynchronize(st));
         if (fl[0] & (kRCap | kRCount)) { delete rt; return SNN_E_STATE; }
+        route_relays(rt, prm->relay, resolve_threads(prm->n_threads));
     } catch (const std::bad_alloc &) {
         delete rt;
         return SNN_E_NOMEM;

@@ -39,13 +39,13 @@ def _oracle_mapping(g, cfg, part_mode, group_mode, P, n_vn, iters=3, seed=5):
 
 
 def _run_pair(snn, g, cfg, T, P, n_vn, part_mode="planted", group_mode="contiguous", cur_every=None,
-              steps_per_graph=32, iters=3, seed=5, **prm_kw):
+              steps_per_graph=32, iters=3, seed=5, relay="per_vn", **prm_kw):
     net = snn.Network.from_synth(g)
     if part_mode == "planted":
         part, _ = snn.snn_partition(net, P, "planted")
     else:
         part, _ = snn.snn_partition(net, P, part_mode, iters=iters, seed=seed)
-    rt = snn.Routing(net, part, P, n_vn, group_mode, iters=iters, seed=seed)
+    rt = snn.Routing(net, part, P, n_vn, group_mode, iters=iters, seed=seed, relay=relay)
     ce = cur_every if cur_every is not None else max(1, T // 8)
     prm = snn.sim_params(cfg.dyn, raster_cap=max(4096, g.M * T // 10), raster_steps=T, hash_steps=T,
                          cur_every=ce, cur_slots=T // ce + 1, steps_per_graph=steps_per_graph,
@@ -54,7 +54,7 @@ def _run_pair(snn, g, cfg, T, P, n_vn, part_mode="planted", group_mode="contiguo
     po, vn = _oracle_mapping(g, cfg, part_mode, group_mode, P, n_vn, iters, seed)
     assert np.array_equal(part, po)
     assert np.array_equal(rt.groups()[0], vn)
-    o = oracle.Oracle(g, P, po, n_vn, vn, cfg.dyn)
+    o = oracle.Oracle(g, P, po, n_vn, vn, cfg.dyn, relay=relay)
     rec = list(range(0, T, ce))
     return sim, o, rec, rt
 
@@ -346,3 +346,18 @@ def test_abi_built_model_against_oracle_reading_its_file(snn, tmp_path, monkeypa
     assert sim.sync_status() == 0
     c, _ = _compare(sim, o, T, list(range(0, T, 50)))
     assert c["spikes"] > 1000 and c["events"] == c["spikes"] * 300
+
+
+@pytest.mark.parametrize("relay", ["per_partition", "balanced"])
+def test_relay_policies_counts_and_currents(snn, relay):
+    """Relays chosen per source partition or by load balancing change which
+    level-2 entries are forwarded (the message classes), not the delivery:
+    counts under the policy and currents bit-exact against the oracle under
+    the same policy, on a greedy mapping."""
+    cfg = synth.SCALE.scaled(M=1 << 15, P=32, n_vn=4, K=200, n_part=140, n_vn_t=40, n_remote=20, seed=47)
+    g = synth.make_network(cfg)
+    sim, o, rec, rt = _run_pair(snn, g, cfg, 120, cfg.P, cfg.n_vn, "greedy", "greedy", relay=relay)
+    assert np.array_equal(rt.relays(), o.relay)
+    sim.step(120)
+    c, _ = _compare(sim, o, 120, rec)
+    assert c["l2_relay_remote"] > 0

@@ -25,10 +25,11 @@ def snn():
     return m
 
 
-def _same(snn, g, part, P, n_vn, grouping="contiguous"):
+def _same(snn, g, part, P, n_vn, grouping="contiguous", relay="per_vn"):
     net = snn.Network.from_synth(g)
-    h = snn.Routing(net, part, P, n_vn, grouping, iters=3, seed=5)
-    d = snn.Routing(net, part, P, n_vn, grouping, iters=3, seed=5, build="device", device="cuda:0")
+    h = snn.Routing(net, part, P, n_vn, grouping, iters=3, seed=5, relay=relay)
+    d = snn.Routing(net, part, P, n_vn, grouping, iters=3, seed=5, build="device", device="cuda:0", relay=relay)
+    assert np.array_equal(h.relays(), d.relays())
     for t in TABLES:
         a, b = h.export(t), d.export(t)
         assert a.shape == b.shape and np.array_equal(a.view(np.uint8), b.view(np.uint8)), t
@@ -55,6 +56,17 @@ def test_planted_network(snn, grouping):
     g = synth.make_network(cfg)
     part, _ = snn.snn_partition(snn.Network.from_synth(g), 16, "planted")
     _same(snn, g, part, 16, 4, grouping)
+
+
+@pytest.mark.parametrize("relay", ["per_partition", "balanced"])
+def test_relay_policies(snn, relay):
+    """The relay classes of the level-2 entries under each relay policy: the
+    device-built tables equal the host builder's byte for byte."""
+    cfg = synth.NetConfig(name="t", M=6000, P=16, n_vn=2, K=40, uniform_all=False, n_part=28, n_vn_t=8,
+                          n_remote=4, dmax=8, seed=19)
+    g = synth.make_network(cfg)
+    part, _ = snn.snn_partition(snn.Network.from_synth(g), 16, "planted")
+    _same(snn, g, part, 16, 2, "greedy", relay)
 
 
 def test_relabelled_ids_random_mapping(snn):
