@@ -158,9 +158,18 @@ def phase_bytes(M: int, d_steps: int, d: dict, gid: bool) -> list:
     return [upd, l1, l2, dl]
 
 
+def model_params_of(snn, cfg):
+    """snn_model_params of a workload's network recipe (the generator seed and
+    statistics of `cfg`)."""
+    return snn.model_params(n_neurons=cfg.M, n_parts=cfg.P, vn_size=cfg.vn_size, syn_per_neuron=cfg.K,
+                            uniform=int(cfg.uniform_all), n_same_part=cfg.n_part, n_same_vn=cfg.n_vn_t,
+                            n_remote=cfg.n_remote, max_delay=cfg.dmax, seed=cfg.seed, v_reset=cfg.dyn.v_reset,
+                            v_th=cfg.dyn.v_th, frac_exc=cfg.frac_exc, mu_e=cfg.mu_e, sd_e=cfg.sd_e,
+                            mu_i=cfg.mu_i, sd_i=cfg.sd_i)
+
+
 def run_ours(args):
     import torch
-    import synth
     import paper_2205_07125_gb300 as snn
 
     dist, rank, world = dist_init()
@@ -168,16 +177,19 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     cfg = workload(rank, args.neurons, args.config)
-    K, W = args.steps, args.warmup
+    K, W, PR = args.steps, args.warmup, args.preroll
+    first = PR + W  # first timed step
 
     t_setup = time.time()
-    g = synth.make_network(cfg)
-    net = snn.Network.from_synth(g)
+    # the network through the C ABI (snn_model_build: the seeded generator)
+    model = snn.Model.build(model_params_of(snn, cfg))
+    net = model.network()
     part, _ = snn.snn_partition(net, cfg.P, "planted")
     rt = snn.Routing(net, part, cfg.P, cfg.n_vn, "contiguous")
     info = rt.info()
-    raster_cap = int(cfg.M * (K + W) * 0.002) + 100000
-    prm = snn.sim_params(cfg.dyn, raster_cap=raster_cap, raster_steps=K + W, steps_per_graph=32,
+    rec_steps = max(first + K, args.e2e_steps)
+    raster_cap = int(cfg.M * rec_steps * 0.0015) + 100000
+    prm = snn.sim_params(cfg.dyn, raster_cap=raster_cap, raster_steps=rec_steps, steps_per_graph=32,
                          pin_host_tables=1, defer_delayed=1 if args.defer else 0,
                          delivery=0 if args.defer else DELIVERY[args.delivery])
     sim = snn.Sim(net, rt, prm, device=dev)
@@ -187,10 +199,11 @@ def run_ours(args):
           % (setup_s, choice, tuned_ms), file=sys.stderr, flush=True)
     stream = sim.stream
 
-    # warm-up, then EXACTLY K timed steps from graph replays
-    sim.step(W)
+    # untimed pre-roll from rest into the steady state, warm-up, then EXACTLY
+    # K timed steps
+    sim.step(PR + W)
     if sim.sync_status() != 0:
-        raise RuntimeError("device status after warm-up: %d" % sim.sync_status())
+        raise RuntimeError("device status after pre-roll and warm-up: %d" % sim.sync_status())
     c0 = sim.read_counts()
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
@@ -220,65 +233,71 @@ def run_ours(args):
     dc = {k: c1[k] - c0[k] for k in c1}
     assert dc["steps"] == K
     events_all, ms_max, spikes_all = reduce_over_ranks(dist, float(dc["events"]), ms, float(dc["spikes"]))
-
-    # time split of a step over more steps: the step's work and the wait for
-    # the other blocks (persistent path: block 0's global-timer stamps; graph
-    # path: CUDA events around every step kernel, no separate wait)
-    NP = min(K, 2048)
-    ca = sim.read_counts()
-    phase_ms = sim.profile_phases(NP)
-    cb = sim.read_counts()
-    dp = {k: cb[k] - ca[k] for k in cb}
-    pb4 = phase_bytes(cfg.M, dp["steps"], dp, not info["identity_order"])
-    persistent = sim.launches(2) == 1
-    phases = {
-        "work": {"what": "update, compaction, level-1 bucketing, level-2 expansion, delivery"
-                         + (" (block 0)" if persistent else " (k_update + k_route kernels)"),
-                 "ms_per_step": phase_ms[0] / NP},
-        "sync": {"what": "block 0's wait at the grid barrier" if persistent else "none (kernel boundary)",
-                 "ms_per_step": phase_ms[1] / NP},
-        "bytes_per_step": dict(zip(["update", "level1", "level2", "deliver"], [x / NP for x in pb4])),
-    }
-    print("[bench] timed %.3f ms for %d steps; work/sync ms per step %s" % (
-        ms, K, [round(x / NP, 5) for x in phase_ms]), file=sys.stderr, flush=True)
+    launches = sim.launches(K)
+    persistent = launches == 1
+    # algorithmic bytes of the timed window, from its own counters
+    pbw = phase_bytes(cfg.M, K, dc, not info["identity_order"])
+    step_bytes = sum(pbw) / K
     peak, peak_kind = _peaks()
-    step_bytes = sum(pb4) / NP
     if persistent:
-        # one cooperative launch runs every timed step: the kernel's launch
-        # duration is the timed region, its algorithmic bytes those of K steps
+        # one cooperative launch runs every timed step: its duration is the
+        # timed region, its algorithmic bytes those of the K steps
         kern = "k_persist"
-        achieved = step_bytes * K / (ms * 1e-3) / 1e9
         per_launch = step_bytes * K
+        achieved = per_launch / (ms * 1e-3) / 1e9
     else:
+        # two kernels per step: the step's bytes over the step's time
         kern = "k_update+k_route"
-        achieved = step_bytes / (phase_ms[0] / NP * 1e-3) / 1e9
         per_launch = step_bytes
-    traffic = load_traffic(kern, events_all / world / K)
+        achieved = step_bytes / (ms / K * 1e-3) / 1e9
+    traffic = load_traffic(kern, events_all / world / K, cfg.M)
     roof = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak,
             "peak_source": ("measured (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                             else "fallback 6.8 TB/s"),
             "algorithmic_bytes_per_launch": per_launch,
+            "bytes_per_step": dict(zip(["update", "level1", "level2", "deliver"], [x / K for x in pbw])),
+            "window": "the timed steps' own counters",
             "traffic": (traffic * (K if persistent else 1)) if traffic is not None else None}
-    # the deliveries are 32-bit reductions into the L2-resident delay ring:
-    # the whole step's event rate against the rate of the same reductions
-    # measured here on random targets
-    red_peak = red_rate(cfg.M * info["max_delay"], 1 << 22)
-    atom = {"what": "synaptic events (one 32-bit L2 reduction each) per second over the whole step, "
-                    "vs torch index_add_ of 4M random int32 reductions into a ring-sized buffer",
+    # the deliveries are 32-bit reductions: the step's event rate against
+    # the rate of the same reductions on random targets in an L2-sized
+    # buffer (the input slots of delivery by arrival step, or the delay
+    # ring), measured here
+    arrival = choice >= 1000
+    n_red = cfg.M * 2 if arrival else cfg.M * (info["max_delay"] + 1)
+    red_peak = red_rate(n_red, 1 << 22)
+    atom = {"what": "synaptic events (one 32-bit reduction each) per second over the whole step, vs torch "
+                    "index_add_ of 4M random int32 reductions into a buffer of the accumulators' size",
+            "buffer_mb": n_red * 4 / 1e6,
             "achieved": events_all / world / (ms_max * 1e-3), "peak": red_peak, "unit": "reductions/s",
             "frac": events_all / world / (ms_max * 1e-3) / red_peak}
+    # spikes of the timed window (for the per-partition route traffic)
+    ids_w, _ = sim.read_raster(first, first + K)
+
+    # parts of a step over more steps (block 0's timers on the persistent
+    # path, events around the two kernels on the graph path)
+    NP = min(K, 1000)
+    phase_ms = sim.profile_phases(NP)
+    persistent_names = ["update", "prefetch_and_queued_delivery", "barrier1_wait", "route",
+                        "next_drive_and_barrier2_wait"]
+    phases = {"what": ("block 0 of the persistent kernel" if persistent else "k_update and k_route kernels")
+                      + ", %d steps after the timed ones" % NP,
+              "ms_per_step": dict(zip(persistent_names, [x / NP for x in phase_ms])) if persistent else
+              {"k_update": phase_ms[0] / NP, "k_route": phase_ms[3] / NP}}
+    print("[bench] timed %.3f ms for %d steps (steps %d..%d); parts ms per step %s" % (
+        ms, K, first, first + K - 1, [round(x / NP, 5) for x in phase_ms]), file=sys.stderr, flush=True)
 
     # end to end through the C ABI: upload of every table from pinned host
-    # memory, K steps, read-back of the raster and the counters
+    # memory, the steps, read-back of the raster and the counters
     e2e = None
     if not args.no_e2e:
+        KE = args.e2e_steps
         torch.cuda.synchronize()
         barrier(dist)
         h0 = time.perf_counter()
         sim.reset(reupload=True)
-        sim.step(K)
-        ids, off = sim.read_raster(0, K)
+        sim.step(KE)
+        ids, off = sim.read_raster(0, KE)
         ce = sim.read_counts()
         h1 = time.perf_counter()
         e2e_ms = (h1 - h0) * 1e3
@@ -290,67 +309,108 @@ def run_ours(args):
                + cfg.M * 6 + (0 if info["identity_order"] else cfg.M * 8))
         d2h = ids.nbytes + off.nbytes + 88
         e2e = {"value": e2e_events / (e2e_ms_max * 1e-3), "unit": UNIT,
-               "h2d_bytes_per_step": h2d / K, "d2h_bytes_per_step": d2h / K,
-               "what": "snn_sim_reset(reupload) from pinned host tables + snn_step(K) + "
-                       "snn_read_raster + snn_read_counts, host wall clock"}
+               "h2d_bytes_per_step": h2d / KE, "d2h_bytes_per_step": d2h / KE, "steps": KE,
+               "what": "snn_sim_reset(reupload) from pinned host tables + snn_step(%d) from rest + "
+                       "snn_read_raster + snn_read_counts, host wall clock" % KE}
 
     result = {
         "metric": METRIC, "value": events_all / (ms_max * 1e-3), "unit": UNIT, "n_gpus": world,
         "steps": K, "warmup": W, "ms_per_step": ms_max / K, "steps_per_s": K / (ms_max * 1e-3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+i32",
-        "data": "synthetic (seeded generator; stands in for the paper's scanned brain model)",
+        "data": "synthetic (seeded generator behind snn_model_build; stands in for the paper's scanned brain "
+                "model)",
         "config": {"workload": cfg.name, "neurons": cfg.M, "partitions": cfg.P,
                    "virtual_nodes": cfg.n_vn, "synapses": info["n_synapses"],
-                   "synapses_per_neuron": cfg.K, "locality": ("uniform" if cfg.uniform_all else "%d/%d/%d" % (cfg.n_part, cfg.n_vn_t, cfg.n_remote)), "delays": "1-%d" % cfg.dmax,
+                   "synapses_per_neuron": cfg.K,
+                   "locality": ("uniform" if cfg.uniform_all else "%d/%d/%d" % (cfg.n_part, cfg.n_vn_t, cfg.n_remote)),
+                   "delays": "1-%d" % cfg.dmax,
                    "drive_lambda_per_step": cfg.dyn.drive_lambda, "w_ext": cfg.dyn.w_ext,
                    "parallelism": "replicas x%d" % world,
-                   "l2": "inputs larger than L2: %.1f GB synapse CSR, the step's rows streamed from HBM; "
-                         "delay ring %.0f MB (L2-resident when it fits the 129 MB L2)"
-                         % (info["n_synapses"] * 6 / 1e9, cfg.M * (info["max_delay"] + 1) * 4 / 1e6),
+                   "step_window": {"preroll": PR, "warmup": W, "first_timed_step": first,
+                                   "last_timed_step": first + K - 1,
+                                   "why": "untimed pre-roll from rest into the steady firing state"},
+                   "l2": "inputs larger than L2: %.1f GB synapse CSR, the step's rows streamed from HBM"
+                         % (info["n_synapses"] * 6 / 1e9),
                    "steps_per_graph": 32,
                    "execution": ("persistent cooperative kernel" if persistent else "CUDA graphs")
-                                + (", minimum-delay batching" if args.defer else ""),
+                                + (", minimum-delay batching" if args.defer else "")
+                                + (", delivery by arrival step" if choice >= 1000 else ", delay-ring delivery"),
                    "autotune": {"choice": choice, "ms_per_step": tuned_ms,
-                                "meaning": "0 graph path, else 100*mode + blocks per SM (mode 2 "
-                                           "shared-memory state, 1 global 16-byte, 0 global scalar)"}},
+                                "meaning": "+1000 delivery by arrival step; 0 graph path, else 100*mode + blocks "
+                                           "per SM (mode 2 shared-memory state, 1 global 16-byte, 0 global scalar)"}},
         "spikes_per_step": spikes_all / world / K,
         "events_per_step": events_all / world / K,
         "rate_hz": spikes_all / world / K / cfg.M / (cfg.dyn.dt_ms * 1e-3),
         "roofline": roof,
         "atomic_roofline": atom,
-        "step_roofline": {"bytes_per_step": step_bytes,
-                          "achieved_gbs": step_bytes / (ms_max / K * 1e-3) / 1e9,
-                          "frac": step_bytes / (ms_max / K * 1e-3) / 1e9 / peak},
         "phases": phases,
-        "gpu_launches": sim.launches(K),
+        "gpu_launches": launches,
         "clocks": clocks.summary(wall0, wall1),
         "e2e": e2e,
-        "routing": routing_report(dc, info, rt),
+        "routing": routing_report(dc, info, rt, ids_w, K),
         "setup_s": setup_s,
     }
+    # the GPU on the oracle's sample window (the first steps from rest)
+    NS = oracle_sample_steps(cfg)
+    sim.reset()
+    ca = sim.read_counts()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    sim.step(NS)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    same_ms = e0.elapsed_time(e1)
+    same_ev = sim.read_counts()["events"] - ca["events"]
     sim.close()
     del sim
+    rt.close()
+    del rt, net, model
+    if rank == 0 and world == 1 and not args.no_forms:
+        result["forms"] = forms_report(args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        result["cpu_baseline"] = cpu_baseline(cfg, g, args.cpu_seconds)
+        cb = oracle_sample(cfg, NS)
+        cb["gpu_same_window"] = {"value": same_ev / (same_ms * 1e-3), "unit": UNIT,
+                                 "what": "this GPU on the same steps 0..%d from rest" % (NS - 1)}
+        result["cpu_baseline"] = cb
     if rank == 0:
         print(json.dumps(result), flush=True)
     if dist is not None:
         dist.destroy_process_group()
 
 
-def routing_report(dc, info, rt):
+def routing_report(dc, info, rt, ids, K):
+    """Messages of the timed window: per spike on each route (device
+    counters), per partition (snn_routing_traffic over the window's spikes)
+    with the peak -- the busiest partition, the paper's comparison -- for the
+    direct route and the two-level route under each relay policy, and the
+    static connections per partition."""
+    import paper_2205_07125_gb300 as snn
     S = max(1, dc["spikes"])
     two = dc["l1_xvn"] + dc["l2_peer"] + dc["l2_relay_remote"]
     cd, ct = rt.connections()
+    per_part = {}
+    for pol in snn.RELAY_POLICIES:
+        tr = rt.traffic(ids, pol)
+        if "direct" not in per_part:
+            d = tr["direct_out"] / K
+            per_part["direct"] = {"sent_peak_per_step": float(d.max()), "sent_mean_per_step": float(d.mean()),
+                                  "received_peak_per_step": float((tr["direct_in"] / K).max())}
+        t = tr["two_level_out"] / K
+        per_part["two_level_" + pol] = {"sent_peak_per_step": float(t.max()), "sent_mean_per_step": float(t.mean()),
+                                        "received_peak_per_step": float((tr["two_level_in"] / K).max())}
+    hist = lambda a: {int(k): int(v) for k, v in zip(*np.unique(a, return_counts=True))}
     return {
         "messages_per_spike": {"direct": dc["direct"] / S, "direct_cross_vn": dc["direct_xvn"] / S,
                                "two_level": two / S, "two_level_l1_cross_vn": dc["l1_xvn"] / S,
                                "two_level_l2_relay_forward": dc["l2_relay_remote"] / S},
         "bytes_per_step": {"direct": 4 * dc["direct"] / dc["steps"],
                            "two_level": 4 * two / dc["steps"]},
+        "per_partition": per_part,
+        "per_partition_what": "messages per partition per step over the timed window (one message = one "
+                              "(spike, destination) pair); peak = the busiest partition",
         "connections_per_partition": {"direct_mean": float(cd.mean()), "direct_max": int(cd.max()),
-                                      "two_level_mean": float(ct.mean()),
-                                      "two_level_max": int(ct.max())},
+                                      "two_level_mean": float(ct.mean()), "two_level_max": int(ct.max()),
+                                      "direct_histogram": hist(cd), "two_level_histogram": hist(ct)},
     }
 
 
@@ -374,7 +434,7 @@ def kernel_source_sha() -> str:
     return hs.hexdigest()[:16]
 
 
-def load_traffic(kernel: str, events_per_step: float):
+def load_traffic(kernel: str, events_per_step: float, M: int):
     """DRAM bytes per step of `kernel` from the committed ncu summary, if it
     was taken on the current kernel source (else null).  The capture runs a
     smaller network of the same recipe; the neuron state stays on chip, so
@@ -386,7 +446,7 @@ def load_traffic(kernel: str, events_per_step: float):
             t = json.load(f)
     except (OSError, ValueError):
         return None
-    ent = t.get(kernel)
+    ent = t.get("%s@%d" % (kernel, M)) or t.get(kernel)
     if not ent or ent.get("source_sha") != kernel_source_sha():
         return None
     return ent["dram_bytes_per_step"] * events_per_step / ent["events_per_step"]
@@ -414,131 +474,101 @@ def red_rate(n_ring: int, n: int, reps: int = 20) -> float:
 
 
 # ------------------------------------------------------------------ CPU oracle
-def cpu_baseline(cfg, g, seconds: float):
-    """The CPU oracle, as it stands, on the host cores: a bounded sample of
-    consecutive steps of the same network, from rest."""
+def oracle_sample_steps(cfg) -> int:
+    """Steps of the CPU oracle's bounded sample (from rest), sized for 10-30 s
+    of sequential work: 1000 at 4,096 neurons, about 30 at 5,000,000."""
+    return int(max(20, min(1000, round(1.5e8 / (cfg.M + 40.0 * cfg.M * cfg.K / 1000.0)))))
+
+
+def oracle_sample(cfg, steps: int) -> dict:
+    """The CPU oracle, as it stands, on one host core: the first `steps`
+    steps from rest of the workload's network (its own copy from the seeded
+    generator), timed; the same sample in both bench arms."""
+    import synth
     import oracle
+    g = synth.make_network(cfg)
     P = cfg.P
     t0 = time.time()
     o = oracle.Oracle(g, P, oracle.partition_planted(g.M, P), cfg.n_vn,
                       oracle.group_contiguous(P, cfg.n_vn), cfg.dyn)
     setup = time.time() - t0
-    steps = 0
     t0 = time.perf_counter()
-    while True:
-        o.run(10, raster=False, hashes=False)
-        steps += 10
-        el = time.perf_counter() - t0
-        if el >= seconds:
-            break
-    ev = o.count_dict()["events"]
-    return {"value": ev / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "steps_per_s": steps / el,
-            "sample": "first %d steps from rest of the same %d-neuron network, sequential C oracle "
-                      "(%.1f s timed, %.1f s setup untimed)" % (steps, g.M, el, setup)}
+    o.run(steps, raster=False, hashes=False)
+    el = time.perf_counter() - t0
+    c = o.count_dict()
+    return {"value": c["events"] / el, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
+            "steps_per_s": steps / el, "spikes_per_step": c["spikes"] / steps, "seconds": el,
+            "sample": "steps 0..%d from rest of the same %d-neuron network, sequential C oracle on one of the "
+                      "host's %d cores (%.1f s timed, %.1f s setup untimed)"
+                      % (steps - 1, g.M, os.cpu_count(), el, setup)}
 
 
 def run_reference(args):
-    """Reference arm: the CPU oracle timed on the host, rank 0 only."""
+    """Reference arm: the CPU oracle timed on the host, rank 0 only: the
+    first steps from rest of the workload's network, the sample the repo
+    arm's cpu_baseline times."""
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if rank != 0:
         return
-    import synth
-    import oracle
-    cfg = workload(0, args.neurons, args.config if args.config in ("scale", "paper", "tiny") else "scale")
-    g = synth.make_network(cfg)
-    P = cfg.P
-    o = oracle.Oracle(g, P, oracle.partition_planted(g.M, P), cfg.n_vn,
-                      oracle.group_contiguous(P, cfg.n_vn), cfg.dyn)
-    # each "step" of this arm is one simulation step; the counts are bounded
-    # so that the whole run ends within a few minutes
-    W = min(args.warmup, 20)
-    K = min(args.steps, args.ref_steps)
-    o.run(W, raster=False, hashes=False)
-    c0 = o.count_dict()
-    t0 = time.perf_counter()
-    o.run(K, raster=False, hashes=False)
-    el = time.perf_counter() - t0
-    c1 = o.count_dict()
-    ev = c1["events"] - c0["events"]
-    v = ev / el
+    cfg = workload(0, args.neurons, args.config if args.config in ("scale", "paper", "tiny") else "paper")
+    steps = oracle_sample_steps(cfg)
+    r = oracle_sample(cfg, steps)
+    v = r["value"]
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
-           "steps": K, "warmup": W, "ms_per_step": el * 1e3 / K, "higher_is_better": True,
+           "steps": steps, "warmup": 0, "ms_per_step": r["seconds"] * 1e3 / steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32+i32", "data": "synthetic",
            "config": {"workload": cfg.name, "neurons": cfg.M, "partitions": cfg.P,
-                      "virtual_nodes": cfg.n_vn, "synapses": g.E},
-           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                            "sample": "steps %d..%d of the %d-neuron network, sequential C oracle"
-                                      % (W, W + K, g.M)},
+                      "virtual_nodes": cfg.n_vn, "synapses": cfg.M * cfg.K},
+           "cpu_baseline": {k: r[k] for k in ("value", "unit", "cores", "host_cores", "kind", "sample")},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
 
-def run_batch(args):
-    """The batched form: 64 independent networks of uneven sizes (10k-500k
-    neurons, 4-32 partitions, out-degree 100-1000, scaled drives) stepped by
-    one sim, against the same networks stepped one after another by one plain
+def batch_form(dev, n_nets: int, K: int, W: int, separate_steps: int, seed: int = 3000) -> dict:
+    """The batched form: n_nets independent networks of uneven sizes (the
+    batched workload's distribution: 10k-500k neurons, 4-32 partitions,
+    out-degree 100-1000, scaled drives) stepped by one sim in the autotuned
+    shape, against the same networks stepped one after another by one plain
     sim each (the same work, one launch per network instead of one in all)."""
     import torch
     import synth
     import paper_2205_07125_gb300 as snn
 
-    dist, rank, world = dist_init()
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    K, W = args.steps, args.warmup
     t_setup = time.time()
-    cfgs = synth.batch_configs(n=args.batch_nets, seed=3000 + 100 * rank)
+    cfgs = synth.batch_configs(n=n_nets, seed=seed)
     b = synth.make_batch(cfgs)
     net = snn.Network.from_synth(b.net)
     rt = snn.Routing(net, b.part, b.P, b.n_vn, "contiguous")
     info = rt.info()
-    plist = [snn.sim_params(c.dyn, steps_per_graph=32) for c in cfgs]
+    plist = [snn.sim_params(c.dyn, steps_per_graph=32, delivery=snn.SNN_DELIVER_AUTO) for c in cfgs]
     sim = snn.Sim(net, rt, plist[0], device=dev, batch=(b.off, plist))
     choice, tuned_ms = sim.autotune(200)
     setup_s = time.time() - t_setup
-    print("[bench] batch of %d networks, %d neurons, %d synapses; setup %.1f s; autotune choice %d (%.4f ms/step)"
-          % (len(cfgs), b.net.M, b.net.E, setup_s, choice, tuned_ms), file=sys.stderr, flush=True)
     stream = sim.stream
     sim.step(W)
     if sim.sync_status() != 0:
         raise RuntimeError("device status after warm-up: %d" % sim.sync_status())
     c0 = sim.read_counts()
-    clocks = ClockSampler(torch.cuda.current_device())
-    clocks.start()
-    time.sleep(0.3)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    barrier(dist)
     torch.cuda.synchronize()
-    wall0 = time.time()
     e0.record(stream)
     sim.step(K)
     e1.record(stream)
     torch.cuda.synchronize()
-    wall1 = time.time()
-    barrier(dist)
-    time.sleep(0.1)
-    clocks.stop()
     ms = e0.elapsed_time(e1)
     if sim.sync_status() != 0:
         raise RuntimeError("device status after the timed steps: %d" % sim.sync_status())
     c1 = sim.read_counts()
     dc = {k: c1[k] - c0[k] for k in c1}
-    assert dc["steps"] == K
-    # per-network firing rates of the timed steps (from a short recorded run)
-    events_all, ms_max, spikes_all = reduce_over_ranks(dist, float(dc["events"]), ms, float(dc["spikes"]))
-    pb4 = phase_bytes(b.net.M, K, dc, not info["identity_order"])
-    step_bytes = sum(pb4) / K
-    peak, peak_kind = _peaks()
     launches = sim.launches(K)
+    pb = phase_bytes(b.net.M, K, dc, not info["identity_order"])
     sim.close()
     del sim
-
+    rt.close()
     # the same networks, one plain sim each, stepped one after another
-    KS = min(K, args.separate_steps)
+    KS = min(K, separate_steps)
     sep_ms, sep_ev = 0.0, 0.0
     for c, g, p in zip(cfgs, b.nets, plist):
         n1 = snn.Network.from_synth(g)
@@ -548,68 +578,36 @@ def run_batch(args):
         s1.step(W)
         a0 = s1.read_counts()
         torch.cuda.synchronize()
-        f0 = torch.cuda.Event(enable_timing=True)
-        f1 = torch.cuda.Event(enable_timing=True)
-        f0.record(s1.stream)
+        e0.record(s1.stream)
         s1.step(KS)
-        f1.record(s1.stream)
+        e1.record(s1.stream)
         torch.cuda.synchronize()
-        sep_ms += f0.elapsed_time(f1)
+        sep_ms += e0.elapsed_time(e1)
         sep_ev += s1.read_counts()["events"] - a0["events"]
         s1.close()
+        r1.close()
         del s1, r1, n1
+    value = dc["events"] / (ms * 1e-3)
     sep_rate = sep_ev / (sep_ms * 1e-3)
-    value = events_all / (ms_max * 1e-3)
-    result = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
-        "ms_per_step": ms_max / K, "steps_per_s": K / (ms_max * 1e-3), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+i32",
-        "data": "synthetic (seeded generator; 64 independent networks stand in for a batch of models)",
-        "config": {"workload": "batch-%dnets-%dn" % (len(cfgs), b.net.M), "networks": len(cfgs),
-                   "neurons": b.net.M, "synapses": b.net.E, "partitions": b.P, "virtual_nodes": b.n_vn,
-                   "sizes": "log-uniform 10k-500k", "synapses_per_neuron": "uniform 100-1000",
-                   "partitions_per_network": "4-32 (VNs of 2)", "drive": "scale drive x r/10, r ~ U[5, 15] Hz",
-                   "parallelism": "replicas x%d" % world, "execution": "autotuned shape %d" % choice,
-                   "l2": "inputs larger than L2: %.1f GB synapse CSR" % (b.net.E * 6 / 1e9)},
-        "spikes_per_step": spikes_all / world / K, "events_per_step": events_all / world / K,
-        "rate_hz": spikes_all / world / K / b.net.M / 1e-4,
-        "roofline": {"bound": "hbm", "kernel": "k_persist" if launches == 1 else "k_update+k_route",
-                     "achieved": step_bytes * K / (ms_max * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
-                     "frac": step_bytes * K / (ms_max * 1e-3) / 1e9 / peak,
-                     "peak_source": ("measured (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
-                                     else "fallback 6.8 TB/s"),
-                     "algorithmic_bytes_per_launch": step_bytes * (K if launches == 1 else 1), "traffic": None},
-        "vs_plain": {"what": "the same %d networks, one plain sim each, stepped one after another "
-                             "(%d steps each)" % (len(cfgs), KS),
-                     "value": sep_rate, "unit": UNIT, "batched_over_plain": value / sep_rate},
-        "autotune": {"choice": choice, "ms_per_step": tuned_ms,
-                     "meaning": "0 graph path, else 100*mode + blocks per SM (mode 2 shared-memory state, "
-                                "1 global 16-byte, 0 global scalar)"},
-        "gpu_launches": launches,
-        "clocks": clocks.summary(wall0, wall1),
-        "e2e": None,
-        "setup_s": setup_s,
-    }
-    if rank == 0:
-        print(json.dumps(result), flush=True)
-    if dist is not None:
-        dist.destroy_process_group()
+    return {"networks": len(cfgs), "neurons": b.net.M, "synapses": b.net.E, "partitions": b.P,
+            "virtual_nodes": b.n_vn, "steps": K, "warmup": W, "ms_per_step": ms / K, "value": value,
+            "unit": UNIT, "spikes_per_step": dc["spikes"] / K, "events_per_step": dc["events"] / K,
+            "rate_hz": dc["spikes"] / K / b.net.M / 1e-4, "step_bytes": sum(pb) / K, "gpu_launches": launches,
+            "autotune": {"choice": choice, "ms_per_step": tuned_ms}, "setup_s": setup_s,
+            "vs_plain": {"what": "the same %d networks, one plain sim each (default launch shape), stepped one "
+                                 "after another (%d steps each)" % (len(cfgs), KS),
+                         "value": sep_rate, "unit": UNIT, "batched_over_plain": value / sep_rate}}
 
 
-def run_adjoint(args):
+def adjoint_form(dev, T: int = 500, CK: int = 50, reps: int = 1, warm: int = 1, rank: int = 0) -> dict:
     """The adjoint form: 131,072 neurons in 8 partitions over 2 VNs, 500
-    synapses per neuron (scale locality mix), 500 steps forward with
-    checkpoints every 50, then the surrogate-gradient backward; against the
+    synapses per neuron (scale locality mix), T steps forward with membrane
+    checkpoints every CK, then the surrogate-gradient backward; against the
     plain step of the same network on the same GPU."""
     import torch
     import synth
     import paper_2205_07125_gb300 as snn
 
-    dist, rank, world = dist_init()
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    T, CK = 500, 50
     cfg = synth.NetConfig(name="adjoint-131072n-8p-2vn-k500", M=131072, P=8, n_vn=2, K=500, uniform_all=False,
                           n_part=350, n_vn_t=100, n_remote=50, dmax=8, seed=1004 + rank, steps=T,
                           dyn=synth.Dynamics(drive_lambda=0.8, w_ext=89, drive_seed=2004 + rank))
@@ -626,12 +624,11 @@ def run_adjoint(args):
     lam = np.full(n_pop, 0.8, np.float32)
     target = (5.0 + 10.0 * rng.random(n_pop)) * 1e-4  # spikes per neuron per step (5-15 Hz)
     setup_s = time.time() - t_setup
-    for _ in range(max(1, args.warmup // 50)):
+    for _ in range(max(1, warm)):
         r = a.forward(G, lam)
         a.backward(2 * (r.astype(np.float64) - target) / n_pop)
-    reps = max(1, min(args.steps // T, 10))
     fw = bw = 0.0
-    for _ in range(reps):
+    for _ in range(max(1, reps)):
         torch.cuda.synchronize()
         h0 = time.perf_counter()
         r = a.forward(G, lam)
@@ -640,13 +637,12 @@ def run_adjoint(args):
         h2 = time.perf_counter()
         fw += h1 - h0
         bw += h2 - h1
-    fw /= reps
-    bw /= reps
+    fw /= max(1, reps)
+    bw /= max(1, reps)
     spikes = a.spikes
-    events = spikes * cfg.K
     a.close()
     # the plain step of the same network (its own Poisson drive), same steps
-    sim = snn.Sim(net, rt, snn.sim_params(cfg.dyn), device=dev)
+    sim = snn.Sim(net, rt, snn.sim_params(cfg.dyn, delivery=snn.SNN_DELIVER_AUTO), device=dev)
     sim.autotune(100)
     sim.step(100)
     c0 = sim.read_counts()
@@ -660,24 +656,107 @@ def run_adjoint(args):
     pms = e0.elapsed_time(e1)
     pev = sim.read_counts()["events"] - c0["events"]
     sim.close()
+    rt.close()
     it = fw + bw
+    return {"workload": cfg.name, "neurons": cfg.M, "partitions": cfg.P, "virtual_nodes": cfg.n_vn,
+            "synapses": g.E, "steps": T, "checkpoint_every": CK, "populations": n_pop,
+            "parameters": "%d gains + %d drive rates" % (n_pop * n_pop, n_pop),
+            "surrogate": "1/(1+5|V-theta|)^2, reset detached",
+            "timing": "host wall clock of snn_adjoint_forward / _backward (each synchronises), %d run(s)" % reps,
+            "forward_ms": fw * 1e3, "backward_ms": bw * 1e3, "forward_spikes": spikes,
+            "value": spikes * cfg.K / it, "unit": UNIT,
+            "rates_hz": [float(x) * 1e4 for x in r],
+            "grad_norm": float(np.sqrt((dG ** 2).sum() + (dlam ** 2).sum())), "setup_s": setup_s,
+            "vs_plain": {"what": "plain step of the same network, %d steps, CUDA events" % T,
+                         "plain_ms_per_step": pms / T, "plain_events_per_s": pev / (pms * 1e-3),
+                         "forward_over_plain_time": fw * 1e3 / pms,
+                         "forward_backward_over_plain_time": it * 1e3 / pms}}
+
+
+def forms_report(args, dev) -> dict:
+    """The batched and adjoint forms against the plain step (the metric's
+    "batched/adjoint vs plain"), at reduced cost for the default line: the
+    first --form-nets networks of the batched workload (seed 3000) for 500
+    steps, and the adjoint workload at full size (500 steps, checkpoints
+    every 50, one timed forward + backward)."""
+    t0 = time.time()
+    bf = batch_form(dev, args.form_nets, 500, 20, 500)
+    af = adjoint_form(dev, 500, 50, reps=1, warm=1)
+    out = {"batched_over_plain": bf["vs_plain"]["batched_over_plain"],
+           "adjoint_fwd_bwd_over_plain": af["vs_plain"]["forward_backward_over_plain_time"],
+           "batched": bf, "adjoint": af, "seconds": time.time() - t0}
+    print("[bench] forms: batched/plain %.2f, adjoint (fwd+bwd)/plain %.1f (%.0f s)"
+          % (out["batched_over_plain"], out["adjoint_fwd_bwd_over_plain"], out["seconds"]),
+          file=sys.stderr, flush=True)
+    return out
+
+
+def run_batch(args):
+    """--config batch: the batched form at the workload's full count of
+    networks, one JSON line."""
+    import torch
+    dist, rank, world = dist_init()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    wall0 = time.time()
+    bf = batch_form(dev, args.batch_nets, args.steps, args.warmup, args.separate_steps, seed=3000 + 100 * rank)
+    wall1 = time.time()
+    clocks.stop()
+    events_all, ms_max, _ = reduce_over_ranks(dist, bf["events_per_step"] * args.steps, bf["ms_per_step"] * args.steps)
+    peak, peak_kind = _peaks()
+    per_launch = bf["step_bytes"] * (args.steps if bf["gpu_launches"] == 1 else 1)
+    t_launch = ms_max if bf["gpu_launches"] == 1 else ms_max / args.steps
     result = {
-        "metric": METRIC, "value": events / it, "unit": UNIT, "n_gpus": world, "steps": T, "warmup": args.warmup,
+        "metric": METRIC, "value": events_all / (ms_max * 1e-3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "steps_per_s": args.steps / (ms_max * 1e-3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+i32",
+        "data": "synthetic (seeded generator; independent networks stand in for a batch of models)",
+        "config": {"workload": "batch-%dnets-%dn" % (bf["networks"], bf["neurons"]), "networks": bf["networks"],
+                   "neurons": bf["neurons"], "synapses": bf["synapses"], "partitions": bf["partitions"],
+                   "virtual_nodes": bf["virtual_nodes"], "sizes": "log-uniform 10k-500k",
+                   "synapses_per_neuron": "uniform 100-1000", "partitions_per_network": "4-32 (VNs of 2)",
+                   "drive": "scale drive x r/10, r ~ U[5, 15] Hz", "parallelism": "replicas x%d" % world,
+                   "execution": "autotuned shape %d" % bf["autotune"]["choice"],
+                   "l2": "inputs larger than L2: %.1f GB synapse CSR" % (bf["synapses"] * 6 / 1e9)},
+        "spikes_per_step": bf["spikes_per_step"], "events_per_step": bf["events_per_step"], "rate_hz": bf["rate_hz"],
+        "roofline": {"bound": "hbm", "kernel": "k_persist" if bf["gpu_launches"] == 1 else "k_update+k_route",
+                     "achieved": per_launch / (t_launch * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": per_launch / (t_launch * 1e-3) / 1e9 / peak,
+                     "peak_source": ("measured (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                                     else "fallback 6.8 TB/s"),
+                     "algorithmic_bytes_per_launch": per_launch, "traffic": None},
+        "vs_plain": bf["vs_plain"], "autotune": bf["autotune"], "gpu_launches": bf["gpu_launches"],
+        "clocks": clocks.summary(wall0, wall1), "e2e": None, "setup_s": bf["setup_s"],
+    }
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_adjoint(args):
+    """--config adjoint: the adjoint form, one JSON line."""
+    import torch
+    dist, rank, world = dist_init()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    T, CK = 500, 50
+    af = adjoint_form(dev, T, CK, reps=max(1, min(args.steps // T, 10)), warm=max(1, args.warmup // 50), rank=rank)
+    it = (af["forward_ms"] + af["backward_ms"]) * 1e-3
+    result = {
+        "metric": METRIC, "value": af["value"], "unit": UNIT, "n_gpus": world, "steps": T, "warmup": args.warmup,
         "ms_per_step": it * 1e3 / T, "steps_per_s": T / it, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 (gradients f64)", "data": "synthetic",
-        "config": {"workload": cfg.name, "neurons": cfg.M, "partitions": cfg.P, "virtual_nodes": cfg.n_vn,
-                   "synapses": g.E, "steps": T, "checkpoint_every": CK, "populations": n_pop,
-                   "parameters": "%d gains + %d drive rates" % (n_pop * n_pop, n_pop),
-                   "surrogate": "1/(1+5|V-theta|)^2, reset detached",
-                   "timing": "host wall clock of snn_adjoint_forward / _backward (each synchronises)"},
-        "forward_ms": fw * 1e3, "backward_ms": bw * 1e3, "forward_spikes": spikes,
-        "rates_hz": [float(x) * 1e4 for x in r],
-        "grad_norm": float(np.sqrt((dG ** 2).sum() + (dlam ** 2).sum())),
-        "vs_plain": {"what": "plain step of the same network, %d steps, CUDA events" % T,
-                     "plain_ms_per_step": pms / T, "plain_events_per_s": pev / (pms * 1e-3),
-                     "forward_over_plain_time": fw * 1e3 / pms,
-                     "forward_backward_over_plain_time": it * 1e3 / pms},
-        "setup_s": setup_s,
+        "config": {k: af[k] for k in ("workload", "neurons", "partitions", "virtual_nodes", "synapses", "steps",
+                                      "checkpoint_every", "populations", "parameters", "surrogate", "timing")},
+        "forward_ms": af["forward_ms"], "backward_ms": af["backward_ms"], "forward_spikes": af["forward_spikes"],
+        "rates_hz": af["rates_hz"], "grad_norm": af["grad_norm"], "vs_plain": af["vs_plain"],
+        "setup_s": af["setup_s"],
     }
     if rank == 0:
         print(json.dumps(result), flush=True)
@@ -961,24 +1040,30 @@ def oracle_free_planted(M, P):
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--steps", type=int, default=5000)
     ap.add_argument("--warmup", type=int, default=100)
+    ap.add_argument("--preroll", type=int, default=1500,
+                    help="untimed steps from rest before the warm-up, into the steady firing state "
+                         "(the paper share's rate settles after about 1,000 steps)")
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--ref-steps", type=int, default=400)
     ap.add_argument("--neurons", type=int, default=0,
-                    help="network size with the scale workload's per-neuron statistics "
-                         "(default: the 1,048,576-neuron workload)")
+                    help="network size with the workload's per-neuron statistics (profiling cases)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=10000,
+                    help="steps of the end-to-end leg (tables uploaded once, then the steps from rest)")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the batched and adjoint forms against the plain step")
+    ap.add_argument("--form-nets", type=int, default=16,
+                    help="networks of the batched form in the default line (--config batch: --batch-nets)")
     ap.add_argument("--defer", action="store_true",
                     help="minimum-delay batching: delay >= 2 synapses delivered during the next step's "
                          "table walk (persistent shared-memory shape)")
     ap.add_argument("--config", choices=("scale", "paper", "tiny", "batch", "adjoint", "partition",
                                          "partition-device"),
-                    default="scale",
-                    help="scale: 1,048,576 neurons / 64 partitions (the headline workload); "
-                         "paper: the paper-shaped per-GPU share, 5,000,000 neurons / 256 partitions; "
+                    default="paper",
+                    help="paper: the paper-shaped per-GPU share, 5,000,000 neurons / 256 partitions (the "
+                         "headline workload); scale: 1,048,576 neurons / 64 partitions; "
                          "tiny: 4,096 neurons; batch: 64 independent networks of uneven sizes; "
                          "adjoint: forward + surrogate-gradient backward of a 131,072-neuron network; "
                          "partition: partition-quality and relay-policy study (JSON report); "

@@ -583,10 +583,12 @@ class Sim:
         return int(c.value), float(ms.value)
 
     def profile_phases(self, T: int) -> np.ndarray:
-        """Advance T steps and return the summed ms of [0] the steps' work
-        (update, compaction, level 1, level 2, delivery) and [1] the wait at
-        the grid barrier between steps (persistent path; 0 on the graph path)."""
-        out = np.zeros(2, np.float64)
+        """Advance T steps and return the summed ms of the parts of a step
+        (snn_profile_phases): persistent path [update half, own-table prefetch
+        and queued deliveries, rest of the first barrier wait, routing half,
+        next step's input-free update and the second barrier wait]; graph
+        path [k_update, 0, 0, k_route, 0]."""
+        out = np.zeros(5, np.float64)
         with self._dev():
             _ck(_lib.snn_profile_phases(self.h, int(T), out.ctypes.data), "snn_profile_phases")
         return out

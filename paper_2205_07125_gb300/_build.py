@@ -57,7 +57,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             # the seeded network generator (C, OpenMP), behind snn_model_build
             cmd = ["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-fvisibility=hidden",
                    "-c", src, "-o", o]
-        if verbose:
+        if verbose and cmd[0] == nvcc:
             cmd.insert(1, "-Xptxas=-v")
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
         objs.append(o)

@@ -315,7 +315,7 @@ static int make_layout(const snn_routing *rt, const snn_sim_params *p, Layout &L
     place(L, L.cur_rec, sizeof(int32_t) * (size_t)M * (size_t)p->cur_slots);
     place(L, L.fwd, rt->identity ? 0 : sizeof(uint32_t) * (size_t)M);
     place(L, L.fo_cnt, 64);
-    place(L, L.phase_ns, 2 * sizeof(unsigned long long));
+    place(L, L.phase_ns, kPhases * sizeof(unsigned long long));
     // SNN_DELIVERY=0|1|2 overrides the parameter (tests of every path)
     int delivery = p->delivery;
     if (const char *e = std::getenv("SNN_DELIVERY"))
@@ -990,37 +990,37 @@ extern "C" int snn_step(snn_sim *s, int32_t T)
 extern "C" int snn_profile_phases(snn_sim *s, int32_t T, double *phase_ms)
 {
     if (!s || T < 0 || !phase_ms) return SNN_E_ARG;
-    phase_ms[0] = phase_ms[1] = 0.0;
+    for (int k = 0; k < kPhases; ++k) phase_ms[k] = 0.0;
     if (s->persist) {
-        // block 0 sums its work of each step and its wait at the grid barrier
-        // after it, with the GPU's global timer
+        // block 0 sums the parts of each step with the GPU's global timer
         Dev dp = s->dev;
         dp.phase_ns = (unsigned long long *)(s->ws + s->L.phase_ns.off);
-        CK(cudaMemsetAsync(dp.phase_ns, 0, 2 * sizeof(unsigned long long), s->stream));
+        CK(cudaMemsetAsync(dp.phase_ns, 0, kPhases * sizeof(unsigned long long), s->stream));
         int rc = launch_persist(s, T, dp);
         if (rc) return rc;
-        unsigned long long ns[2];
+        unsigned long long ns[kPhases];
         CK(cudaMemcpyAsync(ns, dp.phase_ns, sizeof(ns), cudaMemcpyDeviceToHost, s->stream));
         CK(cudaStreamSynchronize(s->stream));
-        phase_ms[0] = ns[0] * 1e-6;
-        phase_ms[1] = ns[1] * 1e-6;
+        for (int k = 0; k < kPhases; ++k) phase_ms[k] = ns[k] * 1e-6;
         return SNN_OK;
     }
     if (!s->gP) {
-        // a graph of U steps with an event-record node before and after every
-        // step kernel (cudaEventRecordExternal: a plain record inside a
-        // capture only orders streams)
+        // a graph of U steps with an event-record node before, between and
+        // after the two step kernels of every step (cudaEventRecordExternal: a
+        // plain record inside a capture only orders streams)
         const int U = 16;
-        s->pev.resize((size_t)U * 2);
+        s->pev.resize((size_t)U * 3);
         for (auto &e : s->pev) CK(cudaEventCreate(&e));
         cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
         cudaError_t le = cudaSuccess;
         const unsigned fl = cudaEventRecordExternal;
         for (int k = 0; k < U && le == cudaSuccess; ++k) {
-            le = cudaEventRecordWithFlags(s->pev[2 * k], s->cap_stream, fl);
-            if (le == cudaSuccess) le = launch_step(s, k, s->cap_stream);
-            if (le == cudaSuccess) le = cudaEventRecordWithFlags(s->pev[2 * k + 1], s->cap_stream, fl);
+            le = cudaEventRecordWithFlags(s->pev[3 * k], s->cap_stream, fl);
+            if (le == cudaSuccess) le = launch_half(s, 0, k, s->cap_stream);
+            if (le == cudaSuccess) le = cudaEventRecordWithFlags(s->pev[3 * k + 1], s->cap_stream, fl);
+            if (le == cudaSuccess) le = launch_half(s, 1, k, s->cap_stream);
+            if (le == cudaSuccess) le = cudaEventRecordWithFlags(s->pev[3 * k + 2], s->cap_stream, fl);
         }
         if (le == cudaSuccess) {
             k_advance<<<1, 1, 0, s->cap_stream>>>(s->dev, U);
@@ -1043,9 +1043,11 @@ extern "C" int snn_profile_phases(snn_sim *s, int32_t T, double *phase_ms)
             CK(cudaGraphLaunch(s->gP, s->stream));
             CK(cudaStreamSynchronize(s->stream));
             for (int k = 0; k < s->UP; ++k) {
-                float ms = 0.f;
-                CK(cudaEventElapsedTime(&ms, s->pev[2 * k], s->pev[2 * k + 1]));
-                phase_ms[0] += ms;
+                float a = 0.f, b = 0.f;
+                CK(cudaEventElapsedTime(&a, s->pev[3 * k], s->pev[3 * k + 1]));
+                CK(cudaEventElapsedTime(&b, s->pev[3 * k + 1], s->pev[3 * k + 2]));
+                phase_ms[0] += a;
+                phase_ms[3] += b;
             }
             left -= s->UP;
         } else {

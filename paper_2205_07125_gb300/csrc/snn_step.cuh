@@ -66,6 +66,12 @@ constexpr uint32_t kStBucket = 1u, kStInbox = 2u, kStRaster = 4u, kStTimeout = 8
 constexpr int kArrPool = 1024;
 constexpr int kMaxArr = 8;
 
+// Parts of a step timed by block 0 of k_persist (snn_profile_phases): the
+// update half, its own-table prefetch and queued deliveries, the rest of the
+// first barrier's wait, the routing half, the next step's input-free update
+// with the second barrier's wait.
+constexpr int kPhases = 5;
+
 // counter slots: steps and spikes in Dev::counters (closing thread), the
 // others in each block's tally row
 enum { C_STEPS = 0, C_SPIKES, C_EVENTS, C_L1_LOCAL, C_L1_XVN, C_L2_BASE /* + cls (4) */, C_N = 16 };
@@ -134,7 +140,7 @@ struct Dev {
     int32_t *cur_rec;
     unsigned long long *counters;  // [C_N] steps and spikes
     unsigned long long *tally;     // [tally_rows][C_N] per-block event and message tallies
-    unsigned long long *phase_ns;  // [2] k_persist: block 0's work and barrier wait (profiling)
+    unsigned long long *phase_ns;  // [kPhases] k_persist: block 0's time per part of a step (profiling)
     Ctrl *ctrl;
     // delivery by arrival step (n_arr > 0; 0: every delay at the spike step
     // into the delay ring)
@@ -824,56 +830,59 @@ __device__ __forceinline__ void route_finish(const Dev &d, int tm, int32_t *fix,
 
 // a6 for runs queued on an arrival list (delivery by arrival step): records
 // recs[lo, hi) (offset << 24 | length) into fix by the block's warps, 32
-// records per warp at a time: runs of up to kShortSeg synapses a lane each
-// (4 loads in flight), longer ones by the whole warp (4 per lane in flight).
+// records per warp at a time.  The warp numbers the synapses of its 32 runs
+// through (a warp scan of the lengths) and takes them 128 at a time, four
+// per lane with every load in flight before the reductions; a lane finds the
+// run of its synapse by a binary search over the lanes' prefix sums.  The
+// next 32 records are loaded while the current ones are delivered.
 __device__ __forceinline__ void deliver_records(const Dev &d, int32_t *fix, const unsigned long long *recs,
                                                 unsigned long long lo, unsigned long long hi)
 {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (unsigned long long b = lo + (unsigned long long)wid * 32u; b < hi; b += (unsigned long long)kWarps * 32u) {
-        const unsigned long long x = b + (unsigned long long)lane;
-        const unsigned long long rec = x < hi ? __ldcs(recs + x) : 0ull;
+    const unsigned long long step = (unsigned long long)kWarps * 32u;
+    unsigned long long b = lo + (unsigned long long)wid * 32u;
+    unsigned long long rec = (b + lane < hi) ? __ldcs(recs + b + lane) : 0ull;
+    for (; b < hi; b += step) {
+        const unsigned long long nx = b + step + (unsigned long long)lane;
+        const unsigned long long rec_next = nx < hi ? __ldcs(recs + nx) : 0ull;
         const unsigned long long o = rec >> kLenBits;
         const unsigned int n = (unsigned int)(rec & kLenMask);
-        if (n <= kShortSeg) {
-            for (unsigned int k0 = 0; k0 < n; k0 += 4u) {
-                uint32_t td[4];
-                int32_t w[4];
+        // exclusive prefix of the run lengths over the warp
+        unsigned int inc = n;
 #pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    if (k0 + k < n) {
-                        td[k] = __ldcs(d.syn_td + o + k0 + k);
-                        w[k] = __ldcs(d.syn_w + o + k0 + k);
-                    }
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    if (k0 + k < n) atomicAdd(fix + (td[k] & kTgtMask), w[k]);
-            }
+        for (int k = 1; k < 32; k <<= 1) {
+            const unsigned int y = __shfl_up_sync(0xFFFFFFFFu, inc, k);
+            if (lane >= k) inc += y;
         }
-        unsigned int m = __ballot_sync(0xFFFFFFFFu, n > kShortSeg);
-        while (m) {
-            const int src = __ffs(m) - 1;
-            m &= m - 1u;
-            const unsigned long long oo = __shfl_sync(0xFFFFFFFFu, o, src);
-            const unsigned int nn = __shfl_sync(0xFFFFFFFFu, n, src);
-            for (unsigned int k0 = 0; k0 < nn; k0 += 128u) {
-                uint32_t td[4];
-                int32_t w[4];
+        const unsigned int ex = inc - n;
+        const unsigned int tot = __shfl_sync(0xFFFFFFFFu, inc, 31);
+        for (unsigned int base = 0; base < tot; base += 128u) {
+            uint32_t td[4];
+            int32_t w[4];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const unsigned int y = k0 + (unsigned int)k * 32u + (unsigned int)lane;
-                    if (y < nn) {
-                        td[k] = __ldcs(d.syn_td + oo + y);
-                        w[k] = __ldcs(d.syn_w + oo + y);
-                    }
+            for (int k = 0; k < 4; ++k) {
+                const unsigned int y = base + (unsigned int)k * 32u + (unsigned int)lane;
+                // the last lane whose run starts at or before y
+                int r = 0;
+#pragma unroll
+                for (int h = 16; h > 0; h >>= 1) {
+                    const unsigned int v = __shfl_sync(0xFFFFFFFFu, ex, r + h);
+                    if (v <= y) r += h;
                 }
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const unsigned int y = k0 + (unsigned int)k * 32u + (unsigned int)lane;
-                    if (y < nn) atomicAdd(fix + (td[k] & kTgtMask), w[k]);
+                const unsigned long long orr = __shfl_sync(0xFFFFFFFFu, o, r);
+                const unsigned int er = __shfl_sync(0xFFFFFFFFu, ex, r);
+                if (y < tot) {
+                    td[k] = __ldcs(d.syn_td + orr + (y - er));
+                    w[k] = __ldcs(d.syn_w + orr + (y - er));
                 }
             }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const unsigned int y = base + (unsigned int)k * 32u + (unsigned int)lane;
+                if (y < tot) atomicAdd(fix + (td[k] & kTgtMask), w[k]);
+            }
         }
+        rec = rec_next;
     }
 }
 
@@ -1124,7 +1133,7 @@ __device__ __forceinline__ int4 take_restored(int32_t *p, int4 i4)
 // block's resident state and `phase` the parity of the bulk copy's
 // mbarrier; a copy that does not complete within limit_ns records
 // kStTimeout.
-template <int MODE, bool ARR>
+template <int MODE, bool ARR, int QB = 4>
 __device__ __forceinline__ void update_step(const Dev &d, long long t, StepShared &sh, const Resident &rs,
                                             uint32_t phase, unsigned long long limit_ns)
 {
@@ -1225,23 +1234,37 @@ __device__ __forceinline__ void update_step(const Dev &d, long long t, StepShare
         const long long qb = (long long)blockIdx.x * kThreads + threadIdx.x;
         for (long long b0 = (long long)blockIdx.x * kThreads; b0 < nq; b0 += 8 * stride) {
             uint32_t bits = 0;
-            for (int k = 0; k < 8; ++k) {
-                const long long q = b0 + k * stride + threadIdx.x;
-                if (q < nq) {
-                    const long long j0 = q * 4;
-                    const float4 v4 = *reinterpret_cast<const float4 *>(d.V + j0);
-                    int4 i4 = *reinterpret_cast<const int4 *>(ring + j0);
-                    uint32_t r4 = *reinterpret_cast<const uint32_t *>(d.ref + j0);
-                    *reinterpret_cast<int4 *>(ring + j0) = make_int4(0, 0, 0, 0);
-                    if (inj) i4 = take_restored(inj + j0, i4);
-                    if (cur) *reinterpret_cast<int4 *>(cur + j0) = i4;
-                    float vv[4] = {v4.x, v4.y, v4.z, v4.w};
-                    const int32_t ii[4] = {i4.x, i4.y, i4.z, i4.w};
-                    const unsigned int m = update_quad(d, sh.th, t, j0, vv, ii, r4, do_hash, hc, hv);
-                    prefetch_rows(d, j0, m);
-                    bits |= m << (4 * k);
-                    *reinterpret_cast<float4 *>(d.V + j0) = make_float4(vv[0], vv[1], vv[2], vv[3]);
-                    *reinterpret_cast<uint32_t *>(d.ref + j0) = r4;
+            // QB quads' state loaded before any of them is written back, so
+            // that their loads are in flight together
+            for (int k0 = 0; k0 < 8; k0 += QB) {
+                float4 v4[QB];
+                int4 i4[QB];
+                uint32_t r4[QB];
+#pragma unroll
+                for (int k = 0; k < QB; ++k) {
+                    const long long q = b0 + (k0 + k) * stride + threadIdx.x;
+                    if (q < nq) {
+                        v4[k] = *reinterpret_cast<const float4 *>(d.V + q * 4);
+                        i4[k] = *reinterpret_cast<const int4 *>(ring + q * 4);
+                        r4[k] = *reinterpret_cast<const uint32_t *>(d.ref + q * 4);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < QB; ++k) {
+                    const long long q = b0 + (k0 + k) * stride + threadIdx.x;
+                    if (q < nq) {
+                        const long long j0 = q * 4;
+                        *reinterpret_cast<int4 *>(ring + j0) = make_int4(0, 0, 0, 0);
+                        if (inj) i4[k] = take_restored(inj + j0, i4[k]);
+                        if (cur) *reinterpret_cast<int4 *>(cur + j0) = i4[k];
+                        float vv[4] = {v4[k].x, v4[k].y, v4[k].z, v4[k].w};
+                        const int32_t ii[4] = {i4[k].x, i4[k].y, i4[k].z, i4[k].w};
+                        const unsigned int m = update_quad(d, sh.th, t, j0, vv, ii, r4[k], do_hash, hc, hv);
+                        prefetch_rows(d, j0, m);
+                        bits |= m << (4 * (k0 + k));
+                        *reinterpret_cast<float4 *>(d.V + j0) = make_float4(vv[0], vv[1], vv[2], vv[3]);
+                        *reinterpret_cast<uint32_t *>(d.ref + j0) = r4[k];
+                    }
                 }
             }
             const long long base = b0 - (long long)blockIdx.x * kThreads;
@@ -1417,7 +1440,8 @@ __global__ void __launch_bounds__(kThreads) k_update(const Dev d, int k)
     __syncthreads();
     const long long t = sh.t0 + k;
     if (k > 0 && blockIdx.x == 0 && threadIdx.x == 0) close_step(d, t - 1);
-    update_step<MODE, ARR>(d, t, sh, Resident{}, 0u, 0ull);
+    // one quad per thread on this grid: no batching of the loads
+    update_step<MODE, ARR, 1>(d, t, sh, Resident{}, 0u, 0ull);
     // delivery by arrival step: the runs queued for this step (they go to
     // the next step's input slot, which no block reads in this kernel)
     if constexpr (ARR) arrival_share(d, t, sh);
@@ -1456,8 +1480,18 @@ __global__ void k_advance(const Dev d, int steps)
 // block computes the next step's drive and leak (pre_update), which need no
 // other block's data.  DEFER: minimum-delay batching (Deferred); the last
 // step's delay >= 2 lists are delivered before the launch ends.
+// Blocks per SM the persistent kernel is built for: 3 with the neuron state in
+// shared memory (80 registers), 2 on global state (128 registers, room for
+// the update's batched loads).
+template <int MODE>
+constexpr int persist_min_blocks()
+{
+    return MODE == kModeSmem ? 3 : 2;
+}
+
 template <int MODE, bool DEFER, bool ARR>
-__global__ void __launch_bounds__(kThreads, 3) k_persist(const Dev d, int T, unsigned long long limit_ns,
+__global__ void __launch_bounds__(kThreads, persist_min_blocks<MODE>()) k_persist(const Dev d, int T,
+                                                                                   unsigned long long limit_ns,
                                                          int skip_arrival)
 {
     __shared__ StepShared sh;
@@ -1504,40 +1538,47 @@ __global__ void __launch_bounds__(kThreads, 3) k_persist(const Dev d, int T, uns
     }
     const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
     const bool prof = d.phase_ns != nullptr && lead;
+    // profiling: each part's time is added to s_prof as soon as it ends
+    __shared__ unsigned long long s_prof[kPhases + 1];
+    auto stamp = [&](int k) {
+        if (prof) {
+            const unsigned long long now = global_ns();
+            if (k >= 0) s_prof[k] += now - s_prof[kPhases];
+            s_prof[kPhases] = now;
+        }
+    };
+    if (prof)
+        for (int k = 0; k < kPhases; ++k) s_prof[k] = 0;
     int done = 0, issued = 0;
     long long closed = t0 - 1;
-    unsigned long long ns[2] = {0, 0};
     for (int s = 0; s < T; ++s) {
         const long long t = t0 + s;
-        const unsigned long long a = prof ? global_ns() : 0;
+        stamp(-1);
         if (s > 0 && lead) {
             close_step(d, t - 1);
             closed = t - 1;
         }
         update_step<MODE, ARR>(d, t, sh, rs, (uint32_t)(s & 1), limit_ns);
         ++issued;
-        const unsigned long long b = prof ? global_ns() : 0;
+        stamp(0);
         // the first barrier carries the block's spike count in the word's high half
         grid_arrive(c, !(skip_arrival && s == 0 && blockIdx.x == 0), 1ull + ((unsigned long long)sh.n_own << 32));
         prefetch_own(d, sh);
         // delivery by arrival step: the runs queued for this step, while the
         // barrier completes (they need no spike of this step)
         if constexpr (ARR) arrival_share(d, t, sh);
+        stamp(1);
         if (!grid_wait(c, 2ull * s, limit_ns, &sh.word)) break;
-        const unsigned long long e = prof ? global_ns() : 0;
+        stamp(2);
         route_step<ARR>(d, t, sh, true, df, s & 1);
+        stamp(3);
         // the next step's input-free update runs while the barrier completes
         grid_arrive(c);
         if constexpr (MODE == kModeSmem) {
             if (s + 1 < T) pre_update(d, t + 1, sh.th, rs);
         }
-        const unsigned long long f = prof ? global_ns() : 0;
         if (!grid_wait(c, 2ull * s + 1ull, limit_ns)) break;
-        if (prof) {
-            const unsigned long long g = global_ns();
-            ns[0] += (b - a) + (f - e);
-            ns[1] += (e - b) + (g - f);
-        }
+        stamp(4);
         ++done;
     }
     if constexpr (DEFER) {
@@ -1576,10 +1617,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_persist(const Dev d, int T, uns
     if (lead) {
         if (t0 + done - 1 > closed) close_step(d, t0 + done - 1);
         c->t = t0 + done;
-        if (prof) {
-            d.phase_ns[0] += ns[0];
-            d.phase_ns[1] += ns[1];
-        }
+        if (prof)
+            for (int k = 0; k < kPhases; ++k) d.phase_ns[k] += s_prof[k];
     }
 }
 
