@@ -224,7 +224,9 @@ int snn_partition_device(const snn_network *net, int32_t n_parts, const snn_part
  * which member of g relays whose traffic is the design choice behind the
  * peak level-2 traffic of Sec. V, Fig. 3(b)).  Members of a VN are ranked
  * by ascending partition label.
- *   PER_VN (default): member (vn(p) mod s) of g, one relay per pair of VNs;
+ *   PER_VN (default): member ((vn(p) - g) mod s) of g, one relay per pair of
+ *     VNs (it depends on the VNs' distance only, so each network of a batch
+ *     gets the relays it has alone);
  *   PER_PARTITION: member (rank of p in its own VN, mod s) of g, which
  *     spreads the s partitions of a VN over the s members of g;
  *   BALANCED: per g, the sources p in decreasing static load (ties: lower
@@ -272,9 +274,9 @@ typedef struct snn_routing snn_routing;
  *     (one message per VN, deduplicated);
  *   - level 2: per (neuron, VN), the destination partitions of that VN
  *     with the neuron's synapse segment for each;
- *   - relay ("bridge") of destination VN g for source VN h: the
- *     (h mod s)-th partition of g in ascending partition label; inside the
- *     own VN the source partition sends directly.
+ *   - relay ("bridge") of destination VN g for a source partition of
+ *     another VN: by relay policy (snn_routing_params.relay, below); inside
+ *     the own VN the source partition sends directly.
  * Greedy grouping reading: for t = 1..iters, groups 0..n_vn-2 are grown
  * from a seed (t = 1: heaviest ungrouped partition by WG, ties lowest label;
  * t > 1: Philox-chosen, counter (t, g, 0xA2, 0)) by adding the ungrouped q
@@ -463,11 +465,18 @@ int snn_batch_create(const snn_network *net, const snn_routing *rt, int32_t n, c
                      snn_sim **out);
 
 /*
- * Advance T steps.  Each step: (a1) consume the delay-ring slot, add the
+ * Advance T steps: the paper's simulation loop, in which every step is the
+ * GPUs' computation followed by the spike exchange between them (Sec. I,
+ * Sec. III), with the exchange taking the two-level route (Sec. IV.B): a
+ * spike goes once to each destination group (level 1) and is forwarded
+ * inside that group to the partitions that hold its targets (level 2).  The
+ * neuron model is LIF, the one the paper lists for its simulators (Table I).
+ * Each step: (a1) consume the step's input (delay-ring slot, or input slot
+ * with SNN_DELIVER_ARRIVAL), add the
  * Poisson drive; (a2) LIF update and threshold; (a3) warp-ballot/prefix-sum
  * spike compaction; (a4) level-1 bucketing by destination VN; (a5) level-2
  * relay expansion into per-partition inboxes; (a6) CSR fan-out of int16
- * weights into int32 ring accumulators.  Asynchronous on the sim's stream.
+ * weights into int32 accumulators.  Asynchronous on the sim's stream.
  * A step runs in two halves: a1-a3 over the neurons into the step's spike
  * list, then a4-a6 over equal shares of that list (a step's deliveries
  * write only the ring slots of later steps).  On a GPU with cooperative
@@ -489,6 +498,9 @@ int snn_step(snn_sim *sim, int32_t T);
 int snn_sync_status(snn_sim *sim);
 
 /*
+ * Read-outs of a simulation (the spikes, inputs, message counts and state
+ * the paper's evaluation is made of, Sec. V: the messages of each route and
+ * their traffic).
  * Spikes of steps t0 .. t1-1 (global ids, ascending within a step):
  * ids[step_off[k] .. step_off[k+1]) for step t0+k; step_off has t1-t0+1
  * entries; *n receives the total.  Synchronises the stream.
@@ -504,11 +516,18 @@ int snn_read_currents(snn_sim *sim, int64_t t, int32_t *out);
  * v = sum_j mix(j<<32 | bits(V_j)) mod 2^64 over global ids j, mix the
  * splitmix64 finaliser. */
 int snn_read_hashes(snn_sim *sim, int64_t t0, int64_t t1, uint64_t *cur, uint64_t *v);
+/* Counters since the start (or the last reset/restore): spikes, synaptic
+ * events, and the messages of the direct route and of the two-level route by
+ * kind (Sec. IV.B: level-1 messages to other groups, direct messages inside
+ * the group, level-2 forwards by the relay; the comparison of Sec. V,
+ * Fig. 3).  With SNN_DELIVER_ARRIVAL the events are counted when routed. */
 int snn_read_counts(snn_sim *sim, snn_counts *out);
 /* Current state in global order: V [M], ref [M]; *t = next step index. */
 int snn_read_state(snn_sim *sim, float *V, uint8_t *ref, int64_t *t);
 /* (spike id << 32 | destination partition label) pairs held in the
- * level-2 inboxes after the last step, unsorted; *n = total (may exceed cap). */
+ * level-2 inboxes after the last step, unsorted; *n = total (may exceed cap):
+ * the spikes each partition received over the two-level route (Sec. IV.B),
+ * which must be the pairs of the direct route. */
 int snn_read_inbox_pairs(snn_sim *sim, uint64_t *pairs, int64_t cap, int64_t *n);
 
 /* Checkpoint: V, ref, delay ring, step index, counters (bytes from

@@ -52,7 +52,9 @@
  *     is the design choice the paper's level-2 traffic result rests on,
  *     Sec. V, Fig. 3(b)), members of a group ranked by ascending partition
  *     index, by policy:
- *       per group (default): the (h mod |g|)-th member of g, h = group of p;
+ *       per group (default): the ((h - g) mod |g|)-th member of g, h = group
+ *       of p (it depends only on the groups' distance, so networks placed
+ *       side by side in one mapping get each their own relays);
  *       per partition: the (rank of p in its own group mod |g|)-th member;
  *       balanced: longest-processing-time first -- the sources of g in
  *       decreasing static load (ties: lower index) each join the member of
@@ -485,10 +487,14 @@ static int32_t member_of(const int32_t *vn_of_part, int32_t P, int32_t g, int32_
     return -1;
 }
 
-/* relay(g, h): the (h mod |g|)-th partition of group g, ascending index. */
+/* relay(g, h): the ((h - g) mod |g|)-th partition of group g, ascending index. */
 static int32_t relay_of(const int32_t *vn_of_part, int32_t P, int32_t g, int32_t h)
 {
-    return member_of(vn_of_part, P, g, h);
+    int32_t sz = 0;
+    for (int32_t p = 0; p < P; ++p) if (vn_of_part[p] == g) ++sz;
+    int32_t k = (h - g) % sz;
+    if (k < 0) k += sz;
+    return member_of(vn_of_part, P, g, k);
 }
 
 /* Rank of partition p among the partitions of its own group (ascending index). */

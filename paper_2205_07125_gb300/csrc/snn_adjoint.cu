@@ -69,7 +69,8 @@ struct AdjDev {
     uint8_t *seg_flag;      // [K][M] bit 0 spike, bit 1 refractory
     int32_t *seg_A;         // [K][M][n_pop]
     // backward
-    float *gring;           // [D][M] adjoint of V_pre by step slot
+    float *gring;           // [D][n_pop][M] G[pop k][b] * (adjoint of V_pre of k) by step slot and
+                            // source population b: a source of population b gathers plane b
     float *gV;              // [M]
     const float *direct;    // [n_pop] dL/dr_a / (T N_a)
     double *dG;             // [n_pop][n_pop]
@@ -203,6 +204,7 @@ __global__ void __launch_bounds__(kAThreads) k_adj_backward(const AdjDev a, int 
     const int lane = threadIdx.x & 31;
     const long long nw = ((long long)gridDim.x * kAThreads) >> 5;
     const float c = 0.0009765625f;
+    const int tm = t % a.D;
     for (long long j = ((long long)blockIdx.x * kAThreads + threadIdx.x) >> 5; j < a.M; j += nw) {
         const int pj = a.pop[j];
         float acc = 0.0f;
@@ -225,10 +227,11 @@ __global__ void __launch_bounds__(kAThreads) k_adj_backward(const AdjDev a, int 
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const uint32_t k = td[u] & kTgtMask;
-                    const int sl = (t + (int)(td[u] >> kTgtBits) + 1) % a.D;
-                    const float gk = a.gring[(long long)sl * a.M + k];
-                    const float gw = __fmul_rn(a.G[a.pop[k] * a.n_pop + pj], (float)w[u]);
-                    acc = __fadd_rn(acc, __fmul_rn(gw, gk));
+                    int sl = tm + (int)(td[u] >> kTgtBits) + 1;
+                    if (sl >= a.D) sl -= a.D;
+                    // G[pop k][pj] * gVpre_k(t + d), stored by k when it was computed
+                    const float hk = a.gring[((long long)sl * a.n_pop + pj) * a.M + k];
+                    acc = __fadd_rn(acc, __fmul_rn((float)w[u], hk));
                 }
             }
         }
@@ -245,7 +248,9 @@ __global__ void __launch_bounds__(kAThreads) k_adj_backward(const AdjDev a, int 
                 const float keep = (fl & 1) ? 0.0f : a.gV[j];
                 gvp = __fadd_rn(keep, __fmul_rn(gS, sg));
             }
-            a.gring[(long long)(t % a.D) * a.M + j] = gvp;
+            // the products each source population gathers
+            for (int b = 0; b < a.n_pop; ++b)
+                a.gring[((long long)tm * a.n_pop + b) * a.M + j] = __fmul_rn(a.G[pj * a.n_pop + b], gvp);
             a.gV[j] = __fmul_rn(a.alpha, gvp);
             if (gvp != 0.0f) {
                 const double gd = (double)gvp * (double)c;
@@ -315,7 +320,7 @@ int adj_layout(const snn_routing *rt, const snn_sim_params *p, const snn_adjoint
     aplace(L, L.seg_vpre, sizeof(float) * (size_t)K * M);
     aplace(L, L.seg_flag, (size_t)K * M);
     aplace(L, L.seg_A, sizeof(int32_t) * (size_t)K * M * L.n_pop);
-    aplace(L, L.gring, sizeof(float) * (size_t)L.D * M);
+    aplace(L, L.gring, sizeof(float) * (size_t)L.D * (size_t)L.n_pop * M);
     aplace(L, L.gV, sizeof(float) * M);
     aplace(L, L.direct, sizeof(float) * kMaxPop);
     aplace(L, L.dG, sizeof(double) * kMaxPop * kMaxPop);

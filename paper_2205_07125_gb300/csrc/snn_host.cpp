@@ -372,11 +372,11 @@ void route_order(snn_routing *rt, const snn_network *net, const int32_t *part_of
             rt->part_of_ip[ip] = p;
         }
     }
-    // relay of VN g for source VN h: (h mod s)-th member of g in label order,
-    // which is internal partition g*s + h % s
+    // relay of VN g for source VN h: ((h - g) mod s)-th member of g in label order,
+    // which is internal partition g*s + (h - g) mod s
     rt->relay.resize((size_t)n_vn * n_vn);
     for (int32_t g = 0; g < n_vn; ++g)
-        for (int32_t h = 0; h < n_vn; ++h) rt->relay[(size_t)g * n_vn + h] = rt->part_of_ip[g * s + h % s];
+        for (int32_t h = 0; h < n_vn; ++h) rt->relay[(size_t)g * n_vn + h] = rt->part_of_ip[g * s + vn_rank(h, g, s)];
 
     // internal neuron order: partition-major, ascending global id
     rt->pbase.assign((size_t)P + 1, 0);
@@ -454,7 +454,7 @@ void route_relay_map(const snn_routing *rt, int32_t policy, std::vector<int32_t>
             if (ip / s == g) continue;
             // internal partitions are VN-major, by ascending label inside a VN:
             // the rank of ip in its VN is ip mod s, member k of g is g*s + k
-            relay_ip[(size_t)g * P + ip] = policy == SNN_RELAY_PER_VN ? g * s + (ip / s) % s : g * s + ip % s;
+            relay_ip[(size_t)g * P + ip] = policy == SNN_RELAY_PER_VN ? g * s + vn_rank(ip / s, g, s) : g * s + ip % s;
         }
     if (policy != SNN_RELAY_BALANCED) return;
     // static load of (g, source ip): its level-2 pairs into the partitions of g
@@ -693,7 +693,7 @@ extern "C" int snn_routing_build(const snn_network *net, const int32_t *part_of,
                     l.q = (uint16_t)q;
                     l.pad = 0;
                     if (g == hs) l.cls = (q == ps) ? kClsLocal : kClsPeer;
-                    else l.cls = (q == g * s + hs % s) ? kClsRelayLocal : kClsRelayRemote;
+                    else l.cls = (q == g * s + vn_rank(hs, g, s)) ? kClsRelayLocal : kClsRelayRemote;
                 }
                 for (int64_t e = sp[i]; e < sp[i + 1]; ++e) {
                     int32_t q = rt->ip_of_part[part_of[tg[e]]];

@@ -115,6 +115,20 @@ struct snn_routing {
 };
 
 namespace snn {
+// Rank of the relay of destination VN g for source VN h under the per-VN
+// relay policy: (h - g) mod s, which depends only on the VNs' distance, so
+// networks concatenated into a batch get each its own relays.
+#if defined(__CUDACC__)
+#define SNN_HOST_DEVICE __host__ __device__
+#else
+#define SNN_HOST_DEVICE
+#endif
+SNN_HOST_DEVICE inline int32_t vn_rank(int32_t h, int32_t g, int32_t s)
+{
+    const int32_t r = (h - g) % s;
+    return r < 0 ? r + s : r;
+}
+
 // Run f(lo, hi) over [0, n) split into contiguous chunks on up to nthreads threads.
 void parallel_for(int64_t n, int nthreads, const std::function<void(int64_t, int64_t, int)> &f);
 int resolve_threads(int requested);

@@ -258,7 +258,7 @@ __device__ __forceinline__ void route_emit(const RDev &d, int lo_deg, unsigned l
             const int g = q / d.s;
             uint8_t cls;
             if (g == hs) cls = q == ps ? kClsLocal : kClsPeer;
-            else cls = q == g * d.s + hs % d.s ? kClsRelayLocal : kClsRelayRemote;
+            else cls = q == g * d.s + vn_rank(hs, g, d.s) ? kClsRelayLocal : kClsRelayRemote;
             L2Entry e;
             e.off = (unsigned long long)(d.csr[kk] + st) | (n1 << kOffBits);
             e.len = (uint32_t)(en - st);

@@ -63,14 +63,16 @@ constexpr uint32_t kStBucket = 1u, kStInbox = 2u, kStRaster = 4u, kStTimeout = 8
 // once; the run of delay d >= 2 is queued on the list of step t + d - 1 and
 // delivered by that step.  Runs staged in shared memory per routing round
 // before one reservation per list and round: kArrPool runs, kMaxArr lists.
-constexpr int kArrPool = 1024;
+constexpr int kArrPool = 2048;
 constexpr int kMaxArr = 8;
 
 // Parts of a step timed by block 0 of k_persist (snn_profile_phases): the
-// update half, its own-table prefetch and queued deliveries, the rest of the
-// first barrier's wait, the routing half, the next step's input-free update
-// with the second barrier's wait.
-constexpr int kPhases = 5;
+// update of the neurons (a1-a2) and their spike compaction (a3), the
+// prefetch of the block's own spikes' tables and its queued deliveries, the
+// rest of the first barrier's wait, the routing walk (a4-a5) and the
+// routing rounds' deliveries and copies (a6), the next step's input-free
+// update with the second barrier's wait.
+constexpr int kPhases = 7;
 
 // counter slots: steps and spikes in Dev::counters (closing thread), the
 // others in each block's tally row
@@ -597,22 +599,51 @@ struct DeferSlot<false> {
     __device__ Deferred *get() { return nullptr; }
 };
 
-// Stage the run of n synapses at o: a short run on the short list, a long
-// one cut into pieces.  What does not fit is delivered by this thread at
-// once (slot base tm: delivering early is exact, the run's slots are read
-// later).  Returns the synapses delivered here.
-__device__ __forceinline__ unsigned int stage_run(const Dev &d, int tm, int32_t *fix, unsigned long long o, unsigned int n,
-                                                  unsigned long long *lng, unsigned int *nl, unsigned int capl,
-                                                  unsigned long long *sht, unsigned int *ns, unsigned int caps)
+// Staging of a run of n synapses at o (stage_run_warp below): a short run
+// on the short list, a long one cut into pieces.  What does not fit is
+// delivered by the thread at once (slot base tm: delivering early is exact,
+// the run's slots are read later).
+
+// Rank of this lane among the lanes of mask m below it.
+__device__ __forceinline__ unsigned int lane_rank(unsigned int m)
 {
+    return __popc(m & ((1u << (threadIdx.x & 31)) - 1u));
+}
+
+// stage_run for a whole warp (every lane calls; n = 0: nothing to stage):
+// one shared-memory reservation per list and warp, not one per lane, so the
+// lanes do not queue on the same shared-memory word.
+__device__ __forceinline__ unsigned int stage_run_warp(const Dev &d, int tm, int32_t *fix, unsigned long long o,
+                                                       unsigned int n, unsigned long long *lng, unsigned int *nl,
+                                                       unsigned int capl, unsigned long long *sht, unsigned int *ns,
+                                                       unsigned int caps)
+{
+    const int lane = threadIdx.x & 31;
     unsigned int ev = 0;
-    if (n <= kShortSeg) {
-        const unsigned int sb = atomicAdd(ns, 1u);
-        if (sb < caps) sht[sb] = (o << 8) | n;
-        else ev += deliver_run(d, tm, fix, o, n);
-    } else {
-        const unsigned int np = (n + kPiece - 1u) / kPiece;
-        unsigned int pb = atomicAdd(nl, np);
+    const bool is_short = n > 0 && n <= kShortSeg;
+    const unsigned int ms = __ballot_sync(0xFFFFFFFFu, is_short);
+    if (ms) {
+        const int lead = __ffs(ms) - 1;
+        unsigned int sb = 0;
+        if (lane == lead) sb = atomicAdd(ns, (unsigned int)__popc(ms));
+        sb = __shfl_sync(0xFFFFFFFFu, sb, lead) + lane_rank(ms);
+        if (is_short) {
+            if (sb < caps) sht[sb] = (o << 8) | n;
+            else ev += deliver_run(d, tm, fix, o, n);
+        }
+    }
+    const unsigned int np = n > kShortSeg ? (n + kPiece - 1u) / kPiece : 0u;
+    unsigned int inc = np;
+#pragma unroll
+    for (int k = 1; k < 32; k <<= 1) {
+        const unsigned int y = __shfl_up_sync(0xFFFFFFFFu, inc, k);
+        if (lane >= k) inc += y;
+    }
+    const unsigned int tot = __shfl_sync(0xFFFFFFFFu, inc, 31);
+    if (tot) {
+        unsigned int pb = 0;
+        if (lane == 0) pb = atomicAdd(nl, tot);
+        pb = __shfl_sync(0xFFFFFFFFu, pb, 0) + inc - np;
         for (unsigned int j = 0; j < np; ++j, ++pb) {
             const unsigned long long oo = o + (unsigned long long)j * kPiece;
             const unsigned int m = min(kPiece, n - j * kPiece);
@@ -641,22 +672,47 @@ __device__ __forceinline__ void sync_part(int nthr)
     else asm volatile("bar.sync 1, %0;" ::"r"(nthr) : "memory");
 }
 
-// Queue the run of n synapses at o on arrival list `list` (delivery by
-// arrival step): in the round's pool, or straight on the list when the pool
-// is full.
-__device__ __forceinline__ void arrival_queue(const Dev &d, const Stage &sg, int list, unsigned long long o,
-                                              unsigned int n, unsigned int &ovf)
+// Queue runs on arrival list `list` (delivery by arrival step) for a whole
+// warp (every lane calls; n = 0: no run): this lane's run of n synapses at
+// o goes to the round's pool, or straight on the list when the pool is full.
+// One pool and one rank reservation per warp.
+__device__ __forceinline__ void arrival_queue_warp(const Dev &d, const Stage &sg, int list, unsigned long long o,
+                                                   unsigned int n, unsigned int &ovf)
 {
+    const unsigned int m = __ballot_sync(0xFFFFFFFFu, n > 0);
+    if (!m) return;
+    const int lane = threadIdx.x & 31, lead = __ffs(m) - 1;
+    unsigned int ps = 0;
+    if (lane == lead) ps = atomicAdd(sg.an, (unsigned int)__popc(m));
+    ps = __shfl_sync(0xFFFFFFFFu, ps, lead) + lane_rank(m);
+    // ranks in the list only for the runs that found room in the pool
+    const bool pooled = n > 0 && ps < (unsigned int)kArrPool;
+    const unsigned int mp = __ballot_sync(0xFFFFFFFFu, pooled);
+    unsigned int r = 0;
+    if (mp) {
+        const int lp = __ffs(mp) - 1;
+        if (lane == lp) r = atomicAdd(&sg.ak[list], (unsigned int)__popc(mp));
+        r = __shfl_sync(0xFFFFFFFFu, r, lp) + lane_rank(mp);
+    }
+    // the runs the pool has no room for go straight on the list: one
+    // reservation for the warp's
+    const bool direct = n > 0 && !pooled;
+    const unsigned int mg = __ballot_sync(0xFFFFFFFFu, direct);
+    unsigned int pos = 0;
+    if (mg) {
+        const int lg = __ffs(mg) - 1;
+        if (lane == lg) pos = atomicAdd(&d.arr_cnt[(size_t)list * kPairStride], (unsigned int)__popc(mg));
+        pos = __shfl_sync(0xFFFFFFFFu, pos, lg) + lane_rank(mg);
+    }
+    if (n == 0) return;
     const unsigned long long rec = (o << kLenBits) | (unsigned long long)n;
-    const unsigned int ps = atomicAdd(sg.an, 1u);
-    if (ps < (unsigned int)kArrPool) {
-        const unsigned int r = atomicAdd(&sg.ak[list], 1u);
+    if (pooled) {
         sg.arec[ps] = rec;
         sg.atag[ps] = (unsigned short)((r << 4) | (unsigned int)list);
+    } else if (pos < d.arr_cap) {
+        d.arr[(size_t)list * d.arr_cap + pos] = rec;
     } else {
-        const unsigned int pos = atomicAdd(&d.arr_cnt[(size_t)list * kPairStride], 1u);
-        if (pos < d.arr_cap) d.arr[(size_t)list * d.arr_cap + pos] = rec;
-        else ovf |= kStArrival;
+        ovf |= kStArrival;
     }
 }
 
@@ -721,7 +777,10 @@ __device__ __forceinline__ Pending route_traverse(const Dev &d, int par, int tm,
     unsigned int l1_loc = 0, l1_xvn = 0;
     unsigned int cls[4] = {0, 0, 0, 0};
     Pending pn{0, 0u, make_ulonglong2(0ull, 0ull), 0ull, 0u, 0u};
-    for (uint32_t x = threadIdx.x; x < N; x += (uint32_t)nthr) {
+    // the lanes of a warp take entries together (the staging below is
+    // warp-collective); a lane past the end only stages nothing
+    for (uint32_t x0 = threadIdx.x & ~31u; x0 < N; x0 += (uint32_t)nthr) {
+        const uint32_t x = x0 + (uint32_t)lane;
         if (pn.pk == 1) {
             if (pn.ppos < pn.pslot.y) d.bucket[pn.pslot.x + pn.ppos] = (uint32_t)pn.pval;
             else pn.ovf |= kStBucket;
@@ -729,6 +788,12 @@ __device__ __forceinline__ Pending route_traverse(const Dev &d, int par, int tm,
             if (pn.ppos < pn.pslot.y) d.inbox[pn.pslot.x + pn.ppos] = pn.pval;
             else pn.ovf |= kStInbox;
         }
+        pn.pk = 0;
+        // the segment this lane stages: the whole one, or its delay-1 head
+        // with the rest on the deferred lists (df) or the arrival lists (ARR)
+        unsigned long long so = 0;
+        unsigned int sn = 0, rest = 0;
+        uint4 dc = make_uint4(0u, 0u, 0u, 0u);
         if (x < N1) {
             // a4: one level-1 entry per destination VN, appended to bucket (p, g)
             const int k = prefix_find(sg.pre1, (int)nr, x);
@@ -741,7 +806,7 @@ __device__ __forceinline__ Pending route_traverse(const Dev &d, int par, int tm,
             pn.pk = 1;
             if (g == sg.part[k] / d.vn_size) ++l1_loc;
             else ++l1_xvn;
-        } else {
+        } else if (x < N) {
             // a5: the relay of the entry's VN expands it into inbox (p, q) of
             // partition q; the segment's delivery is staged
             const uint32_t y = x - N1;
@@ -754,35 +819,41 @@ __device__ __forceinline__ Pending route_traverse(const Dev &d, int par, int tm,
             const unsigned long long off = l.off & kOffMask;
             pn.pval = (off << kLenBits) | (unsigned long long)l.len;
             pn.pk = 2;
+            so = off;
             if constexpr (ARR) {
-                // runs by delay: c[k] = synapses of delay <= k + 1
-                const uint4 dc = d.dcnt[f];
-                const uint32_t c[kMaxArr] = {dc.x & 0xFFFFu, dc.x >> 16, dc.y & 0xFFFFu, dc.y >> 16,
-                                             dc.z & 0xFFFFu, dc.z >> 16, dc.w & 0xFFFFu, dc.w >> 16};
-                if (c[0]) stage_run(d, tm, fix, off, c[0], sg.lng, sg.nl, kLongCap, sg.sht, sg.ns, kShortCap);
-#pragma unroll
-                for (int k = 1; k < kMaxArr; ++k) {
-                    if (k < d.n_arr && c[k] > c[k - 1]) {
-                        int li = tmod + k;
-                        if (li >= d.n_arr) li -= d.n_arr;
-                        arrival_queue(d, sg, li, off + c[k - 1], c[k] - c[k - 1], pn.ovf);
-                    }
-                }
-                pn.ev += l.len;  // events counted when routed
+                dc = d.dcnt[f];         // runs by delay: synapses of delay <= k + 1
+                sn = dc.x & 0xFFFFu;    // the delay-1 head
+                pn.ev += l.len;         // events counted when routed
             } else if (!df) {
-                pn.ev += stage_run(d, tm, nullptr, off, l.len, sg.lng, sg.nl, kLongCap, sg.sht, sg.ns, kShortCap);
+                sn = l.len;
             } else {
-                const unsigned int n1 = (unsigned int)(l.off >> kOffBits);  // delay-1 head of the segment
-                if (n1) pn.ev += stage_run(d, tm, nullptr, off, n1, sg.lng, sg.nl, kLongCap, sg.sht, sg.ns, kShortCap);
-                if (l.len > n1)
-                    pn.ev += stage_run(d, tm, nullptr, off + n1, l.len - n1, df->lng[cur], &df->nl[cur], kDefLong,
-                                       df->sht[cur], &df->ns[cur], kDefShort);
+                sn = (unsigned int)(l.off >> kOffBits);  // delay-1 head of the segment
+                rest = l.len - sn;
             }
             // per-class tallies without a dynamically indexed (local-memory) array
             cls[0] += l.cls == 0;
             cls[1] += l.cls == 1;
             cls[2] += l.cls == 2;
             cls[3] += l.cls == 3;
+        }
+        if constexpr (ARR) {
+            stage_run_warp(d, tm, fix, so, sn, sg.lng, sg.nl, kLongCap, sg.sht, sg.ns, kShortCap);
+            const uint32_t c[kMaxArr] = {dc.x & 0xFFFFu, dc.x >> 16, dc.y & 0xFFFFu, dc.y >> 16,
+                                         dc.z & 0xFFFFu, dc.z >> 16, dc.w & 0xFFFFu, dc.w >> 16};
+#pragma unroll
+            for (int k = 1; k < kMaxArr; ++k) {
+                if (k < d.n_arr) {  // (block-uniform)
+                    int li = tmod + k;
+                    if (li >= d.n_arr) li -= d.n_arr;
+                    arrival_queue_warp(d, sg, li, so + c[k - 1], c[k] > c[k - 1] ? c[k] - c[k - 1] : 0u, pn.ovf);
+                }
+            }
+        } else if (!df) {
+            pn.ev += stage_run_warp(d, tm, nullptr, so, sn, sg.lng, sg.nl, kLongCap, sg.sht, sg.ns, kShortCap);
+        } else {
+            pn.ev += stage_run_warp(d, tm, nullptr, so, sn, sg.lng, sg.nl, kLongCap, sg.sht, sg.ns, kShortCap);
+            pn.ev += stage_run_warp(d, tm, nullptr, so + sn, rest, df->lng[cur], &df->nl[cur], kDefLong,
+                                    df->sht[cur], &df->ns[cur], kDefShort);
         }
     }
     tally_add(sg, 1, l1_loc);
@@ -831,10 +902,11 @@ __device__ __forceinline__ void route_finish(const Dev &d, int tm, int32_t *fix,
 // a6 for runs queued on an arrival list (delivery by arrival step): records
 // recs[lo, hi) (offset << 24 | length) into fix by the block's warps, 32
 // records per warp at a time.  The warp numbers the synapses of its 32 runs
-// through (a warp scan of the lengths) and takes them 128 at a time, four
-// per lane with every load in flight before the reductions; a lane finds the
+// through (a warp scan of the lengths) and takes them 32 U at a time, U per
+// lane with every load in flight before the reductions; a lane finds the
 // run of its synapse by a binary search over the lanes' prefix sums.  The
 // next 32 records are loaded while the current ones are delivered.
+template <int U>
 __device__ __forceinline__ void deliver_records(const Dev &d, int32_t *fix, const unsigned long long *recs,
                                                 unsigned long long lo, unsigned long long hi)
 {
@@ -856,11 +928,11 @@ __device__ __forceinline__ void deliver_records(const Dev &d, int32_t *fix, cons
         }
         const unsigned int ex = inc - n;
         const unsigned int tot = __shfl_sync(0xFFFFFFFFu, inc, 31);
-        for (unsigned int base = 0; base < tot; base += 128u) {
-            uint32_t td[4];
-            int32_t w[4];
+        for (unsigned int base = 0; base < tot; base += 32u * U) {
+            uint32_t td[U];
+            int32_t w[U];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
+            for (int k = 0; k < U; ++k) {
                 const unsigned int y = base + (unsigned int)k * 32u + (unsigned int)lane;
                 // the last lane whose run starts at or before y
                 int r = 0;
@@ -877,7 +949,7 @@ __device__ __forceinline__ void deliver_records(const Dev &d, int32_t *fix, cons
                 }
             }
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
+            for (int k = 0; k < U; ++k) {
                 const unsigned int y = base + (unsigned int)k * 32u + (unsigned int)lane;
                 if (y < tot) atomicAdd(fix + (td[k] & kTgtMask), w[k]);
             }
@@ -1039,11 +1111,25 @@ struct StepShared {
     unsigned long long abase[kMaxArr];
     unsigned int arr_n;
     long long inj_until;
+    // profiling (block 0 of k_persist): time per part, last stamp
+    unsigned long long prof[kPhases + 1];
+    int prof_on;
 };
+
+// Add the time since the last stamp to part k (k < 0: only restart).
+__device__ __forceinline__ void prof_stamp(StepShared &sh, int k)
+{
+    if (sh.prof_on && threadIdx.x == 0) {
+        const unsigned long long now = global_ns();
+        if (k >= 0) sh.prof[k] += now - sh.prof[kPhases];
+        sh.prof[kPhases] = now;
+    }
+}
 
 // Delivery by arrival step: this block's equal share of the runs queued for
 // step t (list t mod n_arr, complete since the last step's routing) into
-// the next step's input slot (all threads call).
+// the next step's input slot (all threads call); U loads per lane in flight.
+template <int U>
 __device__ __forceinline__ void arrival_share(const Dev &d, long long t, StepShared &sh)
 {
     const int li = (int)(t % d.n_arr);
@@ -1053,19 +1139,21 @@ __device__ __forceinline__ void arrival_share(const Dev &d, long long t, StepSha
     __syncthreads();
     const unsigned long long n = sh.arr_n;
     const unsigned long long lo = n * blockIdx.x / gridDim.x, hi = n * (blockIdx.x + 1) / gridDim.x;
-    deliver_records(d, d.acc + (size_t)((t + 1) & 1) * (size_t)d.M, d.arr + (size_t)li * d.arr_cap, lo, hi);
+    deliver_records<U>(d, d.acc + (size_t)((t + 1) & 1) * (size_t)d.M, d.arr + (size_t)li * d.arr_cap, lo, hi);
 }
 
-// a3: compaction of the spikes each thread collected in `bits` (bit b is
-// neuron id_of(b)) into step t's spike list: a block-wide scan numbers them
-// and one reservation per block places them (all threads call; without
-// spikes this costs one barrier).
-template <class IdOf>
-__device__ __forceinline__ void compact_spikes(const Dev &d, long long t, StepShared &sh, uint32_t bits,
-                                               IdOf id_of)
+// a3: compaction of the spikes each thread collected in bits[0, NC) (bit b
+// of word c is neuron id_of(c, b)) into step t's spike list: a block-wide
+// scan numbers them and one reservation per block places them (all threads
+// call; without spikes this costs one barrier).
+template <int NC, class IdOf>
+__device__ __forceinline__ void compact_spikes_multi(const Dev &d, long long t, StepShared &sh,
+                                                     const uint32_t (&bits)[NC], IdOf id_of)
 {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const unsigned int cnt = __popc(bits);
+    unsigned int cnt = 0;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) cnt += __popc(bits[c]);
     if (!__syncthreads_or(cnt)) return;
     unsigned int x = cnt;
 #pragma unroll
@@ -1089,11 +1177,22 @@ __device__ __forceinline__ void compact_spikes(const Dev &d, long long t, StepSh
     __syncthreads();
     unsigned int pos = sh.gbase + sh.wsum[wid] + x - cnt;
     unsigned int lp = sh.obase + sh.wsum[wid] + x - cnt;
-    for (uint32_t bb = bits; bb; bb &= bb - 1u, ++lp) {
-        const uint32_t id = id_of(__ffs(bb) - 1);
-        d.spk_step[pos++] = id;
-        if (lp < (unsigned int)kOwn) sh.own[lp] = id;
-    }
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+        for (uint32_t bb = bits[c]; bb; bb &= bb - 1u, ++lp) {
+            const uint32_t id = id_of(c, __ffs(bb) - 1);
+            d.spk_step[pos++] = id;
+            if (lp < (unsigned int)kOwn) sh.own[lp] = id;
+        }
+}
+
+// The same for one word of bits (bit b is neuron id_of(b)).
+template <class IdOf>
+__device__ __forceinline__ void compact_spikes(const Dev &d, long long t, StepShared &sh, uint32_t bits,
+                                               IdOf id_of)
+{
+    const uint32_t b1[1] = {bits};
+    compact_spikes_multi<1>(d, t, sh, b1, [&](int, int b) { return id_of(b); });
 }
 
 // While the block waits at the grid barrier after a3: pull the routing
@@ -1226,13 +1325,23 @@ __device__ __forceinline__ void update_step(const Dev &d, long long t, StepShare
                     rs.ref[lq] = r_out;
                 }
             }
+            prof_stamp(sh, 0);
             compact_spikes(d, t, sh, bits,
                           [&](int b) { return (uint32_t)((qb + l0 + (b >> 2) * kThreads) * 4 + (b & 3)); });
+            prof_stamp(sh, 1);
         }
     } else if constexpr (MODE == kModeVec) {
         const long long nq = d.M / 4, stride = (long long)gridDim.x * kThreads;
         const long long qb = (long long)blockIdx.x * kThreads + threadIdx.x;
-        for (long long b0 = (long long)blockIdx.x * kThreads; b0 < nq; b0 += 8 * stride) {
+        // NCH chunks of 8 quads per thread, their spikes compacted together
+        constexpr int NCH = QB > 1 ? 4 : 1;
+        for (long long B = (long long)blockIdx.x * kThreads; B < nq; B += NCH * 8 * stride) {
+        uint32_t bw[NCH];
+#pragma unroll
+        for (int c = 0; c < NCH; ++c) bw[c] = 0u;
+        for (int c = 0; c < NCH; ++c) {
+            const long long b0 = B + c * 8 * stride;
+            if (b0 >= nq) break;  // (block-uniform)
             uint32_t bits = 0;
             // QB quads' state loaded before any of them is written back, so
             // that their loads are in flight together
@@ -1267,9 +1376,14 @@ __device__ __forceinline__ void update_step(const Dev &d, long long t, StepShare
                     }
                 }
             }
-            const long long base = b0 - (long long)blockIdx.x * kThreads;
-            compact_spikes(d, t, sh, bits,
-                          [&](int b) { return (uint32_t)((qb + base + (b >> 2) * stride) * 4 + (b & 3)); });
+            bw[c] = bits;
+        }
+        const long long base = B - (long long)blockIdx.x * kThreads;
+        prof_stamp(sh, 0);
+        compact_spikes_multi<NCH>(d, t, sh, bw, [&](int c, int b) {
+            return (uint32_t)((qb + base + (long long)c * 8 * stride + (b >> 2) * stride) * 4 + (b & 3));
+        });
+        prof_stamp(sh, 1);
         }
     } else {
         const long long stride = (long long)gridDim.x * kThreads;
@@ -1382,6 +1496,7 @@ __device__ __forceinline__ void route_step(const Dev &d, long long t, StepShared
         const unsigned int nr = min(hi - b, (unsigned int)kRound);
         const bool split = df && b == lo;
         Pending pn{0, 0u, make_ulonglong2(0ull, 0ull), 0ull, 0u, 0u};
+        prof_stamp(sh, 5);
         if (!split || threadIdx.x < kTravWarps * 32)
             pn = route_traverse<ARR>(d, par, tm, b, nr, sg, split ? kTravWarps * 32 : kThreads, df, cur, fix, tmod);
         else
@@ -1389,6 +1504,7 @@ __device__ __forceinline__ void route_step(const Dev &d, long long t, StepShared
                       deliver_lists(d, tmp, nullptr, df->lng[prev], pl, df->sht[prev], ps, kTravWarps,
                                     kWarps - kTravWarps));
         __syncthreads();
+        prof_stamp(sh, 4);
         route_finish<ARR>(d, tm, fix, sg, pn);
         __syncthreads();
     }
@@ -1436,6 +1552,7 @@ __global__ void __launch_bounds__(kThreads) k_update(const Dev d, int k)
     if (threadIdx.x == 0) {
         sh.t0 = *(volatile long long *)&d.ctrl->t;
         sh.inj_until = *(volatile long long *)&d.ctrl->inject_until;
+        sh.prof_on = 0;
     }
     __syncthreads();
     const long long t = sh.t0 + k;
@@ -1444,7 +1561,7 @@ __global__ void __launch_bounds__(kThreads) k_update(const Dev d, int k)
     update_step<MODE, ARR, 1>(d, t, sh, Resident{}, 0u, 0ull);
     // delivery by arrival step: the runs queued for this step (they go to
     // the next step's input slot, which no block reads in this kernel)
-    if constexpr (ARR) arrival_share(d, t, sh);
+    if constexpr (ARR) arrival_share<8>(d, t, sh);
 }
 
 template <bool ARR>
@@ -1452,7 +1569,10 @@ __global__ void __launch_bounds__(kThreads) k_route(const Dev d, int k)
 {
     __shared__ StepShared sh;
     pdl_enter();
-    if (threadIdx.x == 0) sh.t0 = *(volatile long long *)&d.ctrl->t;
+    if (threadIdx.x == 0) {
+        sh.t0 = *(volatile long long *)&d.ctrl->t;
+        sh.prof_on = 0;
+    }
     __syncthreads();
     route_step<ARR>(d, sh.t0 + k, sh);
 }
@@ -1537,18 +1657,14 @@ __global__ void __launch_bounds__(kThreads, persist_min_blocks<MODE>()) k_persis
         if (T > 0) pre_update(d, t0, sh.th, rs);
     }
     const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+    // profiling: each part's time is added to sh.prof as soon as it ends
     const bool prof = d.phase_ns != nullptr && lead;
-    // profiling: each part's time is added to s_prof as soon as it ends
-    __shared__ unsigned long long s_prof[kPhases + 1];
-    auto stamp = [&](int k) {
-        if (prof) {
-            const unsigned long long now = global_ns();
-            if (k >= 0) s_prof[k] += now - s_prof[kPhases];
-            s_prof[kPhases] = now;
-        }
-    };
-    if (prof)
-        for (int k = 0; k < kPhases; ++k) s_prof[k] = 0;
+    if (threadIdx.x == 0) {
+        sh.prof_on = prof ? 1 : 0;
+        for (int k = 0; k <= kPhases; ++k) sh.prof[k] = 0;
+    }
+    __syncthreads();
+    auto stamp = [&](int k) { prof_stamp(sh, k); };
     int done = 0, issued = 0;
     long long closed = t0 - 1;
     for (int s = 0; s < T; ++s) {
@@ -1560,25 +1676,25 @@ __global__ void __launch_bounds__(kThreads, persist_min_blocks<MODE>()) k_persis
         }
         update_step<MODE, ARR>(d, t, sh, rs, (uint32_t)(s & 1), limit_ns);
         ++issued;
-        stamp(0);
+        stamp(1);
         // the first barrier carries the block's spike count in the word's high half
         grid_arrive(c, !(skip_arrival && s == 0 && blockIdx.x == 0), 1ull + ((unsigned long long)sh.n_own << 32));
         prefetch_own(d, sh);
         // delivery by arrival step: the runs queued for this step, while the
         // barrier completes (they need no spike of this step)
-        if constexpr (ARR) arrival_share(d, t, sh);
-        stamp(1);
-        if (!grid_wait(c, 2ull * s, limit_ns, &sh.word)) break;
+        if constexpr (ARR) arrival_share<MODE == kModeSmem ? 4 : 8>(d, t, sh);
         stamp(2);
-        route_step<ARR>(d, t, sh, true, df, s & 1);
+        if (!grid_wait(c, 2ull * s, limit_ns, &sh.word)) break;
         stamp(3);
+        route_step<ARR>(d, t, sh, true, df, s & 1);
+        stamp(5);
         // the next step's input-free update runs while the barrier completes
         grid_arrive(c);
         if constexpr (MODE == kModeSmem) {
             if (s + 1 < T) pre_update(d, t + 1, sh.th, rs);
         }
         if (!grid_wait(c, 2ull * s + 1ull, limit_ns)) break;
-        stamp(4);
+        stamp(6);
         ++done;
     }
     if constexpr (DEFER) {
@@ -1618,7 +1734,7 @@ __global__ void __launch_bounds__(kThreads, persist_min_blocks<MODE>()) k_persis
         if (t0 + done - 1 > closed) close_step(d, t0 + done - 1);
         c->t = t0 + done;
         if (prof)
-            for (int k = 0; k < kPhases; ++k) d.phase_ns[k] += s_prof[k];
+            for (int k = 0; k < kPhases; ++k) d.phase_ns[k] += sh.prof[k];
     }
 }
 

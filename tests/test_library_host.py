@@ -119,12 +119,12 @@ def test_routing_tables_and_groups(snn, grouping):
         assert rt.info()["group_cost"] == ocost
     else:
         assert np.array_equal(vn, oracle.group_contiguous(8, 4))
-    # relay: (h mod s)-th member of group g in ascending label order
+    # relay: ((h - g) mod s)-th member of group g in ascending label order
     s = 2
     for gg in range(4):
         members = sorted(q for q in range(8) if vn[q] == gg)
         for h in range(4):
-            assert relay[gg, h] == members[h % s]
+            assert relay[gg, h] == members[(h - gg) % s]
     info = rt.info()
     n_l1, n_l2, direct, two = _brute_tables(g, part, vn)
     assert info["n_l1"] == n_l1 and info["n_l2"] == n_l2
@@ -323,7 +323,7 @@ def test_exported_tables_follow_the_network(snn):
             assert ent["off"] & ((1 << 40) - 1) == start and ent["len"] == n and ent["q"] == q
             assert ent["off"] >> 40 == sum(1 for x in want if x[0] == q and x[1] == 0)
             gq = q // s
-            cls = (0 if q == ps else 1) if gq == hs else (2 if q == gq * s + hs % s else 3)
+            cls = (0 if q == ps else 1) if gq == hs else (2 if q == gq * s + (hs - gq) % s else 3)
             assert ent["cls"] == cls
             pid = l2pair[f]
             assert iptr[ps] <= pid < iptr[ps + 1] and idst[pid] == q

@@ -194,7 +194,7 @@ def _brute_counts(net, part_of, vn_of_part, spikes):
     groups = {}
     for p in range(P):
         groups.setdefault(int(vn_of_part[p]), []).append(p)
-    relay = {(g, h): sorted(groups[g])[h % len(groups[g])] for g in groups for h in groups}
+    relay = {(g, h): sorted(groups[g])[(h - g) % len(groups[g])] for g in groups for h in groups}
     c = dict.fromkeys(oracle.COUNT_NAMES[3:], 0)
     for i in spikes:
         p = int(part_of[i])
@@ -244,10 +244,12 @@ def test_counts_star_graph_by_hand():
     assert c2["l2_relay_local"] == 1 and c2["l2_relay_remote"] == 1
 
 
-def test_counts_ring_graph_by_hand():
-    """Directed ring over 8 partitions in 4 VNs: each spike reaches exactly the next partition."""
+@pytest.mark.parametrize("step", [1, 3])
+def test_counts_ring_graph_by_hand(step):
+    """Directed ring over 8 partitions in 4 VNs of 2: each spike of partition p
+    reaches exactly partition p + step (mod 8)."""
     M, P = 16, 8
-    edges = [(i, (i + 2) % M, 3, 1) for i in range(M)]
+    edges = [(i, (i + 2 * step) % M, 3, 1) for i in range(M)]
     v0 = np.full(M, -40.0, np.float32)
     net = synth.make_edges(M, edges, v0=v0)
     part = (np.arange(M) // 2).astype(np.int32)
@@ -255,14 +257,24 @@ def test_counts_ring_graph_by_hand():
     o = oracle.Oracle(net, P, part, 4, vn, synth.Dynamics(drive_lambda=0.0))
     o.run(1)
     c = o.count_dict()
-    # all 16 neurons spike once; partition p -> p+1: same VN when p even, next VN when p odd
+    # all 16 neurons spike once, two per partition
     assert c["spikes"] == 16 and c["direct"] == 16
-    assert c["direct_xvn"] == 8 and c["l1_xvn"] == 8 and c["l1_local"] == 8
-    assert c["l2_peer"] == 8 and c["l2_local"] == 0
-    # source VN h, destination g = h+1 (group {2g, 2g+1}); relay = 2g + (h % 2); target 2g
-    want_local = sum(1 for h in range(4) if (h % 2) == 0)
-    assert c["l2_relay_local"] == 2 * want_local
-    assert c["l2_relay_remote"] == 8 - 2 * want_local
+    same_vn = [p for p in range(P) if (p + step) % P // 2 == p // 2]
+    assert c["l2_peer"] == 2 * len(same_vn) and c["l2_local"] == 0
+    assert c["l1_local"] == 2 * len(same_vn) and c["l1_xvn"] == 16 - 2 * len(same_vn)
+    assert c["direct_xvn"] == c["l1_xvn"]
+    # the relay of VN g for source VN h is member (h - g) mod 2 of g: partition 2g + (h - g) % 2
+    local = 0
+    for p in range(P):
+        q, h = (p + step) % P, p // 2
+        g = q // 2
+        if g != h and q == 2 * g + (h - g) % 2:
+            local += 1
+    assert c["l2_relay_local"] == 2 * local
+    assert c["l2_relay_remote"] == c["l1_xvn"] - 2 * local
+    # step 1: odd p -> 2g with relay 2g + 1 (all forwarded); step 3: p -> the
+    # relay itself (none forwarded)
+    assert local == (0 if step == 1 else 8)
 
 
 @pytest.mark.parametrize("seed", [1, 2, 3])

@@ -52,8 +52,8 @@ def test_traffic_against_definition_and_oracle_totals(snn, mode):
     vn, relay = rt.groups()
     s = cfg.P // cfg.n_vn
     members = [sorted(np.nonzero(vn == gg)[0].tolist()) for gg in range(cfg.n_vn)]
-    # the relay of VN g for a source in VN h: the (h mod s)-th member of g in label order
-    assert all(relay[gg, h] == members[gg][h % s] for gg in range(cfg.n_vn) for h in range(cfg.n_vn))
+    # the relay of VN g for a source in VN h: the ((h - g) mod s)-th member of g in label order
+    assert all(relay[gg, h] == members[gg][(h - gg) % s] for gg in range(cfg.n_vn) for h in range(cfg.n_vn))
     o = oracle.Oracle(g, cfg.P, part, cfg.n_vn, vn, cfg.dyn)
     r = o.run(150)
     ids = r["raster_ids"]
@@ -93,7 +93,7 @@ def _hand_network():
 
 @pytest.mark.parametrize("policy,want", [
     # relay[g, p]: -1 inside the own VN
-    ("per_vn", [[-1, -1, 1, 1], [2, 2, -1, -1]]),
+    ("per_vn", [[-1, -1, 1, 1], [3, 3, -1, -1]]),
     ("per_partition", [[-1, -1, 0, 1], [2, 3, -1, -1]]),
     # loads into VN 0: p2 5, p3 3 -> p2 to member 0, p3 to member 1;
     # into VN 1: p1 7, p0 2 -> p1 to member 0 (partition 2), p0 to member 1
