@@ -278,12 +278,12 @@ def run_ours(args):
     # path, events around the two kernels on the graph path)
     NP = min(K, 1000)
     phase_ms = sim.profile_phases(NP)
-    persistent_names = ["update", "prefetch_and_queued_delivery", "barrier1_wait", "route",
-                        "next_drive_and_barrier2_wait"]
+    persistent_names = ["update", "compaction", "prefetch_and_queued_delivery", "barrier1_wait", "route_walk",
+                        "route_delivery_and_copies", "next_drive_and_barrier2_wait"]
     phases = {"what": ("block 0 of the persistent kernel" if persistent else "k_update and k_route kernels")
                       + ", %d steps after the timed ones" % NP,
               "ms_per_step": dict(zip(persistent_names, [x / NP for x in phase_ms])) if persistent else
-              {"k_update": phase_ms[0] / NP, "k_route": phase_ms[3] / NP}}
+              {"k_update": phase_ms[0] / NP, "k_route": phase_ms[4] / NP}}
     print("[bench] timed %.3f ms for %d steps (steps %d..%d); parts ms per step %s" % (
         ms, K, first, first + K - 1, [round(x / NP, 5) for x in phase_ms]), file=sys.stderr, flush=True)
 

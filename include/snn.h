@@ -623,14 +623,15 @@ int64_t snn_launches(const snn_sim *sim, int32_t T);
 
 /*
  * Advance T steps like snn_step and return, in milliseconds summed over the
- * steps, the time of the parts of a step (phase_ms: caller-owned [5]).
- * Persistent path, as seen by block 0 (GPU global timer): [0] the update
- * half (a1-a3), [1] the prefetch of its own spikes' tables and its share of
- * the runs queued for the step (delivery by arrival step), [2] the rest of
- * the wait at the first grid barrier, [3] the routing half (a4-a6), [4] the
- * next step's input-free update and the wait at the second barrier.  Graph
- * path: [0] the k_update kernel and [3] the k_route kernel of every step
- * (CUDA events between them, which add a little time), [1] = [2] = [4] = 0.
+ * steps, the time of the parts of a step (phase_ms: caller-owned [7]).
+ * Persistent path, as seen by block 0 (GPU global timer): [0] the neurons'
+ * update (a1-a2), [1] the spike compaction (a3), [2] the prefetch of its own
+ * spikes' tables and its share of the runs queued for the step (delivery by
+ * arrival step), [3] the rest of the wait at the first grid barrier, [4] the
+ * routing walk (a4-a5), [5] the routing rounds' deliveries and copies (a6),
+ * [6] the next step's input-free update and the wait at the second barrier.
+ * Graph path: [0] the k_update kernel and [4] the k_route kernel of every
+ * step (CUDA events between them, which add a little time), the rest 0.
  * Synchronises the stream.  Errors: SNN_E_ARG, SNN_E_CUDA.
  */
 int snn_profile_phases(snn_sim *sim, int32_t T, double *phase_ms);

@@ -584,11 +584,11 @@ class Sim:
 
     def profile_phases(self, T: int) -> np.ndarray:
         """Advance T steps and return the summed ms of the parts of a step
-        (snn_profile_phases): persistent path [update half, own-table prefetch
-        and queued deliveries, rest of the first barrier wait, routing half,
-        next step's input-free update and the second barrier wait]; graph
-        path [k_update, 0, 0, k_route, 0]."""
-        out = np.zeros(5, np.float64)
+        (snn_profile_phases): persistent path [update, compaction, own-table
+        prefetch and queued deliveries, rest of the first barrier wait, routing
+        walk, routing deliveries and copies, next step's input-free update and
+        the second barrier wait]; graph path [k_update, 0, 0, 0, k_route, 0, 0]."""
+        out = np.zeros(7, np.float64)
         with self._dev():
             _ck(_lib.snn_profile_phases(self.h, int(T), out.ctypes.data), "snn_profile_phases")
         return out

@@ -1047,7 +1047,7 @@ extern "C" int snn_profile_phases(snn_sim *s, int32_t T, double *phase_ms)
                 CK(cudaEventElapsedTime(&a, s->pev[3 * k], s->pev[3 * k + 1]));
                 CK(cudaEventElapsedTime(&b, s->pev[3 * k + 1], s->pev[3 * k + 2]));
                 phase_ms[0] += a;
-                phase_ms[3] += b;
+                phase_ms[4] += b;
             }
             left -= s->UP;
         } else {
