@@ -395,18 +395,30 @@ typedef struct {
      *     (segments are sorted by delay).  Two input slots of M int32 stay
      *     hot in L2 however large the ring would be.  Needs max_delay <= 8
      *     and segments of at most 65535 synapses (else SNN_E_RANGE);
-     *   AUTO: the workspace holds both; snn_autotune picks the faster (until
-     *     then ARRIVAL when it is available, else RING).
+     *   OWNER: every run of a routed segment, of every delay, is queued on
+     *     its destination partition's list of its arrival step; at step t
+     *     the block that owns a partition adds that partition's runs into a
+     *     shared-memory accumulator and updates the partition's neurons
+     *     from it, so no global input slot and no global reductions remain
+     *     (each partition receives its messages and delivers them into its
+     *     own neurons).  Persistent kernel only; needs cooperative launch,
+     *     max_delay <= 8, segments of at most 65535 synapses and the
+     *     largest partition's accumulator in one block's shared memory
+     *     (else SNN_E_RANGE);
+     *   AUTO: the workspace holds every available mode; snn_autotune picks
+     *     the fastest (until then ARRIVAL when it is available, else RING).
      * Sums are integers, so every mode gives the same results bit for bit. */
     int32_t delivery;
-    /* capacity of each arrival list as a fraction of its exact worst case
-     * (1.0, the default, never overflows; overflow sets SNN_E_CAPACITY) */
+    /* capacity of each arrival list (ARRIVAL and OWNER) as a fraction of its
+     * exact worst case (1.0, the default, never overflows; overflow sets
+     * SNN_E_CAPACITY) */
     float arrival_frac;
 } snn_sim_params;
 
 #define SNN_DELIVER_RING    0
 #define SNN_DELIVER_ARRIVAL 1
 #define SNN_DELIVER_AUTO    2
+#define SNN_DELIVER_OWNER   3
 
 /* Fill p with the defaults (no records, exact capacities, 32 steps/graph). */
 void snn_sim_params_default(snn_sim_params *p);

@@ -32,7 +32,7 @@ _lib = ctypes.CDLL(_SO)
 
 SNN_PART_PLANTED, SNN_PART_GREEDY, SNN_PART_RANDOM = 0, 1, 2
 SNN_GROUP_CONTIGUOUS, SNN_GROUP_GREEDY = 0, 1
-SNN_DELIVER_RING, SNN_DELIVER_ARRIVAL, SNN_DELIVER_AUTO = 0, 1, 2
+SNN_DELIVER_RING, SNN_DELIVER_ARRIVAL, SNN_DELIVER_AUTO, SNN_DELIVER_OWNER = 0, 1, 2, 3
 SNN_RELAY_PER_VN, SNN_RELAY_PER_PARTITION, SNN_RELAY_BALANCED = 0, 1, 2
 RELAY_POLICIES = {"per_vn": SNN_RELAY_PER_VN, "per_partition": SNN_RELAY_PER_PARTITION,
                   "balanced": SNN_RELAY_BALANCED}

@@ -7,6 +7,7 @@
 #include <cstring>
 #include <functional>
 #include <memory>
+#include <mutex>
 #include <thread>
 #include <vector>
 
@@ -112,6 +113,11 @@ struct snn_routing {
     // >= 2; the sum over segments of min(max_delay - 1, synapses of delay >= 2)
     // (-1: not computed yet).
     mutable std::atomic<int64_t> seg_maxlen{-1}, seg_delayed{-1}, seg_runs{-1};
+    // Partition-owned delivery, per internal destination partition q: the
+    // segments into q and the sum over them of min(max_delay, length)
+    // (computed once, on first use).
+    mutable std::once_flag own_once;
+    mutable std::vector<int64_t> own_segs, own_runs;
 };
 
 namespace snn {

@@ -160,6 +160,30 @@ __global__ void __launch_bounds__(kThreads) k_materialize(const Dev d, long long
     }
 }
 
+// The same for partition-owned delivery, next step t: every list (q, li)
+// holds runs arriving at step s = the step in t .. t + n_own - 1 with
+// s mod n_own = li, added into ring slot s mod D.
+__global__ void __launch_bounds__(kThreads) k_materialize_owner(const Dev d, long long t)
+{
+    for (int q = blockIdx.x; q < d.P; q += gridDim.x) {
+        const ulonglong2 sl = d.inb_slot[q];
+        for (int li = 0; li < d.n_own; ++li) {
+            const long long s = t + ((li - (int)(t % d.n_own)) % d.n_own + d.n_own) % d.n_own;
+            int32_t *dst = d.ring + (size_t)(s % d.D) * (size_t)d.M;
+            const unsigned long long n =
+                min((unsigned long long)d.inb_cnt[((size_t)q * d.n_own + li) * kPairStride], sl.y);
+            const unsigned long long *recs = d.inb + sl.x + (unsigned long long)li * sl.y;
+            for (unsigned long long r = threadIdx.x; r < n; r += kThreads) {
+                const unsigned long long rec = recs[r];
+                const unsigned long long o = rec >> kLenBits;
+                const unsigned int len = (unsigned int)(rec & kLenMask);
+                for (unsigned int y = 0; y < len; ++y)
+                    atomicAdd(dst + (d.syn_td[o + y] & kTgtMask), (int32_t)d.syn_w[o + y]);
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------- host helpers
 struct Region {
     size_t off = 0, bytes = 0;
@@ -174,9 +198,13 @@ struct Layout {
     Region fwd, fo_cnt;  // snn_deliver_spikes: global -> internal map, scratch counters
     Region phase_ns;
     Region acc, arr, arr_cnt, dcnt;  // delivery by arrival step (absent with SNN_DELIVER_RING)
+    Region inb, inb_slot, inb_cnt, pbase;  // partition-owned delivery
     size_t total = 0;
     int n_arr = 0;                   // arrival lists (the largest delay); 0: no arrival regions
     uint64_t arr_cap = 0;            // runs per arrival list
+    int n_own = 0;                   // lists per partition of owned delivery; 0: no owner regions
+    int64_t own_max = 0;             // neurons of the largest partition
+    std::vector<uint64_t> inb_base_h, inb_cap_h;  // per internal partition: first record, list capacity
     std::vector<uint64_t> bucket_base_h, inbox_base_h;
     std::vector<uint32_t> bucket_cap_h, inbox_cap_h;
     int64_t tally_rows = 0;
@@ -242,6 +270,48 @@ static bool arrival_possible(const snn_routing *rt)
 {
     arrival_stats(rt);
     return rt->max_delay <= kMaxArr && rt->seg_maxlen.load() <= 0xFFFF;
+}
+
+// Per internal destination partition: the level-2 segments into it and the
+// sum over them of min(max_delay, length) (cached in the routing).
+static void owner_stats(const snn_routing *rt)
+{
+    std::call_once(rt->own_once, [rt]() {
+        const int32_t P = rt->P;
+        const int nt = resolve_threads(0);
+        std::vector<std::vector<int64_t>> sg((size_t)nt), rn((size_t)nt);
+        const int64_t lim = std::max(1, rt->max_delay);
+        parallel_for(rt->n_l2, nt, [&](int64_t lo, int64_t hi, int k) {
+            sg[k].assign((size_t)P, 0);
+            rn[k].assign((size_t)P, 0);
+            for (int64_t f = lo; f < hi; ++f) {
+                const L2Entry &e = rt->l2[f];
+                sg[k][e.q] += 1;
+                rn[k][e.q] += std::min<int64_t>(lim, e.len);
+            }
+        });
+        rt->own_segs.assign((size_t)P, 0);
+        rt->own_runs.assign((size_t)P, 0);
+        for (int k = 0; k < nt; ++k)
+            if (!sg[k].empty())
+                for (int32_t q = 0; q < P; ++q) {
+                    rt->own_segs[q] += sg[k][q];
+                    rt->own_runs[q] += rn[k][q];
+                }
+    });
+}
+
+// The largest accumulator a block of k_owner may hold in shared memory.
+constexpr int64_t kOwnerSmemMax = 200 * 1024;
+
+// The delivery a sim uses: the parameter, or SNN_DELIVERY=0|1|2|3 from the
+// environment (tests of every path).
+static int effective_delivery(const snn_sim_params *p)
+{
+    int delivery = p->delivery;
+    if (const char *e = std::getenv("SNN_DELIVERY"))
+        if (e[0] >= '0' && e[0] <= '3' && e[1] == 0) delivery = e[0] - '0';
+    return delivery;
 }
 
 static int make_layout(const snn_routing *rt, const snn_sim_params *p, Layout &L, int32_t n_net = 0)
@@ -316,11 +386,40 @@ static int make_layout(const snn_routing *rt, const snn_sim_params *p, Layout &L
     place(L, L.fwd, rt->identity ? 0 : sizeof(uint32_t) * (size_t)M);
     place(L, L.fo_cnt, 64);
     place(L, L.phase_ns, kPhases * sizeof(unsigned long long));
-    // SNN_DELIVERY=0|1|2 overrides the parameter (tests of every path)
-    int delivery = p->delivery;
-    if (const char *e = std::getenv("SNN_DELIVERY"))
-        if (e[0] >= '0' && e[0] <= '2' && e[1] == 0) delivery = e[0] - '0';
-    if (delivery != SNN_DELIVER_RING && !p->defer_delayed) {
+    const int delivery = effective_delivery(p);
+    const bool want_arr = (delivery == SNN_DELIVER_ARRIVAL || delivery == SNN_DELIVER_AUTO) && !p->defer_delayed;
+    const bool want_own = (delivery == SNN_DELIVER_OWNER || delivery == SNN_DELIVER_AUTO) && !p->defer_delayed;
+    if (want_own) {
+        int64_t mx = 0;
+        for (int32_t q = 0; q < P; ++q) mx = std::max(mx, rt->pbase[q + 1] - rt->pbase[q]);
+        // (quads of 4 ids with 16-byte accesses: M % 4 == 0)
+        if (!arrival_possible(rt) || mx * 4 > kOwnerSmemMax || rt->M % 4 != 0) {
+            if (delivery == SNN_DELIVER_OWNER) return SNN_E_RANGE;
+        } else {
+            // each list's exact worst case: with t_ref >= max_delay - 1 a neuron
+            // spikes at most once in the max_delay steps that feed a list (one run
+            // per segment into q), else one run per delay present in a segment
+            owner_stats(rt);
+            L.n_own = rt->max_delay;
+            L.own_max = mx;
+            L.inb_base_h.assign((size_t)P, 0);
+            L.inb_cap_h.assign((size_t)P, 0);
+            uint64_t tot = 0;
+            for (int32_t q = 0; q < P; ++q) {
+                const int64_t worst = p->t_ref >= L.n_own - 1 ? rt->own_segs[q] : rt->own_runs[q];
+                const uint64_t c = cap((uint64_t)worst, p->arrival_frac);
+                if (c > 0xFFFFFFFFull) return SNN_E_RANGE;  // 32-bit fill counters
+                L.inb_base_h[q] = tot;
+                L.inb_cap_h[q] = c;
+                tot += c * (uint64_t)L.n_own;
+            }
+            place(L, L.inb, sizeof(unsigned long long) * (size_t)tot);
+            place(L, L.inb_slot, sizeof(ulonglong2) * (size_t)P);
+            place(L, L.inb_cnt, sizeof(uint32_t) * kPairStride * (size_t)P * (size_t)L.n_own);
+            place(L, L.pbase, sizeof(long long) * (size_t)(P + 1));
+        }
+    }
+    if (want_arr) {
         if (!arrival_possible(rt)) {
             if (delivery == SNN_DELIVER_ARRIVAL) return SNN_E_RANGE;
         } else {
@@ -337,9 +436,9 @@ static int make_layout(const snn_routing *rt, const snn_sim_params *p, Layout &L
             place(L, L.acc, 2 * sizeof(int32_t) * (size_t)M);
             place(L, L.arr, sizeof(unsigned long long) * (size_t)L.n_arr * (size_t)L.arr_cap);
             place(L, L.arr_cnt, sizeof(uint32_t) * kPairStride * (size_t)L.n_arr);
-            place(L, L.dcnt, sizeof(uint4) * (size_t)rt->n_l2);
         }
     }
+    if (L.n_arr > 0 || L.n_own > 0) place(L, L.dcnt, sizeof(uint4) * (size_t)rt->n_l2);
     return SNN_OK;
 }
 
@@ -354,9 +453,9 @@ static bool params_ok(const snn_sim_params *p)
     if (!(p->bucket_frac >= 0.0f) || !(p->inbox_frac >= 0.0f)) return false;
     if (p->steps_per_graph < 1 || p->steps_per_graph > 256) return false;
     if (p->defer_delayed != 0 && p->defer_delayed != 1) return false;
-    if (p->delivery < SNN_DELIVER_RING || p->delivery > SNN_DELIVER_AUTO) return false;
+    if (p->delivery < SNN_DELIVER_RING || p->delivery > SNN_DELIVER_OWNER) return false;
     if (!(p->arrival_frac >= 0.0f)) return false;
-    if (p->defer_delayed && p->delivery == SNN_DELIVER_ARRIVAL) return false;
+    if (p->defer_delayed && (p->delivery == SNN_DELIVER_ARRIVAL || p->delivery == SNN_DELIVER_OWNER)) return false;
     return true;
 }
 
@@ -423,6 +522,8 @@ struct snn_sim {
     bool persist = false;  // one cooperative launch per snn_step (k_persist)
     bool defer = false;    // k_persist with minimum-delay batching (shared-memory state only)
     bool arrival = false;  // delivery by arrival step active (the workspace holds its regions)
+    bool owner = false;    // partition-owned delivery active (k_owner; the workspace holds its regions)
+    size_t owner_smem = 0; // dynamic shared memory of k_owner: the largest partition's accumulator
     unsigned grid_persist = 1;
     // bound on one grid-barrier wait of k_persist: a healthy barrier takes
     // microseconds; past this the kernel records a timeout and returns
@@ -501,6 +602,13 @@ static int upload_tables(snn_sim *s)
     }
     CK(up(L.l2_pair, rt->l2_pair.data()));
     CK(up(L.csr, rt->csr.data()));
+    if (L.n_own > 0) {
+        // partition bounds and each partition's list region
+        CK(cudaMemcpyAsync(w + L.pbase.off, rt->pbase.data(), L.pbase.bytes, cudaMemcpyHostToDevice, st));
+        std::vector<ulonglong2> v((size_t)rt->P);
+        for (int32_t q = 0; q < rt->P; ++q) v[q] = make_ulonglong2(L.inb_base_h[q], L.inb_cap_h[q]);
+        CK(cudaMemcpy(w + L.inb_slot.off, v.data(), L.inb_slot.bytes, cudaMemcpyHostToDevice));
+    }
     if (L.dcnt.bytes && rt->n_l2 > 0) {
         // delay counts of every segment, from the uploaded tables
         const long long g = std::min<long long>((rt->n_l2 + kThreads - 1) / kThreads, (long long)s->sms * 8);
@@ -541,6 +649,7 @@ static int reset_state(snn_sim *s)
     if (L.cur_rec.bytes) CK(cudaMemsetAsync(w + L.cur_rec.off, 0, L.cur_rec.bytes, st));
     if (L.acc.bytes) CK(cudaMemsetAsync(w + L.acc.off, 0, L.acc.bytes, st));
     if (L.arr_cnt.bytes) CK(cudaMemsetAsync(w + L.arr_cnt.off, 0, L.arr_cnt.bytes, st));
+    if (L.inb_cnt.bytes) CK(cudaMemsetAsync(w + L.inb_cnt.off, 0, L.inb_cnt.bytes, st));
     Ctrl c;
     std::memset(&c, 0, sizeof(c));
     const bool rec = s->prm.raster_cap > 0 && s->prm.raster_steps > 0;
@@ -692,16 +801,48 @@ extern "C" int snn_batch_create(const snn_network *net, const snn_routing *rt, i
 
 // The k_persist instance of a state-access mode; the minimum-delay
 // batching one exists for the shared-memory mode.
-static const void *persist_fn(int mode, bool defer, bool arr)
+static const void *persist_fn(int mode, bool defer, bool arr, int b = 2)
 {
+    // global neuron state: the instance built for 3 blocks per SM when that
+    // many are asked for, else the one for 2
+    const bool three = b >= 3;
     if (arr) {
-        if (mode == kModeSmem) return (const void *)k_persist<kModeSmem, false, true>;
-        return mode == kModeVec ? (const void *)k_persist<kModeVec, false, true>
-                                : (const void *)k_persist<kModeScalar, false, true>;
+        if (mode == kModeSmem) return (const void *)k_persist<kModeSmem, false, true, 3>;
+        if (mode == kModeVec)
+            return three ? (const void *)k_persist<kModeVec, false, true, 3> : (const void *)k_persist<kModeVec, false, true, 2>;
+        return three ? (const void *)k_persist<kModeScalar, false, true, 3> : (const void *)k_persist<kModeScalar, false, true, 2>;
     }
     if (mode == kModeSmem)
-        return defer ? (const void *)k_persist<kModeSmem, true, false> : (const void *)k_persist<kModeSmem, false, false>;
-    return mode == kModeVec ? (const void *)k_persist<kModeVec, false, false> : (const void *)k_persist<kModeScalar, false, false>;
+        return defer ? (const void *)k_persist<kModeSmem, true, false, 3> : (const void *)k_persist<kModeSmem, false, false, 3>;
+    if (mode == kModeVec)
+        return three ? (const void *)k_persist<kModeVec, false, false, 3> : (const void *)k_persist<kModeVec, false, false, 2>;
+    return three ? (const void *)k_persist<kModeScalar, false, false, 3> : (const void *)k_persist<kModeScalar, false, false, 2>;
+}
+
+// Select the partition-owned kernel with b blocks per SM if that many stay
+// resident with the largest partition's accumulator in shared memory.
+// Returns whether it was selected (the persistent path then runs k_owner).
+static bool shape_owner(snn_sim *s, int b)
+{
+    if (s->L.n_own == 0 || !s->coop || !s->allow_persist) return false;
+    const size_t dyn = (size_t)((s->L.own_max * 4 + 15) / 16 * 16);
+    if (cudaFuncSetAttribute((const void *)k_owner, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    int op = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&op, (const void *)k_owner, kThreads, dyn) != cudaSuccess ||
+        op < b) {
+        cudaGetLastError();
+        return false;
+    }
+    s->persist = true;
+    s->owner = true;
+    s->persist_bps = b;
+    s->grid_persist = (unsigned)std::min<int64_t>((int64_t)s->sms * b, s->L.tally_rows);
+    s->owner_smem = dyn;
+    return true;
 }
 
 // Select the persistent kernel in neuron-state mode `mode` with b blocks per
@@ -713,7 +854,7 @@ static bool shape_persist(snn_sim *s, int mode, int b)
     const int64_t grid = std::min<int64_t>((int64_t)s->sms * b, s->L.tally_rows);
     size_t dyn = 0;
     int64_t cq = 0;
-    const void *fn = persist_fn(mode, s->defer, s->arrival);
+    const void *fn = persist_fn(mode, s->defer, s->arrival, b);
     if (mode != kModeScalar && !s->vec) return false;
     if (mode == kModeSmem) {
         int smax = 0;
@@ -732,6 +873,7 @@ static bool shape_persist(snn_sim *s, int mode, int b)
         return false;
     }
     s->persist = true;
+    s->owner = false;
     s->pmode = mode;
     s->persist_bps = b;
     s->grid_persist = (unsigned)grid;
@@ -904,11 +1046,18 @@ static int sim_create(const snn_network *net, const snn_routing *rt, const snn_s
     d.hash_steps = p->hash_steps;
     d.cur_every = p->cur_every;
     d.cur_slots = p->cur_slots;
+    if (L.n_arr > 0 || L.n_own > 0) d.dcnt = (const uint4 *)(w + L.dcnt.off);
+    if (L.n_own > 0) {
+        d.inb = (unsigned long long *)(w + L.inb.off);
+        d.inb_slot = (const ulonglong2 *)(w + L.inb_slot.off);
+        d.inb_cnt = (uint32_t *)(w + L.inb_cnt.off);
+        d.pbase = (const long long *)(w + L.pbase.off);
+        d.n_own = L.n_own;
+    }
     if (L.n_arr > 0) {
         d.acc = (int32_t *)(w + L.acc.off);
         d.arr = (unsigned long long *)(w + L.arr.off);
         d.arr_cnt = (uint32_t *)(w + L.arr_cnt.off);
-        d.dcnt = (const uint4 *)(w + L.dcnt.off);
         d.arr_cap = L.arr_cap;
         // SNN_DELIVER_AUTO starts with delivery by arrival step (snn_autotune
         // may switch); minimum-delay batching (SNN_PERSIST_DEFER) keeps the ring
@@ -921,6 +1070,16 @@ static int sim_create(const snn_network *net, const snn_routing *rt, const snn_s
         s->persist = false;
         for (int bb = b; bb >= 1 && !s->persist; --bb) shape_persist(s, m, bb);
         cudaGetLastError();
+    }
+    if (effective_delivery(p) == SNN_DELIVER_OWNER && !s->defer) {
+        // partition-owned delivery asked for: its persistent kernel, or an error
+        const bool prev = s->persist;
+        s->persist = false;
+        if (!shape_owner(s, 2) && !shape_owner(s, 1)) {
+            s->persist = prev;
+            snn_sim_destroy(s);
+            return SNN_E_RANGE;
+        }
     }
     finite_thresholds(p->drive_lambda, d.th32, &d.th_fin);
     if (L.n_net > 0) {
@@ -953,7 +1112,8 @@ static int sim_create(const snn_network *net, const snn_routing *rt, const snn_s
 static int launch_persist(snn_sim *s, int32_t T, const Dev &d)
 {
     unsigned long long lim = s->barrier_limit_ns;
-    const void *fn = persist_fn(s->pmode, s->defer, s->arrival);
+    const void *fn = s->owner ? (const void *)k_owner : persist_fn(s->pmode, s->defer, s->arrival, s->persist_bps);
+    const size_t smem = s->owner ? s->owner_smem : s->persist_smem;
     // a launch's barrier arrivals (2 per step per block) stay below 2^32
     const int32_t cap = (int32_t)std::min<unsigned long long>(
         0x7FFFFFFFull, (0xFFFFFFFFull / (2ull * s->grid_persist)) - 1ull);
@@ -964,8 +1124,7 @@ static int launch_persist(snn_sim *s, int32_t T, const Dev &d)
         void *args[] = {(void *)&d, (void *)&tt, (void *)&lim, (void *)&skip};
         // the grid barrier counts arrivals from zero in every launch
         CK(cudaMemsetAsync(s->ws + s->L.ctrl.off + offsetof(Ctrl, bar), 0, sizeof(unsigned long long), s->stream));
-        CK(cudaLaunchCooperativeKernel(fn, dim3(s->grid_persist), dim3(kThreads), args, s->persist_smem,
-                                       s->stream));
+        CK(cudaLaunchCooperativeKernel(fn, dim3(s->grid_persist), dim3(kThreads), args, smem, s->stream));
         T -= tt;
     }
     return SNN_OK;
@@ -1064,9 +1223,11 @@ extern "C" int snn_profile_phases(snn_sim *s, int32_t T, double *phase_ms)
 static int read_ctrl(snn_sim *s, Ctrl *c);
 
 // Turn delivery by arrival step on or off (the workspace holds its regions);
-// captured graphs hold the old device view and are dropped.
+// captured graphs hold the old device view and are dropped.  The owner
+// kernel is chosen by shape_owner; any other shape turns it off.
 static void set_arrival(snn_sim *s, bool on)
 {
+    s->owner = false;
     on = on && s->L.n_arr > 0 && !s->defer;
     if (on == s->arrival) return;
     s->arrival = on;
@@ -1084,27 +1245,32 @@ extern "C" int snn_autotune(snn_sim *s, int32_t steps, int32_t *choice, double *
     struct Shape {
         bool persist;
         int mode, b;
-        bool arrival;
+        bool arrival, owner;
     };
     std::vector<Shape> cand;
+    if (s->L.n_own > 0 && !s->defer && s->allow_persist)
+        for (int b = 2; b >= 1; --b) cand.push_back({true, 0, b, false, true});
     std::vector<bool> dels{false};
     if (s->L.n_arr > 0 && !s->defer) dels = {true, false};
     for (bool arr : dels) {
         if (s->allow_persist)
             for (int mode : {kModeSmem, kModeVec, kModeScalar})
                 for (int b = 4; b >= 1; --b)
-                    if (mode != kModeSmem || s->allow_smem) cand.push_back({true, mode, b, arr});
-        cand.push_back({false, 0, 0, arr});
+                    if (mode != kModeSmem || s->allow_smem) cand.push_back({true, mode, b, arr, false});
+        cand.push_back({false, 0, 0, arr, false});
     }
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     double best = 1e300;
-    Shape pick = {s->persist, s->pmode, s->persist_bps, s->arrival};
+    Shape pick = {s->persist, s->pmode, s->persist_bps, s->arrival, s->owner};
     int rc = SNN_OK;
     for (const Shape &c : cand) {
         set_arrival(s, c.arrival);
-        if (c.persist) {
+        if (c.owner) {
+            s->persist = false;
+            if (!shape_owner(s, c.b)) continue;
+        } else if (c.persist) {
             s->persist = false;
             if (!shape_persist(s, c.mode, c.b)) continue;
         } else {
@@ -1133,10 +1299,13 @@ extern "C" int snn_autotune(snn_sim *s, int32_t steps, int32_t *choice, double *
     cudaEventDestroy(e1);
     s->persist = false;
     set_arrival(s, pick.arrival);
-    if (pick.persist) shape_persist(s, pick.mode, pick.b);
+    if (pick.owner) shape_owner(s, pick.b);
+    else if (pick.persist) shape_persist(s, pick.mode, pick.b);
     const int rr = reset_state(s);
     if (rc == SNN_OK) rc = rr;
-    if (choice) *choice = (pick.persist ? 100 * pick.mode + pick.b : 0) + (pick.arrival ? 1000 : 0);
+    if (choice)
+        *choice = pick.owner ? 2000 + pick.b
+                             : (pick.persist ? 100 * pick.mode + pick.b : 0) + (pick.arrival ? 1000 : 0);
     if (best_ms) *best_ms = best < 1e300 ? best / steps : -1.0;
     return rc;
 }
@@ -1513,6 +1682,16 @@ extern "C" int snn_save_state(snn_sim *s, void *buf, size_t capb)
         CK(cudaMemcpyAsync(s->ws + L.ctrl.off + offsetof(Ctrl, inject_until), &until, sizeof(until),
                            cudaMemcpyHostToDevice, s->stream));
         CK(cudaStreamSynchronize(s->stream));
+    } else if (s->owner) {
+        // partition-owned delivery: the queued runs move into the delay ring
+        const unsigned g = (unsigned)std::max(1, std::min(s->rt->P, s->sms * 4));
+        k_materialize_owner<<<g, kThreads, 0, s->stream>>>(s->dev, (long long)c.t);
+        CK(cudaGetLastError());
+        CK(cudaMemsetAsync(s->ws + L.inb_cnt.off, 0, L.inb_cnt.bytes, s->stream));
+        const long long until = c.t + L.D;
+        CK(cudaMemcpyAsync(s->ws + L.ctrl.off + offsetof(Ctrl, inject_until), &until, sizeof(until),
+                           cudaMemcpyHostToDevice, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
     }
     char *b = (char *)buf;
     CkptHeader h{kCkptMagic, s->rt->M, L.D, 0, c.t};
@@ -1550,7 +1729,7 @@ extern "C" int snn_load_state(snn_sim *s, const void *buf, size_t bytes)
     c.t = h.t;
     // delivery by arrival step: the ring holds the restored partial sums of
     // steps h.t .. h.t + D - 1, which those steps consume
-    c.inject_until = s->arrival ? h.t + L.D : 0;
+    c.inject_until = (s->arrival || s->owner) ? h.t + L.D : 0;
     for (int k = 0; k < 3; ++k) c.head[k] = -1;  // records restart empty and stay off after a restore
     CK(cudaMemcpy(s->dev.ctrl, &c, sizeof(c), cudaMemcpyHostToDevice));
     if (h.t < s->prm.hash_steps)
@@ -1559,6 +1738,7 @@ extern "C" int snn_load_state(snn_sim *s, const void *buf, size_t bytes)
     CK(cudaMemset(s->dev.inbox_cnt, 0, L.inbox_cnt.bytes));
     if (L.acc.bytes) CK(cudaMemset(s->ws + L.acc.off, 0, L.acc.bytes));
     if (L.arr_cnt.bytes) CK(cudaMemset(s->ws + L.arr_cnt.off, 0, L.arr_cnt.bytes));
+    if (L.inb_cnt.bytes) CK(cudaMemset(s->ws + L.inb_cnt.off, 0, L.inb_cnt.bytes));
     return SNN_OK;
 }
 

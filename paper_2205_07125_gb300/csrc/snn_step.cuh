@@ -66,6 +66,12 @@ constexpr uint32_t kStBucket = 1u, kStInbox = 2u, kStRaster = 4u, kStTimeout = 8
 constexpr int kArrPool = 2048;
 constexpr int kMaxArr = 8;
 
+// Routing variants of a step: every delay into the delay ring (or the
+// deferred lists), delivery by arrival step, delivery into the destination
+// partition's own input (k_owner: every run queued on its partition's list
+// of its arrival step, nothing delivered during the routing).
+enum { kRtRing = 0, kRtArrival = 1, kRtOwner = 2 };
+
 // Parts of a step timed by block 0 of k_persist (snn_profile_phases): the
 // update of the neurons (a1-a2) and their spike compaction (a3), the
 // prefetch of the block's own spikes' tables and its queued deliveries, the
@@ -152,6 +158,14 @@ struct Dev {
     const uint4 *dcnt;             // [n_l2] u16 x 8: synapses of delay <= k + 1 in the segment
     unsigned long long arr_cap;
     int n_arr;                     // lists: the largest delay (list of step s: s mod n_arr)
+    // delivery into each partition's own input (k_owner): per internal
+    // partition q and arrival step s, the runs that arrive at q at step s
+    // (list s mod n_own of q)
+    unsigned long long *inb;       // records: offset << 24 | length
+    const ulonglong2 *inb_slot;    // [P] {first record of q's list 0, capacity of each of q's lists}
+    unsigned int *inb_cnt;         // [P * n_own * kPairStride] fill of each list
+    const long long *pbase;        // [P + 1] first internal neuron of each internal partition
+    int n_own;                     // lists per partition (the largest delay); 0: not available
     // scalars
     long long M;
     int P, n_vn, vn_size, D;
@@ -716,6 +730,41 @@ __device__ __forceinline__ void arrival_queue_warp(const Dev &d, const Stage &sg
     }
 }
 
+// Delivery into the partitions' own input: queue the runs of the segment of
+// synapses at o (delay counts dc) into destination partition q on q's
+// lists of their arrival steps (the run of delay d on list (t + d) mod
+// n_own; tmod = t mod n_own).
+__device__ __forceinline__ void owner_queue(const Dev &d, unsigned int q, unsigned long long o, uint4 dc, int tmod,
+                                            unsigned int &ovf)
+{
+    const ulonglong2 sl = d.inb_slot[q];
+    const uint32_t c[kMaxArr] = {dc.x & 0xFFFFu, dc.x >> 16, dc.y & 0xFFFFu, dc.y >> 16,
+                                 dc.z & 0xFFFFu, dc.z >> 16, dc.w & 0xFFFFu, dc.w >> 16};
+    unsigned int pos[kMaxArr];
+    // the reservations first, all in flight together, then the records
+#pragma unroll
+    for (int k = 0; k < kMaxArr; ++k) {
+        const uint32_t lo = k ? c[k - 1] : 0u;
+        pos[k] = 0xFFFFFFFFu;
+        if (k < d.n_own && c[k] > lo) {
+            int li = tmod + k + 1;
+            while (li >= d.n_own) li -= d.n_own;
+            pos[k] = atomicAdd(&d.inb_cnt[((size_t)q * d.n_own + li) * kPairStride], 1u);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kMaxArr; ++k) {
+        if (pos[k] == 0xFFFFFFFFu) continue;
+        const uint32_t lo = k ? c[k - 1] : 0u;
+        int li = tmod + k + 1;
+        while (li >= d.n_own) li -= d.n_own;
+        if (pos[k] < sl.y)
+            d.inb[sl.x + (unsigned long long)li * sl.y + pos[k]] = ((o + lo) << kLenBits) | (unsigned long long)(c[k] - lo);
+        else
+            ovf |= kStArrival;
+    }
+}
+
 // a4 + a5 for the nr <= kRound spikes at positions b0 .. b0+nr of the step's
 // list, by the threads [0, nthr) (whole warps): the level-1 and level-2
 // entries of all of them are numbered through and taken a thread each, so
@@ -727,7 +776,7 @@ __device__ __forceinline__ void arrival_queue_warp(const Dev &d, const Stage &sg
 // slot) the delay-1 head is staged for fix and the run of each delay
 // d >= 2 is queued for step t + d - 1 (t = the step, tmod = t mod n_arr).
 // Counters of step parity par.
-template <bool ARR>
+template <int RT>
 __device__ __forceinline__ Pending route_traverse(const Dev &d, int par, int tm, unsigned int b0, unsigned int nr,
                                                   const Stage &sg, int nthr, Deferred *df, int cur,
                                                   int32_t *fix = nullptr, int tmod = 0)
@@ -745,9 +794,9 @@ __device__ __forceinline__ Pending route_traverse(const Dev &d, int par, int tm,
     if (threadIdx.x == 0) {
         *sg.nl = 0;
         *sg.ns = 0;
-        if (ARR) *sg.an = 0;
+        if (RT == kRtArrival) *sg.an = 0;
     }
-    if (ARR && threadIdx.x < kMaxArr) sg.ak[threadIdx.x] = 0;
+    if (RT == kRtArrival && threadIdx.x < kMaxArr) sg.ak[threadIdx.x] = 0;
     sync_part(nthr);
     if (threadIdx.x < 32) {
         // inclusive scans of the counts (kRound <= 32: one warp)
@@ -792,7 +841,7 @@ __device__ __forceinline__ Pending route_traverse(const Dev &d, int par, int tm,
         // the segment this lane stages: the whole one, or its delay-1 head
         // with the rest on the deferred lists (df) or the arrival lists (ARR)
         unsigned long long so = 0;
-        unsigned int sn = 0, rest = 0;
+        unsigned int sn = 0, rest = 0, oq = 0xFFFFFFFFu;
         uint4 dc = make_uint4(0u, 0u, 0u, 0u);
         if (x < N1) {
             // a4: one level-1 entry per destination VN, appended to bucket (p, g)
@@ -820,10 +869,14 @@ __device__ __forceinline__ Pending route_traverse(const Dev &d, int par, int tm,
             pn.pval = (off << kLenBits) | (unsigned long long)l.len;
             pn.pk = 2;
             so = off;
-            if constexpr (ARR) {
+            if constexpr (RT == kRtArrival) {
                 dc = d.dcnt[f];         // runs by delay: synapses of delay <= k + 1
                 sn = dc.x & 0xFFFFu;    // the delay-1 head
                 pn.ev += l.len;         // events counted when routed
+            } else if constexpr (RT == kRtOwner) {
+                dc = d.dcnt[f];
+                oq = l.q;
+                pn.ev += l.len;
             } else if (!df) {
                 sn = l.len;
             } else {
@@ -836,7 +889,9 @@ __device__ __forceinline__ Pending route_traverse(const Dev &d, int par, int tm,
             cls[2] += l.cls == 2;
             cls[3] += l.cls == 3;
         }
-        if constexpr (ARR) {
+        if constexpr (RT == kRtOwner) {
+            if (oq != 0xFFFFFFFFu) owner_queue(d, oq, so, dc, tmod, pn.ovf);
+        } else if constexpr (RT == kRtArrival) {
             stage_run_warp(d, tm, fix, so, sn, sg.lng, sg.nl, kLongCap, sg.sht, sg.ns, kShortCap);
             const uint32_t c[kMaxArr] = {dc.x & 0xFFFFu, dc.x >> 16, dc.y & 0xFFFFu, dc.y >> 16,
                                          dc.z & 0xFFFFu, dc.z >> 16, dc.w & 0xFFFFu, dc.w >> 16};
@@ -868,15 +923,16 @@ __device__ __forceinline__ Pending route_traverse(const Dev &d, int par, int tm,
 // did not walk).  With delivery by arrival step (fix) the round's queued
 // runs go to their lists: one reservation per list, issued before the
 // delivery, the copy after it.
-template <bool ARR>
+template <int RT>
 __device__ __forceinline__ void route_finish(const Dev &d, int tm, int32_t *fix, const Stage &sg, Pending pn)
 {
-    if (ARR && threadIdx.x < (unsigned int)d.n_arr) {
+    if (RT == kRtArrival && threadIdx.x < (unsigned int)d.n_arr) {
         const unsigned int n = sg.ak[threadIdx.x];
         if (n) sg.abase[threadIdx.x] = atomicAdd(&d.arr_cnt[(size_t)threadIdx.x * kPairStride], n);
     }
-    deliver_staged(d, tm, fix, sg, min(*sg.nl, (unsigned int)kLongCap), min(*sg.ns, (unsigned int)kShortCap));
-    if constexpr (ARR) {
+    if constexpr (RT != kRtOwner)
+        deliver_staged(d, tm, fix, sg, min(*sg.nl, (unsigned int)kLongCap), min(*sg.ns, (unsigned int)kShortCap));
+    if constexpr (RT == kRtArrival) {
         __syncthreads();
         const unsigned int na = min(*sg.an, (unsigned int)kArrPool);
         for (unsigned int x = threadIdx.x; x < na; x += kThreads) {
@@ -1083,6 +1139,21 @@ __device__ __forceinline__ void pre_update(const Dev &d, long long t, const uint
     }
 }
 
+// The routing round's pool of queued runs (delivery by arrival step), in
+// the kernels that route with it; nothing in the others.
+template <bool ON>
+struct ArrivalPool {
+    unsigned long long rec[kArrPool];
+    unsigned short tag[kArrPool];
+    __device__ unsigned long long *r() { return rec; }
+    __device__ unsigned short *g() { return tag; }
+};
+template <>
+struct ArrivalPool<false> {
+    __device__ unsigned long long *r() { return nullptr; }
+    __device__ unsigned short *g() { return nullptr; }
+};
+
 // Shared-memory scratch of a block's step.
 struct StepShared {
     unsigned long long lng[kLongCap];
@@ -1105,8 +1176,8 @@ struct StepShared {
     long long headv;
     // delivery by arrival step: the routing round's queued runs (Stage), the
     // step's arrival list share of this block, restored ring slots
-    unsigned long long arec[kArrPool];
-    unsigned short atag[kArrPool];
+    unsigned long long *arec;   // -> the kernel's ArrivalPool (delivery by arrival step)
+    unsigned short *atag;
     unsigned int an, ak[kMaxArr];
     unsigned long long abase[kMaxArr];
     unsigned int arr_n;
@@ -1445,7 +1516,7 @@ __device__ __forceinline__ void update_step(const Dev &d, long long t, StepShare
 // Second half of step t (all threads call): a4-a6 for this block's share of
 // the step's spikes, an equal share of the list for every block, and their
 // raster copy.
-template <bool ARR>
+template <int RT>
 __device__ __forceinline__ void route_step(const Dev &d, long long t, StepShared &sh, bool carried = false,
                                            Deferred *df = nullptr, int cur = 0)
 {
@@ -1454,8 +1525,8 @@ __device__ __forceinline__ void route_step(const Dev &d, long long t, StepShared
     Ctrl *c = d.ctrl;
     // delivery by arrival step: everything this step delivers goes to the
     // next step's input slot
-    int32_t *fix = ARR ? d.acc + (size_t)((t + 1) & 1) * (size_t)d.M : nullptr;
-    const int tmod = ARR ? (int)(t % d.n_arr) : 0;
+    int32_t *fix = RT == kRtArrival ? d.acc + (size_t)((t + 1) & 1) * (size_t)d.M : nullptr;
+    const int tmod = RT == kRtArrival ? (int)(t % d.n_arr) : RT == kRtOwner ? (int)(t % d.n_own) : 0;
     if (threadIdx.x == 0) {
         if (carried) {
             // k_persist: the step's spike count from the barrier word (the sum
@@ -1498,14 +1569,14 @@ __device__ __forceinline__ void route_step(const Dev &d, long long t, StepShared
         Pending pn{0, 0u, make_ulonglong2(0ull, 0ull), 0ull, 0u, 0u};
         prof_stamp(sh, 5);
         if (!split || threadIdx.x < kTravWarps * 32)
-            pn = route_traverse<ARR>(d, par, tm, b, nr, sg, split ? kTravWarps * 32 : kThreads, df, cur, fix, tmod);
+            pn = route_traverse<RT>(d, par, tm, b, nr, sg, split ? kTravWarps * 32 : kThreads, df, cur, fix, tmod);
         else
             tally_add(sg, 0,
                       deliver_lists(d, tmp, nullptr, df->lng[prev], pl, df->sht[prev], ps, kTravWarps,
                                     kWarps - kTravWarps));
         __syncthreads();
         prof_stamp(sh, 4);
-        route_finish<ARR>(d, tm, fix, sg, pn);
+        route_finish<RT>(d, tm, fix, sg, pn);
         __syncthreads();
     }
     if (sh.head >= 0)
@@ -1553,6 +1624,8 @@ __global__ void __launch_bounds__(kThreads) k_update(const Dev d, int k)
         sh.t0 = *(volatile long long *)&d.ctrl->t;
         sh.inj_until = *(volatile long long *)&d.ctrl->inject_until;
         sh.prof_on = 0;
+        sh.arec = nullptr;
+        sh.atag = nullptr;
     }
     __syncthreads();
     const long long t = sh.t0 + k;
@@ -1568,13 +1641,16 @@ template <bool ARR>
 __global__ void __launch_bounds__(kThreads) k_route(const Dev d, int k)
 {
     __shared__ StepShared sh;
+    __shared__ ArrivalPool<ARR> pool;
     pdl_enter();
     if (threadIdx.x == 0) {
         sh.t0 = *(volatile long long *)&d.ctrl->t;
         sh.prof_on = 0;
+        sh.arec = pool.r();
+        sh.atag = pool.g();
     }
     __syncthreads();
-    route_step<ARR>(d, sh.t0 + k, sh);
+    route_step<ARR ? kRtArrival : kRtRing>(d, sh.t0 + k, sh);
 }
 
 __global__ void k_advance(const Dev d, int steps)
@@ -1600,21 +1676,23 @@ __global__ void k_advance(const Dev d, int steps)
 // block computes the next step's drive and leak (pre_update), which need no
 // other block's data.  DEFER: minimum-delay batching (Deferred); the last
 // step's delay >= 2 lists are delivered before the launch ends.
-// Blocks per SM the persistent kernel is built for: 3 with the neuron state in
-// shared memory (80 registers), 2 on global state (128 registers, room for
-// the update's batched loads).
-template <int MODE>
-constexpr int persist_min_blocks()
+// Blocks per SM the persistent kernel is built for (MINB): 3 with the neuron
+// state in shared memory (80 registers); on global state 2 (128 registers,
+// four quads' loads batched) or 3 (80 registers, two quads batched: more
+// warps per SM for the latency-bound halves).
+template <int MINB>
+__host__ __device__ constexpr int persist_quad_batch()
 {
-    return MODE == kModeSmem ? 3 : 2;
+    return MINB >= 3 ? 2 : 4;
 }
 
-template <int MODE, bool DEFER, bool ARR>
-__global__ void __launch_bounds__(kThreads, persist_min_blocks<MODE>()) k_persist(const Dev d, int T,
+template <int MODE, bool DEFER, bool ARR, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) k_persist(const Dev d, int T,
                                                                                    unsigned long long limit_ns,
                                                          int skip_arrival)
 {
     __shared__ StepShared sh;
+    __shared__ ArrivalPool<ARR> pool;
     __shared__ DeferSlot<DEFER> dslot;
     Deferred *df = dslot.get();
     __shared__ __align__(8) unsigned long long s_bar;
@@ -1645,6 +1723,8 @@ __global__ void __launch_bounds__(kThreads, persist_min_blocks<MODE>()) k_persis
         sh.inj_until = *(volatile long long *)&c->inject_until;
         sh.headv = *(volatile long long *)&c->head[slot3(sh.t0)];
         sh.prevS = 0u;
+        sh.arec = pool.r();
+        sh.atag = pool.g();
         if constexpr (DEFER) {
             df->nl[0] = df->nl[1] = 0u;
             df->ns[0] = df->ns[1] = 0u;
@@ -1674,7 +1754,7 @@ __global__ void __launch_bounds__(kThreads, persist_min_blocks<MODE>()) k_persis
             close_step(d, t - 1);
             closed = t - 1;
         }
-        update_step<MODE, ARR>(d, t, sh, rs, (uint32_t)(s & 1), limit_ns);
+        update_step<MODE, ARR, persist_quad_batch<MINB>()>(d, t, sh, rs, (uint32_t)(s & 1), limit_ns);
         ++issued;
         stamp(1);
         // the first barrier carries the block's spike count in the word's high half
@@ -1682,11 +1762,11 @@ __global__ void __launch_bounds__(kThreads, persist_min_blocks<MODE>()) k_persis
         prefetch_own(d, sh);
         // delivery by arrival step: the runs queued for this step, while the
         // barrier completes (they need no spike of this step)
-        if constexpr (ARR) arrival_share<MODE == kModeSmem ? 4 : 8>(d, t, sh);
+        if constexpr (ARR) arrival_share<(MODE == kModeSmem || MINB >= 3) ? 4 : 8>(d, t, sh);
         stamp(2);
         if (!grid_wait(c, 2ull * s, limit_ns, &sh.word)) break;
         stamp(3);
-        route_step<ARR>(d, t, sh, true, df, s & 1);
+        route_step<ARR ? kRtArrival : kRtRing>(d, t, sh, true, df, s & 1);
         stamp(5);
         // the next step's input-free update runs while the barrier completes
         grid_arrive(c);
@@ -1734,6 +1814,285 @@ __global__ void __launch_bounds__(kThreads, persist_min_blocks<MODE>()) k_persis
         if (t0 + done - 1 > closed) close_step(d, t0 + done - 1);
         c->t = t0 + done;
         if (prof)
+            for (int k = 0; k < kPhases; ++k) d.phase_ns[k] += sh.prof[k];
+    }
+}
+
+
+// ---------------------------------------------------------------- partition-owned delivery
+// Delivery into each partition's own input: at step t the block that owns
+// partition q adds the runs on q's list of step t (the runs of every delay
+// whose arrival step is t, queued by the routing of steps t - 8 .. t - 1)
+// into a shared-memory accumulator with shared-memory reductions, then runs
+// a1-a3 on q's neurons from it.  No global input slot, no global reductions:
+// each partition receives its messages and delivers them into its own
+// neurons, as each GPU of the paper's system does (Sec. I, Sec. IV.B).
+
+// Shared-memory reduction at p (a shared-memory address).
+__device__ __forceinline__ void red_shared_add(const int32_t *p, int32_t v)
+{
+    asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(smem_u32(p)), "r"(v) : "memory");
+}
+
+// The records recs[0, n) (offset << 24 | length) into acc[target - b0], all
+// warps of the block: a warp numbers the synapses of 32 runs through and
+// takes them U per lane with every load in flight (as deliver_records).
+template <int U>
+__device__ __forceinline__ void owner_deliver(const Dev &d, int32_t *acc, long long b0,
+                                              const unsigned long long *recs, unsigned long long n)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned long long step = (unsigned long long)kWarps * 32u;
+    unsigned long long b = (unsigned long long)wid * 32u;
+    unsigned long long rec = (b + lane < n) ? __ldcs(recs + b + lane) : 0ull;
+    for (; b < n; b += step) {
+        const unsigned long long nx = b + step + (unsigned long long)lane;
+        const unsigned long long rec_next = nx < n ? __ldcs(recs + nx) : 0ull;
+        const unsigned long long o = rec >> kLenBits;
+        const unsigned int len = (unsigned int)(rec & kLenMask);
+        unsigned int inc = len;
+#pragma unroll
+        for (int k = 1; k < 32; k <<= 1) {
+            const unsigned int y = __shfl_up_sync(0xFFFFFFFFu, inc, k);
+            if (lane >= k) inc += y;
+        }
+        const unsigned int ex = inc - len;
+        const unsigned int tot = __shfl_sync(0xFFFFFFFFu, inc, 31);
+        for (unsigned int base = 0; base < tot; base += 32u * U) {
+            uint32_t td[U];
+            int32_t w[U];
+#pragma unroll
+            for (int k = 0; k < U; ++k) {
+                const unsigned int y = base + (unsigned int)k * 32u + (unsigned int)lane;
+                int r = 0;
+#pragma unroll
+                for (int h = 16; h > 0; h >>= 1) {
+                    const unsigned int v = __shfl_sync(0xFFFFFFFFu, ex, r + h);
+                    if (v <= y) r += h;
+                }
+                const unsigned long long orr = __shfl_sync(0xFFFFFFFFu, o, r);
+                const unsigned int er = __shfl_sync(0xFFFFFFFFu, ex, r);
+                if (y < tot) {
+                    td[k] = __ldcs(d.syn_td + orr + (y - er));
+                    w[k] = __ldcs(d.syn_w + orr + (y - er));
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < U; ++k) {
+                const unsigned int y = base + (unsigned int)k * 32u + (unsigned int)lane;
+                if (y < tot) red_shared_add(acc + ((long long)(td[k] & kTgtMask) - b0), w[k]);
+            }
+        }
+        rec = rec_next;
+    }
+}
+
+// a1 + a2 of neuron j with recurrent input irec (scalar path of the owner's
+// partition ends); returns true on a spike.
+__device__ __forceinline__ bool owner_neuron(const Dev &d, const uint32_t *th, long long t, long long j, int32_t irec,
+                                             bool do_hash, unsigned long long &hc, unsigned long long &hv)
+{
+    float v = d.V[j];
+    uint32_t r = d.ref[j];
+    const uint32_t g = d.gid ? d.gid[j] : (uint32_t)j;
+    const Drive dr = drive_of(d, th, g);
+    const uint32_t u = uint4_word(philox4(dr.key0, dr.key1, (uint32_t)((g - dr.off) >> 2), (uint32_t)t), g & 3u);
+    const bool spk = lif_neuron(d, dr, u, irec, v, r);
+    if (do_hash) {
+        hc += mix64(((unsigned long long)g << 32) | (uint32_t)irec);
+        hv += mix64(((unsigned long long)g << 32) | __float_as_uint(v));
+    }
+    d.V[j] = v;
+    d.ref[j] = (uint8_t)r;
+    return spk;
+}
+
+// Phase A of step t for the partitions this block owns (q = blockIdx.x,
+// + gridDim.x, ...): the partition's queued runs of step t into the
+// shared accumulator acc, then a1-a3 on its neurons (all threads call).
+__device__ __forceinline__ void owner_update(const Dev &d, long long t, StepShared &sh, int32_t *acc)
+{
+    Ctrl *c = d.ctrl;
+    const int par = (int)(t & 1);
+    const int slot = (int)(t % d.D);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const bool do_hash = t < d.hash_steps;
+    const bool do_cur = d.cur_every > 0 && (t % d.cur_every) == 0 && (t / d.cur_every) < d.cur_slots;
+    int32_t *inj = t < sh.inj_until ? d.ring + (long long)slot * d.M : nullptr;
+    int32_t *cur = do_cur ? d.cur_rec + (t / d.cur_every) * d.M : nullptr;
+    const int li = (int)(t % d.n_own);
+    {
+        // clear the other parity of the exchange counters (used by step t - 1
+        // only) and the spike count of step t + 1
+        uint32_t *b1 = bucket_cnt_of(d, par ^ 1), *i1 = inbox_cnt_of(d, par ^ 1);
+        const int nb = d.n_bpair, ni = nb + d.n_ipair;
+        for (int x = blockIdx.x * kThreads + threadIdx.x; x < ni; x += gridDim.x * kThreads) {
+            if (x < nb) b1[(size_t)x * kPairStride] = 0;
+            else i1[(size_t)(x - nb) * kPairStride] = 0;
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) c->S_acc[slot3(t + 1)] = 0;
+    }
+    if (threadIdx.x < kPTab) sh.th[threadIdx.x] = d.th32[threadIdx.x];
+    if (threadIdx.x == 0) sh.n_own = 0u;
+    unsigned long long hc = 0, hv = 0;
+    for (int q = blockIdx.x; q < d.P; q += gridDim.x) {
+        const long long b0 = d.pbase[q], b1 = d.pbase[q + 1];
+        const int n = (int)(b1 - b0);
+        for (int x = threadIdx.x; x < n; x += kThreads) acc[x] = 0;
+        __syncthreads();
+        // the runs arriving at q at step t
+        const ulonglong2 sl = d.inb_slot[q];
+        unsigned int *cnt = &d.inb_cnt[((size_t)q * d.n_own + li) * kPairStride];
+        if (threadIdx.x == 0) sh.arr_n = min(*(volatile unsigned int *)cnt, (unsigned int)sl.y);
+        __syncthreads();
+        owner_deliver<8>(d, acc, b0, d.inb + sl.x + (unsigned long long)li * sl.y, sh.arr_n);
+        __syncthreads();
+        // the list is consumed: step t's routing refills it for step t + n_own
+        if (threadIdx.x == 0) *cnt = 0u;
+        prof_stamp(sh, 0);
+        // a1 + a2: quads of 4 aligned ids [qa, qb), the ends one by one
+        const long long qa = (b0 + 3) / 4, qb = b1 / 4;
+        const int nh = qa * 4 > b1 ? n : (int)(qa * 4 - b0);           // head neurons
+        const int nt = qb >= qa ? (int)(b1 - qb * 4) : 0;              // tail neurons
+        constexpr int NCH = 4, QB = 4;
+        const long long stride = kThreads;
+        uint32_t bx = 0;  // head / tail spikes of this thread (bit 0)
+        long long jx = -1;
+        if (threadIdx.x < nh + nt) {
+            jx = threadIdx.x < nh ? b0 + threadIdx.x : qb * 4 + (threadIdx.x - nh);
+            int32_t irec = acc[jx - b0];
+            if (inj) {
+                irec = (int32_t)((uint32_t)irec + (uint32_t)inj[jx]);
+                inj[jx] = 0;
+            }
+            if (cur) cur[jx] = irec;
+            if (owner_neuron(d, sh.th, t, jx, irec, do_hash, hc, hv)) {
+                bx = 1u;
+                prefetch_rows(d, jx, 1u);
+            }
+        }
+        bool first = true;
+        for (long long B = qa + threadIdx.x; first || B - threadIdx.x < qb; B += NCH * 8 * stride) {
+            // (block-uniform trip count; the head/tail word joins the first compaction)
+            uint32_t bw[NCH + 1];
+#pragma unroll
+            for (int k = 0; k <= NCH; ++k) bw[k] = 0u;
+            for (int cc = 0; cc < NCH; ++cc) {
+                for (int k0 = 0; k0 < 8; k0 += QB) {
+                    float4 v4[QB];
+                    uint32_t r4[QB];
+#pragma unroll
+                    for (int k = 0; k < QB; ++k) {
+                        const long long Q = B + (cc * 8 + k0 + k) * stride;
+                        if (Q < qb) {
+                            v4[k] = *reinterpret_cast<const float4 *>(d.V + Q * 4);
+                            r4[k] = *reinterpret_cast<const uint32_t *>(d.ref + Q * 4);
+                        }
+                    }
+#pragma unroll
+                    for (int k = 0; k < QB; ++k) {
+                        const long long Q = B + (cc * 8 + k0 + k) * stride;
+                        if (Q < qb) {
+                            const long long j0 = Q * 4;
+                            const int a = (int)(j0 - b0);
+                            int4 i4 = make_int4(acc[a], acc[a + 1], acc[a + 2], acc[a + 3]);
+                            if (inj) i4 = take_restored(inj + j0, i4);
+                            if (cur) *reinterpret_cast<int4 *>(cur + j0) = i4;
+                            float vv[4] = {v4[k].x, v4[k].y, v4[k].z, v4[k].w};
+                            const int32_t ii[4] = {i4.x, i4.y, i4.z, i4.w};
+                            const unsigned int m = update_quad(d, sh.th, t, j0, vv, ii, r4[k], do_hash, hc, hv);
+                            prefetch_rows(d, j0, m);
+                            bw[cc] |= m << (4 * (k0 + k));
+                            *reinterpret_cast<float4 *>(d.V + j0) = make_float4(vv[0], vv[1], vv[2], vv[3]);
+                            *reinterpret_cast<uint32_t *>(d.ref + j0) = r4[k];
+                        }
+                    }
+                }
+            }
+            if (first) bw[NCH] = bx;
+            const long long Bb = B - threadIdx.x;
+            const long long jxx = jx;
+            prof_stamp(sh, 0);
+            compact_spikes_multi<NCH + 1>(d, t, sh, bw, [&](int cc, int b) {
+                if (cc == NCH) return (uint32_t)jxx;
+                return (uint32_t)((Bb + threadIdx.x + (long long)cc * 8 * stride + (b >> 2) * stride) * 4 + (b & 3));
+            });
+            prof_stamp(sh, 1);
+            first = false;
+        }
+        __syncthreads();  // the accumulator is reused by the next partition
+    }
+    if (do_hash) {
+        hc = warp_sum(hc);
+        hv = warp_sum(hv);
+        if (lane == 0) {
+            sh.h[0][wid] = hc;
+            sh.h[1][wid] = hv;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long a = 0, b = 0;
+            for (int w = 0; w < kWarps; ++w) {
+                a += sh.h[0][w];
+                b += sh.h[1][w];
+            }
+            atomicAdd(&d.hash[2 * t], a);
+            atomicAdd(&d.hash[2 * t + 1], b);
+        }
+    }
+}
+
+// T steps in one cooperative launch with partition-owned delivery: phase A
+// (owner_update), grid barrier, the routing half (route_step<kRtOwner>),
+// grid barrier.  Bounded waits, closing of steps and the skip_arrival test
+// switch as in k_persist.  Dynamic shared memory: the accumulator of the
+// largest partition.
+__global__ void __launch_bounds__(kThreads, 2) k_owner(const Dev d, int T, unsigned long long limit_ns,
+                                                       int skip_arrival)
+{
+    __shared__ StepShared sh;
+    extern __shared__ __align__(16) int32_t s_acc[];
+    Ctrl *c = d.ctrl;
+    const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+    if (threadIdx.x == 0) {
+        sh.t0 = *(volatile long long *)&c->t;
+        sh.inj_until = *(volatile long long *)&c->inject_until;
+        sh.headv = *(volatile long long *)&c->head[slot3(sh.t0)];
+        sh.prevS = 0u;
+        sh.arec = nullptr;
+        sh.atag = nullptr;
+        sh.prof_on = (d.phase_ns != nullptr && lead) ? 1 : 0;
+        for (int k = 0; k <= kPhases; ++k) sh.prof[k] = 0;
+    }
+    __syncthreads();
+    const long long t0 = sh.t0;
+    int done = 0;
+    long long closed = t0 - 1;
+    for (int s = 0; s < T; ++s) {
+        const long long t = t0 + s;
+        prof_stamp(sh, -1);
+        if (s > 0 && lead) {
+            close_step(d, t - 1);
+            closed = t - 1;
+        }
+        owner_update(d, t, sh, s_acc);
+        prof_stamp(sh, 1);
+        grid_arrive(c, !(skip_arrival && s == 0 && blockIdx.x == 0), 1ull + ((unsigned long long)sh.n_own << 32));
+        prefetch_own(d, sh);
+        prof_stamp(sh, 2);
+        if (!grid_wait(c, 2ull * s, limit_ns, &sh.word)) break;
+        prof_stamp(sh, 3);
+        route_step<kRtOwner>(d, t, sh, true, nullptr, 0);
+        prof_stamp(sh, 5);
+        grid_arrive(c);
+        if (!grid_wait(c, 2ull * s + 1ull, limit_ns)) break;
+        prof_stamp(sh, 6);
+        ++done;
+    }
+    if (lead) {
+        if (t0 + done - 1 > closed) close_step(d, t0 + done - 1);
+        c->t = t0 + done;
+        if (sh.prof_on)
             for (int k = 0; k < kPhases; ++k) d.phase_ns[k] += sh.prof[k];
     }
 }

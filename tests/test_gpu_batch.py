@@ -22,13 +22,13 @@ def snn():
 
 
 @pytest.fixture(params=["persistent", "persistent-global", "graph", "persistent-deferred",
-                        "persistent-arrival", "persistent-global-arrival", "graph-arrival"])
+                        "persistent-arrival", "persistent-global-arrival", "graph-arrival", "persistent-owner"])
 def path(request, monkeypatch):
     p = request.param
     monkeypatch.setenv("SNN_PERSIST", "0" if p.startswith("graph") else "1")
     monkeypatch.setenv("SNN_PERSIST_SMEM", "0" if p.startswith("persistent-global") else "1")
     monkeypatch.setenv("SNN_PERSIST_DEFER", "1" if p == "persistent-deferred" else "0")
-    monkeypatch.setenv("SNN_DELIVERY", "1" if p.endswith("arrival") else "0")
+    monkeypatch.setenv("SNN_DELIVERY", "1" if p.endswith("arrival") else "3" if p.endswith("owner") else "0")
     return p
 
 

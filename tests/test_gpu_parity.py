@@ -83,7 +83,7 @@ def _compare(sim, o, T, rec, t0=0):
 
 
 @pytest.fixture(params=["persistent", "persistent-global", "graph", "persistent-deferred",
-                        "persistent-arrival", "persistent-global-arrival", "graph-arrival"])
+                        "persistent-arrival", "persistent-global-arrival", "graph-arrival", "persistent-owner"])
 def path(request, monkeypatch):
     """Run a test on the persistent kernel (neuron state resident in shared
     memory where it fits, or read from global memory every step; with
@@ -93,7 +93,7 @@ def path(request, monkeypatch):
     monkeypatch.setenv("SNN_PERSIST", "0" if p.startswith("graph") else "1")
     monkeypatch.setenv("SNN_PERSIST_SMEM", "0" if p.startswith("persistent-global") else "1")
     monkeypatch.setenv("SNN_PERSIST_DEFER", "1" if p == "persistent-deferred" else "0")
-    monkeypatch.setenv("SNN_DELIVERY", "1" if p.endswith("arrival") else "0")
+    monkeypatch.setenv("SNN_DELIVERY", "1" if p.endswith("arrival") else "3" if p.endswith("owner") else "0")
     return p
 
 
@@ -132,7 +132,18 @@ def test_locality_delays_several_tiles(snn, spg, path):
 
 
 def test_ragged_sizes_and_uneven_partitions(snn, path):
-    """M not a multiple of the block size, uneven greedy partitions, 3 VNs of 1."""
+    """M not a multiple of the block size, uneven greedy partitions, 3 VNs of 1
+    (partition-owned delivery needs M % 4 == 0 and reports SNN_E_RANGE)."""
+    if path == "persistent-owner":
+        cfg = synth.NetConfig(name="ragged", M=1007, P=3, n_vn=3, K=37, uniform_all=True, dmax=4, seed=99)
+        g = synth.make_network(cfg)
+        net = snn.Network.from_synth(g)
+        part, _ = snn.snn_partition(net, 3, "greedy", iters=3, seed=5)
+        rt = snn.Routing(net, part, 3, 3)
+        with pytest.raises(snn.SnnError) as e:
+            snn.Sim(net, rt, snn.sim_params(cfg.dyn), device="cuda:0")
+        assert e.value.code == -5
+        return
     cfg = synth.NetConfig(name="ragged", M=1000 + 7, P=3, n_vn=3, K=37, uniform_all=True, dmax=4,
                           seed=99, dyn=synth.Dynamics(drive_lambda=1.1, w_ext=120, drive_seed=9))
     g = synth.make_network(cfg)
@@ -279,7 +290,9 @@ def test_checkpoint_across_delivery_modes(snn, monkeypatch):
     net = snn.Network.from_synth(g)
     rt = snn.Routing(net, oracle.partition_planted(g.M, cfg.P), cfg.P, cfg.n_vn)
     for src_mode, dst_mode in ((snn.SNN_DELIVER_ARRIVAL, snn.SNN_DELIVER_RING),
-                               (snn.SNN_DELIVER_RING, snn.SNN_DELIVER_ARRIVAL)):
+                               (snn.SNN_DELIVER_RING, snn.SNN_DELIVER_ARRIVAL),
+                               (snn.SNN_DELIVER_ARRIVAL, snn.SNN_DELIVER_OWNER),
+                               (snn.SNN_DELIVER_OWNER, snn.SNN_DELIVER_RING)):
         a = snn.Sim(net, rt, snn.sim_params(cfg.dyn, hash_steps=400, delivery=src_mode), device="cuda:0")
         a.step(150)
         blob = a.save_state()
@@ -309,18 +322,18 @@ def test_arrival_list_overflow_is_reported(snn, monkeypatch):
     g = synth.make_network(cfg)
     net = snn.Network.from_synth(g)
     rt = snn.Routing(net, oracle.partition_planted(g.M, cfg.P), cfg.P, cfg.n_vn)
-    sim = snn.Sim(net, rt, snn.sim_params(cfg.dyn, delivery=snn.SNN_DELIVER_ARRIVAL, arrival_frac=1e-5),
-                  device="cuda:0")
-    sim.step(100)
-    assert sim.sync_status() == snn.SNN_E_CAPACITY
-    sim.close()
+    for mode in (snn.SNN_DELIVER_ARRIVAL, snn.SNN_DELIVER_OWNER):
+        sim = snn.Sim(net, rt, snn.sim_params(cfg.dyn, delivery=mode, arrival_frac=1e-5), device="cuda:0")
+        sim.step(100)
+        assert sim.sync_status() == snn.SNN_E_CAPACITY, mode
+        sim.close()
     sim = snn.Sim(net, rt, snn.sim_params(cfg.dyn, delivery=snn.SNN_DELIVER_ARRIVAL), device="cuda:0")
     sim.step(100)
     assert sim.sync_status() == 0
     assert sim.read_counts()["spikes"] > 0
 
 
-@pytest.mark.parametrize("delivery", [0, 1])
+@pytest.mark.parametrize("delivery", [0, 1, 3])
 def test_abi_built_model_against_oracle_reading_its_file(snn, tmp_path, monkeypatch, delivery):
     """The whole boundary: the network built behind the C ABI
     (snn_model_build), written as an edge-list file (snn_model_save) that the
