@@ -31,7 +31,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "synaptic events/s & sim steps/s vs HBM roofline; batched/adjoint vs plain"
-DELIVERY = {"ring": 0, "arrival": 1, "auto": 2}
+DELIVERY = {"ring": 0, "arrival": 1, "auto": 2, "owner": 3}
 UNIT = "synaptic events/s"
 
 
@@ -193,15 +193,16 @@ def run_ours(args):
                          pin_host_tables=1, defer_delayed=1 if args.defer else 0,
                          delivery=0 if args.defer else DELIVERY[args.delivery])
     sim = snn.Sim(net, rt, prm, device=dev)
+    # untimed pre-roll from rest into the steady state, the launch shape
+    # tuned there (every shape from the same state), warm-up, then EXACTLY K
+    # timed steps
+    sim.step(PR)
     choice, tuned_ms = sim.autotune(200)
     setup_s = time.time() - t_setup
-    print("[bench] setup %.1f s (generate + partition + routing + upload + autotune: shape %d, %.4f ms/step)"
-          % (setup_s, choice, tuned_ms), file=sys.stderr, flush=True)
+    print("[bench] setup %.1f s (generate + partition + routing + upload + pre-roll + autotune: shape %d, "
+          "%.4f ms/step)" % (setup_s, choice, tuned_ms), file=sys.stderr, flush=True)
     stream = sim.stream
-
-    # untimed pre-roll from rest into the steady state, warm-up, then EXACTLY
-    # K timed steps
-    sim.step(PR + W)
+    sim.step(W)
     if sim.sync_status() != 0:
         raise RuntimeError("device status after pre-roll and warm-up: %d" % sim.sync_status())
     c0 = sim.read_counts()
@@ -263,11 +264,12 @@ def run_ours(args):
     # the rate of the same reductions on random targets in an L2-sized
     # buffer (the input slots of delivery by arrival step, or the delay
     # ring), measured here
-    arrival = choice >= 1000
+    arrival = 1000 <= choice < 2000
     n_red = cfg.M * 2 if arrival else cfg.M * (info["max_delay"] + 1)
     red_peak = red_rate(n_red, 1 << 22)
     atom = {"what": "synaptic events (one 32-bit reduction each) per second over the whole step, vs torch "
-                    "index_add_ of 4M random int32 reductions into a buffer of the accumulators' size",
+                    "index_add_ of 4M random int32 reductions into a buffer of the accumulators' size"
+                    + (" (partition-owned delivery reduces in shared memory: context only)" if choice >= 2000 else ""),
             "buffer_mb": n_red * 4 / 1e6,
             "achieved": events_all / world / (ms_max * 1e-3), "peak": red_peak, "unit": "reductions/s",
             "frac": events_all / world / (ms_max * 1e-3) / red_peak}
@@ -326,7 +328,8 @@ def run_ours(args):
                    "delays": "1-%d" % cfg.dmax,
                    "drive_lambda_per_step": cfg.dyn.drive_lambda, "w_ext": cfg.dyn.w_ext,
                    "parallelism": "replicas x%d" % world,
-                   "step_window": {"preroll": PR, "warmup": W, "first_timed_step": first,
+                   "step_window": {"preroll": PR, "autotune_steps": "250 per shape from step %d, then restored" % PR,
+                                   "warmup": W, "first_timed_step": first,
                                    "last_timed_step": first + K - 1,
                                    "why": "untimed pre-roll from rest into the steady firing state"},
                    "l2": "inputs larger than L2: %.1f GB synapse CSR, the step's rows streamed from HBM"
@@ -334,10 +337,12 @@ def run_ours(args):
                    "steps_per_graph": 32,
                    "execution": ("persistent cooperative kernel" if persistent else "CUDA graphs")
                                 + (", minimum-delay batching" if args.defer else "")
-                                + (", delivery by arrival step" if choice >= 1000 else ", delay-ring delivery"),
-                   "autotune": {"choice": choice, "ms_per_step": tuned_ms,
-                                "meaning": "+1000 delivery by arrival step; 0 graph path, else 100*mode + blocks "
-                                           "per SM (mode 2 shared-memory state, 1 global 16-byte, 0 global scalar)"}},
+                                + (", partition-owned delivery" if choice >= 2000 else
+                                   ", delivery by arrival step" if choice >= 1000 else ", delay-ring delivery"),
+                   "autotune": {"choice": choice, "ms_per_step": tuned_ms, "at_step": PR,
+                                "meaning": "+1000 delivery by arrival step; 2000 + blocks per SM partition-owned "
+                                           "delivery; else 0 graph path, or 100*mode + blocks per SM (mode 2 "
+                                           "shared-memory state, 1 global 16-byte, 0 global scalar)"}},
         "spikes_per_step": spikes_all / world / K,
         "events_per_step": events_all / world / K,
         "rate_hz": spikes_all / world / K / cfg.M / (cfg.dyn.dt_ms * 1e-3),

@@ -560,15 +560,20 @@ int snn_sim_reset(snn_sim *sim, int32_t reupload);
  * (after steps/4 warm-up steps) of every shape this GPU can run -- the
  * persistent kernel with 4, 3, 2 or 1 blocks per SM and the neuron state in
  * shared memory, in global memory with 16-byte accesses or one neuron per
- * thread, and the CUDA-graph path -- each from the initial state, and keep
- * the fastest (shapes excluded by SNN_PERSIST=0 / SNN_PERSIST_SMEM=0 at
- * creation are not tried).  Every shape gives the same results bit for bit.  The
- * exchange capacities need no tuning: they are the exact worst case of the
- * routing tables.  Leaves the sim in its initial state (as snn_sim_reset
- * without re-upload); call it before stepping.  choice (may be NULL): 0 =
- * graph path, else 100 * mode + blocks per SM (mode 2 shared-memory state,
- * 1 global 16-byte, 0 global one neuron per thread); best_ms (may be NULL):
- * the chosen shape's time per step.  Synchronises the stream.
+ * thread, the CUDA-graph path, each with delivery into the delay ring and
+ * (workspace of SNN_DELIVER_AUTO) by arrival step, and the partition-owned
+ * kernel -- each from the sim's current state, and keep the fastest (shapes
+ * excluded by SNN_PERSIST=0 / SNN_PERSIST_SMEM=0 at creation are not
+ * tried).  Every shape gives the same results bit for bit.  The exchange
+ * capacities need no tuning: they are the exact worst case of the routing
+ * tables.  Leaves the sim in the state it had (records included), so it can
+ * be called after a pre-roll into the regime that is to be timed.
+ * choice (may be NULL): 0 = graph path, else 100 * mode + blocks per SM
+ * (mode 2 shared-memory state, 1 global 16-byte, 0 global one neuron per
+ * thread), + 1000 with delivery by arrival step; 2000 + blocks per SM for
+ * the partition-owned kernel; best_ms (may be NULL): the chosen shape's time
+ * per step.  Synchronises the stream.  Host memory: a copy of the neuron
+ * state and the delay ring.
  * Errors: SNN_E_ARG, SNN_E_CUDA.
  */
 int snn_autotune(snn_sim *sim, int32_t steps, int32_t *choice, double *best_ms);

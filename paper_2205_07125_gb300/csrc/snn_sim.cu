@@ -1046,6 +1046,11 @@ static int sim_create(const snn_network *net, const snn_routing *rt, const snn_s
     d.hash_steps = p->hash_steps;
     d.cur_every = p->cur_every;
     d.cur_slots = p->cur_slots;
+    {
+        // SNN_VEC_PIECES=1: staged pieces delivered with 16-byte / 8-byte loads
+        const char *e = std::getenv("SNN_VEC_PIECES");
+        d.vec_pieces = (e && e[0] == '1') ? 1 : 0;
+    }
     if (L.n_arr > 0 || L.n_own > 0) d.dcnt = (const uint4 *)(w + L.dcnt.off);
     if (L.n_own > 0) {
         d.inb = (unsigned long long *)(w + L.inb.off);
@@ -1222,6 +1227,67 @@ extern "C" int snn_profile_phases(snn_sim *s, int32_t T, double *phase_ms)
 // ---------------------------------------------------------------- launch-shape autotuner
 static int read_ctrl(snn_sim *s, Ctrl *c);
 
+// A copy of a sim's dynamic state (snn_autotune): neuron state, delay ring,
+// counters, tally rows, the hash slots from the current step on and the
+// control word, taken after the queued runs of delivery by arrival step or
+// by owner were moved into the ring (as a checkpoint does).  Restoring it
+// puts the sim back at that step with its records intact.
+struct Snapshot {
+    std::vector<char> v, ref, ring, counters, tally, hash;
+    Ctrl ctrl;
+    long long t = 0;
+};
+
+static int materialize_queued(snn_sim *s, long long t);
+
+static int snapshot_take(snn_sim *s, Snapshot &sn)
+{
+    const Layout &L = s->L;
+    Ctrl c;
+    int rc = read_ctrl(s, &c);
+    if (rc) return rc;
+    rc = materialize_queued(s, c.t);
+    if (rc) return rc;
+    rc = read_ctrl(s, &sn.ctrl);
+    if (rc) return rc;
+    sn.t = sn.ctrl.t;
+    // the ring now holds every pending input of steps t .. t + D - 1, which
+    // any delivery mode restored from the snapshot consumes
+    sn.ctrl.inject_until = sn.t + L.D;
+    auto take = [&](std::vector<char> &b, const Region &r, size_t off, size_t bytes) -> cudaError_t {
+        b.resize(bytes);
+        return bytes ? cudaMemcpy(b.data(), s->ws + r.off + off, bytes, cudaMemcpyDeviceToHost) : cudaSuccess;
+    };
+    CK(take(sn.v, L.V, 0, L.V.bytes));
+    CK(take(sn.ref, L.ref, 0, L.ref.bytes));
+    CK(take(sn.ring, L.ring, 0, L.ring.bytes));
+    CK(take(sn.counters, L.counters, 0, L.counters.bytes));
+    CK(take(sn.tally, L.tally, 0, L.tally.bytes));
+    const long long h0 = std::min<long long>(sn.t, s->prm.hash_steps);
+    CK(take(sn.hash, L.hash, (size_t)h0 * 16, (size_t)(s->prm.hash_steps - h0) * 16));
+    return SNN_OK;
+}
+
+static int snapshot_restore(snn_sim *s, const Snapshot &sn)
+{
+    const Layout &L = s->L;
+    char *w = s->ws;
+    CK(cudaStreamSynchronize(s->stream));
+    auto put = [&](const std::vector<char> &b, const Region &r, size_t off) -> cudaError_t {
+        return b.empty() ? cudaSuccess : cudaMemcpy(w + r.off + off, b.data(), b.size(), cudaMemcpyHostToDevice);
+    };
+    CK(put(sn.v, L.V, 0));
+    CK(put(sn.ref, L.ref, 0));
+    CK(put(sn.ring, L.ring, 0));
+    CK(put(sn.counters, L.counters, 0));
+    CK(put(sn.tally, L.tally, 0));
+    CK(put(sn.hash, L.hash, (size_t)std::min<long long>(sn.t, s->prm.hash_steps) * 16));
+    CK(cudaMemcpy(w + L.ctrl.off, &sn.ctrl, sizeof(Ctrl), cudaMemcpyHostToDevice));
+    for (const Region *r : {&L.acc, &L.arr_cnt, &L.inb_cnt, &L.bucket_cnt, &L.inbox_cnt})
+        if (r->bytes) CK(cudaMemset(w + r->off, 0, r->bytes));
+    return SNN_OK;
+}
+
 // Turn delivery by arrival step on or off (the workspace holds its regions);
 // captured graphs hold the old device view and are dropped.  The owner
 // kernel is chosen by shape_owner; any other shape turns it off.
@@ -1263,6 +1329,13 @@ extern "C" int snn_autotune(snn_sim *s, int32_t steps, int32_t *choice, double *
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     double best = 1e300;
+    // every shape starts from the sim's current state
+    Snapshot snap;
+    if (int r0 = snapshot_take(s, snap)) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return r0;
+    }
     Shape pick = {s->persist, s->pmode, s->persist_bps, s->arrival, s->owner};
     int rc = SNN_OK;
     for (const Shape &c : cand) {
@@ -1276,8 +1349,8 @@ extern "C" int snn_autotune(snn_sim *s, int32_t steps, int32_t *choice, double *
         } else {
             s->persist = false;
         }
-        // from the initial state: a quarter of the steps to warm up, then the timed steps
-        if ((rc = reset_state(s)) != SNN_OK) break;
+        // from the sim's state: a quarter of the steps to warm up, then the timed steps
+        if ((rc = snapshot_restore(s, snap)) != SNN_OK) break;
         if ((rc = snn_step(s, std::max(1, steps / 4))) != SNN_OK) break;
         if (cudaEventRecord(e0, s->stream) != cudaSuccess) { rc = SNN_E_CUDA; break; }
         if ((rc = snn_step(s, steps)) != SNN_OK) break;
@@ -1301,7 +1374,7 @@ extern "C" int snn_autotune(snn_sim *s, int32_t steps, int32_t *choice, double *
     set_arrival(s, pick.arrival);
     if (pick.owner) shape_owner(s, pick.b);
     else if (pick.persist) shape_persist(s, pick.mode, pick.b);
-    const int rr = reset_state(s);
+    const int rr = snapshot_restore(s, snap);
     if (rc == SNN_OK) rc = rr;
     if (choice)
         *choice = pick.owner ? 2000 + pick.b
@@ -1655,6 +1728,32 @@ struct CkptHeader {
 constexpr uint64_t kCkptMagic = 0x534E4E434B505431ULL;
 }  // namespace
 
+// Move the runs queued by delivery by arrival step or by owner, and the
+// input slot, into the delay ring (next step t), so that the ring and the
+// neuron state are the whole dynamic state; steps < t + D then consume the
+// ring slots (Ctrl::inject_until).  Nothing to do with ring delivery.
+static int materialize_queued(snn_sim *s, long long t)
+{
+    const Layout &L = s->L;
+    if (!s->arrival && !s->owner) return SNN_OK;
+    if (s->arrival) {
+        const unsigned g = (unsigned)std::max(1, s->sms * 4);
+        k_materialize<<<g, kThreads, 0, s->stream>>>(s->dev, t);
+        CK(cudaGetLastError());
+        CK(cudaMemsetAsync(s->ws + L.arr_cnt.off, 0, L.arr_cnt.bytes, s->stream));
+    } else {
+        const unsigned g = (unsigned)std::max(1, std::min(s->rt->P, s->sms * 4));
+        k_materialize_owner<<<g, kThreads, 0, s->stream>>>(s->dev, t);
+        CK(cudaGetLastError());
+        CK(cudaMemsetAsync(s->ws + L.inb_cnt.off, 0, L.inb_cnt.bytes, s->stream));
+    }
+    const long long until = t + L.D;
+    CK(cudaMemcpyAsync(s->ws + L.ctrl.off + offsetof(Ctrl, inject_until), &until, sizeof(until),
+                       cudaMemcpyHostToDevice, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return SNN_OK;
+}
+
 extern "C" int snn_state_bytes(snn_sim *s, size_t *bytes)
 {
     if (!s || !bytes) return SNN_E_ARG;
@@ -1671,28 +1770,8 @@ extern "C" int snn_save_state(snn_sim *s, void *buf, size_t capb)
     int rc = read_ctrl(s, &c);
     if (rc) return rc;
     const Layout &L = s->L;
-    if (s->arrival) {
-        // delivery by arrival step: the input slot and the queued runs move
-        // into the delay ring the checkpoint holds (the sim goes on unchanged)
-        const unsigned g = (unsigned)std::max(1, s->sms * 4);
-        k_materialize<<<g, kThreads, 0, s->stream>>>(s->dev, (long long)c.t);
-        CK(cudaGetLastError());
-        CK(cudaMemsetAsync(s->ws + L.arr_cnt.off, 0, L.arr_cnt.bytes, s->stream));
-        const long long until = c.t + L.D;
-        CK(cudaMemcpyAsync(s->ws + L.ctrl.off + offsetof(Ctrl, inject_until), &until, sizeof(until),
-                           cudaMemcpyHostToDevice, s->stream));
-        CK(cudaStreamSynchronize(s->stream));
-    } else if (s->owner) {
-        // partition-owned delivery: the queued runs move into the delay ring
-        const unsigned g = (unsigned)std::max(1, std::min(s->rt->P, s->sms * 4));
-        k_materialize_owner<<<g, kThreads, 0, s->stream>>>(s->dev, (long long)c.t);
-        CK(cudaGetLastError());
-        CK(cudaMemsetAsync(s->ws + L.inb_cnt.off, 0, L.inb_cnt.bytes, s->stream));
-        const long long until = c.t + L.D;
-        CK(cudaMemcpyAsync(s->ws + L.ctrl.off + offsetof(Ctrl, inject_until), &until, sizeof(until),
-                           cudaMemcpyHostToDevice, s->stream));
-        CK(cudaStreamSynchronize(s->stream));
-    }
+    rc = materialize_queued(s, (long long)c.t);
+    if (rc) return rc;
     char *b = (char *)buf;
     CkptHeader h{kCkptMagic, s->rt->M, L.D, 0, c.t};
     std::memcpy(b, &h, sizeof(h));

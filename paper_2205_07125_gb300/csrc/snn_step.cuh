@@ -166,6 +166,7 @@ struct Dev {
     unsigned int *inb_cnt;         // [P * n_own * kPairStride] fill of each list
     const long long *pbase;        // [P + 1] first internal neuron of each internal partition
     int n_own;                     // lists per partition (the largest delay); 0: not available
+    int vec_pieces;                // deliver staged pieces with 16-byte / 8-byte loads
     // scalars
     long long M;
     int P, n_vn, vn_size, D;
@@ -533,7 +534,40 @@ __device__ __forceinline__ unsigned int deliver_lists(const Dev &d, int tm, int3
     unsigned int ev = 0;
     const unsigned int units = nl + (ns + 31u) / 32u;
     for (unsigned int u = (unsigned int)wid; u < units; u += (unsigned int)nwarp) {
-        if (u < nl) {
+        if (u < nl && d.vec_pieces) {
+            // the piece as 16-byte target words and 8-byte weight words: lane
+            // l takes synapses a + 4l .. a + 4l + 3 of the 4-aligned window
+            // a = o & ~3 (and lane 0 the window's last four when the piece
+            // runs past it), synapses outside [o, o + n) masked
+            const unsigned long long e = lng[u];
+            const unsigned long long o = e >> 8;
+            const unsigned int n = (unsigned int)(e & 0xFFu);
+            const unsigned long long a = o & ~3ull, end = o + n;
+            const unsigned long long x0 = a + 4ull * (unsigned long long)lane;
+            uint4 tv = make_uint4(0u, 0u, 0u, 0u), tx = tv;
+            uint2 wv = make_uint2(0u, 0u), wx = wv;
+            if (x0 < end) {
+                tv = __ldcs(reinterpret_cast<const uint4 *>(d.syn_td + x0));
+                wv = __ldcs(reinterpret_cast<const uint2 *>(d.syn_w + x0));
+            }
+            const bool extra = lane == 0 && a + 128ull < end;
+            if (extra) {
+                tx = __ldcs(reinterpret_cast<const uint4 *>(d.syn_td + a + 128ull));
+                wx = __ldcs(reinterpret_cast<const uint2 *>(d.syn_w + a + 128ull));
+            }
+            const uint32_t tds[8] = {tv.x, tv.y, tv.z, tv.w, tx.x, tx.y, tx.z, tx.w};
+            const uint32_t wws[4] = {wv.x, wv.y, wx.x, wx.y};
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const unsigned long long x = (k < 4 ? x0 : a + 128ull) + (unsigned long long)(k & 3);
+                if ((k < 4 || extra) && x >= o && x < end) {
+                    const uint32_t ww = wws[k >> 1];
+                    const int32_t w = (int32_t)(int16_t)(uint16_t)((k & 1) ? (ww >> 16) : (ww & 0xFFFFu));
+                    atomicAdd(syn_dst(d, tm, fix, tds[k]), w);
+                }
+            }
+            if (lane == 0) ev += n;
+        } else if (u < nl) {
             const unsigned long long e = lng[u];
             const unsigned long long o = e >> 8;
             const unsigned int n = (unsigned int)(e & 0xFFu);

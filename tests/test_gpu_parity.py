@@ -279,6 +279,22 @@ def test_autotune_keeps_results(snn):
     assert sim.sync_status() == 0
 
 
+def test_autotune_mid_run_keeps_state_and_records(snn, monkeypatch):
+    """The autotuner called after 120 steps times every shape (ring, arrival,
+    owner, graph) from that state and leaves the sim there with its records:
+    the 260 steps (120 before, 140 after) are the oracle's run."""
+    monkeypatch.delenv("SNN_DELIVERY", raising=False)
+    cfg = synth.SCALE.scaled(M=16384, P=16, n_vn=4, K=200, n_part=140, n_vn_t=40, n_remote=20, seed=29)
+    g = synth.make_network(cfg)
+    sim, o, rec, _ = _run_pair(snn, g, cfg, 260, cfg.P, cfg.n_vn, cur_every=20, delivery=snn.SNN_DELIVER_AUTO)
+    sim.step(120)
+    choice, ms = sim.autotune(30)
+    assert ms > 0
+    sim.step(140)
+    assert sim.sync_status() == 0
+    _compare(sim, o, 260, rec)
+
+
 def test_checkpoint_across_delivery_modes(snn, monkeypatch):
     """A checkpoint holds the delay-ring form of the state whatever the
     delivery: saved under delivery by arrival step (queued runs and the input
