@@ -197,7 +197,10 @@ def run_ours(args):
     # tuned there (every shape from the same state), warm-up, then EXACTLY K
     # timed steps
     sim.step(PR)
-    choice, tuned_ms = sim.autotune(200)
+    if args.no_autotune:
+        choice, tuned_ms = -1, -1.0
+    else:
+        choice, tuned_ms = sim.autotune(200)
     setup_s = time.time() - t_setup
     print("[bench] setup %.1f s (generate + partition + routing + upload + pre-roll + autotune: shape %d, "
           "%.4f ms/step)" % (setup_s, choice, tuned_ms), file=sys.stderr, flush=True)
@@ -442,9 +445,10 @@ def kernel_source_sha() -> str:
 def load_traffic(kernel: str, events_per_step: float, M: int):
     """DRAM bytes per step of `kernel` from the committed ncu summary, if it
     was taken on the current kernel source (else null).  The capture runs a
-    smaller network of the same recipe; the neuron state stays on chip, so
-    the traffic is the synapse and routing-table reads of the step's spikes:
-    it is scaled by the synaptic events per step."""
+    smaller network of the same recipe, scaled to this one by the entry's
+    unit: synaptic events per step (the neuron state on chip, the traffic is
+    the synapse and routing-table reads of the step's spikes), or neurons
+    (where two capture sizes agree per neuron-step and not per event)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
@@ -454,6 +458,8 @@ def load_traffic(kernel: str, events_per_step: float, M: int):
     ent = t.get("%s@%d" % (kernel, M)) or t.get(kernel)
     if not ent or ent.get("source_sha") != kernel_source_sha():
         return None
+    if ent.get("scale_by") == "neurons":
+        return ent["dram_bytes_per_step"] * M / ent["neurons"]
     return ent["dram_bytes_per_step"] * events_per_step / ent["events_per_step"]
 
 
@@ -1055,6 +1061,8 @@ def main(argv=None):
     ap.add_argument("--neurons", type=int, default=0,
                     help="network size with the workload's per-neuron statistics (profiling cases)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the sim's default launch shape (profiling one shape; SNN_PERSIST_* select it)")
     ap.add_argument("--e2e-steps", type=int, default=10000,
                     help="steps of the end-to-end leg (tables uploaded once, then the steps from rest)")
     ap.add_argument("--no-forms", action="store_true",
