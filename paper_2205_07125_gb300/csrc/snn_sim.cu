@@ -1050,6 +1050,10 @@ static int sim_create(const snn_network *net, const snn_routing *rt, const snn_s
         // SNN_VEC_PIECES=1: staged pieces delivered with 16-byte / 8-byte loads
         const char *e = std::getenv("SNN_VEC_PIECES");
         d.vec_pieces = (e && e[0] == '1') ? 1 : 0;
+        // SNN_BAR_GROUPS=G (2..16): two-level grid-barrier arrival over G groups
+        const char *eb = std::getenv("SNN_BAR_GROUPS");
+        const int g = eb ? std::atoi(eb) : 0;
+        d.bar_groups = (g > 1) ? std::min(g, kBarGroups) : 0;
     }
     if (L.n_arr > 0 || L.n_own > 0) d.dcnt = (const uint4 *)(w + L.dcnt.off);
     if (L.n_own > 0) {
@@ -1128,7 +1132,8 @@ static int launch_persist(snn_sim *s, int32_t T, const Dev &d)
         s->test_skip_arrival = 0;  // once: the test checks the first launch's status
         void *args[] = {(void *)&d, (void *)&tt, (void *)&lim, (void *)&skip};
         // the grid barrier counts arrivals from zero in every launch
-        CK(cudaMemsetAsync(s->ws + s->L.ctrl.off + offsetof(Ctrl, bar), 0, sizeof(unsigned long long), s->stream));
+        CK(cudaMemsetAsync(s->ws + s->L.ctrl.off + offsetof(Ctrl, bar), 0, sizeof(Ctrl) - offsetof(Ctrl, bar),
+                           s->stream));
         CK(cudaLaunchCooperativeKernel(fn, dim3(s->grid_persist), dim3(kThreads), args, smem, s->stream));
         T -= tt;
     }

@@ -85,6 +85,8 @@ constexpr int kPhases = 7;
 enum { C_STEPS = 0, C_SPIKES, C_EVENTS, C_L1_LOCAL, C_L1_XVN, C_L2_BASE /* + cls (4) */, C_N = 16 };
 constexpr int kTally = 7;  // slots C_EVENTS .. C_L2_BASE + 3, consecutive
 
+constexpr int kBarGroups = 16;  // groups of the two-level grid-barrier arrival
+
 struct Ctrl {
     long long t;              // next step to run
     long long head[3];        // raster write head of step t at slot t mod 3 (-1: recording stopped)
@@ -95,6 +97,12 @@ struct Ctrl {
     int pad;
     alignas(128) unsigned int S_acc[3];   // spikes of step t at slot t mod 3
     alignas(128) unsigned long long bar;  // grid-barrier arrivals of the running k_persist launch
+    // two-level arrival (Dev::bar_groups > 1): the blocks b = g mod G arrive
+    // on grp[g].arr; the last of them forwards one arrival to bar (fwd: the
+    // group's spike count forwarded so far).  Zeroed with bar.
+    struct alignas(128) BarGroup {
+        unsigned long long arr, fwd;
+    } grp[kBarGroups];
 };
 
 // Drive of one network of a batch (independent networks stepped together);
@@ -167,6 +175,7 @@ struct Dev {
     const long long *pbase;        // [P + 1] first internal neuron of each internal partition
     int n_own;                     // lists per partition (the largest delay); 0: not available
     int vec_pieces;                // deliver staged pieces with 16-byte / 8-byte loads
+    int bar_groups;                // > 1: two-level grid-barrier arrival over this many groups
     // scalars
     long long M;
     int P, n_vn, vn_size, D;
@@ -287,6 +296,13 @@ __device__ __forceinline__ void red_release(unsigned long long *p, unsigned long
     asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(x) : "memory");
 }
 
+__device__ __forceinline__ unsigned long long atom_add_acq_rel(unsigned long long *p, unsigned long long x)
+{
+    unsigned long long old;
+    asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(x) : "memory");
+    return old;
+}
+
 // Programmatic dependent launch (graph path): wait for the grid before this
 // one (all of its writes visible) before touching shared state, and let the
 // next grid be scheduled early.  Both are no-ops for a plain launch.
@@ -309,19 +325,44 @@ __device__ __forceinline__ void pdl_enter()
 // The barrier in two halves: grid_arrive (block-wide barrier, then the
 // release add) and grid_wait (the bounded acquire wait, then a block-wide
 // barrier); work between them must not depend on other blocks.
-__device__ __forceinline__ void grid_arrive(Ctrl *c, bool arrive = true, unsigned long long add = 1ull)
+// Two-level arrival (groups G > 1, G <= gridDim.x): block b arrives on
+// the word of group g = b mod G with an acquire-release add; the block that
+// completes its group's barrier k (its group's arrivals reach (k + 1) n_g)
+// forwards one arrival and the group's spike count since its last forward
+// to Ctrl::bar with a release add.  Barrier k is then complete when bar's
+// arrivals reach (k + 1) G.  The acquire-release chain makes every write of
+// the group's blocks visible to whoever acquires bar.
+__device__ __forceinline__ void grid_arrive(Ctrl *c, unsigned long long k, int groups, bool arrive = true,
+                                            unsigned long long add = 1ull)
 {
     __syncthreads();
-    if (threadIdx.x == 0 && arrive) red_release(&c->bar, add);
+    groups = min(groups, (int)gridDim.x);
+    if (threadIdx.x == 0 && arrive) {
+        if (groups <= 1) {
+            red_release(&c->bar, add);
+        } else {
+            const unsigned int g = blockIdx.x % (unsigned int)groups;
+            const unsigned int n_g = (gridDim.x - g + (unsigned int)groups - 1u) / (unsigned int)groups;
+            Ctrl::BarGroup *gr = &c->grp[g];
+            const unsigned long long old = atom_add_acq_rel(&gr->arr, add);
+            if ((unsigned int)old + 1u == (unsigned int)((k + 1ull) * n_g)) {
+                const unsigned long long cum = (old >> 32) + (add >> 32);
+                const unsigned long long fw = *(volatile unsigned long long *)&gr->fwd;
+                *(volatile unsigned long long *)&gr->fwd = cum;
+                red_release(&c->bar, 1ull + ((cum - fw) << 32));
+            }
+        }
+    }
 }
 
-__device__ __forceinline__ bool grid_wait(Ctrl *c, unsigned long long k, unsigned long long limit_ns,
+__device__ __forceinline__ bool grid_wait(Ctrl *c, unsigned long long k, int groups, unsigned long long limit_ns,
                                           unsigned long long *word = nullptr)
 {
     __shared__ int s_ok;
+    groups = min(groups, (int)gridDim.x);
     if (threadIdx.x == 0) {
         int ok = 1;
-        const unsigned long long target = (k + 1ull) * gridDim.x;
+        const unsigned long long target = (k + 1ull) * (groups > 1 ? (unsigned long long)groups : gridDim.x);
         const unsigned long long deadline = global_ns() + limit_ns;
         unsigned int spins = 0;
         unsigned long long v;
@@ -346,12 +387,6 @@ __device__ __forceinline__ bool grid_wait(Ctrl *c, unsigned long long k, unsigne
     return s_ok != 0;
 }
 
-__device__ __forceinline__ bool grid_sync(Ctrl *c, unsigned long long k, unsigned long long limit_ns,
-                                          bool arrive = true)
-{
-    grid_arrive(c, arrive);
-    return grid_wait(c, k, limit_ns);
-}
 
 // Drive of a neuron: the Poisson thresholds (the first four as values, the
 // rest behind a pointer: shared memory for a single network, the batch table
@@ -1792,22 +1827,23 @@ __global__ void __launch_bounds__(kThreads, MINB) k_persist(const Dev d, int T,
         ++issued;
         stamp(1);
         // the first barrier carries the block's spike count in the word's high half
-        grid_arrive(c, !(skip_arrival && s == 0 && blockIdx.x == 0), 1ull + ((unsigned long long)sh.n_own << 32));
+        grid_arrive(c, 2ull * s, d.bar_groups, !(skip_arrival && s == 0 && blockIdx.x == 0),
+                    1ull + ((unsigned long long)sh.n_own << 32));
         prefetch_own(d, sh);
         // delivery by arrival step: the runs queued for this step, while the
         // barrier completes (they need no spike of this step)
         if constexpr (ARR) arrival_share<(MODE == kModeSmem || MINB >= 3) ? 4 : 8>(d, t, sh);
         stamp(2);
-        if (!grid_wait(c, 2ull * s, limit_ns, &sh.word)) break;
+        if (!grid_wait(c, 2ull * s, d.bar_groups, limit_ns, &sh.word)) break;
         stamp(3);
         route_step<ARR ? kRtArrival : kRtRing>(d, t, sh, true, df, s & 1);
         stamp(5);
         // the next step's input-free update runs while the barrier completes
-        grid_arrive(c);
+        grid_arrive(c, 2ull * s + 1ull, d.bar_groups);
         if constexpr (MODE == kModeSmem) {
             if (s + 1 < T) pre_update(d, t + 1, sh.th, rs);
         }
-        if (!grid_wait(c, 2ull * s + 1ull, limit_ns)) break;
+        if (!grid_wait(c, 2ull * s + 1ull, d.bar_groups, limit_ns)) break;
         stamp(6);
         ++done;
     }
@@ -2111,15 +2147,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_owner(const Dev d, int T, unsig
         }
         owner_update(d, t, sh, s_acc);
         prof_stamp(sh, 1);
-        grid_arrive(c, !(skip_arrival && s == 0 && blockIdx.x == 0), 1ull + ((unsigned long long)sh.n_own << 32));
+        grid_arrive(c, 2ull * s, d.bar_groups, !(skip_arrival && s == 0 && blockIdx.x == 0),
+                    1ull + ((unsigned long long)sh.n_own << 32));
         prefetch_own(d, sh);
         prof_stamp(sh, 2);
-        if (!grid_wait(c, 2ull * s, limit_ns, &sh.word)) break;
+        if (!grid_wait(c, 2ull * s, d.bar_groups, limit_ns, &sh.word)) break;
         prof_stamp(sh, 3);
         route_step<kRtOwner>(d, t, sh, true, nullptr, 0);
         prof_stamp(sh, 5);
-        grid_arrive(c);
-        if (!grid_wait(c, 2ull * s + 1ull, limit_ns)) break;
+        grid_arrive(c, 2ull * s + 1ull, d.bar_groups);
+        if (!grid_wait(c, 2ull * s + 1ull, d.bar_groups, limit_ns)) break;
         prof_stamp(sh, 6);
         ++done;
     }

@@ -265,6 +265,32 @@ def test_barrier_wait_is_bounded(snn, monkeypatch):
     assert t == 20
 
 
+@pytest.mark.parametrize("groups", [4, 16])
+def test_two_level_barrier_bit_exact(snn, monkeypatch, groups):
+    """The two-level grid-barrier arrival (blocks arrive on group words, the
+    last of a group forwards one arrival and the group's spike count) gives
+    the oracle's spikes, currents and counts on every persistent shape, and a
+    block that never arrives still ends in a reported timeout."""
+    monkeypatch.setenv("SNN_PERSIST", "1")
+    monkeypatch.setenv("SNN_BAR_GROUPS", str(groups))
+    cfg = synth.SCALE.scaled(M=1 << 16, seed=43)
+    g = synth.make_network(cfg)
+    for smem in ("1", "0"):
+        monkeypatch.setenv("SNN_PERSIST_SMEM", smem)
+        sim, o, rec, _ = _run_pair(snn, g, cfg, 120, cfg.P, cfg.n_vn)
+        if sim.launches(10) != 1:
+            pytest.skip("no cooperative launch on this device")
+        sim.step(120)
+        _compare(sim, o, 120, rec)
+    monkeypatch.setenv("SNN_BARRIER_LIMIT_NS", "20000000")  # 20 ms
+    monkeypatch.setenv("SNN_TEST_SKIP_BARRIER", "1")
+    net = snn.Network.from_synth(synth.make_network(synth.TINY))
+    rt = snn.Routing(net, oracle.partition_planted(synth.TINY.M, 4), 4, 2)
+    sim = snn.Sim(net, rt, snn.sim_params(synth.TINY.dyn), device="cuda:0")
+    sim.step(50)
+    assert sim.sync_status() == -8  # SNN_E_TIMEOUT
+
+
 def test_autotune_keeps_results(snn):
     """The autotuner tries every launch shape from the initial state, keeps the
     fastest and leaves the sim in its initial state: the run after it is the
