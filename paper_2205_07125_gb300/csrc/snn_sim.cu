@@ -117,11 +117,19 @@ __global__ void __launch_bounds__(kThreads) k_delay_counts(const DevL2 *l2, cons
          f += (long long)gridDim.x * kThreads) {
         const DevL2 l = l2[f];
         const unsigned long long o = l.off & kOffMask;
-        uint32_t c[kMaxArr] = {0, 0, 0, 0, 0, 0, 0, 0};
-        for (uint32_t k = 0; k < l.len; ++k) {
-            const uint32_t dl = syn_td[o + k] >> kTgtBits;
+        // a segment is sorted by (delay, target): the count of delay <= x + 1
+        // is where the delay first exceeds it (a binary search per delay, so
+        // that the long own-partition segments do not hold up their warps)
+        uint32_t c[kMaxArr];
 #pragma unroll
-            for (int x = 0; x < kMaxArr; ++x) c[x] += dl <= (uint32_t)x;
+        for (int x = 0; x < kMaxArr; ++x) {
+            uint32_t lo = 0, hi = l.len;
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if ((syn_td[o + mid] >> kTgtBits) <= (uint32_t)x) lo = mid + 1;
+                else hi = mid;
+            }
+            c[x] = lo;
         }
         dcnt[f] = make_uint4(c[0] | (c[1] << 16), c[2] | (c[3] << 16), c[4] | (c[5] << 16), c[6] | (c[7] << 16));
     }
@@ -529,6 +537,7 @@ struct snn_sim {
     // microseconds; past this the kernel records a timeout and returns
     unsigned long long barrier_limit_ns = 1000000000ull;
     int test_skip_arrival = 0;  // tests of the bounded wait (SNN_TEST_SKIP_BARRIER)
+    std::vector<uint2> row_h;   // the uploaded per-neuron rows (host copy, kept for re-uploads)
     std::vector<void *> pinned;
     // batches: the network of each quad and each network's drive (host copies)
     std::vector<uint16_t> net_of_h;
@@ -595,10 +604,14 @@ static int upload_tables(snn_sim *s)
     }
     CK(up(L.l1_pair, rt->l1_pair.data()));
     {
-        // first level-1 and level-2 entry of each neuron, read together
-        std::vector<uint2> row((size_t)rt->M + 1);
-        for (int64_t i = 0; i <= rt->M; ++i) row[i] = make_uint2(rt->l1_ptr[i], rt->l1_l2[rt->l1_ptr[i]]);
-        CK(cudaMemcpy(w + L.row.off, row.data(), L.row.bytes, cudaMemcpyHostToDevice));
+        // first level-1 and level-2 entry of each neuron, read together (built
+        // once per sim)
+        if (s->row_h.size() != (size_t)rt->M + 1) {
+            s->row_h.resize((size_t)rt->M + 1);
+            for (int64_t i = 0; i <= rt->M; ++i)
+                s->row_h[i] = make_uint2(rt->l1_ptr[i], rt->l1_l2[rt->l1_ptr[i]]);
+        }
+        CK(cudaMemcpyAsync(w + L.row.off, s->row_h.data(), L.row.bytes, cudaMemcpyHostToDevice, st));
     }
     CK(up(L.l2_pair, rt->l2_pair.data()));
     CK(up(L.csr, rt->csr.data()));
@@ -989,6 +1002,12 @@ static int sim_create(const snn_network *net, const snn_routing *rt, const snn_s
         pin(rt->syn_td.data(), s->L.syn_td.bytes);
         pin(rt->syn_w.data(), s->L.syn_w.bytes);
         pin(rt->l2.data(), s->L.l2.bytes);
+        pin(rt->l2_pair.data(), s->L.l2_pair.bytes);
+        pin(rt->l1_vn.data(), s->L.l1_vn.bytes);
+        pin(rt->l1_l2.data(), s->L.l1_l2.bytes);
+        pin(rt->l1_pair.data(), s->L.l1_pair.bytes);
+        pin(rt->l1_ptr.data(), s->L.l1_ptr.bytes);
+        pin(rt->csr.data(), s->L.csr.bytes);
     }
     // device view
     const Layout &L = s->L;
@@ -1560,6 +1579,48 @@ extern "C" int snn_sync_status(snn_sim *s)
     return SNN_OK;
 }
 
+// Raster read-back: the spikes of step t0 + b (spk[off[b] .. off[b+1]),
+// internal ids in the order the blocks reserved them) sorted in place by
+// global id (gid; nullptr: the same), one block per step, a bitonic sort in
+// shared memory of (global id << 32 | internal id).  Steps with more than
+// cap spikes are left to the host.  Sorting again gives the same order.
+__global__ void __launch_bounds__(1024) k_raster_sort(uint32_t *spk, const long long *off, const uint32_t *gid,
+                                                      int cap)
+{
+    extern __shared__ unsigned long long keys[];
+    const long long a = off[blockIdx.x], b = off[blockIdx.x + 1];
+    const int n = (int)(b - a);
+    if (n <= 1 || n > cap) return;
+    int m = 1;
+    while (m < n) m <<= 1;
+    for (int x = threadIdx.x; x < m; x += blockDim.x) {
+        if (x < n) {
+            const uint32_t i = spk[a + x];
+            keys[x] = ((unsigned long long)(gid ? gid[i] : i) << 32) | i;
+        } else {
+            keys[x] = ~0ull;
+        }
+    }
+    __syncthreads();
+    for (int k = 2; k <= m; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int x = threadIdx.x; x < m; x += blockDim.x) {
+                const int y = x ^ j;
+                if (y > x) {
+                    const unsigned long long u = keys[x], v = keys[y];
+                    const bool up = (x & k) == 0;
+                    if ((u > v) == up) {
+                        keys[x] = v;
+                        keys[y] = u;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int x = threadIdx.x; x < n; x += blockDim.x) spk[a + x] = (uint32_t)keys[x];
+}
+
 extern "C" int snn_read_raster(snn_sim *s, int64_t t0, int64_t t1, uint32_t *ids, int64_t cap,
                                int64_t *step_off, int64_t *n)
 {
@@ -1578,12 +1639,33 @@ extern "C" int snn_read_raster(snn_sim *s, int64_t t0, int64_t t1, uint32_t *ids
     for (int64_t k = 0; k <= nst; ++k) step_off[k] = off[k] - off[0];
     if (tot > cap || (tot > 0 && !ids)) return tot > cap ? SNN_E_CAPACITY : SNN_E_ARG;
     if (tot > 0) {
-        CK(cudaMemcpy(ids, s->dev.spk + off[0], sizeof(uint32_t) * (size_t)tot, cudaMemcpyDeviceToHost));
+        // every step's ids sorted by global id on the device (steps of up to
+        // kSortCap spikes), then copied back and mapped to global ids
+        constexpr int kSortCap = 8192;
+        int64_t widest = 0;
+        for (int64_t k = 0; k < nst; ++k) widest = std::max<int64_t>(widest, step_off[k + 1] - step_off[k]);
+        const int cap_dev = (int)std::min<int64_t>(kSortCap, widest);
+        if (cap_dev > 1) {
+            int m = 1;
+            while (m < cap_dev) m <<= 1;
+            const size_t smem = sizeof(unsigned long long) * (size_t)m;
+            CK(cudaFuncSetAttribute(k_raster_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            for (int64_t k0 = 0; k0 < nst; k0 += 65535) {
+                const int64_t nb = std::min<int64_t>(65535, nst - k0);
+                k_raster_sort<<<(unsigned)nb, 1024, smem, s->stream>>>(
+                    s->dev.spk, s->dev.raster_off + t0 + k0, s->rt->identity ? nullptr : s->dev.gid, cap_dev);
+                CK(cudaGetLastError());
+            }
+        }
+        CK(cudaMemcpyAsync(ids, s->dev.spk + off[0], sizeof(uint32_t) * (size_t)tot, cudaMemcpyDeviceToHost,
+                           s->stream));
+        CK(cudaStreamSynchronize(s->stream));
         const uint32_t *inv = s->rt->perm_inv.data();
         for (int64_t k = 0; k < nst; ++k) {
             uint32_t *b = ids + step_off[k], *e = ids + step_off[k + 1];
-            for (uint32_t *x = b; x < e; ++x) *x = inv[*x];
-            std::sort(b, e);
+            if (!s->rt->identity)
+                for (uint32_t *x = b; x < e; ++x) *x = inv[*x];
+            if (e - b > cap_dev) std::sort(b, e);
         }
     }
     return SNN_OK;

@@ -170,6 +170,22 @@ def test_degenerate_networks(snn):
     assert c2["spikes"] == 0
 
 
+@pytest.mark.parametrize("group_mode", ["contiguous", "greedy"])
+def test_raster_of_wide_steps(snn, group_mode):
+    """Steps with more spikes than the device-side raster sort takes (all
+    20,000 neurons start above threshold, and again after the refractory
+    period) come back sorted by global id, in the identity and in a permuted
+    internal order."""
+    M = 20000
+    g = synth.make_edges(M, [], v0=np.full(M, -45.0, np.float32))
+    cfg = synth.NetConfig(name="burst", M=M, P=4, n_vn=2, K=0, uniform_all=True,
+                          dyn=synth.Dynamics(drive_lambda=0.5, w_ext=200))
+    sim, o, rec, _ = _run_pair(snn, g, cfg, 48, 4, 2, group_mode=group_mode)
+    sim.step(48)
+    c, _ = _compare(sim, o, 48, rec)
+    assert c["spikes"] >= 2 * M
+
+
 def test_step_in_chunks_equals_one_call(snn, path):
     cfg = synth.TINY
     g = synth.make_network(cfg)
