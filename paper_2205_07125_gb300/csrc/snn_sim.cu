@@ -1073,6 +1073,9 @@ static int sim_create(const snn_network *net, const snn_routing *rt, const snn_s
         const char *eb = std::getenv("SNN_BAR_GROUPS");
         const int g = eb ? std::atoi(eb) : 0;
         d.bar_groups = (g > 1) ? std::min(g, kBarGroups) : 0;
+        // SNN_PREFETCH_STATE=0 turns off the next-step state prefetch (global state)
+        const char *ep = std::getenv("SNN_PREFETCH_STATE");
+        d.prefetch_state = (ep && ep[0] == '0') ? 0 : 1;
     }
     if (L.n_arr > 0 || L.n_own > 0) d.dcnt = (const uint4 *)(w + L.dcnt.off);
     if (L.n_own > 0) {

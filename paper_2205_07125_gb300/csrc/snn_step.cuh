@@ -176,6 +176,7 @@ struct Dev {
     int n_own;                     // lists per partition (the largest delay); 0: not available
     int vec_pieces;                // deliver staged pieces with 16-byte / 8-byte loads
     int bar_groups;                // > 1: two-level grid-barrier arrival over this many groups
+    int prefetch_state;            // global neuron state: prefetch the next step's lines into L2
     // scalars
     long long M;
     int P, n_vn, vn_size, D;
@@ -1367,6 +1368,26 @@ __device__ __forceinline__ int4 take_restored(int32_t *p, int4 i4)
                      (int)((uint32_t)i4.z + (uint32_t)x.z), (int)((uint32_t)i4.w + (uint32_t)x.w));
 }
 
+// Global neuron state (kModeVec): while the step's last grid barrier
+// completes, pull into L2 the lines the next step's update of this block
+// reads (potentials, refractory counters, input slot), so that the update's
+// loads do not wait on DRAM.  Prefetches only: nothing is read or written.
+template <bool ARR>
+__device__ __forceinline__ void prefetch_state_vec(const Dev &d, long long t)
+{
+    const long long nq = d.M / 4, stride = (long long)gridDim.x * kThreads;
+    const int32_t *in = ARR ? d.acc + (size_t)(t & 1) * (size_t)d.M : d.ring + (long long)(t % d.D) * d.M;
+    // a 128-byte line holds 8 quads of V and of the input, 32 of ref: one
+    // lane in 8 (in 32 for ref lines) issues the prefetch
+    for (long long q = (long long)blockIdx.x * kThreads + threadIdx.x; q < nq; q += stride) {
+        if ((threadIdx.x & 7) == 0) {
+            prefetch_l2(d.V + q * 4);
+            prefetch_l2(in + q * 4);
+        }
+        if ((threadIdx.x & 31) == 0) prefetch_l2(d.ref + q * 4);
+    }
+}
+
 // First half of step t on this block's share of the neurons (all threads
 // call): a1-a3, the spikes into the step's list.  In kModeSmem, rs is the
 // block's resident state and `phase` the parity of the bulk copy's
@@ -1842,6 +1863,8 @@ __global__ void __launch_bounds__(kThreads, MINB) k_persist(const Dev d, int T,
         grid_arrive(c, 2ull * s + 1ull, d.bar_groups);
         if constexpr (MODE == kModeSmem) {
             if (s + 1 < T) pre_update(d, t + 1, sh.th, rs);
+        } else if constexpr (MODE == kModeVec) {
+            if (s + 1 < T && d.prefetch_state) prefetch_state_vec<ARR>(d, t + 1);
         }
         if (!grid_wait(c, 2ull * s + 1ull, d.bar_groups, limit_ns)) break;
         stamp(6);
