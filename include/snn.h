@@ -595,7 +595,12 @@ int snn_autotune(snn_sim *sim, int32_t steps, int32_t *choice, double *best_ms);
  * Rates r_a = (spikes of population a) / (T N_a).  Backward: surrogate
  * dS/dV_pre = 1 / (1 + beta |V_pre - V_th|)^2, reset detached; each neuron
  * gathers its targets' adjoints along its own level-2 entries (the
- * transpose of the routed delivery); gradients in float64.
+ * transpose of the routed delivery).  Backward step t gathers the newest
+ * adjoint plane only, h(t + 1) = G[pop k][b] * dL/dV_pre of k at t + 1, and
+ * adds each synapse's term to a per-step partial sum by its delay; the
+ * float32 terms are summed in a fixed order per neuron, so the gradients do
+ * not depend on the checkpoint interval.  Gradients are accumulated in
+ * float64 (per-warp float pairs first).
  */
 typedef struct {
     int32_t T;            /* forward steps per run (>= 1) */
@@ -616,7 +621,8 @@ int snn_adjoint_workspace_bytes(const snn_routing *rt, const snn_sim_params *p, 
 /* is_exc: [M] global order (1 excitatory).  p gives the LIF constants,
  * w_ext, drive_seed and raster_cap (spike record of the forward).
  * Workspace and stream as snn_sim_create.  Errors: SNN_E_ARG, SNN_E_NOMEM,
- * SNN_E_CUDA, SNN_E_NODEV. */
+ * SNN_E_CUDA, SNN_E_NODEV, SNN_E_STATE (a neuron's level-2 entries do not
+ * tile its synapse run: routing tables not built by this library). */
 int snn_adjoint_create(const snn_network *net, const uint8_t *is_exc, const snn_routing *rt,
                        const snn_sim_params *p, const snn_adjoint_params *ap, void *workspace,
                        size_t workspace_bytes, void *stream, snn_adjoint **out);
