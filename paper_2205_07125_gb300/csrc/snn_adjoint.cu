@@ -44,9 +44,9 @@ using namespace snn;
 namespace {
 
 constexpr int kAThreads = 256;
-constexpr int kBThreads = 768;   // backward: one block per SM, up to 80 registers
+constexpr int kBThreads = 1024;  // backward: one block per SM, up to 64 registers (32 warps hide latency)
 constexpr int kBWarps = kBThreads / 32;
-constexpr int kBGroups = 4;      // groups of 4 synapses per lane per batch (a run of 512 in one batch)
+constexpr int kBGroups = 2;      // groups of 4 synapses per lane per batch (a run of 256 in one batch)
 constexpr int kDWarps = 4;       // forward delivery: warps per spike
 constexpr int kDUnroll = 4;
 constexpr int kMaxPop = 8;
