@@ -1076,6 +1076,9 @@ static int sim_create(const snn_network *net, const snn_routing *rt, const snn_s
         // SNN_PREFETCH_STATE=0 turns off the next-step state prefetch (global state)
         const char *ep = std::getenv("SNN_PREFETCH_STATE");
         d.prefetch_state = (ep && ep[0] == '0') ? 0 : 1;
+        // queued runs delivered through asynchronous copies (SNN_ASYNC_RECORDS=0: plain loads)
+        const char *ea = std::getenv("SNN_ASYNC_RECORDS");
+        d.async_rec = (ea && ea[0] == '0') ? 0 : 1;
     }
     if (L.n_arr > 0 || L.n_own > 0) d.dcnt = (const uint4 *)(w + L.dcnt.off);
     if (L.n_own > 0) {

@@ -177,6 +177,7 @@ struct Dev {
     int vec_pieces;                // deliver staged pieces with 16-byte / 8-byte loads
     int bar_groups;                // > 1: two-level grid-barrier arrival over this many groups
     int prefetch_state;            // global neuron state: prefetch the next step's lines into L2
+    int async_rec;                 // queued runs delivered with asynchronous copies (deliver_records_async)
     // scalars
     long long M;
     int P, n_vn, vn_size, D;
@@ -1084,6 +1085,106 @@ __device__ __forceinline__ void deliver_records(const Dev &d, int32_t *fix, cons
     }
 }
 
+// deliver_records with the synapse loads as asynchronous 4-byte copies into
+// a per-warp shared-memory stage (two stages): while one batch's copies are
+// in flight, the previous batch's reductions run, so the loads in flight do
+// not cost registers.  Each lane reads back only the slots it copied itself
+// (cp.async.wait_group is per thread), so no warp barrier is needed.  The
+// weight comes as the aligned 4-byte word holding it.
+template <int U>
+__device__ __forceinline__ void deliver_records_async(const Dev &d, int32_t *fix, const unsigned long long *recs,
+                                                      unsigned long long lo, unsigned long long hi)
+{
+    __shared__ uint32_t s_td[kWarps][2][U * 32];
+    __shared__ uint32_t s_w[kWarps][2][U * 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned long long step = (unsigned long long)kWarps * 32u;
+    const uint32_t *w32 = reinterpret_cast<const uint32_t *>(d.syn_w);
+    unsigned long long b = lo + (unsigned long long)wid * 32u;
+    unsigned long long rec = (b + lane < hi) ? __ldcs(recs + b + lane) : 0ull;
+    unsigned long long rec_next = 0ull;
+    unsigned long long o = 0ull;
+    unsigned int ex = 0, tot = 0, base = 0;
+    // the group of 32 records starting at b: run offsets and the exclusive
+    // prefix of their lengths over the warp
+    auto group = [&]() {
+        const unsigned long long nx = b + step + (unsigned long long)lane;
+        rec_next = nx < hi ? __ldcs(recs + nx) : 0ull;
+        o = rec >> kLenBits;
+        const unsigned int n = (unsigned int)(rec & kLenMask);
+        unsigned int inc = n;
+#pragma unroll
+        for (int k = 1; k < 32; k <<= 1) {
+            const unsigned int y = __shfl_up_sync(0xFFFFFFFFu, inc, k);
+            if (lane >= k) inc += y;
+        }
+        ex = inc - n;
+        tot = __shfl_sync(0xFFFFFFFFu, inc, 31);
+        base = 0;
+    };
+    if (b < hi) group();
+    int st = 0;
+    bool pend = false;
+    unsigned int pmask = 0, psel = 0;
+    auto reduce = [&](int s2, unsigned int mask, unsigned int sel) {
+#pragma unroll
+        for (int k = 0; k < U; ++k)
+            if (mask & (1u << k)) {
+                const uint32_t td = s_td[wid][s2][k * 32 + lane];
+                const uint32_t ww = s_w[wid][s2][k * 32 + lane];
+                const int32_t w = (sel & (1u << k)) ? (int32_t)(int16_t)(ww >> 16) : (int32_t)(int16_t)(ww & 0xFFFFu);
+                atomicAdd(fix + (td & kTgtMask), w);
+            }
+    };
+    while (b < hi) {
+        // issue the batch (b, base) into stage st
+        unsigned int mask = 0, sel = 0;
+#pragma unroll
+        for (int k = 0; k < U; ++k) {
+            const unsigned int y = base + (unsigned int)k * 32u + (unsigned int)lane;
+            int r = 0;
+#pragma unroll
+            for (int h = 16; h > 0; h >>= 1) {
+                const unsigned int v = __shfl_sync(0xFFFFFFFFu, ex, r + h);
+                if (v <= y) r += h;
+            }
+            const unsigned long long orr = __shfl_sync(0xFFFFFFFFu, o, r);
+            const unsigned int er = __shfl_sync(0xFFFFFFFFu, ex, r);
+            if (y < tot) {
+                const unsigned long long idx = orr + (y - er);
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((uint32_t)__cvta_generic_to_shared(&s_td[wid][st][k * 32 + lane])),
+                             "l"(d.syn_td + idx)
+                             : "memory");
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"((uint32_t)__cvta_generic_to_shared(&s_w[wid][st][k * 32 + lane])),
+                             "l"(w32 + (idx >> 1))
+                             : "memory");
+                mask |= 1u << k;
+                sel |= (unsigned int)(idx & 1ull) << k;
+            }
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        // the previous batch's reductions while this one is in flight
+        if (pend) {
+            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+            reduce(st ^ 1, pmask, psel);
+        }
+        pend = true;
+        pmask = mask;
+        psel = sel;
+        st ^= 1;
+        base += 32u * U;
+        if (base >= tot) {
+            b += step;
+            rec = rec_next;
+            if (b < hi) group();
+        }
+    }
+    if (pend) {
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        reduce(st ^ 1, pmask, psel);
+    }
+}
+
 // ---------------------------------------------------------------- a1-a6
 // How a step reaches its neurons' state:
 //   kModeScalar  one neuron per thread, grid-stride over global memory;
@@ -1280,7 +1381,11 @@ __device__ __forceinline__ void arrival_share(const Dev &d, long long t, StepSha
     __syncthreads();
     const unsigned long long n = sh.arr_n;
     const unsigned long long lo = n * blockIdx.x / gridDim.x, hi = n * (blockIdx.x + 1) / gridDim.x;
-    deliver_records<U>(d, d.acc + (size_t)((t + 1) & 1) * (size_t)d.M, d.arr + (size_t)li * d.arr_cap, lo, hi);
+    if (d.async_rec)
+        deliver_records_async<U>(d, d.acc + (size_t)((t + 1) & 1) * (size_t)d.M, d.arr + (size_t)li * d.arr_cap, lo,
+                                 hi);
+    else
+        deliver_records<U>(d, d.acc + (size_t)((t + 1) & 1) * (size_t)d.M, d.arr + (size_t)li * d.arr_cap, lo, hi);
 }
 
 // a3: compaction of the spikes each thread collected in bits[0, NC) (bit b
