@@ -1444,7 +1444,9 @@ __device__ __forceinline__ void compact_spikes(const Dev &d, long long t, StepSh
 // While the block waits at the grid barrier after a3: pull the routing
 // tables and synapses of its own spikes (whichever block routes them) from
 // HBM into L2 — level-1 and level-2 entries, their pair ids and the synapse
-// run — one spike per warp.
+// run — one spike per warp.  With delivery by arrival step the synapse run
+// is left out: this step delivers only the delay-1 head of each segment,
+// and the rest is read up to seven steps later, after L2 has turned over.
 __device__ __forceinline__ void prefetch_own(const Dev &d, const StepShared &sh)
 {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -1452,14 +1454,16 @@ __device__ __forceinline__ void prefetch_own(const Dev &d, const StepShared &sh)
     for (unsigned int x = wid; x < n; x += kWarps) {
         const uint32_t i = sh.own[x];
         const uint2 r0 = d.row[i], r1 = d.row[i + 1];
-        const unsigned long long s0 = d.csr[i], s1 = d.csr[i + 1];
         prefetch_span(d.l1_vn + r0.x, d.l1_vn + r1.x, lane);
         prefetch_span(d.l1_l2 + r0.x, d.l1_l2 + r1.x, lane);
         prefetch_span(d.l1_pair + r0.x, d.l1_pair + r1.x, lane);
         prefetch_span(d.l2 + r0.y, d.l2 + r1.y, lane);
         prefetch_span(d.l2_pair + r0.y, d.l2_pair + r1.y, lane);
-        prefetch_span(d.syn_td + s0, d.syn_td + s1, lane);
-        prefetch_span(d.syn_w + s0, d.syn_w + s1, lane);
+        if (d.n_arr == 0) {
+            const unsigned long long s0 = d.csr[i], s1 = d.csr[i + 1];
+            prefetch_span(d.syn_td + s0, d.syn_td + s1, lane);
+            prefetch_span(d.syn_w + s0, d.syn_w + s1, lane);
+        }
     }
 }
 
