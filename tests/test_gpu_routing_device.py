@@ -7,7 +7,9 @@ on device-built tables equals one on host-built tables."""
 import numpy as np
 import pytest
 
+import oracle
 import synth
+from _routing_defs import check_tables
 
 pytestmark = pytest.mark.gpu
 
@@ -151,3 +153,17 @@ def test_errors(snn):
     g = synth.make_edges(10, [(0, 1, 1, 1)])
     with pytest.raises(RuntimeError):  # partition 1 is empty
         snn.Routing(snn.Network.from_synth(g), np.zeros(10, np.int32), 2, 1, build="device", device="cuda:0")
+
+
+def test_device_tables_follow_the_network(snn):
+    """The device-built tables against their definitions rebuilt with numpy
+    (not only against the host builder): internal order, sorted CSR, level-1
+    and level-2 entries with relay classes and delay-1 counts, exchange pairs
+    and capacities."""
+    cfg = synth.NetConfig(name="t", M=1500, P=6, n_vn=3, K=18, uniform_all=False, n_part=10,
+                          n_vn_t=5, n_remote=3, dmax=7, seed=12)
+    g = synth.make_network(cfg)
+    net = snn.Network.from_synth(g)
+    part = np.random.default_rng(3).permutation(oracle.partition_planted(g.M, 6)).astype(np.int32)
+    rt = snn.Routing(net, part, 6, 3, "greedy", iters=2, seed=1, build="device", device="cuda:0")
+    check_tables(rt, g, part, 6, 3)
