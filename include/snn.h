@@ -449,6 +449,28 @@ int snn_sim_workspace_bytes(const snn_routing *rt, const snn_sim_params *p, size
  * empty delay ring, t = 0) on `stream` (a cudaStream_t, NULL = legacy
  * default stream).  `rt` must outlive the sim.  Uses the current device.
  * Errors: SNN_E_ARG, SNN_E_NOMEM (workspace too small), SNN_E_CUDA, SNN_E_NODEV.
+ *
+ * Environment variables read here (launch-shape and tuning switches; none
+ * changes a result, every combination is bit-exact):
+ *   SNN_PERSIST=0               CUDA-graph path instead of the persistent kernel
+ *   SNN_PERSIST_SMEM=0          persistent kernel on global neuron state only
+ *   SNN_PERSIST_BLOCKS_PER_SM=b at most b (1..4) resident blocks per SM
+ *   SNN_PERSIST_DEFER=1         minimum-delay batching, as defer_delayed = 1
+ *   SNN_DELIVERY=0..3           overrides snn_sim_params.delivery
+ *   SNN_PDL=0                   graph kernels in plain stream order (no
+ *                               programmatic dependent launch)
+ *   SNN_BAR_GROUPS=G            two-level grid-barrier arrival over G (2..16)
+ *                               group words (default: one word)
+ *   SNN_PREFETCH_STATE=0        no L2 prefetch of the next step's neuron state
+ *                               (global-state persistent kernel)
+ *   SNN_ASYNC_RECORDS=0         queued runs delivered with plain loads instead
+ *                               of asynchronous copies into shared memory
+ *   SNN_VEC_PIECES=1            staged pieces delivered with 16- / 8-byte loads
+ *   SNN_BARRIER_LIMIT_NS=n      bound of each grid-barrier wait (default 1 s);
+ *                               one that runs out is reported by
+ *                               snn_sync_status as SNN_E_TIMEOUT
+ *   SNN_TEST_SKIP_BARRIER=1     tests only: block 0 skips its first arrival,
+ *                               so the others' bounded wait runs out
  */
 int snn_sim_create(const snn_network *net, const snn_routing *rt, const snn_sim_params *p,
                    void *workspace, size_t workspace_bytes, void *stream, snn_sim **out);
