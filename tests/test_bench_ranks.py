@@ -1,5 +1,6 @@
-"""Multi-rank host logic of bench.py on CPU: two gloo ranks, replicas with
-summed work and the maximum time over ranks (no data-path collective)."""
+"""Host logic of bench.py on CPU: two gloo ranks (replicas with summed work
+and the maximum time over ranks, no data-path collective), the byte
+formulas, the reference arm, the study helpers and the traffic lookup."""
 import os
 import socket
 
@@ -99,3 +100,32 @@ def test_study_helpers_against_the_oracle():
     assert a == b
     planted = oracle.partition_planted(g.M, 8)
     assert oracle.cut(h, planted[np.argsort(perm)]) == oracle.cut(g, planted)
+
+
+def test_traffic_entries_scale_and_go_stale(tmp_path, monkeypatch):
+    """roofline.traffic from profiles/traffic.json: a "kernel@M" entry wins
+    over the kernel's own; an entry scales by neurons or by synaptic events
+    per step as it says; an entry taken on other kernel code gives null."""
+    import json
+    import bench
+    (tmp_path / "profiles").mkdir()
+    t = {"k": {"source_sha": "s1", "events_per_step": 100.0, "dram_bytes_per_step": 800.0, "neurons": 10},
+         "k@5000": {"source_sha": "s1", "scale_by": "neurons", "neurons": 500, "events_per_step": 1.0,
+                    "dram_bytes_per_step": 7000.0}}
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(t))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_source_sha", lambda: "s1")
+    assert bench.load_traffic("k", 250.0, 64) == 800.0 * 250.0 / 100.0
+    assert bench.load_traffic("k", 250.0, 5000) == 7000.0 * 5000 / 500
+    assert bench.load_traffic("other", 250.0, 64) is None
+    monkeypatch.setattr(bench, "kernel_source_sha", lambda: "s2")
+    assert bench.load_traffic("k", 250.0, 64) is None
+
+
+def test_source_hash_ignores_comments():
+    """The hash that dates a capture covers code, not comments or blank lines."""
+    import bench
+    a = "int f(int x)\n{\n    return x + 1;  // one more\n}\n"
+    b = "/* doc\n   more */\nint f(int x)\n{\n\n    return x + 1;\n}\n"
+    c = "int f(int x)\n{\n    return x + 2;\n}\n"
+    assert bench._code_only(a) == bench._code_only(b) != bench._code_only(c)
